@@ -1,0 +1,260 @@
+"""Pins of the CPU oracle against facts fixed by mathematics and the paper.
+
+Each test checks the oracle against something other than itself:
+Green's second identity (an independent boundary-integral evaluation of the
+same area integrals), closed-form potentials (uniform and Gaussian sources),
+exact reproduction of polynomials by the extension (Section 3.2: least squares
+in a space that contains the data), brute-force tree invariants (Section 4)
+and Lagrange-interpolation exactness.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy.integrate import quad
+from scipy.special import exp1
+
+import workloads as W
+from oracle import oracle as O
+
+EPS = np.finfo(float).eps
+
+
+def _green_area_integral(qfun, gradq, x, x0, x1, y0, y1):
+    """int_B log|x-y| (Laplacian q)(y) dy by Green's second identity:
+    2 pi q(x) [x in B] + sum over edges of int (log r dq/dn - q d(log r)/dn) ds,
+    each edge integral by adaptive 1D quadrature split at the foot of x."""
+    tot = 0.0
+    corners = [(x0, y0), (x1, y0), (x1, y1), (x0, y1)]
+    normals = [(0, -1), (1, 0), (0, 1), (-1, 0)]
+    for k in range(4):
+        a = np.array(corners[k], float)
+        b = np.array(corners[(k + 1) % 4], float)
+        n = np.array(normals[k], float)
+        L = np.linalg.norm(b - a)
+        tdir = (b - a) / L
+        s0 = float(np.clip(np.dot(x - a, tdir), 0.0, L))
+
+        def integrand(s):
+            y = a + s * tdir
+            r = y - x
+            r2 = r @ r
+            return 0.5 * np.log(r2) * (gradq(y) @ n) - qfun(y) * (r @ n) / r2
+        pts = [s0] if 0.0 < s0 < L else None
+        v, _ = quad(integrand, 0.0, L, points=pts, epsabs=1e-15, epsrel=1e-14, limit=500)
+        tot += v
+    inside = x0 < x[0] < x1 and y0 < x[1] < y1
+    return tot + (2.0 * math.pi * qfun(x) if inside else 0.0)
+
+
+def _poly_q(K, cx, cy, h, seed):
+    """Random q of total degree K+1 (so p = Laplacian q has total degree K-1)."""
+    rng = np.random.default_rng(seed)
+    c = rng.standard_normal((K + 2, K + 2))
+    terms = [(m, n) for m in range(K + 2) for n in range(K + 2 - m)]
+
+    def q(y):
+        u, v = (y[0] - cx) / h, (y[1] - cy) / h
+        return sum(c[m, n] * u ** m * v ** n for m, n in terms)
+
+    def gq(y):
+        u, v = (y[0] - cx) / h, (y[1] - cy) / h
+        gx = sum(c[m, n] * m * u ** (m - 1) * v ** n for m, n in terms if m >= 1) / h
+        gy = sum(c[m, n] * n * u ** m * v ** (n - 1) for m, n in terms if n >= 1) / h
+        return np.array([gx, gy])
+
+    def lap(y):
+        u, v = (y[0] - cx) / h, (y[1] - cy) / h
+        s = 0.0
+        for m, n in terms:
+            if m >= 2:
+                s += c[m, n] * m * (m - 1) * u ** (m - 2) * v ** n
+            if n >= 2:
+                s += c[m, n] * n * (n - 1) * u ** m * v ** (n - 2)
+        return s / (h * h)
+    return q, gq, lap
+
+
+def test_gauss_legendre_exact_on_monomials():
+    L = O.lib()
+    for n in (4, 8, 12, 16, 20):
+        x = np.zeros(n)
+        w = np.zeros(n)
+        L.orc_gauss_legendre(n, O._ptr(x), O._ptr(w))
+        assert np.all(np.diff(x) > 0)
+        for k in range(2 * n):
+            exact = 2.0 / (k + 1) if k % 2 == 0 else 0.0
+            assert abs(np.sum(w * x ** k) - exact) < 1e-14
+
+
+@pytest.mark.parametrize("K", [8, 16])
+@pytest.mark.parametrize("where", ["self", "self_corner_node", "edge_near", "corner_near", "adjacent", "diag", "far"])
+def test_leaf_integrals_match_green_identity(K, where):
+    """Near/self/far leaf integrals of a polynomial density against Green's identity."""
+    L = O.lib()
+    t, _ = O.gauss_legendre(K)
+    cx, cy, h = 0.1, -0.2, 0.05
+    x = {
+        "self": (cx + 0.3 * h, cy - 0.7 * h),
+        "self_corner_node": (cx + h * t[-1], cy + h * t[0]),
+        "edge_near": (cx + 1.003 * h, cy + 0.2 * h),
+        "corner_near": (cx - 1.0001 * h, cy - 1.0002 * h),
+        "adjacent": (cx + 2.5 * h, cy + 0.1 * h),
+        "diag": (cx + 1.9 * h, cy + 1.9 * h),
+        "far": (cx + 5.0 * h, cy - 3.1 * h),
+    }[where]
+    x = np.array(x)
+    q, gq, lap = _poly_q(K, cx, cy, h, seed=K * 7 + len(where))
+    X, Y = np.meshgrid(cx + h * t, cy + h * t, indexing="xy")
+    nodes = np.stack([X.ravel(), Y.ravel()], axis=1)
+    p = np.array([lap(y) for y in nodes])
+    I = np.zeros(K * K)
+    L.orc_leaf_basis_integrals(K, O._ptr(np.ascontiguousarray(t)), cx, cy, h, x[0], x[1], O._ptr(I))
+    got = I @ p
+    want = _green_area_integral(q, gq, x, cx - h, cx + h, cy - h, cy + h)
+    scale = np.max(np.abs(p)) * h * h * (1 + abs(math.log(h)))
+    assert abs(got - want) <= 1e-12 * scale, (got, want, scale)
+
+
+def _uniform_tree(K, level, dom=None):
+    dom = dom or W.WholeBoxDomain()
+    return O.build_tree(dom, W.TreeOptions(K=K, min_level=level, max_level=level), lambda xy: 0 * xy[:, 0])
+
+
+def test_potential_of_unit_source_on_D():
+    """f = 1 on all of D: V(x) = (1/2pi) int_D log|x-y| dy, here evaluated by
+    Green's identity with q = |y - x|^2 / 4 (Laplacian 1)."""
+    tree = _uniform_tree(8, 3)
+    vals = np.ones((tree.n_leaves, 1, 64))
+    rng = np.random.default_rng(3)
+    tg = np.concatenate([O.all_leaf_nodes(tree)[::97], rng.uniform(-0.5, 0.5, (8, 2))])
+    V = O.volume_potential(tree, vals, tg)[:, 0]
+    for k, x in enumerate(tg):
+        q = lambda y, x=x: ((y[0] - x[0]) ** 2 + (y[1] - x[1]) ** 2) / 4.0
+        gq = lambda y, x=x: np.array([(y[0] - x[0]) / 2.0, (y[1] - x[1]) / 2.0])
+        want = _green_area_integral(q, gq, x, -0.5, 0.5, -0.5, 0.5) / (2 * math.pi)
+        assert abs(V[k] - want) < 1e-14, (x, V[k], want)
+
+
+def test_potential_of_gaussian_matches_closed_form():
+    """f = exp(-r^2/s^2) has V(r) = (s^2/4)(ln r^2 + E1(r^2/s^2)); the source is
+    negligible on the edge of D.  Error is the leaf interpolation error."""
+    s, c = 0.05, np.array([0.03, -0.02])
+    f = W.make_gaussian(c, s)
+    tree = _uniform_tree(16, 4)
+    nodes = O.all_leaf_nodes(tree)
+    vals = f(nodes).reshape(tree.n_leaves, 1, 256)
+    rng = np.random.default_rng(5)
+    idx = rng.choice(len(nodes), 24, replace=False)
+    tg = np.concatenate([nodes[idx], [[0.0301, -0.0199], [0.2, 0.3], [-0.41, 0.45]]])
+    V = O.volume_potential(tree, vals, tg)[:, 0]
+    r2 = np.sum((tg - c) ** 2, axis=1)
+    want = (s * s / 4) * (np.log(r2) + exp1(r2 / (s * s)))
+    assert np.max(np.abs(V - want)) < 1e-12 * np.max(np.abs(want)) * 10
+
+
+def test_potential_linear_in_source_and_zero_leaves_skipped():
+    tree = _uniform_tree(8, 2)
+    rng = np.random.default_rng(11)
+    a = rng.standard_normal((tree.n_leaves, 1, 64))
+    b = rng.standard_normal((tree.n_leaves, 1, 64))
+    a[3] = 0.0
+    tg = rng.uniform(-0.5, 0.5, (5, 2))
+    va = O.volume_potential(tree, a, tg)
+    vb = O.volume_potential(tree, b, tg)
+    vab = O.volume_potential(tree, np.concatenate([a, 2 * a - b], axis=1), tg)
+    assert np.allclose(vab[:, 0], va[:, 0], rtol=0, atol=1e-14)
+    assert np.allclose(vab[:, 1], 2 * va[:, 0] - vb[:, 0], rtol=0, atol=1e-13)
+
+
+def _extension_operator_norm(tree, meta, i, targets):
+    off, n, masks = meta[i]
+    M, _ = O.extend_cut_leaf(tree.leaves[i], tree.K, tree.t, masks, np.eye(n), targets)
+    return np.abs(M).sum(axis=1).max()
+
+
+@pytest.mark.parametrize("wl", ["disk_l3_k8", "disk_l4_k8", "disk_l4_k16"])
+def test_extension_reproduces_total_degree_q_polynomials(wl):
+    """Section 3.2 least squares on P_q: a polynomial of total degree q = K+2
+    is reproduced at every extension node, up to rounding times the
+    conditioning of the extrapolation."""
+    lev, K = {"disk_l3_k8": (3, 8), "disk_l4_k8": (4, 8), "disk_l4_k16": (4, 16)}[wl]
+    w = W.disk_sincos(level=lev, K=K)
+    tree = O.build_tree(w.domain, w.opts, w.sources[0])
+    q = K + 2
+    rng = np.random.default_rng(lev * 100 + K)
+    cc = rng.standard_normal((q + 1, q + 1))
+
+    def f(xy):
+        x, y = 3 * xy[:, 0], 3 * xy[:, 1]
+        return sum(cc[m, n] * x ** m * y ** n for m in range(q + 1) for n in range(q + 1 - m))
+    pts, meta = O.stencil_points(tree, w.domain)
+    vals, _ = O.leaf_values(tree, w.domain, f(pts)[:, None], meta)
+    owned = {}
+    for j, o in enumerate(tree.owner):
+        if o >= 0:
+            owned.setdefault(o, []).append(j)
+    for i in tree.cut_leaves():
+        off, n, masks = meta[i]
+        tg = np.concatenate([O.leaf_nodes(tree.leaves[i], tree.t)] +
+                            [O.leaf_nodes(tree.leaves[j], tree.t) for j in owned.get(i, [])])
+        got = np.concatenate([vals[i, 0]] + [vals[j, 0] for j in owned.get(i, [])])
+        kappa = _extension_operator_norm(tree, meta, i, tg)
+        tol = 100 * EPS * max(kappa, 1.0) * np.max(np.abs(f(pts[off:off + n])))
+        assert np.max(np.abs(got - f(tg))) <= tol, (tree.leaves[i], kappa)
+
+
+def test_extension_is_not_identity_on_nonpolynomial_data():
+    """Guard against a vacuous pass: a degree q+3 polynomial is NOT reproduced."""
+    w = W.disk_sincos(level=3, K=8)
+    tree = O.build_tree(w.domain, w.opts, w.sources[0])
+    f = lambda xy: (3 * xy[:, 0]) ** 13 + (3 * xy[:, 1]) ** 12
+    pts, meta = O.stencil_points(tree, w.domain)
+    vals, _ = O.leaf_values(tree, w.domain, f(pts)[:, None], meta)
+    errs = [np.max(np.abs(vals[i, 0] - f(O.leaf_nodes(tree.leaves[i], tree.t)))) for i in tree.cut_leaves()]
+    assert max(errs) > 1e-6
+
+
+@pytest.mark.parametrize("which", ["disk3", "disk4", "starfish_k8", "lshape_small"])
+def test_tree_invariants_brute_force(which):
+    if which == "disk3":
+        w = W.disk_sincos(level=3)
+    elif which == "disk4":
+        w = W.disk_sincos(level=4)
+    elif which == "starfish_k8":
+        w = W.starfish_gaussian(K=8, tol=1e-8, max_level=8)
+    else:
+        w = W.lshape_expsin(K=8, base_level=4, max_level=7, corner_levels=4)
+    tree = O.build_tree(w.domain, w.opts, w.sources[0])
+    assert O.check_tree_invariants(tree) == []
+    # classification is by the leaf's own nodes
+    for b, c in zip(tree.leaves, tree.cls):
+        ins = w.domain.inside(O.leaf_nodes(b, tree.t))
+        assert c == (O.CUT if (ins.any() and not ins.all()) else (O.REGULAR if ins.all() else O.EXTERIOR))
+    # owners are cut leaves and only exterior leaves are owned
+    for j, o in enumerate(tree.owner):
+        if o >= 0:
+            assert tree.cls[o] == O.CUT and tree.cls[j] == O.EXTERIOR
+
+
+def test_uniform_disk_tree_counts():
+    """Uniform level-4 tree of the disk r = 0.35: 256 leaves; a leaf is cut
+    exactly when its 64 nodes straddle the circle (checked by direct distance)."""
+    w = W.disk_sincos(level=4)
+    tree = O.build_tree(w.domain, w.opts, w.sources[0])
+    assert tree.n_leaves == 256 and all(b[0] == 4 for b in tree.leaves)
+    ncut = 0
+    for b in tree.leaves:
+        r = np.hypot(*O.leaf_nodes(b, tree.t).T)
+        ncut += int((r < 0.35).any() and not (r < 0.35).all())
+    assert ncut == len(tree.cut_leaves())
+
+
+def test_interpolation_exact_for_tensor_polynomials():
+    tree = _uniform_tree(8, 2)
+    f = lambda xy: (1 + xy[:, 0]) ** 7 * (2 - xy[:, 1]) ** 7
+    vals = f(O.all_leaf_nodes(tree)).reshape(tree.n_leaves, 64, 1)
+    rng = np.random.default_rng(2)
+    p = np.concatenate([rng.uniform(-0.5, 0.5, (30, 2)), [[0.25, 0.0], [0.5, 0.5], [-0.5, -0.5]]])
+    got = O.interpolate_at(tree, vals, p)[:, 0]
+    assert np.max(np.abs(got - f(p)) / np.abs(f(p))) < 1e-12

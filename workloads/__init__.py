@@ -1,0 +1,342 @@
+"""Seeded synthetic problem definitions: domains, boundary panels, sources.
+
+This module is shared by the CUDA library's tests/benchmark and by the CPU
+oracle.  It defines *inputs only* -- the geometry of Omega (an inside/outside
+predicate and a panel parametrisation gamma_i(t), t in [-1,1]), the source
+density f, and the tree options of each workload -- and holds none of the
+method's arithmetic (no quadrature, no extension, no potential).
+
+Geometry follows the problem statement of Section 4 (Omega inside the unit
+box D centred at the origin, boundary given as panels gamma_i([-1,1])).
+Random draws use NumPy's PCG64 with seed 2211 + workload id.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+from typing import Callable, List, Optional, Sequence, Tuple
+
+import numpy as np
+
+TWO_PI = 2.0 * math.pi
+
+# ---------------------------------------------------------------------------
+# Domains
+# ---------------------------------------------------------------------------
+
+
+class StarDomain:
+    """Star-shaped domain r(theta) = r0 * (1 + sum_k a_k cos(k theta + phi_k)).
+
+    Covers the disk (no modes), the starfish of the adaptive interior
+    workload (one mode k=5) and the random star shapes of the batch workload.
+    The boundary is split into ``n_panels`` equal arcs in theta; panel i maps
+    t in [-1,1] to theta = theta_i + (t+1)/2 * dtheta.
+    """
+
+    def __init__(self, r0: float, modes: Sequence[Tuple[int, float, float]] = (),
+                 n_panels: Optional[int] = None, center=(0.0, 0.0)):
+        self.r0 = float(r0)
+        self.modes = [(int(k), float(a), float(p)) for (k, a, p) in modes]
+        self.center = (float(center[0]), float(center[1]))
+        self.n_panels = int(n_panels) if n_panels else choose_panel_count(self)
+
+    # r(theta) and dr/dtheta
+    def r(self, th):
+        th = np.asarray(th, dtype=np.float64)
+        s = np.ones_like(th)
+        for k, a, p in self.modes:
+            s = s + a * np.cos(k * th + p)
+        return self.r0 * s
+
+    def dr(self, th):
+        th = np.asarray(th, dtype=np.float64)
+        s = np.zeros_like(th)
+        for k, a, p in self.modes:
+            s = s - a * k * np.sin(k * th + p)
+        return self.r0 * s
+
+    def inside(self, xy: np.ndarray) -> np.ndarray:
+        """Strict interior test: |x - c| < r(theta(x))."""
+        xy = np.asarray(xy, dtype=np.float64).reshape(-1, 2)
+        dx = xy[:, 0] - self.center[0]
+        dy = xy[:, 1] - self.center[1]
+        rho = np.hypot(dx, dy)
+        th = np.arctan2(dy, dx)
+        return rho < self.r(th)
+
+    def panel_theta(self, i: int, t):
+        dth = TWO_PI / self.n_panels
+        return i * dth + (np.asarray(t, dtype=np.float64) + 1.0) * 0.5 * dth
+
+    def curve(self, i: int, t) -> Tuple[np.ndarray, np.ndarray]:
+        """gamma_i(t) and gamma_i'(t) (derivative w.r.t. t) as (n,2) arrays."""
+        th = self.panel_theta(i, t)
+        dth_dt = 0.5 * TWO_PI / self.n_panels
+        r = self.r(th)
+        dr = self.dr(th)
+        c, s = np.cos(th), np.sin(th)
+        xy = np.stack([self.center[0] + r * c, self.center[1] + r * s], axis=1)
+        dxy = np.stack([(dr * c - r * s) * dth_dt, (dr * s + r * c) * dth_dt], axis=1)
+        return xy, dxy
+
+
+class PolygonDomain:
+    """Polygon given by its vertices (counter-clockwise).
+
+    Each side is split into ``panels_per_side`` equal panels; the first and
+    last panel of every side are further split dyadically ``corner_levels``
+    times toward the vertex, so that panel length halves toward each corner.
+    """
+
+    def __init__(self, vertices: Sequence[Tuple[float, float]], panels_per_side: int = 16,
+                 corner_levels: int = 0, inside_fn: Optional[Callable] = None):
+        self.vertices = np.asarray(vertices, dtype=np.float64)
+        self._inside_fn = inside_fn
+        segs = []  # (p0, p1) per panel
+        nv = len(self.vertices)
+        for v in range(nv):
+            a = self.vertices[v]
+            b = self.vertices[(v + 1) % nv]
+            # parameters along the side in [0,1]
+            cuts = list(np.linspace(0.0, 1.0, panels_per_side + 1))
+            head = [0.0]
+            x = cuts[1]
+            for _ in range(corner_levels):
+                x = x * 0.5
+                head.append(x)
+            head = sorted(head)
+            tail = [1.0 - h for h in head]
+            pts = sorted(set(head + cuts[1:-1] + tail + [cuts[1], cuts[-2]]))
+            for j in range(len(pts) - 1):
+                segs.append((a + (b - a) * pts[j], a + (b - a) * pts[j + 1]))
+        self.segments = segs
+        self.n_panels = len(segs)
+
+    def inside(self, xy: np.ndarray) -> np.ndarray:
+        xy = np.asarray(xy, dtype=np.float64).reshape(-1, 2)
+        if self._inside_fn is not None:
+            return self._inside_fn(xy)
+        # crossing-number test (points exactly on an edge count as outside)
+        x, y = xy[:, 0], xy[:, 1]
+        res = np.zeros(len(xy), dtype=bool)
+        vs = self.vertices
+        n = len(vs)
+        for i in range(n):
+            x0, y0 = vs[i]
+            x1, y1 = vs[(i + 1) % n]
+            cond = (y0 > y) != (y1 > y)
+            with np.errstate(divide="ignore", invalid="ignore"):
+                xc = x0 + (y - y0) * (x1 - x0) / (y1 - y0)
+            res ^= cond & (x < xc)
+        return res
+
+    def curve(self, i: int, t) -> Tuple[np.ndarray, np.ndarray]:
+        t = np.asarray(t, dtype=np.float64)
+        a, b = self.segments[i]
+        s = (t + 1.0) * 0.5
+        xy = a[None, :] + s[:, None] * (b - a)[None, :]
+        dxy = np.repeat(((b - a) * 0.5)[None, :], len(t), axis=0)
+        return xy, dxy
+
+
+def choose_panel_count(dom: StarDomain, candidates=None) -> int:
+    """Panel count rule for star boundaries (Section 6, boundary discretisation).
+
+    The smallest N among ``candidates`` such that, on every panel, the
+    16-point Legendre expansion of |gamma'(t)| has its two highest
+    coefficients below 1e-15 times its largest one.  This is input
+    preparation (how finely the user samples the boundary), not part of the
+    volume-potential method.
+    """
+    if candidates is None:
+        candidates = [16, 24, 32, 40, 48, 64, 80, 96, 128, 160, 192, 256, 320, 384, 512]
+    t, _ = np.polynomial.legendre.leggauss(16)
+    V = np.polynomial.legendre.legvander(t, 15)
+    Vinv = np.linalg.inv(V)
+    for n in candidates:
+        dom.n_panels = n
+        ok = True
+        for i in range(n):
+            _, d = dom.curve(i, t)
+            sp = np.hypot(d[:, 0], d[:, 1])
+            c = Vinv @ sp
+            if max(abs(c[-1]), abs(c[-2])) > 1e-15 * np.max(np.abs(c)):
+                ok = False
+                break
+        if ok:
+            return n
+    return candidates[-1]
+
+
+def l_shape_inside(xy):
+    x, y = xy[:, 0], xy[:, 1]
+    box = (x > -0.4) & (x < 0.4) & (y > -0.4) & (y < 0.4)
+    notch = (x >= 0.0) & (y >= 0.0)
+    return box & ~notch
+
+
+def l_shape_domain(panels_per_side: int = 16, corner_levels: int = 11) -> PolygonDomain:
+    """L-shaped polygon, side 0.8: [-0.4,0.4]^2 minus [0,0.4]^2, 6 corners."""
+    verts = [(-0.4, -0.4), (0.4, -0.4), (0.4, 0.0), (0.0, 0.0), (0.0, 0.4), (-0.4, 0.4)]
+    return PolygonDomain(verts, panels_per_side, corner_levels, inside_fn=l_shape_inside)
+
+
+class WholeBoxDomain:
+    """Omega = a region containing D: every point of D is interior.
+
+    No boundary panels; every leaf is regular.  Used by closed-form checks.
+    """
+    n_panels = 0
+
+    def inside(self, xy):
+        xy = np.asarray(xy, dtype=np.float64).reshape(-1, 2)
+        return np.ones(len(xy), dtype=bool)
+
+    def curve(self, i, t):  # pragma: no cover - never called (no panels)
+        raise IndexError("no panels")
+
+
+# ---------------------------------------------------------------------------
+# Sources
+# ---------------------------------------------------------------------------
+
+
+def f_sincos(xy):
+    """f = -13 sin(3x) cos(2y) = Laplacian of sin(3x) cos(2y)."""
+    xy = np.asarray(xy, dtype=np.float64).reshape(-1, 2)
+    return -13.0 * np.sin(3.0 * xy[:, 0]) * np.cos(2.0 * xy[:, 1])
+
+
+def make_gaussian(center, width, amp=1.0):
+    cx, cy = float(center[0]), float(center[1])
+    w2 = float(width) ** 2
+    a = float(amp)
+
+    def f(xy):
+        xy = np.asarray(xy, dtype=np.float64).reshape(-1, 2)
+        return a * np.exp(-((xy[:, 0] - cx) ** 2 + (xy[:, 1] - cy) ** 2) / w2)
+    return f
+
+
+def make_gaussian_mixture(centers, widths, amps):
+    centers = np.asarray(centers, dtype=np.float64)
+    widths = np.asarray(widths, dtype=np.float64)
+    amps = np.asarray(amps, dtype=np.float64)
+
+    def f(xy):
+        xy = np.asarray(xy, dtype=np.float64).reshape(-1, 2)
+        out = np.zeros(len(xy))
+        for c, w, a in zip(centers, widths, amps):
+            out += a * np.exp(-((xy[:, 0] - c[0]) ** 2 + (xy[:, 1] - c[1]) ** 2) / (w * w))
+        return out
+    return f
+
+
+def f_exp_sin(xy):
+    """f = -3 e^x sin(2y) = Laplacian of e^x sin(2y)."""
+    xy = np.asarray(xy, dtype=np.float64).reshape(-1, 2)
+    return -3.0 * np.exp(xy[:, 0]) * np.sin(2.0 * xy[:, 1])
+
+
+def sample_inside(dom, n, rng, box=0.5):
+    """Rejection-sample n points uniformly inside the domain."""
+    pts = []
+    while len(pts) < n:
+        p = rng.uniform(-box, box, size=(4 * n, 2))
+        p = p[dom.inside(p)]
+        pts.extend(p.tolist())
+    return np.asarray(pts[:n])
+
+
+def random_mixture(dom, rng, n_gauss=8, wmin=0.01, wmax=0.1):
+    c = sample_inside(dom, n_gauss, rng)
+    w = np.exp(rng.uniform(math.log(wmin), math.log(wmax), size=n_gauss))
+    a = rng.standard_normal(n_gauss)
+    return make_gaussian_mixture(c, w, a), (c, w, a)
+
+
+# ---------------------------------------------------------------------------
+# Tree options and workloads
+# ---------------------------------------------------------------------------
+
+
+@dataclass
+class TreeOptions:
+    """Discretisation options shared by the library and the oracle.
+
+    K: nodes per dimension on a leaf (Gauss-Legendre).  min_level: every box
+    above this level is split (a uniform base).  max_level: no box is split
+    beyond it.  refine_tol: adaptive resolution tolerance (0 = uniform tree
+    at min_level).  f_scale: the scale the tolerance is relative to.
+    """
+    K: int = 8
+    min_level: int = 4
+    max_level: int = 4
+    refine_tol: float = 0.0
+    f_scale: float = 1.0
+
+
+@dataclass
+class Workload:
+    name: str
+    wid: int
+    domain: object
+    opts: TreeOptions
+    sources: List[Callable] = field(default_factory=list)  # one per right-hand side
+    description: str = ""
+
+
+def disk_sincos(level: int = 4, K: int = 8) -> Workload:
+    """Disk r=0.35, f=-13 sin3x cos2y, uniform tree, 16 panels x 16 nodes."""
+    dom = StarDomain(0.35, (), n_panels=16)
+    return Workload("disk_sincos_uniform_l%d_k%d" % (level, K), 1, dom,
+                    TreeOptions(K=K, min_level=level, max_level=level), [f_sincos],
+                    "disk r=0.35, f=-13sin(3x)cos(2y), uniform level %d, K=%d" % (level, K))
+
+
+def starfish_gaussian(K: int = 16, tol: float = 1e-10, min_level: int = 2, max_level: int = 12) -> Workload:
+    """Starfish r=0.35(1+0.3cos5t), Gaussian sigma=0.02 at (0.1,0.05), adaptive."""
+    dom = StarDomain(0.35, [(5, 0.3, 0.0)])
+    f = make_gaussian((0.1, 0.05), 0.02)
+    return Workload("starfish_gaussian_adaptive_k%d" % K, 2, dom,
+                    TreeOptions(K=K, min_level=min_level, max_level=max_level, refine_tol=tol, f_scale=1.0),
+                    [f], "starfish r=.35(1+.3cos5t), f=exp(-|x-(.1,.05)|^2/.02^2), adaptive tol %g, K=%d" % (tol, K))
+
+
+def disk_multi_rhs(nrhs: int = 64, level: int = 4, K: int = 8, n_gauss: int = 8) -> Workload:
+    """Disk geometry of the uniform workload with nrhs Gaussian-mixture sources."""
+    rng = np.random.Generator(np.random.PCG64(2211 + 3))
+    dom = StarDomain(0.35, (), n_panels=16)
+    srcs = [random_mixture(dom, rng, n_gauss)[0] for _ in range(nrhs)]
+    return Workload("disk_mixture_x%d_l%d_k%d" % (nrhs, level, K), 3, dom,
+                    TreeOptions(K=K, min_level=level, max_level=level), srcs,
+                    "disk r=0.35, %d RHS of %d-Gaussian mixtures, uniform level %d" % (nrhs, n_gauss, level))
+
+
+def lshape_expsin(K: int = 16, base_level: int = 6, max_level: int = 14, corner_levels: int = 11) -> Workload:
+    dom = l_shape_domain(16, corner_levels)
+    return Workload("lshape_expsin_k%d" % K, 4, dom,
+                    TreeOptions(K=K, min_level=base_level, max_level=max_level, refine_tol=1e-10, f_scale=3.0),
+                    [f_exp_sin], "L-shape side 0.8, f=-3e^x sin2y, base level %d, corners to level %d" % (base_level, max_level))
+
+
+def star_batch(n_domains: int = 32, K: int = 8, tol: float = 1e-10, max_level: int = 12):
+    """Random star domains r=.35(1+sum_{k=2..8} a_k cos(k t+phi_k)), own mixtures."""
+    rng = np.random.Generator(np.random.PCG64(2211 + 5))
+    out = []
+    for d in range(n_domains):
+        modes = [(k, rng.uniform(0.0, 0.04), rng.uniform(0.0, TWO_PI)) for k in range(2, 9)]
+        dom = StarDomain(0.35, modes)
+        f, _ = random_mixture(dom, rng)
+        out.append(Workload("star%02d" % d, 5, dom,
+                            TreeOptions(K=K, min_level=2, max_level=max_level, refine_tol=tol, f_scale=1.0),
+                            [f], "random star %d" % d))
+    return out
+
+
+def gauss_legendre_panel_nodes(dom, nq: int = 16):
+    """Boundary target points y_ij = gamma_i(t_j) on every panel (j fastest)."""
+    t, _ = np.polynomial.legendre.leggauss(nq)
+    pts = [dom.curve(i, t)[0] for i in range(dom.n_panels)]
+    return np.concatenate(pts, axis=0) if pts else np.zeros((0, 2))
