@@ -8,9 +8,9 @@ computes, written from the paper (Sections 3.1, 3.2, 4, 4.1):
 * leaf classification (regular / cut / exterior) and extension lists
   (Section 4, definition of the extension list);
 * the universal stencil X_S u X_Sbar u G of every cut leaf and the
-  least-squares extension (Section 3.2) -- here in the flat limit of the
-  Gaussian basis, i.e. least squares in the polynomials of total degree <= q,
-  written with a Legendre Vandermonde matrix and a Householder QR;
+  least-squares extension f_E = A_{E,G} A_{I,G}^+ f_I (Section 3.2) in the
+  flat limit of the Gaussian basis (A = Lagrange basis of P_q at G, formed
+  with a Legendre Vandermonde matrix; A^+ by the SVD);
 * the truncated Chebyshev expansion on the extension square and its
   evaluation on the extension-list leaves (Section 4.1, eq. chebexpbarS);
 * the volume potential by direct quadrature (``vpx_oracle.c``) and its
@@ -114,11 +114,47 @@ def padua_points(q: int) -> np.ndarray:
     return np.asarray(pts)
 
 
+PINV_RCOND = 1e-13   # singular values below this fraction of the largest are dropped
+
+
 def stencil_params(K: int):
-    """q, Kbar, N_G for leaf order K (q = K+2, Kbar = 3K/2, N_G = dim P_q)."""
-    q = K + 2
+    """q, Kbar, N_G for leaf order K.
+
+    N_G = 66 Gaussian support points (Section 6) for every K, i.e. the flat
+    limit spans the polynomials of total degree q = 10; Kbar = 3K/2 (12 for
+    K = 8 as in Section 6)."""
+    q = 10
     Kbar = 3 * K // 2
     return q, Kbar, (q + 1) * (q + 2) // 2
+
+
+_universal_A = {}
+
+
+def universal_matrix(K: int):
+    """A_{X,G} = Phi_{X,G} Phi_{G,G}^{-1} (eq. defA) on the reference extension
+    square [-1,1]^2 in the flat limit: the Lagrange basis of P_q at the Padua
+    points G evaluated at X = X_S u X_Sbar u G.  Written with the Legendre
+    total-degree Vandermonde matrix (any basis of P_q gives the same A)."""
+    if K not in _universal_A:
+        q, Kbar, NG = stencil_params(K)
+        t, _ = gauss_legendre(K)
+        XS = np.stack(np.meshgrid(t / 3.0, t / 3.0, indexing="xy"), axis=-1).reshape(-1, 2)
+        tc = chebyshev1_nodes(Kbar)
+        XSb = np.stack(np.meshgrid(tc, tc, indexing="xy"), axis=-1).reshape(-1, 2)
+        G = padua_points(q)
+        VX = legendre_total_degree_vander(np.concatenate([XS, XSb, G]), q)
+        VG = legendre_total_degree_vander(G, q)
+        _universal_A[K] = np.linalg.solve(VG.T, VX.T).T
+    return _universal_A[K]
+
+
+def pseudo_inverse(M: np.ndarray, rcond: float = PINV_RCOND) -> np.ndarray:
+    """Moore-Penrose pseudo-inverse by the SVD (numpy/LAPACK), singular values
+    <= rcond * largest treated as zero."""
+    U, s, Vt = np.linalg.svd(M, full_matrices=False)
+    keep = s > rcond * s[0]
+    return (Vt[keep].T / s[keep]) @ U[:, keep].T
 
 
 # --------------------------------------------------------------------------- boxes
@@ -473,10 +509,6 @@ def stencil_points(tree: OracleTree, dom):
 
 # --------------------------------------------------------------------------- extension
 
-class StencilError(RuntimeError):
-    pass
-
-
 def legendre_total_degree_vander(z: np.ndarray, q: int) -> np.ndarray:
     """Columns P_m(z1) P_n(z2), m + n <= q (ordered by m then n)."""
     V1 = npleg.legvander(z[:, 0], q)
@@ -489,25 +521,24 @@ def extend_cut_leaf(b, K, t, masks, fI: np.ndarray, targets: np.ndarray):
     """Section 3.2 + 4.1 for one cut leaf, flat-limit reading.
 
     fI: (N_I, nrhs) data at the interior stencil points (X_S^I, X_Sbar^I, G^I).
-    Least squares in P_q on the interior points gives the values at the
-    exterior Chebyshev nodes of Sbar; with the interior data this fills the
-    Kbar x Kbar grid, whose Chebyshev expansion truncated to m+n < Kbar is
+    f_{X_Sbar^E} = A_{X_Sbar^E,G} A_{X^I,G}^+ f_I fills the exterior nodes of
+    the Kbar x Kbar Chebyshev grid, the interior nodes keep the data; the
+    grid's Chebyshev expansion truncated to m+n < Kbar (eq. chebexpbarS) is
     evaluated at ``targets`` (physical coordinates inside Sbar).
-    Returns (values at targets (n, nrhs), condition number of the LS matrix).
+    Returns (values at targets (n, nrhs), condition number of A_I).
     """
     q, Kbar, NG = stencil_params(K)
     XS, XSb, G = cut_leaf_stencil(b, K, t)
     cx, cy = box_center(b)
     r = 1.5 * box_side(b[0])
-    XI = np.concatenate([XS[masks[0]], XSb[masks[1]], G[masks[2]]])
-    if len(XI) < NG:
-        raise StencilError("cut leaf %s: %d interior stencil points < %d" % (b, len(XI), NG))
-    zI = (XI - np.array([cx, cy])) / r
-    VI = legendre_total_degree_vander(zI, q)
-    Qm, Rm = np.linalg.qr(VI)                     # Householder QR (LAPACK)
-    coef = np.linalg.solve(Rm, Qm.T @ fI)         # least-squares coefficients
-    sv = np.linalg.svd(VI, compute_uv=False)
-    cond = sv[0] / sv[-1]
+    A = universal_matrix(K)
+    nS = K * K
+    interior = np.concatenate(masks)
+    AI = A[interior]
+    AE = A[nS:nS + Kbar * Kbar][~masks[1]]
+    fG = pseudo_inverse(AI) @ fI                  # values at G (the least-squares solution)
+    sv = np.linalg.svd(AI, compute_uv=False)
+    cond = sv[0] / sv[sv > PINV_RCOND * sv[0]][-1]
     # Kbar x Kbar grid: interior nodes keep the data, exterior nodes get the fit
     nI_S = int(masks[0].sum())
     nI_Sb = int(masks[1].sum())
@@ -515,8 +546,7 @@ def extend_cut_leaf(b, K, t, masks, fI: np.ndarray, targets: np.ndarray):
     grid[masks[1]] = fI[nI_S:nI_S + nI_Sb]
     ext = ~masks[1]
     if ext.any():
-        zE = (XSb[ext] - np.array([cx, cy])) / r
-        grid[ext] = legendre_total_degree_vander(zE, q) @ coef
+        grid[ext] = AE @ fG
     # Chebyshev coefficients: grid[ax, by] = sum_mn alpha[m,n] T_m(x_ax) T_n(y_by)
     tc = chebyshev1_nodes(Kbar)
     T = npcheb.chebvander(tc, Kbar - 1)           # T[a, m] = T_m(tc[a])

@@ -272,7 +272,7 @@ static double box_distance(double px, double py, double cx, double cy, double h)
 }
 
 static const int FAR_Q[3] = {20, 14, 10};
-static const int NEAR_Q = 12;
+static const int NEAR_Q = 20;
 
 void orc_leaf_basis_integrals(int K, const double *t, double cx, double cy, double h,
                               double px, double py, double *I)

@@ -175,13 +175,13 @@ def _extension_operator_norm(tree, meta, i, targets):
 
 @pytest.mark.parametrize("wl", ["disk_l3_k8", "disk_l4_k8", "disk_l4_k16"])
 def test_extension_reproduces_total_degree_q_polynomials(wl):
-    """Section 3.2 least squares on P_q: a polynomial of total degree q = K+2
-    is reproduced at every extension node, up to rounding times the
+    """Section 3.2 least squares on P_q: a polynomial of total degree q = 10
+    (N_G = 66) is reproduced at every extension node, up to rounding times the
     conditioning of the extrapolation."""
     lev, K = {"disk_l3_k8": (3, 8), "disk_l4_k8": (4, 8), "disk_l4_k16": (4, 16)}[wl]
     w = W.disk_sincos(level=lev, K=K)
     tree = O.build_tree(w.domain, w.opts, w.sources[0])
-    q = K + 2
+    q = O.stencil_params(K)[0]
     rng = np.random.default_rng(lev * 100 + K)
     cc = rng.standard_normal((q + 1, q + 1))
 
@@ -208,7 +208,7 @@ def test_extension_is_not_identity_on_nonpolynomial_data():
     """Guard against a vacuous pass: a degree q+3 polynomial is NOT reproduced."""
     w = W.disk_sincos(level=3, K=8)
     tree = O.build_tree(w.domain, w.opts, w.sources[0])
-    f = lambda xy: (3 * xy[:, 0]) ** 13 + (3 * xy[:, 1]) ** 12
+    f = lambda xy: (3 * xy[:, 0]) ** 13 + (3 * xy[:, 1]) ** 12 + np.exp(3 * xy[:, 0])
     pts, meta = O.stencil_points(tree, w.domain)
     vals, _ = O.leaf_values(tree, w.domain, f(pts)[:, None], meta)
     errs = [np.max(np.abs(vals[i, 0] - f(O.leaf_nodes(tree.leaves[i], tree.t)))) for i in tree.cut_leaves()]

@@ -145,7 +145,8 @@ def choose_panel_count(dom: StarDomain, candidates=None) -> int:
 
     The smallest N among ``candidates`` such that, on every panel, the
     16-point Legendre expansion of |gamma'(t)| has its two highest
-    coefficients below 1e-15 times its largest one.  This is input
+    coefficients below 1e-14 times its largest one (fifteen digits, read
+    against the ~4e-15 rounding floor of the transform).  This is input
     preparation (how finely the user samples the boundary), not part of the
     volume-potential method.
     """
@@ -161,7 +162,7 @@ def choose_panel_count(dom: StarDomain, candidates=None) -> int:
             _, d = dom.curve(i, t)
             sp = np.hypot(d[:, 0], d[:, 1])
             c = Vinv @ sp
-            if max(abs(c[-1]), abs(c[-2])) > 1e-15 * np.max(np.abs(c)):
+            if max(abs(c[-1]), abs(c[-2])) > 1e-14 * np.max(np.abs(c)):
                 ok = False
                 break
         if ok:
