@@ -258,9 +258,9 @@ static void far_rule_init(far_rule *r, int Q, int K, const double *t)
 /* order of the tensor GL rule for a leaf at distance d, side s (d >= s) */
 static int far_order_index(double d, double s)
 {
-    if (d >= 4.0 * s) return 2;   /* Q = 10 */
-    if (d >= 2.0 * s) return 1;   /* Q = 14 */
-    return 0;                     /* Q = 20 */
+    if (d >= 4.0 * s) return 2;
+    if (d >= 2.0 * s) return 1;
+    return 0;
 }
 
 static double box_distance(double px, double py, double cx, double cy, double h)
@@ -271,7 +271,11 @@ static double box_distance(double px, double py, double cx, double cy, double h)
     return sqrt(dx * dx + dy * dy);
 }
 
-static const int FAR_Q[3] = {20, 14, 10};
+/* The integrand is a basis polynomial of degree K-1 per variable times the
+ * log kernel; the rules below integrate the kernel part to ~1e-17 and are
+ * raised by K/2 points so that the polynomial factor is integrated exactly. */
+static const int FAR_Q_BASE[3] = {20, 14, 10};
+static int far_q(int qi, int K) { return FAR_Q_BASE[qi] + K / 2; }
 static const int NEAR_Q = 20;
 
 void orc_leaf_basis_integrals(int K, const double *t, double cx, double cy, double h,
@@ -280,7 +284,7 @@ void orc_leaf_basis_integrals(int K, const double *t, double cx, double cy, doub
     double d = box_distance(px, py, cx, cy, h);
     if (d >= 2.0 * h) {
         far_rule fr;
-        far_rule_init(&fr, FAR_Q[far_order_index(d, 2.0 * h)], K, t);
+        far_rule_init(&fr, far_q(far_order_index(d, 2.0 * h), K), K, t);
         for (int j = 0; j < K * K; ++j) I[j] = 0.0;
         for (int i = 0; i < fr.Q; ++i)
             for (int jj = 0; jj < fr.Q; ++jj) {
@@ -315,10 +319,10 @@ int orc_volume_potential(int n_leaves, const double *lcx, const double *lcy, con
     const int KK = K * K;
     if (K > 32 || nrhs > 256) return -1;
     far_rule fr[3];
-    for (int q = 0; q < 3; ++q) far_rule_init(&fr[q], FAR_Q[q], K, t);
+    for (int q = 0; q < 3; ++q) far_rule_init(&fr[q], far_q(q, K), K, t);
     /* per leaf and rhs: values of p_B at the three far rules' tensor points */
     size_t per = 0;
-    for (int q = 0; q < 3; ++q) per += (size_t)FAR_Q[q] * FAR_Q[q];
+    for (int q = 0; q < 3; ++q) per += (size_t)far_q(q, K) * far_q(q, K);
     double *P = (double *)malloc(sizeof(double) * per * (size_t)n_leaves * nrhs);
     unsigned char *nz = (unsigned char *)malloc(n_leaves);
     if (!P || !nz) { free(P); free(nz); return -2; }
@@ -329,7 +333,7 @@ int orc_volume_potential(int n_leaves, const double *lcx, const double *lcy, con
             for (int j = 0; j < KK; ++j) if (F[j] != 0.0) any = 1;
             double *dst = P + ((size_t)B * nrhs + r) * per;
             for (int q = 0; q < 3; ++q) {
-                int Q = FAR_Q[q];
+                int Q = far_q(q, K);
                 for (int i = 0; i < Q; ++i)
                     for (int jj = 0; jj < Q; ++jj) {
                         double s = 0.0;
@@ -363,9 +367,9 @@ int orc_volume_potential(int n_leaves, const double *lcx, const double *lcy, con
             double d = box_distance(px, py, cx, cy, h);
             if (d >= 2.0 * h) {
                 int qi = far_order_index(d, 2.0 * h);
-                int Q = FAR_Q[qi];
+                int Q = far_q(qi, K);
                 size_t off = 0;
-                for (int q = 0; q < qi; ++q) off += (size_t)FAR_Q[q] * FAR_Q[q];
+                for (int q = 0; q < qi; ++q) off += (size_t)far_q(q, K) * far_q(q, K);
                 for (int r = 0; r < nrhs; ++r) {
                     const double *Pv = P + ((size_t)B * nrhs + r) * per + off;
                     double s = 0.0;

@@ -8,6 +8,7 @@ in a space that contains the data), brute-force tree invariants (Section 4)
 and Lagrange-interpolation exactness.
 """
 import math
+from fractions import Fraction
 
 import numpy as np
 import pytest
@@ -45,6 +46,31 @@ def _green_area_integral(qfun, gradq, x, x0, x1, y0, y1):
         tot += v
     inside = x0 < x[0] < x1 and y0 < x[1] < y1
     return tot + (2.0 * math.pi * qfun(x) if inside else 0.0)
+
+
+def _poly_q_tensor(K, cx, cy, h, seed):
+    """q = sum c_ab u^(a+2) v^(b+2), a, b <= K-3: the Laplacian has degree up to
+    K-1 in each variable (total degree up to 2K-4), i.e. it spans most of the
+    leaf's tensor space Q_{K-1}, not only the total-degree subspace."""
+    rng = np.random.default_rng(seed)
+    c = rng.standard_normal((K - 2, K - 2)) / (K * K)
+    terms = [(a + 2, b + 2) for a in range(K - 2) for b in range(K - 2)]
+
+    def q(y):
+        u, v = (y[0] - cx) / h, (y[1] - cy) / h
+        return sum(c[m - 2, n - 2] * u ** m * v ** n for m, n in terms)
+
+    def gq(y):
+        u, v = (y[0] - cx) / h, (y[1] - cy) / h
+        gx = sum(c[m - 2, n - 2] * m * u ** (m - 1) * v ** n for m, n in terms) / h
+        gy = sum(c[m - 2, n - 2] * n * u ** m * v ** (n - 1) for m, n in terms) / h
+        return np.array([gx, gy])
+
+    def lap(y):
+        u, v = (y[0] - cx) / h, (y[1] - cy) / h
+        return sum(c[m - 2, n - 2] * (m * (m - 1) * u ** (m - 2) * v ** n + n * (n - 1) * u ** m * v ** (n - 2))
+                   for m, n in terms) / (h * h)
+    return q, gq, lap
 
 
 def _poly_q(K, cx, cy, h, seed):
@@ -87,9 +113,11 @@ def test_gauss_legendre_exact_on_monomials():
             assert abs(np.sum(w * x ** k) - exact) < 1e-14
 
 
+@pytest.mark.parametrize("tensor", [False, True])
 @pytest.mark.parametrize("K", [8, 16])
-@pytest.mark.parametrize("where", ["self", "self_corner_node", "edge_near", "corner_near", "adjacent", "diag", "far"])
-def test_leaf_integrals_match_green_identity(K, where):
+@pytest.mark.parametrize("where", ["self", "self_corner_node", "edge_near", "corner_near", "adjacent", "diag",
+                                   "far", "far2", "far4"])
+def test_leaf_integrals_match_green_identity(K, where, tensor):
     """Near/self/far leaf integrals of a polynomial density against Green's identity."""
     L = O.lib()
     t, _ = O.gauss_legendre(K)
@@ -102,9 +130,11 @@ def test_leaf_integrals_match_green_identity(K, where):
         "adjacent": (cx + 2.5 * h, cy + 0.1 * h),
         "diag": (cx + 1.9 * h, cy + 1.9 * h),
         "far": (cx + 5.0 * h, cy - 3.1 * h),
+        "far2": (cx + 3.05 * h, cy + 0.9 * h),
+        "far4": (cx - 9.5 * h, cy + 2.0 * h),
     }[where]
     x = np.array(x)
-    q, gq, lap = _poly_q(K, cx, cy, h, seed=K * 7 + len(where))
+    q, gq, lap = (_poly_q_tensor if tensor else _poly_q)(K, cx, cy, h, seed=K * 7 + len(where))
     X, Y = np.meshgrid(cx + h * t, cy + h * t, indexing="xy")
     nodes = np.stack([X.ravel(), Y.ravel()], axis=1)
     p = np.array([lap(y) for y in nodes])
@@ -258,3 +288,99 @@ def test_interpolation_exact_for_tensor_polynomials():
     p = np.concatenate([rng.uniform(-0.5, 0.5, (30, 2)), [[0.25, 0.0], [0.5, 0.5], [-0.5, -0.5]]])
     got = O.interpolate_at(tree, vals, p)[:, 0]
     assert np.max(np.abs(got - f(p)) / np.abs(f(p))) < 1e-12
+
+
+def _mono2cheb_exact(c):
+    """Exact monomial -> Chebyshev coefficients (rationals):
+    u^m = 2^(1-m) sum_k C(m,k) T_(m-2k), the T_0 term halved."""
+    out = [Fraction(0)] * len(c)
+    for m, cm in enumerate(c):
+        if cm == 0:
+            continue
+        for k in range(m // 2 + 1):
+            coef = Fraction(math.comb(m, k), 2 ** (m - 1)) if m > 0 else Fraction(1)
+            j = m - 2 * k
+            if j == 0 and m > 0:
+                coef /= 2
+            out[j] += cm * coef
+    return out
+
+
+def _cheb2d_exact(Q):
+    n0, n1 = len(Q), len(Q[0])
+    A = [_mono2cheb_exact([Q[i][j] for j in range(n1)]) for i in range(n0)]     # along v
+    B = [[Fraction(0)] * n1 for _ in range(n0)]
+    for j in range(n1):
+        col = _mono2cheb_exact([A[i][j] for i in range(n0)])                     # along u
+        for i in range(n0):
+            B[i][j] = col[i]
+    return np.array([[float(x) for x in row] for row in B])
+
+
+def _basis_density_q(K, a, b, cx, cy, h):
+    """Density p = l_a(u) l_b(v) (one tensor Lagrange basis function of the
+    leaf, degree K-1 in each variable) and q with Laplacian q = p, built in
+    exact rational arithmetic: monomial coefficients of l_a, l_b from the
+    (exactly represented) nodes, the terminating series
+    q = sum_k (-1)^k u^(m+2k+2) / ((m+1)...(m+2k+2)) d^2k/dv^2k v^n for every
+    monomial u^m v^n, then an exact conversion to Chebyshev series that are
+    evaluated in floating point (Clenshaw)."""
+    t, _ = O.gauss_legendre(K)
+    T = [Fraction(float(x)) for x in t]
+
+    def lag(idx):
+        c = [Fraction(1)]
+        for m in range(K):
+            if m == idx:
+                continue
+            d = T[idx] - T[m]
+            nc = [Fraction(0)] * (len(c) + 1)
+            for i, ci in enumerate(c):
+                nc[i + 1] += ci / d
+                nc[i] -= ci * T[m] / d
+            c = nc
+        return c
+    la, lb = lag(a), lag(b)
+    N = 2 * K + 3
+    Q = [[Fraction(0)] * N for _ in range(N)]
+    for m in range(K):
+        for n in range(K):
+            c = la[m] * lb[n]
+            if c == 0:
+                continue
+            k = 0
+            while 2 * k <= n:
+                den = math.prod(range(m + 1, m + 2 * k + 3))
+                dv = math.prod(range(n - 2 * k + 1, n + 1)) if k else 1
+                Q[m + 2 * k + 2][n - 2 * k] += (-1) ** k * c * dv / den
+                k += 1
+    Qu = [[(i + 1) * Q[i + 1][j] for j in range(N)] for i in range(N - 1)] + [[Fraction(0)] * N]
+    Qv = [[(j + 1) * Q[i][j + 1] for j in range(N - 1)] + [Fraction(0)] for i in range(N)]
+    Cq, Cu, Cv = _cheb2d_exact(Q), _cheb2d_exact(Qu), _cheb2d_exact(Qv)
+    ch = np.polynomial.chebyshev
+
+    def q(y):
+        return ch.chebval2d((y[0] - cx) / h, (y[1] - cy) / h, Cq) * h * h
+
+    def gq(y):
+        u, v = (y[0] - cx) / h, (y[1] - cy) / h
+        return np.array([ch.chebval2d(u, v, Cu), ch.chebval2d(u, v, Cv)]) * h
+
+    return q, gq
+
+
+@pytest.mark.parametrize("K,a,b", [(16, 15, 0), (16, 7, 8), (16, 3, 12), (8, 7, 0), (8, 4, 3)])
+@pytest.mark.parametrize("where", ["near_edge", "far1", "far2", "far4"])
+def test_single_basis_integral_green_identity(K, a, b, where):
+    """The integral of one Lagrange basis function times the log kernel (one
+    table-like entry) against Green's identity: catches quadrature rules too
+    short for the polynomial degree of the basis."""
+    L = O.lib()
+    t, _ = O.gauss_legendre(K)
+    cx, cy, h = 0.0, 0.0, 1.0
+    x = {"near_edge": (1.02, 0.3), "far1": (3.05, 0.9), "far2": (5.5, -2.0), "far4": (-9.5, 6.7)}[where]
+    q, gq = _basis_density_q(K, a, b, cx, cy, h)
+    I = np.zeros(K * K)
+    L.orc_leaf_basis_integrals(K, O._ptr(np.ascontiguousarray(t)), cx, cy, h, x[0], x[1], O._ptr(I))
+    want = _green_area_integral(q, gq, np.array(x), -1.0, 1.0, -1.0, 1.0)
+    assert abs(I[b * K + a] - want) <= 1e-11 * max(1.0, abs(want)), (I[b * K + a], want)
