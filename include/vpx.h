@@ -1,0 +1,190 @@
+/*
+ * vpx.h -- C ABI of the GB300 library for the particular-solution stage of the
+ * FMM-accelerated Poisson solver with function extension (Fryklund &
+ * Greengard, arXiv 2211.14537):
+ *
+ *   (a) extension of the source f from the interior of Omega to the
+ *       boundary-cut leaves and their extension lists (Sections 3.2, 4.1);
+ *   (b) the volume potential  V[f^e](x) = (1/2pi) int_E log|x-y| f^e(y) dy
+ *       (eq. volinte) at every leaf node of an adaptive, level-restricted
+ *       quad-tree and at the Gauss-Legendre nodes of the boundary panels
+ *       (Section 4.1, last paragraph; Section 5, boundary nodes y_ij).
+ *
+ * Conventions shared by every call
+ *   - Every function returns an int status: VPX_OK (0) or a negative
+ *     VPX_ERR_* code; nothing throws across the ABI.  vpx_error_string()
+ *     names a code; vpx_last_error_message() gives detail for this thread.
+ *   - D = [-0.5, 0.5]^2 is the root box (Section 4: Omega and the support E
+ *     of f^e lie inside the unit square centred at the origin).
+ *   - Points are interleaved (x, y) doubles.  Leaves are listed in Z-order
+ *     (depth first, children SW, SE, NW, NE); the K*K nodes of a leaf are
+ *     Gauss-Legendre tensor nodes, node (a, b) at index b*K + a (x varies
+ *     fastest).
+ *   - Right-hand sides are columns: column r of an input/output array starts
+ *     at ptr + r*ld.  Device pointers are raw CUDA device addresses; the
+ *     caller allocates and owns them.  `stream` is a cudaStream_t (NULL =
+ *     legacy default stream).  Device calls are asynchronous on `stream`;
+ *     kernel-side errors are latched in a device status word that
+ *     vpx_sync_status() reads after synchronising the stream.
+ *   - A plan owns every device buffer it allocates (tree, lists, tables,
+ *     extension operators, workspace) and frees them in vpx_plan_destroy().
+ *   - A plan is used by one host thread at a time.
+ */
+#ifndef VPX_H
+#define VPX_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ status codes */
+#define VPX_OK             0
+#define VPX_ERR_ARG       -1  /* invalid argument (null pointer, bad size, bad option) */
+#define VPX_ERR_CUDA      -2  /* a CUDA runtime call failed */
+#define VPX_ERR_NOMEM     -3  /* host or device allocation failed */
+#define VPX_ERR_STENCIL   -4  /* a cut leaf has fewer interior stencil points than N_G, or a rank-deficient fit */
+#define VPX_ERR_DOMAIN    -5  /* the extension square of a cut leaf leaves D */
+#define VPX_ERR_LEVEL     -6  /* refinement would exceed the compiled maximum level */
+#define VPX_ERR_TIMEOUT   -7  /* a bounded device wait gave up */
+#define VPX_ERR_NAN       -8  /* non-finite value detected in input or output */
+#define VPX_ERR_CALLBACK  -9  /* a user callback returned non-zero */
+#define VPX_ERR_STATE    -10  /* call not valid for this plan (e.g. host-only plan) */
+#define VPX_ERR_NODEV    -11  /* no CUDA device available */
+
+/* ----------------------------------------------------------------- options */
+#define VPX_PREC_FP64   0   /* every step in FP64 */
+#define VPX_PREC_MIXED  1   /* near-field and M2L contractions on tensor cores with exact bf16 slices */
+
+#define VPX_PLAN_HOST_ONLY 1u /* build tree, lists and stencil on the host only; no device work */
+
+typedef struct {
+    int    K;            /* leaf nodes per dimension (Gauss-Legendre), 4..16, even */
+    int    min_level;    /* every box above this level is split (uniform base) */
+    int    max_level;    /* no box is split below this level (<= 15) */
+    double refine_tol;   /* resolution tolerance (0: uniform tree at min_level) */
+    double f_scale;      /* tolerance is relative to this magnitude of f (> 0) */
+    int    p;            /* multipole / local expansion order (terms 0..p), 8..60 */
+    int    precision;    /* VPX_PREC_FP64 or VPX_PREC_MIXED */
+    int    max_rhs;      /* largest nrhs a later vpx_execute may pass */
+    int    n_quad_bdry;  /* Gauss-Legendre nodes per boundary panel (default 16) */
+} vpx_options;
+
+/* ---------------------------------------------------------------- callbacks
+ * All return 0 on success; non-zero aborts plan creation with VPX_ERR_CALLBACK.
+ *   vpx_points_cb: out[i] = f(xy[2i], xy[2i+1]) for i < n  (the source used
+ *                  for adaptive refinement; may be called outside Omega).
+ *   vpx_inside_cb: inside[i] = 1 iff point i lies strictly inside Omega.
+ *   vpx_curve_cb : for panel `panel` (0-based) and n parameters t[k] in [-1,1],
+ *                  xy[2k..] = gamma_panel(t[k]), dxy[2k..] = gamma_panel'(t[k]).
+ */
+typedef int (*vpx_points_cb)(const double *xy, int64_t n, double *out, void *ctx);
+typedef int (*vpx_inside_cb)(const double *xy, int64_t n, uint8_t *inside, void *ctx);
+typedef int (*vpx_curve_cb)(int panel, const double *t, int n, double *xy, double *dxy, void *ctx);
+
+typedef struct vpx_plan *vpx_plan_t;
+
+/* Fill `opt` with defaults (K=8, levels 4/4, p=44, FP64, max_rhs=1, 16 boundary nodes). */
+int vpx_default_options(vpx_options *opt);
+
+/*
+ * Build the plan for one geometry (Section 4): the adaptive quad-tree
+ * (resolution and cut-size refinement, 2:1 level restriction, extension
+ * restriction), leaf classification and extension lists, the universal
+ * stencil of every cut leaf and its least-squares extension operator
+ * (Section 3.2), the near-field, expansion and translation tables of the box
+ * FMM, the interaction lists (built on the device), and the boundary nodes.
+ * n_panels may be 0 (no boundary: every leaf must then be regular).
+ * flags: 0 or VPX_PLAN_HOST_ONLY.  On success *out owns all resources.
+ */
+int vpx_plan_create(const vpx_options *opt, int n_panels, vpx_curve_cb curve, vpx_inside_cb inside,
+                    vpx_points_cb refine_f, void *ctx, unsigned flags, vpx_plan_t *out);
+
+/* Sizes: leaves, leaf nodes (n_leaves*K*K), stencil points (length of the f
+ * input column), boundary nodes (n_panels * n_quad_bdry).  Any pointer may be NULL. */
+int vpx_plan_sizes(vpx_plan_t plan, int64_t *n_leaves, int64_t *n_leaf_nodes, int64_t *n_stencil,
+                   int64_t *n_bdry);
+
+/* Host copies of the leaf table, each of length n_leaves (any may be NULL):
+ * level, ix, iy (box = [-0.5+ix*s, -0.5+(ix+1)*s] x ..., s = 2^-level),
+ * cls (0 regular, 1 cut, 2 exterior), owner (exterior leaves: the leaf index
+ * of the cut leaf whose extension list holds it, else -1). */
+int vpx_plan_leaves(vpx_plan_t plan, int32_t *level, int32_t *ix, int32_t *iy, int32_t *cls, int32_t *owner);
+
+/* Host array of 2*n_stencil doubles: every point where f must be supplied --
+ * the K*K nodes of each regular leaf (leaf order), then for each cut leaf
+ * (leaf order) its interior stencil points X_S^I, X_Sbar^I, G^I (Section 3.2). */
+int vpx_stencil_points(vpx_plan_t plan, double *xy);
+
+/* Host array of 2*n_leaf_nodes doubles: all target nodes, leaf-major. */
+int vpx_leaf_nodes(vpx_plan_t plan, double *xy);
+
+/* Host array of 2*n_bdry doubles: boundary nodes gamma_i(t_j), j fastest. */
+int vpx_boundary_nodes(vpx_plan_t plan, double *xy);
+
+/* Interaction-list counts of the plan (host): near pairs, M2L (list i)
+ * pairs, S2L (list i+) pairs, M2T (list i-) pairs, boxes, levels.  Any may be NULL. */
+int vpx_plan_list_counts(vpx_plan_t plan, int64_t *near, int64_t *m2l, int64_t *s2l, int64_t *m2t,
+                         int64_t *n_boxes, int32_t *n_levels);
+
+/* Host copies of the fixed-slot interaction lists (-1 = empty slot), for
+ * inspection and tests: near (n_leaves x 33: the source leaf of each of the
+ * 9 colleague, 12 coarse and 12 fine configurations), list i (n_boxes x 40
+ * offsets), list i+ (n_boxes x 20), list i- (n_leaves x 20), and the boxes
+ * (level, ix, iy, leaf index or -1), n_boxes each.  Any pointer may be NULL. */
+int vpx_plan_lists(vpx_plan_t plan, int32_t *near, int32_t *vlist, int32_t *xlist, int32_t *wlist,
+                   int32_t *box_level, int32_t *box_ix, int32_t *box_iy, int32_t *box_leaf);
+
+/* Host copy of the near-field tables (33 x K*K x K*K doubles): entry
+ * [c][i][j] = int over the source box [-1,1]^2 of log|x_i - y| l_j(y) dy, x_i the
+ * i-th target node of configuration c in source reference coordinates
+ * (Section 4, near-neighbour tables).  Device plans only. */
+int vpx_plan_near_tables(vpx_plan_t plan, double *out);
+
+/*
+ * The hot path.  f_stencil: device, nrhs columns of n_stencil values (ld_f >= n_stencil).
+ * v_leaf: device, nrhs columns of n_leaf_nodes values (ld_v >= n_leaf_nodes).
+ * v_bdry: device, nrhs columns of n_bdry values (ld_b >= n_bdry); may be NULL.
+ * Computes f^e on all leaves (extension) and V[f^e] at all targets.
+ * Asynchronous on `stream`.  nrhs <= opt.max_rhs.
+ */
+int vpx_execute(vpx_plan_t plan, const double *f_stencil, int nrhs, int64_t ld_f,
+                double *v_leaf, int64_t ld_v, double *v_bdry, int64_t ld_b, void *stream);
+
+/* Extension only: f^e at all leaf nodes (device, nrhs columns, ld_fe >= n_leaf_nodes). */
+int vpx_extend(vpx_plan_t plan, const double *f_stencil, int nrhs, int64_t ld_f,
+               double *fe_leaf, int64_t ld_fe, void *stream);
+
+/* Volume potential only (the box FMM of Section 4.1) for given leaf-node
+ * values fe_leaf (device, nrhs columns of n_leaf_nodes values). */
+int vpx_potential(vpx_plan_t plan, const double *fe_leaf, int nrhs, int64_t ld_fe,
+                  double *v_leaf, int64_t ld_v, double *v_bdry, int64_t ld_b, void *stream);
+
+/* End to end with HOST buffers (contiguous columns): copies f in, runs
+ * vpx_execute on the plan's own stream, copies V out, synchronises. */
+int vpx_execute_host(vpx_plan_t plan, const double *f_stencil_host, int nrhs,
+                     double *v_leaf_host, double *v_bdry_host);
+
+/* Synchronise the plan's last stream and return the latched device status
+ * (VPX_OK, VPX_ERR_NAN, VPX_ERR_TIMEOUT, ...); clears it. */
+int vpx_sync_status(vpx_plan_t plan);
+
+/* Per-pass device times (ms) of the last vpx_execute when timing is enabled
+ * (vpx_set_timing(plan, 1)); n <= VPX_N_PASSES entries are written. */
+#define VPX_N_PASSES 8
+int vpx_set_timing(vpx_plan_t plan, int enable);
+int vpx_get_timings(vpx_plan_t plan, double *ms, int n);
+
+/* Names of the passes timed by vpx_get_timings, in order. */
+const char *vpx_pass_name(int i);
+
+const char *vpx_error_string(int code);
+const char *vpx_last_error_message(void);
+
+void vpx_plan_destroy(vpx_plan_t plan);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VPX_H */

@@ -1,0 +1,91 @@
+// internal.h -- private declarations of the vpx library (host + device).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/vpx.h"
+
+namespace vpx {
+
+constexpr int kMaxLevel = 15;     // ix, iy < 2^15
+constexpr int kMaxK = 16;
+constexpr int kMaxP = 64;         // expansion terms (p + 1)
+constexpr int kNearConfigs = 33;  // 9 colleagues + 12 coarse + 12 fine (Section 4, Fig. tree_levels)
+constexpr int kVSlots = 40;       // list i offsets: [-3,3]^2 minus [-1,1]^2
+constexpr int kXSlots = 20;       // list i+ (coarse leaf) relative positions
+constexpr int kWSlots = 20;       // list i- (fine box) relative positions
+constexpr double kPi = 3.14159265358979323846;
+
+enum LeafClass : int32_t { kRegular = 0, kCut = 1, kExterior = 2 };
+
+// ------------------------------------------------------------------ errors
+struct Error {
+    int code;
+    std::string msg;
+};
+void set_error_message(const std::string &m);
+[[noreturn]] void fail(int code, const std::string &m);
+
+// ------------------------------------------------------------- quadrature
+void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w);   // [-1,1], ascending
+void gauss_log_rule(int n, std::vector<double> &x, std::vector<double> &w);   // weight -r log r on [0,1]
+std::vector<double> chebyshev1(int n);                                        // ascending
+void padua(int q, std::vector<double> &x, std::vector<double> &y);
+std::vector<double> barycentric_weights(const std::vector<double> &t);
+void lagrange_eval(const std::vector<double> &t, const std::vector<double> &bw, double s, double *out);
+
+// ------------------------------------------------------------- box keys
+inline uint64_t box_key(int level, int ix, int iy) {
+    return (uint64_t(level) << 56) | (uint64_t(uint32_t(ix)) << 28) | uint64_t(uint32_t(iy));
+}
+inline int key_level(uint64_t k) { return int(k >> 56); }
+inline int key_ix(uint64_t k) { return int((k >> 28) & 0xFFFFFFF); }
+inline int key_iy(uint64_t k) { return int(k & 0xFFFFFFF); }
+uint32_t morton2(uint32_t ix, uint32_t iy);   // x in even bits, y in odd bits
+
+struct Leaf {
+    int32_t level, ix, iy, cls, owner;
+};
+
+// The tree as the host builds it.
+struct HostTree {
+    int K = 0;
+    std::vector<Leaf> leaves;            // Z-order
+    int max_level = 0;
+};
+
+struct Callbacks {
+    vpx_curve_cb curve;
+    vpx_inside_cb inside;
+    vpx_points_cb f;
+    void *ctx;
+    int n_panels;
+};
+
+void build_tree(const vpx_options &opt, const Callbacks &cb, HostTree &tree);
+
+// ------------------------------------------------------- stencil / extension
+struct StencilInfo {
+    int q = 0, Kbar = 0, NG = 0, NX = 0;       // NX = K*K + Kbar*Kbar + NG universal points
+    std::vector<double> ref_xy;                // NX universal points on [-1,1]^2 of Sbar (X_S, X_Sbar, G)
+    std::vector<double> A;                     // NX x NG universal matrix (row-major): Lagrange basis of P_q at G
+    std::vector<double> cheb_inv;              // Kbar x Kbar: alpha_m = sum_a C[m][a] F_a
+    // per cut leaf
+    std::vector<int32_t> cut_leaf;             // leaf index
+    std::vector<int64_t> stencil_off;          // offset of its block in the f column
+    std::vector<int32_t> n_interior;           // N_I
+    std::vector<int64_t> pinv_off;             // offset of P_S (NG x N_I, row-major)
+    std::vector<double> pinv;                  // all P_S
+    std::vector<int32_t> grid_src;             // [ncut][Kbar^2]: index into the block, -1 exterior
+    std::vector<int32_t> node_src;             // [ncut][K^2]: index into the block, -1 exterior node
+    std::vector<int32_t> owned_off, owned;     // CSR: owned exterior leaves per cut leaf
+    std::vector<int64_t> reg_leaf_off;         // [n_leaves] stencil offset of a regular leaf, -1 otherwise
+    double max_pinv_norm = 0.0, max_cond = 0.0;
+};
+
+void build_stencil(const vpx_options &opt, const Callbacks &cb, const HostTree &tree,
+                   std::vector<double> &stencil_xy, StencilInfo &st, bool compute_operators);
+
+}  // namespace vpx

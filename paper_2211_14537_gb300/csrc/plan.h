@@ -1,0 +1,126 @@
+// plan.h -- the plan object behind vpx_plan_t (host + device state).
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include "internal.h"
+
+struct vpx_plan;
+
+namespace vpx {
+
+// Device-resident tree and lists (raw device pointers).
+struct DevTree {
+    int n_leaves = 0, n_boxes = 0, n_levels = 0;
+    int32_t level_start[kMaxLevel + 2] = {0};
+    int32_t *box_level = nullptr, *box_ix = nullptr, *box_iy = nullptr, *box_parent = nullptr;
+    int32_t *box_child0 = nullptr, *box_leaf = nullptr;
+    uint32_t *box_morton = nullptr;     // Morton key within its level (sorted per level)
+    uint8_t *box_nz = nullptr;          // subtree carries a non-zero source
+    int32_t *leaf_box = nullptr, *leaf_cls = nullptr;
+    uint8_t *leaf_nz = nullptr;
+    // fixed-slot interaction lists (-1 = empty)
+    int32_t *near = nullptr;   // [n_leaves][33]  source leaf per near-field configuration
+    int32_t *vlist = nullptr;  // [n_boxes][40]   source box per list-i offset
+    int32_t *xlist = nullptr;  // [n_boxes][20]   source leaf per list-i+ configuration
+    int32_t *wlist = nullptr;  // [n_leaves][20]  source box per list-i- position
+};
+
+struct DevTables {
+    double *near = nullptr;     // [33][KK][KK]
+    double *w2 = nullptr;       // [KK] tensor Gauss-Legendre weights on [-1,1]^2
+    double *l2m = nullptr;      // [2P][KK]  rows 2k, 2k+1 = Re, Im of Q_k
+    double *l2t = nullptr;      // [KK][2P]  (Re xi^l, -Im xi^l) interleaved
+    double *m2m = nullptr;      // [4][P][P] complex (interleaved re, im)
+    double *l2l = nullptr;      // [4][P][P] complex
+    double *m2l_b = nullptr;    // [P][P]    real, B'_{lk} = C(l+k-1,k-1) / 2^(l+k)
+    double *s2l = nullptr;      // [20][P][KK] complex
+    double *bary = nullptr;     // [K] barycentric weights of the leaf nodes
+    double *tnodes = nullptr;   // [K] leaf nodes on [-1,1]
+};
+
+struct DevExt {
+    int ncut = 0;
+    int32_t *cut_leaf = nullptr, *n_interior = nullptr, *grid_src = nullptr, *node_src = nullptr;
+    int64_t *stencil_off = nullptr, *pinv_off = nullptr, *reg_leaf_off = nullptr;
+    int32_t *owned_off = nullptr, *owned = nullptr;
+    double *pinv = nullptr;       // all P_S
+    double *A_grid = nullptr;     // [Kbar^2][NG] rows of the universal A at X_Sbar
+    double *cheb_inv = nullptr;   // [Kbar][Kbar]
+    int32_t *leaf_level = nullptr, *leaf_ix = nullptr, *leaf_iy = nullptr;
+    int32_t *owned_flag_dev = nullptr;   // [n_leaves] 1 if the leaf is in an extension list
+    double *m2l_pw = nullptr;            // [40][P] complex tau^-k per list-i offset
+};
+
+struct NearTile {                 // one CTA of the grouped near-field GEMM
+    int32_t config, first, count; // pairs [first, first+count) of that configuration
+};
+
+struct DevWork {
+    int max_rhs = 0;
+    double *fe = nullptr;         // [max_rhs][n_leaves][KK]
+    double *mpole = nullptr;      // [max_rhs][n_boxes][2P]
+    double *local = nullptr;      // [max_rhs][n_boxes][2P]
+    int32_t *near_tgt = nullptr, *near_src = nullptr;   // pairs sorted by configuration
+    NearTile *near_tiles = nullptr;
+    int n_near_tiles = 0;
+    int64_t n_near_pairs = 0;
+    int32_t *nz_leaves = nullptr; // leaves with non-zero source
+    int n_nz_leaves = 0;
+    int32_t *bdry_leaf = nullptr; // [n_bdry]
+    double *bdry_w = nullptr;     // [n_bdry][2K] Lagrange weights (x then y)
+    int *status = nullptr;        // device status word
+    double *f_tmp = nullptr, *v_tmp = nullptr, *b_tmp = nullptr;   // for vpx_execute_host
+};
+
+}  // namespace vpx
+
+struct vpx_plan {
+    vpx_options opt{};
+    bool host_only = false;
+    int K = 0, KK = 0, P = 0;
+    vpx::HostTree tree;
+    vpx::StencilInfo st;
+    std::vector<double> stencil_xy;
+    std::vector<double> leaf_xy;
+    std::vector<double> bdry_xy;
+    std::vector<int32_t> bdry_leaf;
+    std::vector<double> bdry_w;
+    // host copies of the boxes (level, Morton order) and lists
+    std::vector<int32_t> box_level, box_ix, box_iy, box_parent, box_child0, box_leaf;
+    std::vector<uint32_t> box_morton;
+    std::vector<uint8_t> box_nz, leaf_nz;
+    std::vector<int32_t> near, vlist, xlist, wlist;
+    int32_t level_start[vpx::kMaxLevel + 2] = {0};
+    int n_levels = 0;
+    int64_t cnt_near = 0, cnt_m2l = 0, cnt_s2l = 0, cnt_m2t = 0;
+    // device
+    int device = -1;
+    void *stream = nullptr;       // plan-owned stream for vpx_execute_host
+    void *last_stream = nullptr;
+    vpx::DevTree dt;
+    vpx::DevTables tab;
+    vpx::DevExt ext;
+    vpx::DevWork wk;
+    bool timing = false;
+    void *events[VPX_N_PASSES + 1] = {nullptr};
+    double pass_ms[VPX_N_PASSES] = {0};
+};
+
+namespace vpx {
+// host list builder (same routine the device kernel runs)
+void build_boxes(vpx_plan *p);
+void build_lists_host(vpx_plan *p);
+// device side (device.cu)
+void device_setup(vpx_plan *p);
+void device_free(vpx_plan *p);
+void device_extend(vpx_plan *p, const double *f, int nrhs, int64_t ldf, double *fe_out, int64_t ldfe, void *stream);
+void device_potential(vpx_plan *p, const double *fe_in, int64_t ldfe, int nrhs, double *v, int64_t ldv,
+                      double *vb, int64_t ldb, void *stream);
+void device_execute(vpx_plan *p, const double *f, int nrhs, int64_t ldf, double *v, int64_t ldv, double *vb,
+                    int64_t ldb, void *stream);
+int device_sync_status(vpx_plan *p);
+void device_copy_near_tables(vpx_plan *p, double *out);
+void device_execute_host(vpx_plan *p, const double *f, int nrhs, double *v, double *vb);
+}  // namespace vpx

@@ -1,0 +1,279 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+* Volume potential (box FMM, Section 4.1) on seeded leaf data: relative
+  max-norm error <= 1e-12 in FP64 -- the near field is exact for the
+  piecewise polynomial and the far field converges with p.
+* Extension (Sections 3.2, 4.1): per cut leaf, |f^e_gpu - f^e_oracle| is
+  bounded by a multiple of eps * kappa_S * max|f_I|, kappa_S the infinity norm
+  of the cut leaf's extension operator (the extrapolation's conditioning),
+  which the oracle computes itself.
+* End to end (stencil data -> V at leaf and boundary nodes): the same
+  conditioning bound propagated through the potential, plus 1e-12.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+EPS = np.finfo(float).eps
+
+
+@pytest.fixture(scope="module")
+def V():
+    import __graft_entry__ as g
+    g.build_library()
+    from paper_2211_14537_gb300 import vpx
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return vpx
+
+
+def make_plan(V, wl, p=50, max_rhs=1, precision=0):
+    o = V.vpx_default_options(K=wl.opts.K, min_level=wl.opts.min_level, max_level=wl.opts.max_level,
+                              refine_tol=wl.opts.refine_tol, f_scale=wl.opts.f_scale, p=p, max_rhs=max_rhs,
+                              precision=precision)
+    return V.vpx_plan_create(o, wl.domain, wl.sources[0])
+
+
+def seeded_leaf_values(tree, nrhs, seed):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    KK = tree.K * tree.K
+    vals = rng.uniform(-1.0, 1.0, size=(tree.n_leaves, nrhs, KK))
+    for i in range(tree.n_leaves):
+        if tree.cls[i] == O.EXTERIOR and tree.owner[i] < 0:
+            vals[i] = 0.0
+    return vals
+
+
+CASES = {
+    "box_l1_k8_near_only": lambda: W.Workload("box1", 0, W.WholeBoxDomain(), W.TreeOptions(K=8, min_level=1, max_level=1),
+                                              [lambda xy: 0 * xy[:, 0]]),
+    "box_l2_k8_near_m2l": lambda: W.Workload("box2", 0, W.WholeBoxDomain(), W.TreeOptions(K=8, min_level=2, max_level=2),
+                                             [lambda xy: 0 * xy[:, 0]]),
+    "disk_l3_k8": lambda: W.disk_sincos(level=3, K=8),
+    "disk_l4_k8": lambda: W.disk_sincos(level=4, K=8),
+    "disk_l3_k16": lambda: W.disk_sincos(level=3, K=16),
+    "starfish_k8_adaptive": lambda: W.starfish_gaussian(K=8, tol=1e-8, max_level=8),
+    "lshape_k8_adaptive": lambda: W.lshape_expsin(K=8, base_level=3, max_level=8, corner_levels=5),
+}
+
+
+def _subset(n, m, seed):
+    if n <= m:
+        return np.arange(n)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return np.sort(rng.choice(n, m, replace=False))
+
+
+def _near_geometry():
+    g = [(-2.0 * dx, -2.0 * dy, 1.0) for dy in (-1, 0, 1) for dx in (-1, 0, 1)]
+    ring = [(x, y) for y in (-1, 0, 1, 2) for x in (-1, 0, 1, 2) if not (0 <= x <= 1 and 0 <= y <= 1)]
+    g += [(x - 0.5, y - 0.5, 0.5) for x, y in ring]
+    g += [(2.0 * (0.5 - x), 2.0 * (0.5 - y), 2.0) for x, y in ring]
+    return g
+
+
+@pytest.mark.parametrize("K", [8, 16])
+def test_near_tables_match_oracle_integrals(V, K):
+    """Every near-field configuration (9 colleague, 12 coarse, 12 fine): table
+    rows against the oracle's singular/near-singular leaf integrals."""
+    wl = W.disk_sincos(level=3, K=K)
+    plan = make_plan(V, wl)
+    T = V.vpx_plan_near_tables(plan)
+    L = O.lib()
+    t, _ = O.gauss_legendre(K)
+    tt = np.ascontiguousarray(t)
+    rng = np.random.Generator(np.random.PCG64(K))
+    worst = 0.0
+    for c, (tx, ty, sg) in enumerate(_near_geometry()):
+        for i in sorted(set([0, K - 1, K * K - 1, K * K - K] + list(rng.choice(K * K, 4, replace=False)))):
+            x, y = tx + sg * t[i % K], ty + sg * t[i // K]
+            I = np.zeros(K * K)
+            L.orc_leaf_basis_integrals(K, O._ptr(tt), 0.0, 0.0, 1.0, x, y, O._ptr(I))
+            e = np.max(np.abs(T[c, i] - I))
+            worst = max(worst, e)
+            assert e <= 1e-13, (c, i, e)
+    print("near tables K=%d worst abs err %.2e" % (K, worst))
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_potential_parity_fp64(V, name):
+    wl = CASES[name]()
+    plan = make_plan(V, wl)
+    tree = O.build_tree(wl.domain, wl.opts, wl.sources[0])
+    vals = seeded_leaf_values(tree, 1, 2211)
+    nodes = O.all_leaf_nodes(tree)
+    sub = _subset(len(nodes), 3000, 7)
+    want = O.volume_potential(tree, vals, nodes[sub])[:, 0]
+    fe = torch.tensor(vals[:, 0, :].ravel(), dtype=torch.float64, device="cuda")
+    v = torch.empty(len(nodes), dtype=torch.float64, device="cuda")
+    nb = plan.sizes()[3]
+    vb = torch.empty(nb, dtype=torch.float64, device="cuda")
+    V.vpx_potential(plan, fe, v, vb)
+    assert V.vpx_sync_status(plan) == 0
+    got = v.cpu().numpy()[sub]
+    err = np.max(np.abs(got - want)) / np.max(np.abs(want))
+    assert err <= 1e-12, err
+    if nb:
+        # boundary values: interpolation of the leaf values (checked against
+        # the oracle's interpolation of the GPU leaf values' exact counterpart)
+        vleaf = v.cpu().numpy().reshape(tree.n_leaves, tree.K * tree.K, 1)
+        wantb = O.interpolate_at(tree, vleaf, O.boundary_nodes(wl.domain))[:, 0]
+        assert np.max(np.abs(vb.cpu().numpy() - wantb)) <= 1e-13 * np.max(np.abs(want))
+
+
+def test_potential_parity_ragged_multi_rhs(V):
+    """Several right-hand sides, columns with a padded leading dimension."""
+    wl = CASES["starfish_k8_adaptive"]()
+    nrhs = 3
+    plan = make_plan(V, wl, max_rhs=nrhs)
+    tree = O.build_tree(wl.domain, wl.opts, wl.sources[0])
+    vals = seeded_leaf_values(tree, nrhs, 99)
+    nodes = O.all_leaf_nodes(tree)
+    sub = _subset(len(nodes), 600, 3)
+    want = O.volume_potential(tree, vals, nodes[sub])
+    nt = len(nodes)
+    fe = torch.zeros((nrhs, nt + 5), dtype=torch.float64, device="cuda")
+    for r in range(nrhs):
+        fe[r, :nt] = torch.tensor(vals[:, r, :].ravel())
+    v = torch.full((nrhs, nt + 3), 7.0, dtype=torch.float64, device="cuda")
+    V.vpx_potential(plan, fe[:, :nt], v[:, :nt])
+    assert V.vpx_sync_status(plan) == 0
+    got = v.cpu().numpy()[:, :nt][:, sub].T
+    err = np.max(np.abs(got - want)) / np.max(np.abs(want))
+    assert err <= 1e-12, err
+    assert np.all(v.cpu().numpy()[:, nt:] == 7.0)   # padding untouched
+
+
+def _extension_bounds(tree, dom, meta):
+    """Per leaf: 64 * eps * kappa * max|f_I| scale factor (kappa from the oracle)."""
+    owned = {}
+    for j, o in enumerate(tree.owner):
+        if o >= 0:
+            owned.setdefault(o, []).append(j)
+    kappa = {}
+    for i in tree.cut_leaves():
+        off, n, masks = meta[i]
+        tg = np.concatenate([O.leaf_nodes(tree.leaves[i], tree.t)] +
+                            [O.leaf_nodes(tree.leaves[j], tree.t) for j in owned.get(i, [])])
+        M, _ = O.extend_cut_leaf(tree.leaves[i], tree.K, tree.t, masks, np.eye(n), tg)
+        k = np.abs(M).sum(axis=1).max()
+        kappa[i] = k
+        for j in owned.get(i, []):
+            kappa[j] = k
+    return kappa
+
+
+@pytest.mark.parametrize("name", ["disk_l3_k8", "disk_l4_k8", "disk_l3_k16", "starfish_k8_adaptive"])
+def test_extension_parity(V, name):
+    wl = CASES[name]()
+    plan = make_plan(V, wl)
+    tree = O.build_tree(wl.domain, wl.opts, wl.sources[0])
+    pts, meta = O.stencil_points(tree, wl.domain)
+    f = wl.sources[0](pts)
+    want, _ = O.leaf_values(tree, wl.domain, f[:, None], meta)
+    fs = torch.tensor(wl.sources[0](plan.stencil_points()), dtype=torch.float64, device="cuda")
+    fe = torch.empty(plan.sizes()[1], dtype=torch.float64, device="cuda")
+    V.vpx_extend(plan, fs, fe)
+    assert V.vpx_sync_status(plan) == 0
+    got = fe.cpu().numpy().reshape(tree.n_leaves, -1)
+    kappa = _extension_bounds(tree, wl.domain, meta)
+    fmax = np.max(np.abs(f))
+    for i in range(tree.n_leaves):
+        if tree.cls[i] == O.REGULAR:
+            # the same data up to the last-bit differences of the two sides' node coordinates
+            assert np.max(np.abs(got[i] - want[i, 0])) <= 1e-14 * fmax
+        elif tree.cls[i] == O.EXTERIOR and tree.owner[i] < 0:
+            assert np.all(got[i] == 0.0)
+        else:
+            tol = 64 * EPS * max(kappa[i], 1.0) * fmax
+            assert np.max(np.abs(got[i] - want[i, 0])) <= tol, (i, kappa[i])
+
+
+def test_execute_parity_end_to_end_disk(V):
+    """Uniform disk, level 4, K = 8: all 16,384 leaf nodes and 256 boundary nodes."""
+    wl = W.disk_sincos(level=4, K=8)
+    plan = make_plan(V, wl)
+    ref = O.solve(wl)
+    fs = torch.tensor(wl.sources[0](plan.stencil_points()), dtype=torch.float64, device="cuda")
+    _, nt, ns, nb = plan.sizes()
+    v = torch.empty(nt, dtype=torch.float64, device="cuda")
+    vb = torch.empty(nb, dtype=torch.float64, device="cuda")
+    V.vpx_execute(plan, fs, v, vb)
+    assert V.vpx_sync_status(plan) == 0
+    want, wantb = ref.v_leaf[:, 0], ref.v_bdry[:, 0]
+    pts, meta = O.stencil_points(ref.tree, wl.domain)
+    kappa = _extension_bounds(ref.tree, wl.domain, meta)
+    # the potential of a perturbation delta on a leaf of side s is bounded by
+    # |delta| * s^2 * (|log s| + 2) / (2 pi); sum over extended leaves
+    ext_bound = 0.0
+    fmax = np.max(np.abs(ref.f_stencil))
+    for i, k in kappa.items():
+        s = 2.0 ** -ref.tree.leaves[i][0]
+        ext_bound += 64 * EPS * k * fmax * s * s * (abs(math.log(s)) + 2) / (2 * math.pi)
+    scale = np.max(np.abs(want))
+    tol = 1e-12 * scale + ext_bound
+    err = np.max(np.abs(v.cpu().numpy() - want))
+    errb = np.max(np.abs(vb.cpu().numpy() - wantb))
+    print("end-to-end disk: err %.3e errb %.3e tol %.3e (rel %.3e)" % (err, errb, tol, err / scale))
+    assert err <= tol and errb <= tol
+
+
+def test_execute_host_matches_device(V):
+    wl = W.disk_sincos(level=3, K=8)
+    plan = make_plan(V, wl)
+    f = wl.sources[0](plan.stencil_points())
+    vh, bh = V.vpx_execute_host(plan, f)
+    fs = torch.tensor(f, dtype=torch.float64, device="cuda")
+    _, nt, ns, nb = plan.sizes()
+    v = torch.empty(nt, dtype=torch.float64, device="cuda")
+    vb = torch.empty(nb, dtype=torch.float64, device="cuda")
+    V.vpx_execute(plan, fs, v, vb)
+    assert V.vpx_sync_status(plan) == 0
+    assert np.max(np.abs(vh[0] - v.cpu().numpy())) <= 1e-14 * np.max(np.abs(vh))
+    assert np.max(np.abs(bh[0] - vb.cpu().numpy())) <= 1e-14 * np.max(np.abs(vh))
+
+
+def test_nan_input_is_reported(V):
+    """Fault injection on the host: a NaN in f must come back as VPX_ERR_NAN."""
+    wl = W.disk_sincos(level=3, K=8)
+    plan = make_plan(V, wl)
+    f = wl.sources[0](plan.stencil_points())
+    f[5] = np.nan
+    fs = torch.tensor(f, dtype=torch.float64, device="cuda")
+    v = torch.empty(plan.sizes()[1], dtype=torch.float64, device="cuda")
+    V.vpx_execute(plan, fs, v)
+    assert V.vpx_sync_status(plan) == -8
+    f[5] = 0.0
+    V.vpx_execute(plan, torch.tensor(f, dtype=torch.float64, device="cuda"), v)
+    assert V.vpx_sync_status(plan) == 0
+
+
+def test_full_size_adaptive_sampled(V):
+    """Adaptive starfish, K = 16, full size: sampled leaf nodes against the
+    oracle's direct quadrature of the oracle's own extended source."""
+    wl = W.starfish_gaussian(K=16)
+    plan = make_plan(V, wl, p=50)
+    tree = O.build_tree(wl.domain, wl.opts, wl.sources[0])
+    pts, meta = O.stencil_points(tree, wl.domain)
+    vals, _ = O.leaf_values(tree, wl.domain, wl.sources[0](pts)[:, None], meta)
+    nodes = O.all_leaf_nodes(tree)
+    rng = np.random.Generator(np.random.PCG64(2213))
+    # sample near the source, near the boundary and uniformly
+    r = np.hypot(nodes[:, 0] - 0.1, nodes[:, 1] - 0.05)
+    sub = np.unique(np.concatenate([rng.choice(len(nodes), 150, replace=False),
+                                    np.argsort(r)[:50]]))
+    want = O.volume_potential(tree, vals, nodes[sub])[:, 0]
+    fs = torch.tensor(wl.sources[0](plan.stencil_points()), dtype=torch.float64, device="cuda")
+    v = torch.empty(len(nodes), dtype=torch.float64, device="cuda")
+    V.vpx_execute(plan, fs, v)
+    assert V.vpx_sync_status(plan) == 0
+    err = np.max(np.abs(v.cpu().numpy()[sub] - want)) / np.max(np.abs(want))
+    print("starfish full size sampled rel err %.3e" % err)
+    assert err <= 1e-12, err

@@ -1,0 +1,148 @@
+"""CPU-side checks of the library: the shared object loads and exports every
+function declared in include/vpx.h; the host tree (Section 4 rules) equals the
+oracle's tree; the interaction lists (the routine the device kernel runs,
+here executed on the host) count every (target leaf, source leaf) pair
+exactly once across near, list i, list i+ and list i- (Fig. tree_levels)."""
+import os
+import re
+from collections import defaultdict
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import oracle as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def V():
+    import __graft_entry__ as g
+    g.build_library()
+    from paper_2211_14537_gb300 import vpx
+    return vpx
+
+
+def test_library_exports_every_declared_symbol(V):
+    hdr = open(os.path.join(ROOT, "include", "vpx.h")).read()
+    names = set(re.findall(r"^(?:int|void|const char \*)\s*\*?\s*(vpx_\w+)\s*\(", hdr, flags=re.M))
+    assert len(names) >= 20
+    L = V.load_library()
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(V.EXPORTED) == names
+
+
+def _plan(V, wl, host_only=True):
+    o = V.vpx_default_options(K=wl.opts.K, min_level=wl.opts.min_level, max_level=wl.opts.max_level,
+                              refine_tol=wl.opts.refine_tol, f_scale=wl.opts.f_scale)
+    return V.vpx_plan_create(o, wl.domain, wl.sources[0], host_only=host_only)
+
+
+WORKLOADS = {
+    "disk_l4": lambda: W.disk_sincos(level=4),
+    "disk_l3_k16": lambda: W.disk_sincos(level=3, K=16),
+    "starfish_k8": lambda: W.starfish_gaussian(K=8, tol=1e-8, max_level=8),
+    "lshape_small": lambda: W.lshape_expsin(K=8, base_level=4, max_level=8, corner_levels=5),
+}
+
+
+@pytest.mark.parametrize("name", list(WORKLOADS))
+def test_tree_matches_oracle_exactly(V, name):
+    wl = WORKLOADS[name]()
+    plan = _plan(V, wl)
+    L = plan.leaves()
+    tr = O.build_tree(wl.domain, wl.opts, wl.sources[0])
+    assert [tuple(x) for x in zip(L["level"], L["ix"], L["iy"])] == tr.leaves
+    assert list(L["cls"]) == tr.cls
+    assert list(L["owner"]) == tr.owner
+    sp = plan.stencil_points()
+    so, _ = O.stencil_points(tr, wl.domain)
+    assert sp.shape == so.shape and np.max(np.abs(sp - so)) < 1e-15
+    ln = plan.leaf_nodes()
+    assert np.max(np.abs(ln - O.all_leaf_nodes(tr))) < 1e-15
+    bn = plan.boundary_nodes()
+    assert np.max(np.abs(bn - O.boundary_nodes(wl.domain))) < 1e-15
+
+
+def test_plan_rejects_bad_options(V):
+    o = V.vpx_default_options(K=7)
+    with pytest.raises(V.VpxError) as e:
+        V.vpx_plan_create(o, W.WholeBoxDomain(), lambda xy: 0 * xy[:, 0], host_only=True)
+    assert e.value.code == -1
+    o = V.vpx_default_options(K=8, min_level=2, max_level=2)
+    with pytest.raises(V.VpxError) as e:   # disk cut leaves touch the edge of D at level 2
+        V.vpx_plan_create(o, W.disk_sincos(level=2).domain, lambda xy: 0 * xy[:, 0], host_only=True)
+    assert e.value.code == -5
+
+
+def test_callback_failure_is_reported(V):
+    o = V.vpx_default_options(K=8, min_level=2, max_level=6, refine_tol=1e-8)
+
+    def bad(xy):
+        raise ValueError("boom")
+    with pytest.raises(V.VpxError) as e:
+        V.vpx_plan_create(o, W.WholeBoxDomain(), bad, host_only=True)
+    assert e.value.code == -9
+
+
+@pytest.mark.parametrize("name", list(WORKLOADS))
+def test_lists_cover_every_pair_exactly_once(V, name):
+    wl = WORKLOADS[name]()
+    plan = _plan(V, wl)
+    Ls = plan.lists()
+    lv = plan.leaves()
+    nl = len(lv["level"])
+    nz = (lv["cls"] != 2) | (lv["owner"] >= 0)
+    blev, bix, biy, bleaf = Ls["box_level"], Ls["box_ix"], Ls["box_iy"], Ls["box_leaf"]
+    nb = len(blev)
+    key = {(int(blev[b]), int(bix[b]), int(biy[b])): b for b in range(nb)}
+    parent = np.full(nb, -1)
+    for b in range(nb):
+        if blev[b] > 0:
+            parent[b] = key[(blev[b] - 1, bix[b] >> 1, biy[b] >> 1)]
+    desc = defaultdict(list)          # box -> descendant leaves
+    leaf_box = np.zeros(nl, dtype=int)
+    for b in range(nb):
+        if bleaf[b] >= 0:
+            leaf_box[bleaf[b]] = b
+            a = b
+            while a >= 0:
+                desc[a].append(bleaf[b])
+                a = parent[a]
+    near, vl, xl, wlst = Ls["near"], Ls["vlist"], Ls["xlist"], Ls["wlist"]
+    for t in range(nl):
+        cnt = np.zeros(nl, dtype=int)
+        for s in near[t]:
+            if s >= 0:
+                cnt[s] += 1
+        for s in wlst[t]:
+            if s >= 0:
+                cnt[desc[s]] += 1
+        a = leaf_box[t]
+        while a >= 0:
+            for s in vl[a]:
+                if s >= 0:
+                    cnt[desc[s]] += 1
+            for s in xl[a]:
+                if s >= 0:
+                    cnt[s] += 1
+            a = parent[a]
+        assert np.all(cnt[nz] == 1), (name, t, np.nonzero(cnt[nz] != 1)[0][:10])
+        assert np.all(cnt[~nz] <= 1)   # zero leaves only ever appear inside a listed box
+    # near configurations are geometrically right: colleague slots are same-level offsets
+    for t in range(nl):
+        for c in range(9):
+            s = near[t, c]
+            if s >= 0:
+                dx, dy = c % 3 - 1, c // 3 - 1
+                assert (lv["level"][s], lv["ix"][s], lv["iy"][s]) == (lv["level"][t], lv["ix"][t] + dx, lv["iy"][t] + dy)
+        for c in range(9, 21):
+            s = near[t, c]
+            if s >= 0:
+                assert lv["level"][s] == lv["level"][t] - 1
+        for c in range(21, 33):
+            s = near[t, c]
+            if s >= 0:
+                assert lv["level"][s] == lv["level"][t] + 1
