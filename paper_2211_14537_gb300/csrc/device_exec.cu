@@ -159,9 +159,8 @@ __global__ void k_l2m(int KK, int P, const int32_t *nz_leaves, const int32_t *le
     const double h = 0.5 * box_side_d(leaf_level[leaf]);
     double *m = mpole + rhs * ldm + (int64_t)leaf_box[leaf] * 2 * P;
     for (int row = threadIdx.x; row < 2 * P; row += blockDim.x) {
-        const double *q = l2m + (size_t)row * KK;
         double s = 0.0;
-        for (int j = 0; j < KK; ++j) s += q[j] * sf[j];
+        for (int j = 0; j < KK; ++j) s += l2m[(size_t)j * 2 * P + row] * sf[j];
         m[row] = h * h * s;
     }
 }
@@ -181,9 +180,10 @@ __global__ void k_m2m(int first, int count, int P, const int32_t *child0, const 
             const int ch = c0 + c;
             if (!box_nz[ch]) continue;
             const double *a = mp + (int64_t)ch * 2 * P;
-            const double *M = m2m + ((size_t)c * P + l) * P * 2;
+            const double *M = m2m + (size_t)c * P * P * 2;
             for (int k = 0; k <= l; ++k) {
-                double mr = M[2 * k], mi = M[2 * k + 1], ar = a[2 * k], ai = a[2 * k + 1];
+                double mr = M[((size_t)k * P + l) * 2], mi = M[((size_t)k * P + l) * 2 + 1];
+                double ar = a[2 * k], ai = a[2 * k + 1];
                 sr += mr * ar - mi * ai;
                 si += mr * ai + mi * ar;
             }
@@ -284,11 +284,11 @@ __global__ void k_m2l(M2LArgs a) {
             __syncthreads();
             if (l < P) {
                 const double H = 0.5 * box_side_d(a.leaf_level[src]);
-                const double *S = a.s2l + (((size_t)s * P + l) * a.KK) * 2;
+                const double *S = a.s2l + (size_t)s * a.KK * P * 2;
                 double vr = 0.0, vi = 0.0;
                 for (int j = 0; j < a.KK; ++j) {
-                    vr += S[2 * j] * sf[j];
-                    vi += S[2 * j + 1] * sf[j];
+                    vr += S[((size_t)j * P + l) * 2] * sf[j];
+                    vi += S[((size_t)j * P + l) * 2 + 1] * sf[j];
                 }
                 if (l == 0) {
                     double w = 0.0;
@@ -320,9 +320,10 @@ __global__ void k_l2l(int first, int count, int P, const int32_t *box_parent, co
     const double *pl = lo + (int64_t)par * 2 * P;
     for (int m = threadIdx.x; m < P; m += blockDim.x) {
         double sr = lo[(int64_t)b * 2 * P + 2 * m], si = lo[(int64_t)b * 2 * P + 2 * m + 1];
-        const double *M = l2l + ((size_t)c * P + m) * P * 2;
+        const double *M = l2l + (size_t)c * P * P * 2;
         for (int l = m; l < P; ++l) {
-            double mr = M[2 * l], mi = M[2 * l + 1], ar = pl[2 * l], ai = pl[2 * l + 1];
+            double mr = M[((size_t)l * P + m) * 2], mi = M[((size_t)l * P + m) * 2 + 1];
+            double ar = pl[2 * l], ai = pl[2 * l + 1];
             sr += mr * ar - mi * ai;
             si += mr * ai + mi * ar;
         }
@@ -357,14 +358,17 @@ __global__ void k_leaf_far(FarArgs a) {
     const double *mp = a.mpole + rhs * a.ldm;
     const int lev = a.box_level[box];
     for (int q = threadIdx.x; q < 2 * P; q += blockDim.x) sl[q] = (lev >= 2) ? lo[q] : 0.0;
+    __shared__ double s_nl[kNearConfigs];
+    if (threadIdx.x < kNearConfigs) {
+        int src = a.near[(size_t)leaf * kNearConfigs + threadIdx.x];
+        double v = 0.0;
+        if (src >= 0) v = log(0.5 * box_side_d(a.leaf_level[src])) * mp[(int64_t)a.leaf_box[src] * 2 * P];
+        s_nl[threadIdx.x] = v;
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
         double s = 0.0;
-        for (int c = 0; c < kNearConfigs; ++c) {
-            int src = a.near[(size_t)leaf * kNearConfigs + c];
-            if (src < 0) continue;
-            double h = 0.5 * box_side_d(a.leaf_level[src]);
-            s += log(h) * mp[(int64_t)a.leaf_box[src] * 2 * P];
-        }
+        for (int c = 0; c < kNearConfigs; ++c) s += s_nl[c];
         snl[0] = s;
     }
     __syncthreads();
@@ -373,8 +377,7 @@ __global__ void k_leaf_far(FarArgs a) {
     double val = 0.0, zx = 0.0, zy = 0.0;
     const int i = threadIdx.x;
     if (i < KK) {
-        const double *E = a.l2t + (size_t)i * 2 * P;
-        for (int q = 0; q < 2 * P; ++q) val += E[q] * sl[q];
+        for (int q = 0; q < 2 * P; ++q) val += a.l2t[(size_t)q * KK + i] * sl[q];
         val += snl[0];
         zx = cx + 0.5 * sT * a.tnodes[i % K];
         zy = cy + 0.5 * sT * a.tnodes[i / K];

@@ -266,7 +266,7 @@ __global__ void __launch_bounds__(K * K) k_s2l_tables(int P, TableRules R, const
         ar += wy * accr;
         ai += wy * acci;
     }
-    size_t o = (((size_t)cfg * P + l) * KK + j) * 2;
+    size_t o = (((size_t)cfg * KK + j) * P + l) * 2;   // [config][j][l]: l fastest
     out[o] = ar;
     out[o + 1] = ai;
 }
@@ -315,8 +315,8 @@ static void host_tables(vpx_plan *p, std::vector<double> &l2m, std::vector<doubl
     gauss_legendre(nq, g, gw);
     std::vector<double> L((size_t)nq * K);
     for (int i = 0; i < nq; ++i) lagrange_eval(t, bw, g[i], &L[(size_t)i * K]);
-    l2m.assign((size_t)2 * P * KK, 0.0);
-    for (int j = 0; j < KK; ++j) l2m[j] = w2[j];
+    l2m.assign((size_t)2 * P * KK, 0.0);   // [j][2P]: row index fastest
+    for (int j = 0; j < KK; ++j) l2m[(size_t)j * 2 * P] = w2[j];
     std::vector<cd> acc((size_t)P * KK, cd(0, 0));
     for (int i = 0; i < nq; ++i)
         for (int i2 = 0; i2 < nq; ++i2) {
@@ -332,8 +332,8 @@ static void host_tables(vpx_plan *p, std::vector<double> &l2m, std::vector<doubl
         }
     for (int k = 1; k < P; ++k)
         for (int j = 0; j < KK; ++j) {
-            l2m[(size_t)(2 * k) * KK + j] = acc[(size_t)k * KK + j].real();
-            l2m[(size_t)(2 * k + 1) * KK + j] = acc[(size_t)k * KK + j].imag();
+            l2m[(size_t)j * 2 * P + 2 * k] = acc[(size_t)k * KK + j].real();
+            l2m[(size_t)j * 2 * P + 2 * k + 1] = acc[(size_t)k * KK + j].imag();
         }
     // L2T: xi = (t_a + i t_b)/2 ; row i: (Re xi^l, -Im xi^l)
     l2t.assign((size_t)KK * 2 * P, 0.0);
@@ -341,8 +341,8 @@ static void host_tables(vpx_plan *p, std::vector<double> &l2m, std::vector<doubl
         for (int a = 0; a < K; ++a) {
             cd xi(0.5 * t[a], 0.5 * t[b]), pw(1.0, 0.0);
             for (int l = 0; l < P; ++l) {
-                l2t[(size_t)(b * K + a) * 2 * P + 2 * l] = pw.real();
-                l2t[(size_t)(b * K + a) * 2 * P + 2 * l + 1] = -pw.imag();
+                l2t[(size_t)(2 * l) * KK + b * K + a] = pw.real();         // [2P][KK]: node fastest
+                l2t[(size_t)(2 * l + 1) * KK + b * K + a] = -pw.imag();
                 pw *= xi;
             }
         }
@@ -355,8 +355,9 @@ static void host_tables(vpx_plan *p, std::vector<double> &l2m, std::vector<doubl
         std::vector<cd> dp(2 * P + 1);
         dp[0] = 1.0;
         for (int i = 1; i <= 2 * P; ++i) dp[i] = dp[i - 1] * delta;
-        auto M = [&](int l, int k) -> double * { return &m2m[(((size_t)c * P + l) * P + k) * 2]; };
-        auto LL = [&](int m, int l) -> double * { return &l2l[(((size_t)c * P + m) * P + l) * 2]; };
+        // output index fastest: m2m[c][k][l] (l = output), l2l[c][l][m] (m = output)
+        auto M = [&](int l, int k) -> double * { return &m2m[(((size_t)c * P + k) * P + l) * 2]; };
+        auto LL = [&](int m, int l) -> double * { return &l2l[(((size_t)c * P + l) * P + m) * 2]; };
         M(0, 0)[0] = 1.0;
         for (int l = 1; l < P; ++l) {
             cd v = -dp[l] / double(l);

@@ -30,12 +30,12 @@ struct DevTree {
 struct DevTables {
     double *near = nullptr;     // [33][KK][KK]
     double *w2 = nullptr;       // [KK] tensor Gauss-Legendre weights on [-1,1]^2
-    double *l2m = nullptr;      // [2P][KK]  rows 2k, 2k+1 = Re, Im of Q_k
-    double *l2t = nullptr;      // [KK][2P]  (Re xi^l, -Im xi^l) interleaved
-    double *m2m = nullptr;      // [4][P][P] complex (interleaved re, im)
-    double *l2l = nullptr;      // [4][P][P] complex
+    double *l2m = nullptr;      // [KK][2P]  entries 2k, 2k+1 = Re, Im of Q_k[j]
+    double *l2t = nullptr;      // [2P][KK]  rows 2l, 2l+1 = Re xi^l, -Im xi^l
+    double *m2m = nullptr;      // [4][k][l] complex (interleaved re, im), output index l fastest
+    double *l2l = nullptr;      // [4][l][m] complex, output index m fastest
     double *m2l_b = nullptr;    // [P][P]    real, B'_{lk} = C(l+k-1,k-1) / 2^(l+k)
-    double *s2l = nullptr;      // [20][P][KK] complex
+    double *s2l = nullptr;      // [20][KK][P] complex
     double *bary = nullptr;     // [K] barycentric weights of the leaf nodes
     double *tnodes = nullptr;   // [K] leaf nodes on [-1,1]
 };

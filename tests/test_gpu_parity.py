@@ -151,19 +151,47 @@ def test_potential_parity_ragged_multi_rhs(V):
     assert np.all(v.cpu().numpy()[:, nt:] == 7.0)   # padding untouched
 
 
+def _chebyshev_stage_norm(b, K, targets):
+    """Infinity norm of the map Kbar x Kbar grid values -> truncated Chebyshev
+    expansion (m + n < Kbar) evaluated at the targets (Section 4.1)."""
+    from numpy.polynomial import chebyshev as C
+    q, Kbar, NG = O.stencil_params(K)
+    cx, cy = O.box_center(b)
+    r = 1.5 * O.box_side(b[0])
+    Tinv = np.linalg.inv(C.chebvander(O.chebyshev1_nodes(Kbar), Kbar - 1))
+    z = (targets - np.array([cx, cy])) / r
+    TX, TY = C.chebvander(z[:, 0], Kbar - 1), C.chebvander(z[:, 1], Kbar - 1)
+    mm, nn = np.meshgrid(np.arange(Kbar), np.arange(Kbar), indexing="ij")
+    keep = (mm + nn) < Kbar
+    # target value = sum_{ax,by} W[t, ax, by] F[ax, by]
+    W = np.einsum("tm,ma,tn,nb,mn->tab", TX, Tinv, TY, Tinv, keep.astype(float))
+    return max(np.abs(W).reshape(len(targets), -1).sum(axis=1).max(), 1.0)
+
+
 def _extension_bounds(tree, dom, meta):
-    """Per leaf: 64 * eps * kappa * max|f_I| scale factor (kappa from the oracle)."""
+    """Per extended leaf: the forward-error factor of the two-stage
+    extrapolation, kappa = Lambda * ||A_E|| * ||A_I^+|| (infinity norms), with
+    Lambda the norm of the Chebyshev stage (grid values -> target values);
+    both implementations are backward stable, so they differ by
+    O(eps * kappa * max|f_I|).  Computed from the oracle's own operators."""
     owned = {}
     for j, o in enumerate(tree.owner):
         if o >= 0:
             owned.setdefault(o, []).append(j)
+    K = tree.K
+    q, Kbar, NG = O.stencil_params(K)
+    A = O.universal_matrix(K)
     kappa = {}
     for i in tree.cut_leaves():
         off, n, masks = meta[i]
+        AI = A[np.concatenate(masks)]
+        AE = A[K * K:K * K + Kbar * Kbar][~masks[1]]
+        nAE = np.abs(AE).sum(axis=1).max() if len(AE) else 0.0
+        nP = np.abs(O.pseudo_inverse(AI)).sum(axis=1).max()
         tg = np.concatenate([O.leaf_nodes(tree.leaves[i], tree.t)] +
                             [O.leaf_nodes(tree.leaves[j], tree.t) for j in owned.get(i, [])])
-        M, _ = O.extend_cut_leaf(tree.leaves[i], tree.K, tree.t, masks, np.eye(n), tg)
-        k = np.abs(M).sum(axis=1).max()
+        lam = _chebyshev_stage_norm(tree.leaves[i], K, tg)
+        k = lam * (1.0 + nAE * nP)
         kappa[i] = k
         for j in owned.get(i, []):
             kappa[j] = k
