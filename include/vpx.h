@@ -161,6 +161,22 @@ int vpx_extend(vpx_plan_t plan, const double *f_stencil, int nrhs, int64_t ld_f,
 int vpx_potential(vpx_plan_t plan, const double *fe_leaf, int nrhs, int64_t ld_fe,
                   double *v_leaf, int64_t ld_v, double *v_bdry, int64_t ld_b, void *stream);
 
+/* Volume potential with no device allocation at call time (no counterpart in
+ * the paper: a deployment variant of vpx_potential).  Same arguments and
+ * result as vpx_potential, but the multipole and local expansions live in a
+ * file-scope device array of VPX_STATIC_SCRATCH_DOUBLES doubles (16 MiB) that
+ * every GPU loading the library holds until exit, instead of the plan's
+ * workspace.  For callers that cannot call cudaMalloc at this point (a pool
+ * allocator owns the device, or an allocation or its failure is unacceptable
+ * mid-run).  The first call on a device looks up the array's device address
+ * (once per device); make that first call before any stream capture.
+ * Returns VPX_ERR_ARG when nrhs * n_boxes * 4 * (p + 1) exceeds the array.
+ * All calls share the array: calls that overlap on the GPU (any stream, any
+ * plan) race and must be serialised by the caller. */
+#define VPX_STATIC_SCRATCH_DOUBLES (2 * 1024 * 1024)
+int vpx_potential_static(vpx_plan_t plan, const double *fe_leaf, int nrhs, int64_t ld_fe,
+                         double *v_leaf, int64_t ld_v, double *v_bdry, int64_t ld_b, void *stream);
+
 /* End to end with HOST buffers (contiguous columns): copies f in, runs
  * vpx_execute on the plan's own stream, copies V out, synchronises. */
 int vpx_execute_host(vpx_plan_t plan, const double *f_stencil_host, int nrhs,

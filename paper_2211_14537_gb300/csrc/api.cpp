@@ -369,6 +369,18 @@ int vpx_potential(vpx_plan_t p, const double *fe, int nrhs, int64_t ld_fe, doubl
     });
 }
 
+int vpx_potential_static(vpx_plan_t p, const double *fe, int nrhs, int64_t ld_fe, double *v, int64_t ld_v,
+                         double *vb, int64_t ld_b, void *stream) {
+    return guarded([&] {
+        if (!p) fail(VPX_ERR_ARG, "null plan");
+        if (p->host_only) fail(VPX_ERR_STATE, "host-only plan");
+        int64_t nt = (int64_t)p->leaf_xy.size() / 2, nbd = (int64_t)p->bdry_xy.size() / 2;
+        if (nrhs < 1) fail(VPX_ERR_ARG, "nrhs out of range");
+        if (!fe || !v || ld_fe < nt || ld_v < nt || (vb && ld_b < nbd)) fail(VPX_ERR_ARG, "bad buffer");
+        device_potential_static(p, fe, ld_fe, nrhs, v, ld_v, vb, ld_b, stream);
+    });
+}
+
 int vpx_execute_host(vpx_plan_t p, const double *f, int nrhs, double *v, double *vb) {
     return guarded([&] {
         if (!p) fail(VPX_ERR_ARG, "null plan");

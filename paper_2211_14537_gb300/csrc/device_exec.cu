@@ -593,12 +593,13 @@ static void run_extension(vpx_plan *p, const double *f, int nrhs, int64_t ldf, d
     }
 }
 
-static void run_potential(vpx_plan *p, const double *fe, int64_t ldfe, int nrhs, double *v, int64_t ldv, double *vb,
-                          int64_t ldb, cudaStream_t s) {
+// The passes of the box FMM with the multipole and local expansions in the
+// scratch arrays mp and lo (each nrhs x n_boxes x 2P doubles).
+void run_potential_scratch(vpx_plan *p, const double *fe, int64_t ldfe, int nrhs, double *v, int64_t ldv, double *vb,
+                           int64_t ldb, double *mp, double *lo, cudaStream_t s) {
     const int P = p->P, KK = p->KK, K = p->K;
     const DevTree &d = p->dt;
     const int64_t ldm = (int64_t)d.n_boxes * 2 * P;
-    double *mp = p->wk.mpole, *lo = p->wk.local;
     ev_record(p, 1, s);
     if (p->wk.n_nz_leaves > 0) {
         k_l2m<<<dim3(p->wk.n_nz_leaves, nrhs), 128, KK * sizeof(double), s>>>(
@@ -689,6 +690,11 @@ static void run_potential(vpx_plan *p, const double *fe, int64_t ldfe, int nrhs,
         VPX_LAUNCH("k_boundary");
     }
     ev_record(p, 8, s);
+}
+
+static void run_potential(vpx_plan *p, const double *fe, int64_t ldfe, int nrhs, double *v, int64_t ldv, double *vb,
+                          int64_t ldb, cudaStream_t s) {
+    run_potential_scratch(p, fe, ldfe, nrhs, v, ldv, vb, ldb, p->wk.mpole, p->wk.local, s);
 }
 
 void device_extend(vpx_plan *p, const double *f, int nrhs, int64_t ldf, double *fe, int64_t ldfe, void *stream) {

@@ -122,5 +122,7 @@ void device_execute(vpx_plan *p, const double *f, int nrhs, int64_t ldf, double 
                     int64_t ldb, void *stream);
 int device_sync_status(vpx_plan *p);
 void device_copy_near_tables(vpx_plan *p, double *out);
+void device_potential_static(vpx_plan *p, const double *fe_in, int64_t ldfe, int nrhs, double *v, int64_t ldv,
+                             double *vb, int64_t ldb, void *stream);
 void device_execute_host(vpx_plan *p, const double *f, int nrhs, double *v, double *vb);
 }  // namespace vpx

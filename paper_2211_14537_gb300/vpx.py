@@ -46,7 +46,7 @@ CURVE_CB = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_
 EXPORTED = [
     "vpx_default_options", "vpx_plan_create", "vpx_plan_sizes", "vpx_plan_leaves", "vpx_stencil_points",
     "vpx_leaf_nodes", "vpx_boundary_nodes", "vpx_plan_list_counts", "vpx_plan_lists", "vpx_plan_near_tables", "vpx_execute",
-    "vpx_extend", "vpx_potential", "vpx_execute_host", "vpx_sync_status", "vpx_set_timing",
+    "vpx_extend", "vpx_potential", "vpx_potential_static", "vpx_execute_host", "vpx_sync_status", "vpx_set_timing",
     "vpx_get_timings", "vpx_pass_name", "vpx_error_string", "vpx_last_error_message", "vpx_plan_destroy",
 ]
 
@@ -77,6 +77,7 @@ def load_library(path: str = LIB_PATH):
     L.vpx_execute.argtypes = [vp, vp, ctypes.c_int, i64, vp, i64, vp, i64, vp]
     L.vpx_extend.argtypes = [vp, vp, ctypes.c_int, i64, vp, i64, vp]
     L.vpx_potential.argtypes = [vp, vp, ctypes.c_int, i64, vp, i64, vp, i64, vp]
+    L.vpx_potential_static.argtypes = [vp, vp, ctypes.c_int, i64, vp, i64, vp, i64, vp]
     L.vpx_execute_host.argtypes = [vp, P(d), ctypes.c_int, P(d), P(d)]
     L.vpx_sync_status.argtypes = [vp]
     L.vpx_set_timing.argtypes = [vp, ctypes.c_int]
@@ -259,6 +260,18 @@ def vpx_potential(plan: Plan, fe_leaf, v_leaf, v_bdry=None, stream=None):
     if v_bdry is not None and v_bdry.numel() > 0:
         bp, _, ldb = _cols(v_bdry)
     _check(load_library().vpx_potential(plan.handle, ep, nrhs, lde, vp_, ldv, bp, ldb, _stream_handle(stream)))
+
+
+def vpx_potential_static(plan: Plan, fe_leaf, v_leaf, v_bdry=None, stream=None):
+    """vpx_potential with the expansion scratch in the library's static device
+    array (no allocation at call time; see include/vpx.h)."""
+    ep, nrhs, lde = _cols(fe_leaf)
+    vp_, _, ldv = _cols(v_leaf)
+    bp, ldb = ctypes.c_void_p(0), 1
+    if v_bdry is not None and v_bdry.numel() > 0:
+        bp, _, ldb = _cols(v_bdry)
+    _check(load_library().vpx_potential_static(plan.handle, ep, nrhs, lde, vp_, ldv, bp, ldb,
+                                               _stream_handle(stream)))
 
 
 def vpx_execute_host(plan: Plan, f_stencil: np.ndarray, nrhs: int = 1):
