@@ -289,98 +289,6 @@ static void near_geometry(std::vector<NearGeom> &g) {
         }
 }
 
-static std::vector<double> binomials(int n) {   // C[i][j], i,j <= n
-    std::vector<double> C((size_t)(n + 1) * (n + 1), 0.0);
-    for (int i = 0; i <= n; ++i) {
-        C[(size_t)i * (n + 1)] = 1.0;
-        for (int j = 1; j <= i; ++j)
-            C[(size_t)i * (n + 1) + j] = C[(size_t)(i - 1) * (n + 1) + j - 1] + (j <= i - 1 ? C[(size_t)(i - 1) * (n + 1) + j] : 0.0);
-    }
-    return C;
-}
-
-static void host_tables(vpx_plan *p, std::vector<double> &l2m, std::vector<double> &l2t, std::vector<double> &m2m,
-                        std::vector<double> &l2l, std::vector<double> &m2lb, std::vector<double> &w2) {
-    const int K = p->K, KK = p->KK, P = p->P;
-    typedef std::complex<double> cd;
-    std::vector<double> t, tw;
-    gauss_legendre(K, t, tw);
-    std::vector<double> bw = barycentric_weights(t);
-    w2.assign(KK, 0.0);
-    for (int b = 0; b < K; ++b)
-        for (int a = 0; a < K; ++a) w2[b * K + a] = tw[a] * tw[b];
-    // L2M: Q_k[j] = -(1/k) 2^-k int l_j(eta) eta^k, row 0 = weights
-    int nq = (K + P) / 2 + 2;
-    std::vector<double> g, gw;
-    gauss_legendre(nq, g, gw);
-    std::vector<double> L((size_t)nq * K);
-    for (int i = 0; i < nq; ++i) lagrange_eval(t, bw, g[i], &L[(size_t)i * K]);
-    l2m.assign((size_t)2 * P * KK, 0.0);   // [j][2P]: row index fastest
-    for (int j = 0; j < KK; ++j) l2m[(size_t)j * 2 * P] = w2[j];
-    std::vector<cd> acc((size_t)P * KK, cd(0, 0));
-    for (int i = 0; i < nq; ++i)
-        for (int i2 = 0; i2 < nq; ++i2) {
-            cd eta(g[i], g[i2]);
-            double w = gw[i] * gw[i2];
-            cd pw(1.0, 0.0);
-            for (int k = 1; k < P; ++k) {
-                pw *= eta * 0.5;
-                cd c = -pw * (w / k);
-                for (int b = 0; b < K; ++b)
-                    for (int a = 0; a < K; ++a) acc[(size_t)k * KK + b * K + a] += c * (L[(size_t)i * K + a] * L[(size_t)i2 * K + b]);
-            }
-        }
-    for (int k = 1; k < P; ++k)
-        for (int j = 0; j < KK; ++j) {
-            l2m[(size_t)j * 2 * P + 2 * k] = acc[(size_t)k * KK + j].real();
-            l2m[(size_t)j * 2 * P + 2 * k + 1] = acc[(size_t)k * KK + j].imag();
-        }
-    // L2T: xi = (t_a + i t_b)/2 ; row i: (Re xi^l, -Im xi^l)
-    l2t.assign((size_t)KK * 2 * P, 0.0);
-    for (int b = 0; b < K; ++b)
-        for (int a = 0; a < K; ++a) {
-            cd xi(0.5 * t[a], 0.5 * t[b]), pw(1.0, 0.0);
-            for (int l = 0; l < P; ++l) {
-                l2t[(size_t)(2 * l) * KK + b * K + a] = pw.real();         // [2P][KK]: node fastest
-                l2t[(size_t)(2 * l + 1) * KK + b * K + a] = -pw.imag();
-                pw *= xi;
-            }
-        }
-    std::vector<double> C = binomials(2 * P + 2);
-    auto Cb = [&](int n, int k) { return (k < 0 || k > n) ? 0.0 : C[(size_t)n * (2 * P + 3) + k]; };
-    m2m.assign((size_t)4 * P * P * 2, 0.0);
-    l2l.assign((size_t)4 * P * P * 2, 0.0);
-    for (int c = 0; c < 4; ++c) {
-        cd delta(((c & 1) - 0.5) * 0.5, ((c >> 1) - 0.5) * 0.5);
-        std::vector<cd> dp(2 * P + 1);
-        dp[0] = 1.0;
-        for (int i = 1; i <= 2 * P; ++i) dp[i] = dp[i - 1] * delta;
-        // output index fastest: m2m[c][k][l] (l = output), l2l[c][l][m] (m = output)
-        auto M = [&](int l, int k) -> double * { return &m2m[(((size_t)c * P + k) * P + l) * 2]; };
-        auto LL = [&](int m, int l) -> double * { return &l2l[(((size_t)c * P + l) * P + m) * 2]; };
-        M(0, 0)[0] = 1.0;
-        for (int l = 1; l < P; ++l) {
-            cd v = -dp[l] / double(l);
-            M(l, 0)[0] = v.real();
-            M(l, 0)[1] = v.imag();
-            for (int k = 1; k <= l; ++k) {
-                cd u = dp[l - k] * (std::ldexp(1.0, -k) * Cb(l - 1, k - 1));
-                M(l, k)[0] = u.real();
-                M(l, k)[1] = u.imag();
-            }
-        }
-        for (int m = 0; m < P; ++m)
-            for (int l = m; l < P; ++l) {
-                cd u = dp[l - m] * (std::ldexp(1.0, -m) * Cb(l, m));
-                LL(m, l)[0] = u.real();
-                LL(m, l)[1] = u.imag();
-            }
-    }
-    m2lb.assign((size_t)P * P, 0.0);
-    for (int l = 0; l < P; ++l)
-        for (int k = 1; k < P; ++k) m2lb[(size_t)l * P + k] = Cb(l + k - 1, k - 1) * std::ldexp(1.0, -(l + k));
-}
-
 static void rules(int K, TableRules &R) {
     std::vector<double> t, tw, g, gw, rl, rlw;
     gauss_legendre(K, t, tw);
@@ -460,13 +368,10 @@ void setup_tables(vpx_plan *p) {
     dev_free(dqw);
     dev_free(droff);
     dev_free(drects);
-    std::vector<double> l2m, l2t, m2m, l2l, m2lb, w2;
-    host_tables(p, l2m, l2t, m2m, l2l, m2lb, w2);
-    p->tab.l2m = dev_upload(l2m);
-    p->tab.l2t = dev_upload(l2t);
-    p->tab.m2m = dev_upload(m2m);
-    p->tab.l2l = dev_upload(l2l);
-    p->tab.m2l_b = dev_upload(m2lb);
+    std::vector<double> tq, tw, w2(KK);
+    gauss_legendre(K, tq, tw);
+    for (int b = 0; b < K; ++b)
+        for (int a = 0; a < K; ++a) w2[b * K + a] = tw[a] * tw[b];
     p->tab.w2 = dev_upload(w2);
     std::vector<double> t(R.t, R.t + K), bw(R.bary, R.bary + K);
     p->tab.tnodes = dev_upload(t);
@@ -476,6 +381,8 @@ void setup_tables(vpx_plan *p) {
 // --------------------------------------------------------------- uploads
 
 void setup_near_pairs(vpx_plan *p);   // device_exec.cu
+void setup_passes(vpx_plan *p);       // fmm_passes.cu
+void free_passes(vpx_plan *p);
 
 void device_setup(vpx_plan *p) {
     int ndev = 0;
@@ -574,6 +481,7 @@ void device_setup(vpx_plan *p) {
     w.status = dev_alloc<int>(1);
     VPX_CUDA(cudaMemset(w.status, 0, sizeof(int)));
     setup_near_pairs(p);
+    setup_passes(p);
     VPX_CUDA(cudaDeviceSynchronize());
 }
 
@@ -588,16 +496,16 @@ void device_free(vpx_plan *p) {
     dev_free(d.leaf_box); dev_free(d.leaf_cls); dev_free(d.leaf_nz);
     dev_free(d.near); dev_free(d.vlist); dev_free(d.xlist); dev_free(d.wlist);
     DevTables &t = p->tab;
-    dev_free(t.near); dev_free(t.w2); dev_free(t.l2m); dev_free(t.l2t); dev_free(t.m2m); dev_free(t.l2l);
-    dev_free(t.m2l_b); dev_free(t.s2l); dev_free(t.bary); dev_free(t.tnodes);
+    dev_free(t.near); dev_free(t.w2); dev_free(t.s2l); dev_free(t.bary); dev_free(t.tnodes);
     DevExt &x = p->ext;
     dev_free(x.cut_leaf); dev_free(x.n_interior); dev_free(x.grid_src); dev_free(x.node_src);
     dev_free(x.stencil_off); dev_free(x.pinv_off); dev_free(x.reg_leaf_off); dev_free(x.owned_off);
     dev_free(x.owned); dev_free(x.pinv); dev_free(x.A_grid); dev_free(x.cheb_inv);
-    dev_free(x.leaf_level); dev_free(x.leaf_ix); dev_free(x.leaf_iy); dev_free(x.owned_flag_dev); dev_free(x.m2l_pw);
+    dev_free(x.leaf_level); dev_free(x.leaf_ix); dev_free(x.leaf_iy); dev_free(x.owned_flag_dev);
+    free_passes(p);
     DevWork &w = p->wk;
-    dev_free(w.fe); dev_free(w.mpole); dev_free(w.local); dev_free(w.near_tgt); dev_free(w.near_src);
-    dev_free(w.near_tiles); dev_free(w.nz_leaves); dev_free(w.bdry_leaf); dev_free(w.bdry_w); dev_free(w.status);
+    dev_free(w.fe); dev_free(w.mpole); dev_free(w.local);
+    dev_free(w.nz_leaves); dev_free(w.bdry_leaf); dev_free(w.bdry_w); dev_free(w.status);
     dev_free(w.f_tmp); dev_free(w.v_tmp); dev_free(w.b_tmp);
     for (auto &ev : p->events)
         if (ev) {

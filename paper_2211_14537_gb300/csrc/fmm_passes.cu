@@ -1,0 +1,412 @@
+// fmm_passes.cu -- the box FMM (Section 4.1 with the lists of Fig. tree_levels)
+// as a sequence of grouped table GEMMs (gemm.cuh), in the FP64 form or the
+// exact-slice mixed form.
+//
+// Expansions of a box of side L and centre c (complex arithmetic written in
+// real 2(p+1)-vectors, entries 2l, 2l+1 = Re, Im):
+//   multipole  Phi(z) = a_0 log(z - c) + sum_{k>=1} at_k (L / (z - c))^k
+//   local      Psi(z) = sum_{l>=0} bt_l ((z - c) / L)^l
+// In these scaled variables every translation operator is independent of the
+// level except for one real term a_0 log(L) (M2L, list i- evaluation) or
+// a_0 log(H) (S2L, near field), which two small kernels add.
+//
+// Passes of one right-hand side (all pairs of a pass in one launch):
+//   L2M (1 table)   leaf values        -> multipole of the leaf box (store)
+//   M2M (4 tables)  child multipoles   -> parent multipole, level by level
+//   M2L (40 tables) list-i multipoles  -> local             (all levels at once)
+//   S2L (20 tables) list-i+ leaf values -> local
+//   L2L (4 tables)  parent local       -> child local, level by level
+//   L2T (1 table)   local              -> V at the K^2 nodes
+//   M2T (20 tables) list-i- multipoles -> V at the K^2 nodes
+//   near (33 tables) leaf values       -> V (tables of Section 4, Remark)
+#include <cmath>
+#include <complex>
+
+#include "dev_common.cuh"
+#include "gemm.cuh"
+#include "lists.h"
+
+namespace vpx {
+
+typedef std::complex<double> cd;
+
+// ------------------------------------------------------- constant terms
+
+// local[b][0] += log(L_b) sum_{list i} a_0(src) + sum_{list i+} log(H_src) a_0(src)
+__global__ void k_local_const(int first, int count, int P, const int32_t *vlist, const int32_t *xlist,
+                              const int32_t *box_level, const int32_t *leaf_level, const int32_t *leaf_box,
+                              const double *mpole, double *local, int64_t ldm) {
+    const int bi = blockIdx.x * blockDim.x + threadIdx.x, rhs = blockIdx.y;
+    if (bi >= count) return;
+    const int b = first + bi;
+    const double *mp = mpole + rhs * ldm;
+    double sv = 0.0, sx = 0.0;
+    for (int s = 0; s < kVSlots; ++s) {
+        int src = vlist[(size_t)b * kVSlots + s];
+        if (src >= 0) sv += mp[(int64_t)src * 2 * P];
+    }
+    for (int s = 0; s < kXSlots; ++s) {
+        int src = xlist[(size_t)b * kXSlots + s];
+        if (src >= 0) sx += log(0.5 * ldexp(1.0, -leaf_level[src])) * mp[(int64_t)leaf_box[src] * 2 * P];
+    }
+    local[rhs * ldm + (int64_t)b * 2 * P] += log(ldexp(1.0, -box_level[b])) * sv + sx;
+}
+
+// V[t][i] += (1/2pi) [sum_near log(h_s) a_0(s) + sum_{list i-} log(L_W) a_0(W)], all i
+__global__ void k_leaf_const(int KK, int P, const int32_t *near, const int32_t *wlist, const int32_t *leaf_level,
+                             const int32_t *leaf_box, const int32_t *box_level, const double *mpole, int64_t ldm,
+                             double *v, int64_t ldv) {
+    const int t = blockIdx.x, rhs = blockIdx.y;
+    __shared__ double s_c;
+    if (threadIdx.x < 32) {
+        const double *mp = mpole + rhs * ldm;
+        double c = 0.0;
+        for (int s = threadIdx.x; s < kNearConfigs + kWSlots; s += 32) {
+            if (s < kNearConfigs) {
+                int src = near[(size_t)t * kNearConfigs + s];
+                if (src >= 0) c += log(0.5 * ldexp(1.0, -leaf_level[src])) * mp[(int64_t)leaf_box[src] * 2 * P];
+            } else {
+                int wb = wlist[(size_t)t * kWSlots + (s - kNearConfigs)];
+                if (wb >= 0) c += log(ldexp(1.0, -box_level[wb])) * mp[(int64_t)wb * 2 * P];
+            }
+        }
+        for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+        if (threadIdx.x == 0) s_c = c * 0.15915494309189533576888376337251;
+    }
+    __syncthreads();
+    double *o = v + rhs * ldv + (int64_t)t * KK;
+    for (int i = threadIdx.x; i < KK; i += blockDim.x) o[i] += s_c;
+}
+
+__global__ void k_nan_check(const double *v, int64_t ldv, int64_t n, int *status) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && !isfinite(v[blockIdx.y * ldv + i])) set_status(status, VPX_ERR_NAN);
+}
+
+// ------------------------------------------------------------ tables
+
+static void real_form(const std::vector<cd> &C, int P, std::vector<double> &out, size_t off) {
+    // C[row l][col k] complex (P x P) -> real 2P x 2P acting on (Re, Im) interleaved vectors
+    for (int l = 0; l < P; ++l)
+        for (int k = 0; k < P; ++k) {
+            cd c = C[(size_t)l * P + k];
+            out[off + (size_t)(2 * l) * 2 * P + 2 * k] = c.real();
+            out[off + (size_t)(2 * l) * 2 * P + 2 * k + 1] = -c.imag();
+            out[off + (size_t)(2 * l + 1) * 2 * P + 2 * k] = c.imag();
+            out[off + (size_t)(2 * l + 1) * 2 * P + 2 * k + 1] = c.real();
+        }
+}
+
+static std::vector<double> binom_table(int n) {
+    std::vector<double> C((size_t)(n + 1) * (n + 1), 0.0);
+    for (int i = 0; i <= n; ++i) {
+        C[(size_t)i * (n + 1)] = 1.0;
+        for (int j = 1; j <= i; ++j)
+            C[(size_t)i * (n + 1) + j] = C[(size_t)(i - 1) * (n + 1) + j - 1] + (j < i ? C[(size_t)(i - 1) * (n + 1) + j] : 0.0);
+    }
+    return C;
+}
+
+void fmm_tables_host(vpx_plan *p, std::vector<double> &l2m, std::vector<double> &l2t, std::vector<double> &m2m,
+                     std::vector<double> &l2l, std::vector<double> &m2l, std::vector<double> &m2t) {
+    const int K = p->K, KK = p->KK, P = p->P, P2 = 2 * P;
+    std::vector<double> t, tw;
+    gauss_legendre(K, t, tw);
+    std::vector<double> bw = barycentric_weights(t);
+    // L2M: row 0 = weights; rows 2k, 2k+1 = Re, Im of -(1/k) 2^-k int l_j eta^k
+    int nq = (K + P) / 2 + 2;
+    std::vector<double> g, gw;
+    gauss_legendre(nq, g, gw);
+    std::vector<double> L((size_t)nq * K);
+    for (int i = 0; i < nq; ++i) lagrange_eval(t, bw, g[i], &L[(size_t)i * K]);
+    l2m.assign((size_t)P2 * KK, 0.0);
+    for (int b = 0; b < K; ++b)
+        for (int a = 0; a < K; ++a) l2m[b * K + a] = tw[a] * tw[b];
+    std::vector<cd> acc((size_t)P * KK, cd(0, 0));
+    for (int i = 0; i < nq; ++i)
+        for (int i2 = 0; i2 < nq; ++i2) {
+            cd eta(g[i], g[i2]), pw(1.0, 0.0);
+            double w = gw[i] * gw[i2];
+            for (int k = 1; k < P; ++k) {
+                pw *= eta * 0.5;
+                cd c = -pw * (w / k);
+                for (int b = 0; b < K; ++b)
+                    for (int a = 0; a < K; ++a) acc[(size_t)k * KK + b * K + a] += c * (L[(size_t)i * K + a] * L[(size_t)i2 * K + b]);
+            }
+        }
+    for (int k = 1; k < P; ++k)
+        for (int j = 0; j < KK; ++j) {
+            l2m[(size_t)(2 * k) * KK + j] = acc[(size_t)k * KK + j].real();
+            l2m[(size_t)(2 * k + 1) * KK + j] = acc[(size_t)k * KK + j].imag();
+        }
+    // L2T: row i = target node: (Re xi^l, -Im xi^l), xi = (t_a + i t_b) / 2
+    l2t.assign((size_t)KK * P2, 0.0);
+    for (int b = 0; b < K; ++b)
+        for (int a = 0; a < K; ++a) {
+            cd xi(0.5 * t[a], 0.5 * t[b]), pw(1.0, 0.0);
+            for (int l = 0; l < P; ++l) {
+                l2t[(size_t)(b * K + a) * P2 + 2 * l] = pw.real();
+                l2t[(size_t)(b * K + a) * P2 + 2 * l + 1] = -pw.imag();
+                pw *= xi;
+            }
+        }
+    std::vector<double> C = binom_table(2 * P + 2);
+    auto Cb = [&](int n, int k) { return (k < 0 || k > n) ? 0.0 : C[(size_t)n * (2 * P + 3) + k]; };
+    // M2M / L2L: child position c, delta = child centre - parent centre in parent sides
+    m2m.assign((size_t)4 * P2 * P2, 0.0);
+    l2l.assign((size_t)4 * P2 * P2, 0.0);
+    for (int c = 0; c < 4; ++c) {
+        cd delta(((c & 1) - 0.5) * 0.5, ((c >> 1) - 0.5) * 0.5);
+        std::vector<cd> dp(2 * P + 1);
+        dp[0] = 1.0;
+        for (int i = 1; i <= 2 * P; ++i) dp[i] = dp[i - 1] * delta;
+        std::vector<cd> M((size_t)P * P, cd(0, 0)), LL((size_t)P * P, cd(0, 0));
+        M[0] = 1.0;
+        for (int l = 1; l < P; ++l) {
+            M[(size_t)l * P] = -dp[l] / double(l);
+            for (int k = 1; k <= l; ++k) M[(size_t)l * P + k] = dp[l - k] * (std::ldexp(1.0, -k) * Cb(l - 1, k - 1));
+        }
+        for (int m = 0; m < P; ++m)
+            for (int l = m; l < P; ++l) LL[(size_t)m * P + l] = dp[l - m] * (std::ldexp(1.0, -m) * Cb(l, m));
+        real_form(M, P, m2m, (size_t)c * P2 * P2);
+        real_form(LL, P, l2l, (size_t)c * P2 * P2);
+    }
+    // M2L per list-i offset t (source - target, in box sides); a_0 log L is added separately
+    m2l.assign((size_t)kVSlots * P2 * P2, 0.0);
+    int idx = 0;
+    for (int y = -3; y <= 3; ++y)
+        for (int x = -3; x <= 3; ++x) {
+            if (x >= -1 && x <= 1 && y >= -1 && y <= 1) continue;
+            cd tt(x, y), it = 1.0 / tt;
+            std::vector<cd> ip(2 * P + 1), mp(2 * P + 1);   // t^-n, (-t)^-n
+            ip[0] = mp[0] = 1.0;
+            for (int n = 1; n <= 2 * P; ++n) {
+                ip[n] = ip[n - 1] * it;
+                mp[n] = mp[n - 1] * (-it);
+            }
+            std::vector<cd> M((size_t)P * P, cd(0, 0));
+            M[0] = std::log(std::abs(tt));   // Re log(-t)
+            for (int k = 1; k < P; ++k) M[k] = mp[k];
+            for (int l = 1; l < P; ++l) {
+                M[(size_t)l * P] = -ip[l] / double(l);
+                for (int k = 1; k < P; ++k) M[(size_t)l * P + k] = ip[l] * mp[k] * Cb(l + k - 1, k - 1);
+            }
+            real_form(M, P, m2l, (size_t)idx * P2 * P2);
+            ++idx;
+        }
+    // M2T per list-i- position: zeta_i = (z_i - c_W) / L_W; row i: (log|zeta|, 0, Re zeta^-k, -Im zeta^-k)
+    m2t.assign((size_t)kWSlots * KK * P2, 0.0);
+    idx = 0;
+    for (int y = -2; y <= 3; ++y)
+        for (int x = -2; x <= 3; ++x) {
+            if (x >= -1 && x <= 2 && y >= -1 && y <= 2) continue;
+            for (int b = 0; b < K; ++b)
+                for (int a = 0; a < K; ++a) {
+                    cd zeta(1.0 + t[a] - (x + 0.5), 1.0 + t[b] - (y + 0.5));
+                    double *row = &m2t[((size_t)idx * KK + b * K + a) * P2];
+                    row[0] = std::log(std::abs(zeta));
+                    cd iz = 1.0 / zeta, pw = 1.0;
+                    for (int k = 1; k < P; ++k) {
+                        pw *= iz;
+                        row[2 * k] = pw.real();
+                        row[2 * k + 1] = -pw.imag();
+                    }
+                }
+            ++idx;
+        }
+}
+
+// ------------------------------------------------------------- setup
+
+void setup_passes(vpx_plan *p) {
+    const bool mixed = p->opt.precision == VPX_PREC_MIXED;
+    const int KK = p->KK, P = p->P, P2 = 2 * P, nl = (int)p->tree.leaves.size(), nb = (int)p->box_level.size();
+    std::vector<double> l2m, l2t, m2m, l2l, m2l, m2t;
+    fmm_tables_host(p, l2m, l2t, m2m, l2l, m2l, m2t);
+    std::vector<double> near((size_t)kNearConfigs * KK * KK);
+    VPX_CUDA(cudaMemcpy(near.data(), p->tab.near, near.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    std::vector<double> s2l_dev((size_t)kXSlots * KK * P * 2), s2l((size_t)kXSlots * P2 * KK);
+    VPX_CUDA(cudaMemcpy(s2l_dev.data(), p->tab.s2l, s2l_dev.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    for (int c = 0; c < kXSlots; ++c)   // device layout [c][j][l] complex -> [c][2P][KK]
+        for (int j = 0; j < KK; ++j)
+            for (int l = 0; l < P; ++l) {
+                s2l[((size_t)c * P2 + 2 * l) * KK + j] = s2l_dev[(((size_t)c * KK + j) * P + l) * 2];
+                s2l[((size_t)c * P2 + 2 * l + 1) * KK + j] = s2l_dev[(((size_t)c * KK + j) * P + l) * 2 + 1];
+            }
+    auto lvl_side = [](int l) { return std::ldexp(1.0, -l); };
+    std::vector<int32_t> leaf_box(nl);
+    for (int b = 0; b < nb; ++b)
+        if (p->box_leaf[b] >= 0) leaf_box[p->box_leaf[b]] = b;
+    FmmPasses &F = p->fmm;
+    typedef std::vector<std::pair<int, GPair>> Tagged;
+    // L2M
+    {
+        Tagged tg;
+        for (int i = 0; i < nl; ++i)
+            if (p->leaf_nz[i]) {
+                double h = 0.5 * lvl_side(p->tree.leaves[i].level);
+                tg.push_back({0, GPair{i, 0, (int64_t)leaf_box[i] * P2, h * h}});
+            }
+        gemm_pass_upload_tables(F.l2m, l2m, 1, P2, KK, mixed);
+        F.l2m.add = 0;
+        gemm_pass_set_pairs(F.l2m, tg);
+    }
+    // M2M per parent level, L2L per child level
+    for (int l = 0; l <= kMaxLevel; ++l) {
+        F.m2m[l] = GemmPass();
+        F.l2l[l] = GemmPass();
+    }
+    for (int l = 2; l + 1 < p->n_levels; ++l) {
+        Tagged tm, tl;
+        for (int b = p->level_start[l]; b < p->level_start[l + 1]; ++b) {
+            if (p->box_child0[b] < 0) continue;
+            for (int c = 0; c < 4; ++c) {
+                int ch = p->box_child0[b] + c;
+                if (p->box_nz[ch]) tm.push_back({c, GPair{ch, 0, (int64_t)b * P2, 1.0}});
+                tl.push_back({c, GPair{b, 0, (int64_t)ch * P2, 1.0}});
+            }
+        }
+        gemm_pass_upload_tables(F.m2m[l], m2m, 4, P2, P2, mixed);
+        gemm_pass_set_pairs(F.m2m[l], tm);
+        gemm_pass_upload_tables(F.l2l[l], l2l, 4, P2, P2, mixed);
+        gemm_pass_set_pairs(F.l2l[l], tl);
+    }
+    // M2L and S2L
+    {
+        Tagged tv, tx;
+        for (int b = p->level_start[std::min(2, p->n_levels)]; b < nb; ++b) {
+            for (int s = 0; s < kVSlots; ++s) {
+                int src = p->vlist[(size_t)b * kVSlots + s];
+                if (src >= 0) tv.push_back({s, GPair{src, 0, (int64_t)b * P2, 1.0}});
+            }
+            for (int s = 0; s < kXSlots; ++s) {
+                int src = p->xlist[(size_t)b * kXSlots + s];
+                if (src >= 0) {
+                    double H = 0.5 * lvl_side(p->tree.leaves[src].level);
+                    tx.push_back({s, GPair{src, 0, (int64_t)b * P2, H * H}});
+                }
+            }
+        }
+        gemm_pass_upload_tables(F.m2l, m2l, kVSlots, P2, P2, mixed);
+        gemm_pass_set_pairs(F.m2l, tv);
+        gemm_pass_upload_tables(F.s2l, s2l, kXSlots, P2, KK, mixed);
+        gemm_pass_set_pairs(F.s2l, tx);
+    }
+    // L2T, M2T, near
+    {
+        const double inv2pi = 0.15915494309189533576888376337251;
+        Tagged tt, tw, tn;
+        for (int i = 0; i < nl; ++i) {
+            if (p->tree.leaves[i].level >= 2) tt.push_back({0, GPair{leaf_box[i], 0, (int64_t)i * KK, inv2pi}});
+            for (int s = 0; s < kWSlots; ++s) {
+                int wb = p->wlist[(size_t)i * kWSlots + s];
+                if (wb >= 0) tw.push_back({s, GPair{wb, 0, (int64_t)i * KK, inv2pi}});
+            }
+            for (int c = 0; c < kNearConfigs; ++c) {
+                int src = p->near[(size_t)i * kNearConfigs + c];
+                if (src >= 0) {
+                    double h = 0.5 * lvl_side(p->tree.leaves[src].level);
+                    tn.push_back({c, GPair{src, 0, (int64_t)i * KK, h * h * inv2pi}});
+                }
+            }
+        }
+        gemm_pass_upload_tables(F.l2t, l2t, 1, KK, P2, mixed);
+        gemm_pass_set_pairs(F.l2t, tt);
+        gemm_pass_upload_tables(F.m2t, m2t, kWSlots, KK, P2, mixed);
+        gemm_pass_set_pairs(F.m2t, tw);
+        gemm_pass_upload_tables(F.near, near, kNearConfigs, KK, KK, mixed);
+        gemm_pass_set_pairs(F.near, tn);
+    }
+    if (mixed) {
+        const int kp_f = (KK + 31) / 32 * 32, kp_m = (P2 + 31) / 32 * 32;
+        F.fe_sl = dev_alloc<uint16_t>((size_t)p->opt.max_rhs * nl * kSlicesS * kp_f);
+        F.fe_ex = dev_alloc<int32_t>((size_t)p->opt.max_rhs * nl);
+        F.mp_sl = dev_alloc<uint16_t>((size_t)p->opt.max_rhs * nb * kSlicesS * kp_m);
+        F.mp_ex = dev_alloc<int32_t>((size_t)p->opt.max_rhs * nb);
+        F.lo_sl = dev_alloc<uint16_t>((size_t)p->opt.max_rhs * nb * kSlicesS * kp_m);
+        F.lo_ex = dev_alloc<int32_t>((size_t)p->opt.max_rhs * nb);
+    }
+    VPX_CUDA(cudaDeviceSynchronize());
+}
+
+void free_passes(vpx_plan *p) {
+    FmmPasses &F = p->fmm;
+    gemm_pass_free(F.l2m);
+    gemm_pass_free(F.m2l);
+    gemm_pass_free(F.s2l);
+    gemm_pass_free(F.l2t);
+    gemm_pass_free(F.m2t);
+    gemm_pass_free(F.near);
+    for (int l = 0; l <= kMaxLevel; ++l) {
+        gemm_pass_free(F.m2m[l]);
+        gemm_pass_free(F.l2l[l]);
+    }
+    dev_free(F.fe_sl);
+    dev_free(F.fe_ex);
+    dev_free(F.mp_sl);
+    dev_free(F.mp_ex);
+    dev_free(F.lo_sl);
+    dev_free(F.lo_ex);
+}
+
+// ------------------------------------------------------------ execute
+
+void ev_record_pass(vpx_plan *p, int i, cudaStream_t s);
+
+void run_potential_passes(vpx_plan *p, const double *fe, int64_t ldfe, int nrhs, double *v, int64_t ldv, double *vb,
+                          int64_t ldb, double *mp, double *lo, cudaStream_t s) {
+    const bool mixed = p->opt.precision == VPX_PREC_MIXED;
+    const int P = p->P, P2 = 2 * P, KK = p->KK, K = p->K;
+    const DevTree &d = p->dt;
+    const int nb = d.n_boxes, nl = d.n_leaves;
+    const int64_t ldm = (int64_t)nb * P2;
+    const int kp_f = (KK + 31) / 32 * 32, kp_m = (P2 + 31) / 32 * 32;
+    FmmPasses &F = p->fmm;
+    VecSet vf{fe, ldfe, KK, F.fe_sl, F.fe_ex, nl};
+    VecSet vm{mp, ldm, P2, F.mp_sl, F.mp_ex, nb};
+    VecSet vl{lo, ldm, P2, F.lo_sl, F.lo_ex, nb};
+    ev_record_pass(p, 1, s);
+    VPX_CUDA(cudaMemsetAsync(mp, 0, sizeof(double) * ldm * nrhs, s));
+    VPX_CUDA(cudaMemsetAsync(lo, 0, sizeof(double) * ldm * nrhs, s));
+    VPX_CUDA(cudaMemset2DAsync(v, sizeof(double) * ldv, 0, sizeof(double) * (size_t)nl * KK, nrhs, s));
+    if (mixed) slice_vectors(vf, 0, nl, KK, kp_f, nrhs, s);
+    gemm_run(F.l2m, vf, mp, ldm, nrhs, mixed, s);
+    ev_record_pass(p, 2, s);
+    for (int l = d.n_levels - 1; l >= 2; --l) {
+        if (mixed) slice_vectors(vm, d.level_start[l], d.level_start[l + 1] - d.level_start[l], P2, kp_m, nrhs, s);
+        if (l - 1 >= 2) gemm_run(F.m2m[l - 1], vm, mp, ldm, nrhs, mixed, s);
+    }
+    ev_record_pass(p, 3, s);
+    gemm_run(F.m2l, vm, lo, ldm, nrhs, mixed, s);
+    gemm_run(F.s2l, vf, lo, ldm, nrhs, mixed, s);
+    {
+        int first = d.level_start[std::min(2, d.n_levels)], count = nb - first;
+        if (count > 0) {
+            k_local_const<<<dim3((count + 127) / 128, nrhs), 128, 0, s>>>(first, count, P, d.vlist, d.xlist, d.box_level,
+                                                                           p->ext.leaf_level, d.leaf_box, mp, lo, ldm);
+            VPX_LAUNCH("k_local_const");
+        }
+    }
+    ev_record_pass(p, 4, s);
+    for (int l = 2; l < d.n_levels; ++l) {
+        if (mixed) slice_vectors(vl, d.level_start[l], d.level_start[l + 1] - d.level_start[l], P2, kp_m, nrhs, s);
+        if (l + 1 < d.n_levels) gemm_run(F.l2l[l], vl, lo, ldm, nrhs, mixed, s);
+    }
+    ev_record_pass(p, 5, s);
+    gemm_run(F.l2t, vl, v, ldv, nrhs, mixed, s);
+    gemm_run(F.m2t, vm, v, ldv, nrhs, mixed, s);
+    k_leaf_const<<<dim3(nl, nrhs), 128, 0, s>>>(KK, P, d.near, d.wlist, p->ext.leaf_level, d.leaf_box, d.box_level, mp,
+                                                ldm, v, ldv);
+    VPX_LAUNCH("k_leaf_const");
+    ev_record_pass(p, 6, s);
+    gemm_run(F.near, vf, v, ldv, nrhs, mixed, s);
+    {
+        const int64_t n = (int64_t)nl * KK;
+        k_nan_check<<<dim3((unsigned)((n + 255) / 256), nrhs), 256, 0, s>>>(v, ldv, n, p->wk.status);
+        VPX_LAUNCH("k_nan_check");
+    }
+    ev_record_pass(p, 7, s);
+    (void)K;
+}
+
+}  // namespace vpx

@@ -1,0 +1,65 @@
+// gemm.cuh -- grouped "table x gathered vectors" GEMM, the one shape every
+// contraction of the hot path takes:
+//
+//   out[dst_p + i] (+)= scale_p * sum_k Tab_{t(p)}[i][k] * vec_{src_p}[k]
+//
+// for every pair p of a pass; pairs are grouped by table into tiles of at most
+// 64 pairs.  Near field (33 tables), L2M (1), M2M (4), M2L (40), S2L (20),
+// L2L (4), L2T (1) and M2T (20) are all passes of this form.  Two engines run
+// it: FP64 register tiles (the FP64 form) and exact bf16 slices on the tensor
+// cores with FP64 recombination (the mixed form, see gemm.cu).
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+namespace vpx {
+
+constexpr int kGemmTileN = 64;   // pairs per tile
+constexpr int kSlicesS = 5;      // bf16 slices per operand in the mixed form
+constexpr int kSliceBitsB = 7;   // bits per slice
+
+struct GPair {
+    int32_t src;      // source vector index
+    int32_t pad;
+    int64_t dst;      // output offset (elements) within one right-hand side
+    double scale;
+};
+
+struct GTile {
+    int32_t tab, first, count, pad;
+};
+
+// One pass on the device.
+struct GemmPass {
+    int M = 0, Kd = 0, Kpad = 0, Mpad = 0, ntab = 0;
+    int add = 1;                       // 1: atomic add into out, 0: store
+    const double *tab = nullptr;       // [ntab][M][Kd] FP64 (row-major)
+    const uint16_t *tslices = nullptr; // [ntab][S][Mpad][Kpad] bf16 bits (mixed form)
+    const int32_t *texpo = nullptr;    // [ntab][Mpad] row exponents (mixed form)
+    GPair *pairs = nullptr;
+    GTile *tiles = nullptr;
+    int n_pairs = 0, n_tiles = 0;
+    std::vector<GPair> h_pairs;        // host copy (setup)
+};
+
+// Host helpers
+void gemm_pass_set_pairs(GemmPass &g, std::vector<std::pair<int, GPair>> &tagged);   // (table, pair)
+void gemm_pass_upload_tables(GemmPass &g, const std::vector<double> &tab, int ntab, int M, int Kd, bool mixed);
+void gemm_pass_free(GemmPass &g);
+
+struct VecSet {                        // source vectors of a pass
+    const double *base = nullptr;      // vector v of rhs r at base + r*ld + v*stride
+    int64_t ld = 0;
+    int stride = 0;
+    uint16_t *slices = nullptr;        // mixed form: [rhs][nvec][S][Kpad]
+    int32_t *expo = nullptr;           // [rhs][nvec]
+    int nvec = 0;
+};
+
+// Launches (stream s): run a pass on nrhs right-hand sides.
+void gemm_run(const GemmPass &g, const VecSet &vs, double *out, int64_t ldo, int nrhs, bool mixed, void *s);
+// Slice vectors [first, first+count) of a set (mixed form), per rhs.
+void slice_vectors(const VecSet &vs, int first, int count, int Kd, int Kpad, int nrhs, void *s);
+
+}  // namespace vpx

@@ -4,6 +4,7 @@
 #include <cstdint>
 #include <vector>
 
+#include "gemm.cuh"
 #include "internal.h"
 
 struct vpx_plan;
@@ -30,11 +31,6 @@ struct DevTree {
 struct DevTables {
     double *near = nullptr;     // [33][KK][KK]
     double *w2 = nullptr;       // [KK] tensor Gauss-Legendre weights on [-1,1]^2
-    double *l2m = nullptr;      // [KK][2P]  entries 2k, 2k+1 = Re, Im of Q_k[j]
-    double *l2t = nullptr;      // [2P][KK]  rows 2l, 2l+1 = Re xi^l, -Im xi^l
-    double *m2m = nullptr;      // [4][k][l] complex (interleaved re, im), output index l fastest
-    double *l2l = nullptr;      // [4][l][m] complex, output index m fastest
-    double *m2l_b = nullptr;    // [P][P]    real, B'_{lk} = C(l+k-1,k-1) / 2^(l+k)
     double *s2l = nullptr;      // [20][KK][P] complex
     double *bary = nullptr;     // [K] barycentric weights of the leaf nodes
     double *tnodes = nullptr;   // [K] leaf nodes on [-1,1]
@@ -50,11 +46,6 @@ struct DevExt {
     double *cheb_inv = nullptr;   // [Kbar][Kbar]
     int32_t *leaf_level = nullptr, *leaf_ix = nullptr, *leaf_iy = nullptr;
     int32_t *owned_flag_dev = nullptr;   // [n_leaves] 1 if the leaf is in an extension list
-    double *m2l_pw = nullptr;            // [40][P] complex tau^-k per list-i offset
-};
-
-struct NearTile {                 // one CTA of the grouped near-field GEMM
-    int32_t config, first, count; // pairs [first, first+count) of that configuration
 };
 
 struct DevWork {
@@ -62,16 +53,20 @@ struct DevWork {
     double *fe = nullptr;         // [max_rhs][n_leaves][KK]
     double *mpole = nullptr;      // [max_rhs][n_boxes][2P]
     double *local = nullptr;      // [max_rhs][n_boxes][2P]
-    int32_t *near_tgt = nullptr, *near_src = nullptr;   // pairs sorted by configuration
-    NearTile *near_tiles = nullptr;
-    int n_near_tiles = 0;
-    int64_t n_near_pairs = 0;
     int32_t *nz_leaves = nullptr; // leaves with non-zero source
     int n_nz_leaves = 0;
     int32_t *bdry_leaf = nullptr; // [n_bdry]
     double *bdry_w = nullptr;     // [n_bdry][2K] Lagrange weights (x then y)
     int *status = nullptr;        // device status word
     double *f_tmp = nullptr, *v_tmp = nullptr, *b_tmp = nullptr;   // for vpx_execute_host
+};
+
+struct FmmPasses {                // every contraction of the box FMM as a grouped table GEMM
+    GemmPass l2m, m2l, s2l, l2t, m2t, near;
+    GemmPass m2m[kMaxLevel + 1];  // parents at level l
+    GemmPass l2l[kMaxLevel + 1];  // parents at level l
+    uint16_t *fe_sl = nullptr, *mp_sl = nullptr, *lo_sl = nullptr;   // exact bf16 slices (mixed form)
+    int32_t *fe_ex = nullptr, *mp_ex = nullptr, *lo_ex = nullptr;
 };
 
 }  // namespace vpx
@@ -103,6 +98,7 @@ struct vpx_plan {
     vpx::DevTables tab;
     vpx::DevExt ext;
     vpx::DevWork wk;
+    vpx::FmmPasses fmm;
     bool timing = false;
     void *events[VPX_N_PASSES + 1] = {nullptr};
     double pass_ms[VPX_N_PASSES] = {0};

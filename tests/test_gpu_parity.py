@@ -305,3 +305,43 @@ def test_full_size_adaptive_sampled(V):
     err = np.max(np.abs(v.cpu().numpy()[sub] - want)) / np.max(np.abs(want))
     print("starfish full size sampled rel err %.3e" % err)
     assert err <= 1e-12, err
+
+
+@pytest.mark.parametrize("name", ["disk_l3_k8", "disk_l3_k16", "starfish_k8_adaptive", "lshape_k8_adaptive"])
+def test_potential_parity_mixed(V, name):
+    """Mixed form (near field on the tensor cores with exact bf16 slices):
+    relative max-norm error <= 1e-9 against the FP64 oracle."""
+    wl = CASES[name]()
+    plan = make_plan(V, wl, precision=1)
+    tree = O.build_tree(wl.domain, wl.opts, wl.sources[0])
+    vals = seeded_leaf_values(tree, 1, 2212)
+    nodes = O.all_leaf_nodes(tree)
+    sub = _subset(len(nodes), 3000, 8)
+    want = O.volume_potential(tree, vals, nodes[sub])[:, 0]
+    fe = torch.tensor(vals[:, 0, :].ravel(), dtype=torch.float64, device="cuda")
+    v = torch.empty(len(nodes), dtype=torch.float64, device="cuda")
+    V.vpx_potential(plan, fe, v)
+    assert V.vpx_sync_status(plan) == 0
+    err = np.max(np.abs(v.cpu().numpy()[sub] - want)) / np.max(np.abs(want))
+    print("mixed %s rel err %.3e" % (name, err))
+    assert err <= 1e-9, err
+
+
+def test_mixed_full_size_sampled(V):
+    wl = W.starfish_gaussian(K=16)
+    plan = make_plan(V, wl, p=40, precision=1)
+    tree = O.build_tree(wl.domain, wl.opts, wl.sources[0])
+    pts, meta = O.stencil_points(tree, wl.domain)
+    vals, _ = O.leaf_values(tree, wl.domain, wl.sources[0](pts)[:, None], meta)
+    nodes = O.all_leaf_nodes(tree)
+    rng = np.random.Generator(np.random.PCG64(2215))
+    r = np.hypot(nodes[:, 0] - 0.1, nodes[:, 1] - 0.05)
+    sub = np.unique(np.concatenate([rng.choice(len(nodes), 150, replace=False), np.argsort(r)[:50]]))
+    want = O.volume_potential(tree, vals, nodes[sub])[:, 0]
+    fs = torch.tensor(wl.sources[0](plan.stencil_points()), dtype=torch.float64, device="cuda")
+    v = torch.empty(len(nodes), dtype=torch.float64, device="cuda")
+    V.vpx_execute(plan, fs, v)
+    assert V.vpx_sync_status(plan) == 0
+    err = np.max(np.abs(v.cpu().numpy()[sub] - want)) / np.max(np.abs(want))
+    print("mixed starfish full size sampled rel err %.3e" % err)
+    assert err <= 1e-9, err
