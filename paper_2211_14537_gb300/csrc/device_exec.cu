@@ -7,6 +7,7 @@
 //   V(x) = (1/2pi) Re Phi  (the complex log kernel; G = (1/2pi) log|x - y|).
 // Leaf values are the K x K Gauss-Legendre node values of f^e on each leaf.
 #include <cmath>
+#include <cstdlib>
 
 #include "dev_common.cuh"
 
@@ -165,6 +166,15 @@ __global__ void k_boundary(int nb, int K, const int32_t *bleaf, const double *bw
 
 // ------------------------------------------------------------ host side
 
+// Opt the extension kernel into the dynamic shared memory its largest cut leaf needs.
+static void prepare_extension(vpx_plan *p) {
+    const StencilInfo &st = p->st;
+    int maxI = 0;
+    for (int c = 0; c < (int)st.cut_leaf.size(); ++c) maxI = std::max(maxI, st.n_interior[c]);
+    size_t smem = sizeof(double) * ((size_t)maxI + st.NG + 3 * st.Kbar * st.Kbar + 3 * p->K * st.Kbar);
+    if (smem > 48 * 1024) VPX_CUDA(cudaFuncSetAttribute(k_extend, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+}
+
 // Per-plan index arrays of the execute path: non-zero leaves and the
 // extension-list membership flag of every leaf.
 void setup_near_pairs(vpx_plan *p) {
@@ -177,6 +187,7 @@ void setup_near_pairs(vpx_plan *p) {
     p->wk.nz_leaves = dev_upload(nz);
     p->wk.n_nz_leaves = (int)nz.size();
     p->ext.owned_flag_dev = dev_upload(of);
+    prepare_extension(p);
 }
 
 void ev_record(vpx_plan *p, int i, cudaStream_t s) {
@@ -225,7 +236,6 @@ static void run_extension(vpx_plan *p, const double *f, int nrhs, int64_t ldf, d
         int maxI = 0;
         for (int c = 0; c < p->ext.ncut; ++c) maxI = std::max(maxI, st.n_interior[c]);
         size_t smem = sizeof(double) * ((size_t)maxI + st.NG + 3 * st.Kbar * st.Kbar + 3 * p->K * st.Kbar);
-        if (smem > 48 * 1024) VPX_CUDA(cudaFuncSetAttribute(k_extend, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         k_extend<<<dim3(p->ext.ncut, nrhs), 256, smem, s>>>(a);
         VPX_LAUNCH("k_extend");
     }
@@ -267,14 +277,53 @@ void device_potential(vpx_plan *p, const double *fe, int64_t ldfe, int nrhs, dou
     run_potential(p, fe, ldfe, nrhs, v, ldv, vb, ldb, s);
 }
 
-void device_execute(vpx_plan *p, const double *f, int nrhs, int64_t ldf, double *v, int64_t ldv, double *vb,
-                    int64_t ldb, void *stream) {
-    cudaStream_t s = (cudaStream_t)stream;
-    p->last_stream = stream;
+static void execute_sequence(vpx_plan *p, const double *f, int nrhs, int64_t ldf, double *v, int64_t ldv, double *vb,
+                             int64_t ldb, cudaStream_t s) {
     const int64_t ldfe = (int64_t)p->dt.n_leaves * p->KK;
     ev_record(p, 0, s);
     run_extension(p, f, nrhs, ldf, p->wk.fe, ldfe, s);
     run_potential(p, p->wk.fe, ldfe, nrhs, v, ldv, vb, ldb, s);
+}
+
+// The whole sequence (about 35 launches) is captured into a CUDA graph on the
+// first call with a given set of buffers, strides and nrhs, and replayed on
+// later calls; calls on the legacy default stream run the launches directly.
+void device_execute(vpx_plan *p, const double *f, int nrhs, int64_t ldf, double *v, int64_t ldv, double *vb,
+                    int64_t ldb, void *stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    p->last_stream = stream;
+    static const bool no_graph = getenv("VPX_NO_GRAPH") != nullptr;
+    if (s == nullptr || no_graph || p->timing) {   // per-pass timing runs the launches directly
+        execute_sequence(p, f, nrhs, ldf, v, ldv, vb, ldb, s);
+        return;
+    }
+    const int64_t key[10] = {(int64_t)(uintptr_t)f, ldf, (int64_t)(uintptr_t)v, ldv, (int64_t)(uintptr_t)vb, ldb,
+                             nrhs, p->timing ? 1 : 0, (int64_t)(uintptr_t)s, 1};
+    bool hit = p->graph_exec != nullptr;
+    for (int i = 0; i < 10 && hit; ++i) hit = key[i] == p->graph_key[i];
+    if (!hit) {
+        if (p->graph_exec) {
+            cudaGraphExecDestroy((cudaGraphExec_t)p->graph_exec);
+            p->graph_exec = nullptr;
+        }
+        cudaGraph_t graph = nullptr;
+        VPX_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        try {
+            execute_sequence(p, f, nrhs, ldf, v, ldv, vb, ldb, s);
+        } catch (...) {
+            cudaStreamEndCapture(s, &graph);
+            if (graph) cudaGraphDestroy(graph);
+            throw;
+        }
+        VPX_CUDA(cudaStreamEndCapture(s, &graph));
+        cudaGraphExec_t exec = nullptr;
+        cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        VPX_CUDA(e);
+        p->graph_exec = exec;
+        for (int i = 0; i < 10; ++i) p->graph_key[i] = key[i];
+    }
+    VPX_CUDA(cudaGraphLaunch((cudaGraphExec_t)p->graph_exec, s));
 }
 
 int device_sync_status(vpx_plan *p) {
@@ -284,10 +333,12 @@ int device_sync_status(vpx_plan *p) {
         for (int i = 0; i < VPX_N_PASSES; ++i) {
             float ms = 0.f;
             if (p->events[i] && p->events[i + 1] &&
-                cudaEventElapsedTime(&ms, (cudaEvent_t)p->events[i], (cudaEvent_t)p->events[i + 1]) == cudaSuccess)
+                cudaEventElapsedTime(&ms, (cudaEvent_t)p->events[i], (cudaEvent_t)p->events[i + 1]) == cudaSuccess) {
                 p->pass_ms[i] = ms;
-            else
+            } else {
                 p->pass_ms[i] = 0.0;
+                (void)cudaGetLastError();   // an unrecorded pair is not an error of the plan
+            }
         }
     }
     int st = 0;

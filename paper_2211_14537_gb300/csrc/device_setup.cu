@@ -512,6 +512,10 @@ void device_free(vpx_plan *p) {
             cudaEventDestroy((cudaEvent_t)ev);
             ev = nullptr;
         }
+    if (p->graph_exec) {
+        cudaGraphExecDestroy((cudaGraphExec_t)p->graph_exec);
+        p->graph_exec = nullptr;
+    }
     if (p->stream) {
         cudaStreamDestroy((cudaStream_t)p->stream);
         p->stream = nullptr;

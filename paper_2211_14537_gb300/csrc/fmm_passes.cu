@@ -21,6 +21,7 @@
 //   near (33 tables) leaf values       -> V (tables of Section 4, Remark)
 #include <cmath>
 #include <complex>
+#include <cstdlib>
 
 #include "dev_common.cuh"
 #include "gemm.cuh"
@@ -318,6 +319,14 @@ void setup_passes(vpx_plan *p) {
         gemm_pass_set_pairs(F.near, tn);
     }
     if (mixed) {
+        // slices per pass: near field and far field separately (environment overrides for experiments)
+        const char *sn = getenv("VPX_SLICES_NEAR"), *sf = getenv("VPX_SLICES_FAR");
+        const int s_near = sn ? std::max(5, std::min(6, atoi(sn))) : 5;
+        const int s_far = sf ? std::max(5, std::min(6, atoi(sf))) : 6;
+        F.near.slices = s_near;
+        for (GemmPass *g : {&F.l2m, &F.m2l, &F.s2l, &F.l2t, &F.m2t}) g->slices = s_far;
+        for (int l = 0; l <= kMaxLevel; ++l) F.m2m[l].slices = F.l2l[l].slices = s_far;
+        gemm_prepare_device();
         const int kp_f = (KK + 31) / 32 * 32, kp_m = (P2 + 31) / 32 * 32;
         F.fe_sl = dev_alloc<uint16_t>((size_t)p->opt.max_rhs * nl * kSlicesS * kp_f);
         F.fe_ex = dev_alloc<int32_t>((size_t)p->opt.max_rhs * nl);

@@ -4,14 +4,14 @@
 // 16-deep k stages in shared memory.
 //
 // Mixed form (exact bf16 slices): each table row i is scaled by 2^-e_i and
-// split into S = 5 integer slices of 7 bits (|a_1| <= 128, |a_k| <= 64), each
+// split into S = 5 or 6 integer slices of 7 bits (|a_1| <= 128, |a_k| <= 64), each
 // source vector likewise with its own exponent.  A product of two slices is
 // an integer of at most 14 bits; for an inner dimension <= 256 the sum of all
 // products of the same order d = k + l stays below 2^24, so the tensor core's
 // fp32 accumulation of each order is exact.  The orders are combined in
 // double-float fp32 (exact 2^-7 steps, TwoSum), converted once to FP64 and
-// scaled by scale_p 2^{e_i + e_v - 14}.  Truncation error ~ 2^-35 relative to
-// max|row| max|vector|.  Operand tiles are staged with cp.async (16-byte
+// scaled by scale_p 2^{e_i + e_v - 14}.  Truncation error ~ 2^-7S relative to
+// max|row| max|vector| (order sums stay below 8 * 2^20 < 2^24 for S <= 6).  Operand tiles are staged with cp.async (16-byte
 // copies, two stages); products use mma.sync m16n8k16 bf16 -> fp32.
 #include <cuda_bf16.h>
 
@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(256) k_gemm_fp64(int M, int Kd, const double *
 
 constexpr int X_M = 64, X_N = 64, X_K = 32;
 constexpr int X_LD = X_K + 8;   // smem pitch (bf16): 80 bytes, 16-byte aligned rows, conflict-free fragments
-constexpr int X_STAGE = kSlicesS * (X_M + X_N) * X_LD;   // bf16 elements per stage
+constexpr int X_STAGE = kSlicesS * (X_M + X_N) * X_LD;   // bf16 elements per stage (room for 6 slices)
 
 __device__ inline void cp_async16(void *smem, const void *gmem, int bytes) {
     unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
@@ -115,7 +115,8 @@ struct SlicedArgs {
     int add;
 };
 
-// 256 threads = 8 warps: 4 along M (16 rows) x 2 along N (32 pairs).
+// 256 threads = 8 warps: 4 along M (16 rows) x 2 along N (32 pairs).  S slices used.
+template <int S>
 __global__ void __launch_bounds__(256) k_gemm_sliced(SlicedArgs a) {
     extern __shared__ __align__(16) uint16_t xs[];
     const GTile tile = a.tiles[blockIdx.x];
@@ -129,13 +130,13 @@ __global__ void __launch_bounds__(256) k_gemm_sliced(SlicedArgs a) {
     auto stage = [&](int buf, int k0) {
         uint16_t *As = xs + buf * X_STAGE;
         uint16_t *Bs = As + kSlicesS * X_M * X_LD;
-        for (int c = threadIdx.x; c < kSlicesS * X_M * 4; c += 256) {
+        for (int c = threadIdx.x; c < S * X_M * 4; c += 256) {
             int s = c / (X_M * 4), rem = c % (X_M * 4), r = rem >> 2, q = rem & 3;
             int gr = m0 + r;
             const uint16_t *src = T + ((size_t)s * a.Mpad + (gr < a.Mpad ? gr : 0)) * a.Kpad + k0 + q * 8;
             cp_async16(As + (s * X_M + r) * X_LD + q * 8, src, gr < a.Mpad ? 16 : 0);
         }
-        for (int c = threadIdx.x; c < kSlicesS * X_N * 4; c += 256) {
+        for (int c = threadIdx.x; c < S * X_N * 4; c += 256) {
             int s = c / (X_N * 4), rem = c % (X_N * 4), n = rem >> 2, q = rem & 3;
             bool ok = n < tile.count;
             int v = ok ? a.pairs[tile.first + n].src : 0;
@@ -144,9 +145,9 @@ __global__ void __launch_bounds__(256) k_gemm_sliced(SlicedArgs a) {
         }
         cp_async_commit();
     };
-    float acc[kSlicesS][4][4];
+    float acc[S][4][4];
 #pragma unroll
-    for (int d = 0; d < kSlicesS; ++d)
+    for (int d = 0; d < S; ++d)
 #pragma unroll
         for (int t = 0; t < 4; ++t)
 #pragma unroll
@@ -165,10 +166,10 @@ __global__ void __launch_bounds__(256) k_gemm_sliced(SlicedArgs a) {
         const uint16_t *Bs = As + kSlicesS * X_M * X_LD;
 #pragma unroll
         for (int kk = 0; kk < X_K; kk += 16) {
-            uint32_t af[kSlicesS][4];
+            uint32_t af[S][4];
             const int ar = wm * 16 + g;
 #pragma unroll
-            for (int s = 0; s < kSlicesS; ++s) {
+            for (int s = 0; s < S; ++s) {
                 const uint16_t *Ar = As + (s * X_M + ar) * X_LD + kk + tq * 2;
                 af[s][0] = *reinterpret_cast<const uint32_t *>(Ar);
                 af[s][1] = *reinterpret_cast<const uint32_t *>(Ar + 8 * X_LD);
@@ -179,14 +180,14 @@ __global__ void __launch_bounds__(256) k_gemm_sliced(SlicedArgs a) {
             for (int t = 0; t < 4; ++t) {
                 const int bn = wn * 32 + t * 8 + g;
 #pragma unroll
-                for (int l = 0; l < kSlicesS; ++l) {
+                for (int l = 0; l < S; ++l) {
                     const uint16_t *Br = Bs + (l * X_N + bn) * X_LD + kk + tq * 2;
                     uint32_t bf[2];
                     bf[0] = *reinterpret_cast<const uint32_t *>(Br);
                     bf[1] = *reinterpret_cast<const uint32_t *>(Br + 8);
 #pragma unroll
-                    for (int s = 0; s < kSlicesS; ++s)
-                        if (s + l < kSlicesS) mma16816(acc[s + l][t], af[s], bf);
+                    for (int s = 0; s < S; ++s)
+                        if (s + l < S) mma16816(acc[s + l][t], af[s], bf);
                 }
             }
         }
@@ -218,9 +219,9 @@ __global__ void __launch_bounds__(256) k_gemm_sliced(SlicedArgs a) {
 #pragma unroll
             for (int half = 0; half < 2; ++half) {
                 if (pdst[t][half] < 0) continue;
-                float hi = acc[kSlicesS - 1][t][rr * 2 + half], lo = 0.f;
+                float hi = acc[S - 1][t][rr * 2 + half], lo = 0.f;
 #pragma unroll
-                for (int d = kSlicesS - 2; d >= 0; --d) {
+                for (int d = S - 2; d >= 0; --d) {
                     hi *= 0x1p-7f;
                     lo *= 0x1p-7f;
                     const float b = acc[d][t][rr * 2 + half];
@@ -340,6 +341,13 @@ void gemm_pass_upload_tables(GemmPass &g, const std::vector<double> &tab, int nt
     g.texpo = dev_upload(ex);
 }
 
+// Opt the sliced engine into its dynamic shared memory (once per device, at setup).
+void gemm_prepare_device() {
+    const size_t smem = 2 * X_STAGE * sizeof(uint16_t);
+    VPX_CUDA(cudaFuncSetAttribute(k_gemm_sliced<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    VPX_CUDA(cudaFuncSetAttribute(k_gemm_sliced<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+}
+
 void gemm_pass_free(GemmPass &g) {
     dev_free(g.tab);
     dev_free(g.tslices);
@@ -373,13 +381,9 @@ void gemm_run(const GemmPass &g, const VecSet &vs, double *out, int64_t ldo, int
     a.ldo = ldo;
     a.add = g.add;
     const size_t smem = 2 * X_STAGE * sizeof(uint16_t);
-    static bool attr_set = false;
-    if (!attr_set) {
-        VPX_CUDA(cudaFuncSetAttribute(k_gemm_sliced, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr_set = true;
-    }
     dim3 grid(g.n_tiles, (g.M + X_M - 1) / X_M, nrhs);
-    k_gemm_sliced<<<grid, 256, smem, s>>>(a);
+    if (g.slices >= 6) k_gemm_sliced<6><<<grid, 256, smem, s>>>(a);
+    else k_gemm_sliced<5><<<grid, 256, smem, s>>>(a);
     VPX_LAUNCH("k_gemm_sliced");
 }
 

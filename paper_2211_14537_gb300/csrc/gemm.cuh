@@ -16,7 +16,7 @@
 namespace vpx {
 
 constexpr int kGemmTileN = 64;   // pairs per tile
-constexpr int kSlicesS = 5;      // bf16 slices per operand in the mixed form
+constexpr int kSlicesS = 6;      // bf16 slices stored per operand in the mixed form (a pass uses 5 or 6)
 constexpr int kSliceBitsB = 7;   // bits per slice
 
 struct GPair {
@@ -34,6 +34,7 @@ struct GTile {
 struct GemmPass {
     int M = 0, Kd = 0, Kpad = 0, Mpad = 0, ntab = 0;
     int add = 1;                       // 1: atomic add into out, 0: store
+    int slices = 5;                    // mixed form: slices used (5 or 6)
     const double *tab = nullptr;       // [ntab][M][Kd] FP64 (row-major)
     const uint16_t *tslices = nullptr; // [ntab][S][Mpad][Kpad] bf16 bits (mixed form)
     const int32_t *texpo = nullptr;    // [ntab][Mpad] row exponents (mixed form)
@@ -47,6 +48,7 @@ struct GemmPass {
 void gemm_pass_set_pairs(GemmPass &g, std::vector<std::pair<int, GPair>> &tagged);   // (table, pair)
 void gemm_pass_upload_tables(GemmPass &g, const std::vector<double> &tab, int ntab, int M, int Kd, bool mixed);
 void gemm_pass_free(GemmPass &g);
+void gemm_prepare_device();
 
 struct VecSet {                        // source vectors of a pass
     const double *base = nullptr;      // vector v of rhs r at base + r*ld + v*stride

@@ -101,6 +101,8 @@ struct vpx_plan {
     vpx::FmmPasses fmm;
     bool timing = false;
     void *events[VPX_N_PASSES + 1] = {nullptr};
+    void *graph_exec = nullptr;   // captured vpx_execute sequence (cudaGraphExec_t)
+    int64_t graph_key[10] = {0};
     double pass_ms[VPX_N_PASSES] = {0};
 };
 
