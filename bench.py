@@ -264,7 +264,9 @@ def main():
         bf16_flops = 15 * r["near_flops"]
         achieved = bf16_flops / (r["near_ms"] * 1e-3) / 1e12
         peak = 1918.1
-        roof = {"kernel": "k_gemm_sliced (near-field pass, exact bf16 slices on mma.sync)", "bound": "tensor",
+        kname = ("k_gemm_sliced (near-field pass, exact bf16 slices on mma.sync)" if os.environ.get("VPX_NO_TC")
+                 else "k_gemm_tc (near-field pass, exact bf16 slices on tcgen05, accumulators in TMEM)")
+        roof = {"kernel": kname, "bound": "tensor",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst)",
                 "fp64_equivalent_tflops": r["near_flops"] / (r["near_ms"] * 1e-3) / 1e12}

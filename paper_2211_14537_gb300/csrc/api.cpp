@@ -412,7 +412,7 @@ int vpx_get_timings(vpx_plan_t p, double *ms, int n) {
 
 const char *vpx_pass_name(int i) {
     static const char *names[VPX_N_PASSES] = {"extension", "l2m", "m2m", "m2l_s2l", "l2l",
-                                              "l2t_m2t",   "near", "boundary"};
+                                              "l2t_const", "near", "join_boundary"};
     return (i >= 0 && i < VPX_N_PASSES) ? names[i] : "";
 }
 

@@ -13,7 +13,6 @@
 
 namespace vpx {
 
-constexpr double kInv2Pi = 0.15915494309189533576888376337251;
 
 __device__ inline double box_side_d(int level) { return ldexp(1.0, -level); }
 
@@ -330,6 +329,7 @@ int device_sync_status(vpx_plan *p) {
     cudaStream_t s = (cudaStream_t)p->last_stream;
     VPX_CUDA(cudaStreamSynchronize(s));
     if (p->timing && p->events[0]) {
+        VPX_CUDA(cudaStreamSynchronize((cudaStream_t)p->aux_stream));
         for (int i = 0; i < VPX_N_PASSES; ++i) {
             float ms = 0.f;
             if (p->events[i] && p->events[i + 1] &&
@@ -340,6 +340,14 @@ int device_sync_status(vpx_plan *p) {
                 (void)cudaGetLastError();   // an unrecorded pair is not an error of the plan
             }
         }
+        // the near field runs on the auxiliary stream: its own pair of events
+        float ms = 0.f;
+        if (p->events[VPX_N_PASSES + 1] && p->events[VPX_N_PASSES + 2] &&
+            cudaEventElapsedTime(&ms, (cudaEvent_t)p->events[VPX_N_PASSES + 1],
+                                 (cudaEvent_t)p->events[VPX_N_PASSES + 2]) == cudaSuccess)
+            p->pass_ms[6] = ms;
+        else
+            (void)cudaGetLastError();
     }
     int st = 0;
     VPX_CUDA(cudaMemcpy(&st, p->wk.status, sizeof(int), cudaMemcpyDeviceToHost));

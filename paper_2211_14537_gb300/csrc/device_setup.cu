@@ -389,9 +389,13 @@ void device_setup(vpx_plan *p) {
     cudaError_t e = cudaGetDeviceCount(&ndev);
     if (e != cudaSuccess || ndev == 0) fail(VPX_ERR_NODEV, "no CUDA device");
     VPX_CUDA(cudaGetDevice(&p->device));
-    cudaStream_t s;
+    cudaStream_t s, aux;
     VPX_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
     p->stream = s;
+    VPX_CUDA(cudaStreamCreateWithFlags(&aux, cudaStreamNonBlocking));
+    p->aux_stream = aux;
+    for (void **e : {&p->ev_fork, &p->ev_up, &p->ev_join})
+        VPX_CUDA(cudaEventCreateWithFlags((cudaEvent_t *)e, cudaEventDisableTiming));
     DevTree &d = p->dt;
     d.n_leaves = (int)p->tree.leaves.size();
     d.n_boxes = (int)p->box_level.size();
@@ -515,6 +519,15 @@ void device_free(vpx_plan *p) {
     if (p->graph_exec) {
         cudaGraphExecDestroy((cudaGraphExec_t)p->graph_exec);
         p->graph_exec = nullptr;
+    }
+    for (void **e : {&p->ev_fork, &p->ev_up, &p->ev_join})
+        if (*e) {
+            cudaEventDestroy((cudaEvent_t)*e);
+            *e = nullptr;
+        }
+    if (p->aux_stream) {
+        cudaStreamDestroy((cudaStream_t)p->aux_stream);
+        p->aux_stream = nullptr;
     }
     if (p->stream) {
         cudaStreamDestroy((cudaStream_t)p->stream);

@@ -76,7 +76,7 @@ __global__ void k_leaf_const(int KK, int P, const int32_t *near, const int32_t *
     }
     __syncthreads();
     double *o = v + rhs * ldv + (int64_t)t * KK;
-    for (int i = threadIdx.x; i < KK; i += blockDim.x) o[i] += s_c;
+    for (int i = threadIdx.x; i < KK; i += blockDim.x) atomicAdd(o + i, s_c);   // concurrent with the near field
 }
 
 __global__ void k_nan_check(const double *v, int64_t ldv, int64_t n, int *status) {
@@ -327,6 +327,7 @@ void setup_passes(vpx_plan *p) {
         for (GemmPass *g : {&F.l2m, &F.m2l, &F.s2l, &F.l2t, &F.m2t}) g->slices = s_far;
         for (int l = 0; l <= kMaxLevel; ++l) F.m2m[l].slices = F.l2l[l].slices = s_far;
         gemm_prepare_device();
+        gemm_tc_prepare_device();
         const int kp_f = (KK + 31) / 32 * 32, kp_m = (P2 + 31) / 32 * 32;
         F.fe_sl = dev_alloc<uint16_t>((size_t)p->opt.max_rhs * nl * kSlicesS * kp_f);
         F.fe_ex = dev_alloc<int32_t>((size_t)p->opt.max_rhs * nl);
@@ -335,6 +336,8 @@ void setup_passes(vpx_plan *p) {
         F.lo_sl = dev_alloc<uint16_t>((size_t)p->opt.max_rhs * nb * kSlicesS * kp_m);
         F.lo_ex = dev_alloc<int32_t>((size_t)p->opt.max_rhs * nb);
     }
+    for (GemmPass *g : {&F.l2m, &F.m2l, &F.s2l, &F.l2t, &F.m2t, &F.near}) g->status = p->wk.status;
+    for (int l = 0; l <= kMaxLevel; ++l) F.m2m[l].status = F.l2l[l].status = p->wk.status;
     VPX_CUDA(cudaDeviceSynchronize());
 }
 
@@ -362,10 +365,14 @@ void free_passes(vpx_plan *p) {
 
 void ev_record_pass(vpx_plan *p, int i, cudaStream_t s);
 
+// Two streams: the near field and the list-i- evaluation (which need only the
+// leaf values and the finished multipoles) run on an auxiliary stream forked
+// from the main one, overlapping the level-by-level passes; both add into V
+// with atomics and the main stream joins before the NaN check.
 void run_potential_passes(vpx_plan *p, const double *fe, int64_t ldfe, int nrhs, double *v, int64_t ldv, double *vb,
                           int64_t ldb, double *mp, double *lo, cudaStream_t s) {
     const bool mixed = p->opt.precision == VPX_PREC_MIXED;
-    const int P = p->P, P2 = 2 * P, KK = p->KK, K = p->K;
+    const int P = p->P, P2 = 2 * P, KK = p->KK;
     const DevTree &d = p->dt;
     const int nb = d.n_boxes, nl = d.n_leaves;
     const int64_t ldm = (int64_t)nb * P2;
@@ -374,17 +381,30 @@ void run_potential_passes(vpx_plan *p, const double *fe, int64_t ldfe, int nrhs,
     VecSet vf{fe, ldfe, KK, F.fe_sl, F.fe_ex, nl};
     VecSet vm{mp, ldm, P2, F.mp_sl, F.mp_ex, nb};
     VecSet vl{lo, ldm, P2, F.lo_sl, F.lo_ex, nb};
+    cudaStream_t aux = (cudaStream_t)p->aux_stream;
     ev_record_pass(p, 1, s);
     VPX_CUDA(cudaMemsetAsync(mp, 0, sizeof(double) * ldm * nrhs, s));
     VPX_CUDA(cudaMemsetAsync(lo, 0, sizeof(double) * ldm * nrhs, s));
     VPX_CUDA(cudaMemset2DAsync(v, sizeof(double) * ldv, 0, sizeof(double) * (size_t)nl * KK, nrhs, s));
     if (mixed) slice_vectors(vf, 0, nl, KK, kp_f, nrhs, s);
+    // fork: near field on the auxiliary stream
+    VPX_CUDA(cudaEventRecord((cudaEvent_t)p->ev_fork, s));
+    VPX_CUDA(cudaStreamWaitEvent(aux, (cudaEvent_t)p->ev_fork, 0));
+    ev_record_pass(p, VPX_N_PASSES + 1, aux);
+    gemm_run(F.near, vf, v, ldv, nrhs, mixed, aux);
+    ev_record_pass(p, VPX_N_PASSES + 2, aux);
+    // main stream: upward pass
     gemm_run(F.l2m, vf, mp, ldm, nrhs, mixed, s);
     ev_record_pass(p, 2, s);
     for (int l = d.n_levels - 1; l >= 2; --l) {
         if (mixed) slice_vectors(vm, d.level_start[l], d.level_start[l + 1] - d.level_start[l], P2, kp_m, nrhs, s);
         if (l - 1 >= 2) gemm_run(F.m2m[l - 1], vm, mp, ldm, nrhs, mixed, s);
     }
+    // list i- on the auxiliary stream once the multipoles are final
+    VPX_CUDA(cudaEventRecord((cudaEvent_t)p->ev_up, s));
+    VPX_CUDA(cudaStreamWaitEvent(aux, (cudaEvent_t)p->ev_up, 0));
+    gemm_run(F.m2t, vm, v, ldv, nrhs, mixed, aux);
+    VPX_CUDA(cudaEventRecord((cudaEvent_t)p->ev_join, aux));
     ev_record_pass(p, 3, s);
     gemm_run(F.m2l, vm, lo, ldm, nrhs, mixed, s);
     gemm_run(F.s2l, vf, lo, ldm, nrhs, mixed, s);
@@ -403,19 +423,17 @@ void run_potential_passes(vpx_plan *p, const double *fe, int64_t ldfe, int nrhs,
     }
     ev_record_pass(p, 5, s);
     gemm_run(F.l2t, vl, v, ldv, nrhs, mixed, s);
-    gemm_run(F.m2t, vm, v, ldv, nrhs, mixed, s);
     k_leaf_const<<<dim3(nl, nrhs), 128, 0, s>>>(KK, P, d.near, d.wlist, p->ext.leaf_level, d.leaf_box, d.box_level, mp,
                                                 ldm, v, ldv);
     VPX_LAUNCH("k_leaf_const");
     ev_record_pass(p, 6, s);
-    gemm_run(F.near, vf, v, ldv, nrhs, mixed, s);
+    VPX_CUDA(cudaStreamWaitEvent(s, (cudaEvent_t)p->ev_join, 0));
     {
         const int64_t n = (int64_t)nl * KK;
         k_nan_check<<<dim3((unsigned)((n + 255) / 256), nrhs), 256, 0, s>>>(v, ldv, n, p->wk.status);
         VPX_LAUNCH("k_nan_check");
     }
     ev_record_pass(p, 7, s);
-    (void)K;
 }
 
 }  // namespace vpx

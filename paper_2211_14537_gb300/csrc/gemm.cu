@@ -17,9 +17,11 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 
 #include "dev_common.cuh"
 #include "gemm.cuh"
+#include "slice_epilogue.cuh"
 
 namespace vpx {
 
@@ -194,7 +196,7 @@ __global__ void __launch_bounds__(256) k_gemm_sliced(SlicedArgs a) {
         __syncthreads();
     }
     // epilogue
-    double pscale[4][2];
+    SliceScale pscale[4][2];
     int64_t pdst[4][2];
 #pragma unroll
     for (int t = 0; t < 4; ++t)
@@ -202,10 +204,10 @@ __global__ void __launch_bounds__(256) k_gemm_sliced(SlicedArgs a) {
         for (int half = 0; half < 2; ++half) {
             const int n = wn * 32 + t * 8 + tq * 2 + half;
             pdst[t][half] = -1;
-            pscale[t][half] = 0.0;
+            pscale[t][half] = SliceScale{0.f, 0.f, 0};
             if (n < tile.count) {
                 const GPair pr = a.pairs[tile.first + n];
-                pscale[t][half] = ldexp(pr.scale, a.vexpo[(size_t)rhs * a.nvec + pr.src] - 2 * kSliceBitsB);
+                pscale[t][half] = slice_pair_scale(pr.scale, a.vexpo[(size_t)rhs * a.nvec + pr.src] - 2 * kSliceBitsB);
                 pdst[t][half] = rhs * a.ldo + pr.dst;
             }
         }
@@ -213,27 +215,17 @@ __global__ void __launch_bounds__(256) k_gemm_sliced(SlicedArgs a) {
     for (int rr = 0; rr < 2; ++rr) {
         const int i = m0 + wm * 16 + g + rr * 8;
         if (i >= a.M) continue;
-        const double rscale = ldexp(1.0, a.texpo[(size_t)tile.tab * a.Mpad + i]);
+        const int row_e = a.texpo[(size_t)tile.tab * a.Mpad + i];
 #pragma unroll
         for (int t = 0; t < 4; ++t)
 #pragma unroll
             for (int half = 0; half < 2; ++half) {
                 if (pdst[t][half] < 0) continue;
-                float hi = acc[S - 1][t][rr * 2 + half], lo = 0.f;
+                float acc_d[S], hi, lo;
 #pragma unroll
-                for (int d = S - 2; d >= 0; --d) {
-                    hi *= 0x1p-7f;
-                    lo *= 0x1p-7f;
-                    const float b = acc[d][t][rr * 2 + half];
-                    const float sm = hi + b, bb = sm - hi;
-                    const float er = (hi - (sm - bb)) + (b - bb);
-                    hi = sm;
-                    lo += er;
-                    const float s2 = hi + lo;
-                    lo = lo - (s2 - hi);
-                    hi = s2;
-                }
-                const double val = ((double)hi + (double)lo) * rscale * pscale[t][half];
+                for (int d = 0; d < S; ++d) acc_d[d] = acc[d][t][rr * 2 + half];
+                slice_recombine<S>(acc_d, hi, lo);
+                const double val = slice_output(hi, lo, pscale[t][half], row_e);
                 double *o = a.out + pdst[t][half] + i;
                 if (a.add) atomicAdd(o, val);
                 else *o = val;
@@ -357,9 +349,16 @@ void gemm_pass_free(GemmPass &g) {
     g.n_pairs = g.n_tiles = 0;
 }
 
+void gemm_tc_run(const GemmPass &g, const VecSet &vs, double *out, int64_t ldo, int nrhs, int *status, void *s);
+
 void gemm_run(const GemmPass &g, const VecSet &vs, double *out, int64_t ldo, int nrhs, bool mixed, void *sv) {
     if (g.n_tiles == 0) return;
     cudaStream_t s = (cudaStream_t)sv;
+    const bool no_tc = getenv("VPX_NO_TC") != nullptr;
+    if (mixed && !no_tc && gemm_tc_eligible(g)) {
+        gemm_tc_run(g, vs, out, ldo, nrhs, g.status, sv);
+        return;
+    }
     if (!mixed) {
         dim3 grid(g.n_tiles, (g.M + G_M - 1) / G_M, nrhs);
         k_gemm_fp64<<<grid, 256, 0, s>>>(g.M, g.Kd, g.tab, g.tiles, g.pairs, vs.base, vs.ld, vs.stride, out, ldo, g.add);

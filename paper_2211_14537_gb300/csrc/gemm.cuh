@@ -35,6 +35,7 @@ struct GemmPass {
     int M = 0, Kd = 0, Kpad = 0, Mpad = 0, ntab = 0;
     int add = 1;                       // 1: atomic add into out, 0: store
     int slices = 5;                    // mixed form: slices used (5 or 6)
+    int *status = nullptr;             // device status word (bounded waits report here)
     const double *tab = nullptr;       // [ntab][M][Kd] FP64 (row-major)
     const uint16_t *tslices = nullptr; // [ntab][S][Mpad][Kpad] bf16 bits (mixed form)
     const int32_t *texpo = nullptr;    // [ntab][Mpad] row exponents (mixed form)
@@ -49,6 +50,9 @@ void gemm_pass_set_pairs(GemmPass &g, std::vector<std::pair<int, GPair>> &tagged
 void gemm_pass_upload_tables(GemmPass &g, const std::vector<double> &tab, int ntab, int M, int Kd, bool mixed);
 void gemm_pass_free(GemmPass &g);
 void gemm_prepare_device();
+// tcgen05 engine (gemm_tc.cu): 5-slice passes whose rows tile by 128
+bool gemm_tc_eligible(const GemmPass &g);
+void gemm_tc_prepare_device();
 
 struct VecSet {                        // source vectors of a pass
     const double *base = nullptr;      // vector v of rhs r at base + r*ld + v*stride

@@ -100,7 +100,9 @@ struct vpx_plan {
     vpx::DevWork wk;
     vpx::FmmPasses fmm;
     bool timing = false;
-    void *events[VPX_N_PASSES + 1] = {nullptr};
+    void *events[VPX_N_PASSES + 3] = {nullptr};   // pass boundaries on the main stream, near field on aux
+    void *aux_stream = nullptr;   // second stream of the execute graph (near field, list i-)
+    void *ev_fork = nullptr, *ev_up = nullptr, *ev_join = nullptr;
     void *graph_exec = nullptr;   // captured vpx_execute sequence (cudaGraphExec_t)
     int64_t graph_key[10] = {0};
     double pass_ms[VPX_N_PASSES] = {0};

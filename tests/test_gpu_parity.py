@@ -345,3 +345,30 @@ def test_mixed_full_size_sampled(V):
     err = np.max(np.abs(v.cpu().numpy()[sub] - want)) / np.max(np.abs(want))
     print("mixed starfish full size sampled rel err %.3e" % err)
     assert err <= 1e-9, err
+
+
+def test_tcgen05_engine_matches_mma_engine(V):
+    """The tcgen05 (tensor-memory) engine and the mma.sync engine compute the
+    same exact slice products: their potentials agree to rounding."""
+    import os
+    wl = CASES["disk_l3_k16"]()
+    plan = make_plan(V, wl, precision=1)
+    tree = O.build_tree(wl.domain, wl.opts, wl.sources[0])
+    vals = seeded_leaf_values(tree, 1, 2216)
+    fe = torch.tensor(vals[:, 0, :].ravel(), dtype=torch.float64, device="cuda")
+    n = fe.numel()
+    v_tc = torch.empty(n, dtype=torch.float64, device="cuda")
+    v_mma = torch.empty(n, dtype=torch.float64, device="cuda")
+    os.environ.pop("VPX_NO_TC", None)
+    V.vpx_potential(plan, fe, v_tc)
+    assert V.vpx_sync_status(plan) == 0
+    os.environ["VPX_NO_TC"] = "1"
+    try:
+        V.vpx_potential(plan, fe, v_mma)
+        assert V.vpx_sync_status(plan) == 0
+    finally:
+        os.environ.pop("VPX_NO_TC", None)
+    scale = float(v_mma.abs().max())
+    diff = float((v_tc - v_mma).abs().max())
+    print("tcgen05 vs mma.sync max diff %.3e (scale %.3e)" % (diff, scale))
+    assert diff <= 1e-14 * scale
