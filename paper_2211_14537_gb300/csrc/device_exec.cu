@@ -10,6 +10,7 @@
 #include <cstdlib>
 
 #include "dev_common.cuh"
+#include "ext.cuh"
 
 namespace vpx {
 
@@ -30,18 +31,6 @@ __global__ void k_leafvals(int n_leaves, int KK, const int32_t *leaf_cls, const 
     if (cls == kRegular) *o = f[rhs * ldf + reg_off[leaf] + j];
     else if (cls == kExterior && owner_flag[leaf] == 0) *o = 0.0;
 }
-
-struct ExtArgs {
-    int K, Kbar, NG;
-    const int32_t *cut_leaf, *n_interior, *grid_src, *node_src, *owned_off, *owned;
-    const int64_t *stencil_off, *pinv_off;
-    const double *pinv, *A_grid, *cheb_inv, *tnodes;
-    const int32_t *leaf_level, *leaf_ix, *leaf_iy;
-    const double *f;
-    int64_t ldf;
-    double *fe;
-    int64_t ldfe;
-};
 
 // One block per (cut leaf, rhs).  c = A_I^+ f_I; the Kbar x Kbar Chebyshev grid
 // on Sbar takes the data at interior nodes and A_{Xbar^E,G} c at exterior
@@ -148,30 +137,35 @@ __global__ void k_extend(ExtArgs a) {
 
 // ---------------------------------------------------------------- boundary
 
+// one warp per boundary node: V(x) = sum_b w_y[b] sum_a w_x[a] V_leaf[b][a]
 __global__ void k_boundary(int nb, int K, const int32_t *bleaf, const double *bw, const double *v, int64_t ldv,
                            double *vb, int64_t ldb) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x, rhs = blockIdx.y;
+    const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31, rhs = blockIdx.y;
     if (k >= nb) return;
     const double *w = bw + (size_t)k * 2 * K;
     const double *V = v + rhs * ldv + (int64_t)bleaf[k] * K * K;
     double s = 0.0;
-    for (int b = 0; b < K; ++b) {
-        double r = 0.0;
-        for (int a2 = 0; a2 < K; ++a2) r += w[a2] * V[b * K + a2];
-        s += w[K + b] * r;
-    }
-    vb[rhs * ldb + k] = s;
+    for (int j = lane; j < K * K; j += 32) s += w[K + j / K] * w[j % K] * V[j];
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) vb[rhs * ldb + k] = s;
 }
 
 // ------------------------------------------------------------ host side
 
-// Opt the extension kernel into the dynamic shared memory its largest cut leaf needs.
-static void prepare_extension(vpx_plan *p) {
+// Dynamic shared memory of the extension kernels (8-byte words: FP64 or a
+// double-float pair) for the largest cut leaf.
+static size_t extension_smem(const vpx_plan *p) {
     const StencilInfo &st = p->st;
     int maxI = 0;
     for (int c = 0; c < (int)st.cut_leaf.size(); ++c) maxI = std::max(maxI, st.n_interior[c]);
-    size_t smem = sizeof(double) * ((size_t)maxI + st.NG + 3 * st.Kbar * st.Kbar + 3 * p->K * st.Kbar);
+    return sizeof(double) * ((size_t)maxI + st.NG + 3 * st.Kbar * st.Kbar + 3 * p->K * st.Kbar);
+}
+
+// Opt the extension kernels into the dynamic shared memory they need.
+static void prepare_extension(vpx_plan *p) {
+    const size_t smem = extension_smem(p);
     if (smem > 48 * 1024) VPX_CUDA(cudaFuncSetAttribute(k_extend, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (p->opt.precision == VPX_PREC_MIXED) extend_df_prepare(p->ext.max_interior, p->K, p->st.Kbar);
 }
 
 // Per-plan index arrays of the execute path: non-zero leaves and the
@@ -232,11 +226,22 @@ static void run_extension(vpx_plan *p, const double *f, int nrhs, int64_t ldf, d
         a.ldf = ldf;
         a.fe = fe;
         a.ldfe = ldfe;
-        int maxI = 0;
-        for (int c = 0; c < p->ext.ncut; ++c) maxI = std::max(maxI, st.n_interior[c]);
-        size_t smem = sizeof(double) * ((size_t)maxI + st.NG + 3 * st.Kbar * st.Kbar + 3 * p->K * st.Kbar);
-        k_extend<<<dim3(p->ext.ncut, nrhs), 256, smem, s>>>(a);
-        VPX_LAUNCH("k_extend");
+        a.pinv_df = reinterpret_cast<const float2 *>(p->ext.pinv_df);
+        a.cheb_df = reinterpret_cast<const float2 *>(p->ext.cheb_df);
+        const size_t smem = extension_smem(p);
+        if (p->opt.precision == VPX_PREC_MIXED) {
+            DevExt &x = p->ext;
+            const int Kb2 = p->st.Kbar * p->st.Kbar;
+            const int64_t ldc = (int64_t)x.ncut * p->st.NG, ldF = (int64_t)x.ncut * Kb2;
+            launch_ext_coeff_df(a, x.ncut, x.max_interior, nrhs, x.cbuf, ldc, s);
+            VecSet vc{x.cbuf, ldc, p->st.NG, nullptr, nullptr, x.ncut, 0};
+            gemm_run(x.grid_pass, vc, x.Fall, ldF, nrhs, true, s);
+            launch_ext_eval_df(a, x.ncut, x.n_tgt, x.tgt_cut, x.tgt_leaf, x.Fall, ldF,
+                               reinterpret_cast<float2 *>(x.alpha), nrhs, s);
+        } else {
+            k_extend<<<dim3(p->ext.ncut, nrhs), 256, smem, s>>>(a);
+            VPX_LAUNCH("k_extend");
+        }
     }
 }
 
@@ -250,8 +255,8 @@ void run_potential_scratch(vpx_plan *p, const double *fe, int64_t ldfe, int nrhs
     run_potential_passes(p, fe, ldfe, nrhs, v, ldv, vb, ldb, mp, lo, s);
     const int nbd = (int)p->bdry_leaf.size();
     if (vb && nbd > 0) {
-        k_boundary<<<dim3((nbd + 127) / 128, nrhs), 128, 0, s>>>(nbd, p->K, p->wk.bdry_leaf, p->wk.bdry_w, v, ldv, vb,
-                                                                ldb);
+        k_boundary<<<dim3((nbd + 7) / 8, nrhs), 256, 0, s>>>(nbd, p->K, p->wk.bdry_leaf, p->wk.bdry_w, v, ldv, vb,
+                                                            ldb);
         VPX_LAUNCH("k_boundary");
     }
     ev_record(p, 8, s);

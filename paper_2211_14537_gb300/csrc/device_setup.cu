@@ -473,6 +473,45 @@ void device_setup(vpx_plan *p) {
         std::copy(&st.A[(size_t)(p->KK + g) * st.NG], &st.A[(size_t)(p->KK + g) * st.NG] + st.NG, &Ag[(size_t)g * st.NG]);
     x.A_grid = dev_upload(Ag);
     x.cheb_inv = dev_upload(st.cheb_inv);
+    if (p->opt.precision == VPX_PREC_MIXED) {
+        // double-float copies for the mixed form's extension
+        auto split = [](double v) {
+            const float h = (float)v;
+            return DevExt::DfPair{h, (float)(v - (double)h)};
+        };
+        std::vector<DevExt::DfPair> pd(st.pinv.size()), cd(st.cheb_inv.size());
+        for (size_t i = 0; i < st.pinv.size(); ++i) pd[i] = split(st.pinv[i]);
+        for (size_t i = 0; i < st.cheb_inv.size(); ++i) cd[i] = split(st.cheb_inv[i]);
+        x.pinv_df = dev_upload(pd);
+        x.cheb_df = dev_upload(cd);
+        // A_{X_Sbar,G} c of every cut leaf as one table pass; targets of the Chebyshev stage
+        const int Kb2 = st.Kbar * st.Kbar;
+        if (x.ncut > 0) {
+            std::vector<std::pair<int, GPair>> tg;
+            for (int c = 0; c < x.ncut; ++c) tg.push_back({0, GPair{c, 0, (int64_t)c * Kb2, 1.0}});
+            gemm_pass_upload_tables(x.grid_pass, Ag, 1, Kb2, st.NG, true);
+            x.grid_pass.add = 0;
+            x.grid_pass.slices = kSlicesS;
+            gemm_pass_set_pairs(x.grid_pass, tg);
+        }
+        std::vector<int32_t> tc, tl;
+        for (int c = 0; c < x.ncut; ++c) {
+            tc.push_back(c);
+            tl.push_back(st.cut_leaf[c]);
+        }
+        for (int c = 0; c < x.ncut; ++c)
+            for (int j = st.owned_off[c]; j < st.owned_off[c + 1]; ++j) {
+                tc.push_back(c);
+                tl.push_back(st.owned[j]);
+            }
+        x.n_tgt = (int)tc.size();
+        x.tgt_cut = dev_upload(tc);
+        x.tgt_leaf = dev_upload(tl);
+        for (int c = 0; c < x.ncut; ++c) x.max_interior = std::max(x.max_interior, st.n_interior[c]);
+        x.cbuf = dev_alloc<double>((size_t)p->opt.max_rhs * x.ncut * st.NG);
+        x.Fall = dev_alloc<double>((size_t)p->opt.max_rhs * x.ncut * Kb2);
+        x.alpha = dev_alloc<DevExt::DfPair>((size_t)p->opt.max_rhs * x.ncut * Kb2);
+    }
     // boundary
     p->wk.bdry_leaf = dev_upload(p->bdry_leaf);
     p->wk.bdry_w = dev_upload(p->bdry_w);
@@ -505,6 +544,9 @@ void device_free(vpx_plan *p) {
     dev_free(x.cut_leaf); dev_free(x.n_interior); dev_free(x.grid_src); dev_free(x.node_src);
     dev_free(x.stencil_off); dev_free(x.pinv_off); dev_free(x.reg_leaf_off); dev_free(x.owned_off);
     dev_free(x.owned); dev_free(x.pinv); dev_free(x.A_grid); dev_free(x.cheb_inv);
+    dev_free(x.pinv_df); dev_free(x.cheb_df);
+    gemm_pass_free(x.grid_pass);
+    dev_free(x.tgt_cut); dev_free(x.tgt_leaf); dev_free(x.cbuf); dev_free(x.Fall); dev_free(x.alpha);
     dev_free(x.leaf_level); dev_free(x.leaf_ix); dev_free(x.leaf_iy); dev_free(x.owned_flag_dev);
     free_passes(p);
     DevWork &w = p->wk;

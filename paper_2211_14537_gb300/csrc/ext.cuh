@@ -1,0 +1,35 @@
+// ext.cuh -- arguments of the extension kernels (Sections 3.2, 4.1): the FP64
+// kernel (device_exec.cu) and the double-float one of the mixed form
+// (extend_df.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace vpx {
+
+struct ExtArgs {
+    int K, Kbar, NG;
+    const int32_t *cut_leaf, *n_interior, *grid_src, *node_src, *owned_off, *owned;
+    const int64_t *stencil_off, *pinv_off;
+    const double *pinv, *A_grid, *cheb_inv, *tnodes;
+    const float2 *pinv_df;      // P_S as double-float (hi, lo), same layout as pinv
+    const float2 *cheb_df;      // [Kbar][Kbar] double-float
+    const int32_t *leaf_level, *leaf_ix, *leaf_iy;
+    const double *f;
+    int64_t ldf;
+    double *fe;
+    int64_t ldfe;
+};
+
+// mixed form (extend_df.cu): c = A_I^+ f_I into cbuf[rhs][cut][NG]; then, after
+// the grid values A_{X_Sbar,G} c are in Fall[rhs][cut][Kbar^2], the Chebyshev
+// stage for every target leaf (tgt_cut[t], tgt_leaf[t])
+void extend_df_prepare(int max_interior, int K, int Kbar);
+void launch_ext_coeff_df(const ExtArgs &a, int ncut, int max_interior, int nrhs, double *cbuf, int64_t ldc,
+                         cudaStream_t s);
+void launch_ext_eval_df(const ExtArgs &a, int ncut, int n_tgt, const int32_t *tgt_cut, const int32_t *tgt_leaf,
+                        const double *Fall, int64_t ldF, float2 *alpha, int nrhs, cudaStream_t s);
+
+}  // namespace vpx

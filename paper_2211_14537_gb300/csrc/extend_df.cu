@@ -1,0 +1,186 @@
+// extend_df.cu -- the extension of f on cut leaves (Sections 3.2, 4.1) in the
+// mixed form: double-float arithmetic (df32.cuh) plus one exact-slice table
+// GEMM.  The steps are those of the FP64 kernel k_extend, spread over four
+// launches so that no CTA streams a whole cut leaf's operators alone:
+//
+//   1. k_ext_coeff_df  c = A_I^+ f_I, one warp per row of A_I^+ (a GEMV
+//                      streaming the per-leaf pseudo-inverses from HBM);
+//   2. table GEMM      A_{X_Sbar,G} c at all Kbar^2 grid points of every cut
+//                      leaf at once (one universal table, gemm_frag.cu);
+//   3. k_ext_alpha_df  one CTA per cut leaf: the grid takes the data at
+//                      interior points; its Chebyshev coefficients, truncated
+//                      to m + n < Kbar;
+//   4. k_ext_eval_df   one CTA per target leaf (the cut leaf itself and each
+//                      leaf of its extension list): the expansion at the
+//                      target's nodes.
+//
+// Operators are stored as double-float pairs; data enter and leave as FP64.
+// Relative errors stay near 2^-47 times the extension's conditioning (step 2:
+// 2^-42 of its own terms), below the 35 and 42 bits of the leaf values that
+// the mixed form's slices keep.
+#include <cmath>
+
+#include "dev_common.cuh"
+#include "df32.cuh"
+#include "ext.cuh"
+
+namespace vpx {
+
+__device__ inline df32 ld_df(const float2 *p) {
+    const float2 v = *p;
+    return df32{v.x, v.y};
+}
+
+__device__ inline float2 st_df(df32 v) { return make_float2(v.hi, v.lo); }
+
+// grid (ncut * nrb, rhs), 256 threads: warp w of block b computes row
+// k = (b % nrb) * 8 + w of c for cut leaf b / nrb
+__global__ void __launch_bounds__(256) k_ext_coeff_df(ExtArgs a, int nrb, double *cbuf, int64_t ldc) {
+    extern __shared__ __align__(16) float2 fI[];
+    const int c = blockIdx.x / nrb, rb = blockIdx.x % nrb, rhs = blockIdx.y;
+    const int nI = a.n_interior[c], NG = a.NG;
+    const double *f = a.f + rhs * a.ldf + a.stencil_off[c];
+    for (int i = threadIdx.x; i < nI; i += blockDim.x) fI[i] = st_df(df_split_bits(f[i]));
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int k = rb * 8 + warp;
+    if (k >= NG) return;
+    const float2 *P = a.pinv_df + a.pinv_off[c] + (size_t)k * nI;
+    df32 s{0.f, 0.f};
+#pragma unroll 4
+    for (int i = lane; i < nI; i += 32) df_mac(s, ld_df(P + i), ld_df(fI + i));
+    s = df_warp_sum(s);
+    if (lane == 0) cbuf[rhs * ldc + (int64_t)c * NG + k] = df_value(s);
+}
+
+// grid (cut leaves, rhs), 256 threads: the grid takes the data at interior
+// points and A_{X_Sbar,G} c elsewhere; alpha = C F C^T truncated to m + n < Kbar
+__global__ void __launch_bounds__(256) k_ext_alpha_df(ExtArgs a, const double *Fall, int64_t ldF, float2 *alpha,
+                                                     int64_t lda) {
+    extern __shared__ __align__(16) float2 smf[];
+    const int c = blockIdx.x, rhs = blockIdx.y;
+    const int Kb = a.Kbar, Kb2 = Kb * Kb;
+    float2 *C = smf;               // Kb2   Chebyshev transform [m][ax]
+    float2 *F = C + Kb2;           // Kb2   grid values [by][ax]
+    float2 *T1 = F + Kb2;          // Kb2   [m][by]
+    const double *f = a.f + rhs * a.ldf + a.stencil_off[c];
+    const int32_t *gs = a.grid_src + (size_t)c * Kb2;
+    const double *Fc = Fall + rhs * ldF + (int64_t)c * Kb2;
+    for (int g = threadIdx.x; g < Kb2; g += blockDim.x) {
+        C[g] = a.cheb_df[g];
+        const int src = gs[g];
+        F[g] = st_df(df_split_bits(src >= 0 ? f[src] : Fc[g]));
+    }
+    __syncthreads();
+    // T1[m][by] = sum_ax C[m][ax] F[by][ax]
+    for (int e = threadIdx.x; e < Kb2; e += blockDim.x) {
+        const int m = e / Kb, by = e % Kb;
+        df32 s{0.f, 0.f};
+        for (int ax = 0; ax < Kb; ++ax) df_mac(s, ld_df(C + m * Kb + ax), ld_df(F + by * Kb + ax));
+        T1[m * Kb + by] = st_df(df_norm(s));
+    }
+    __syncthreads();
+    // alpha[m][n] = sum_by T1[m][by] C[n][by], m + n < Kb (zero beyond)
+    float2 *al = alpha + rhs * lda + (int64_t)c * Kb2;
+    for (int e = threadIdx.x; e < Kb2; e += blockDim.x) {
+        const int m = e / Kb, n = e % Kb;
+        df32 s{0.f, 0.f};
+        if (m + n < Kb)
+            for (int by = 0; by < Kb; ++by) df_mac(s, ld_df(T1 + m * Kb + by), ld_df(C + n * Kb + by));
+        al[e] = st_df(df_norm(s));
+    }
+}
+
+// grid (targets, rhs), 256 threads: the truncated expansion of the target's
+// cut leaf at the target's K x K nodes (interior nodes of the cut leaf itself
+// keep the data)
+__global__ void __launch_bounds__(256) k_ext_eval_df(ExtArgs a, const int32_t *tgt_cut, const int32_t *tgt_leaf,
+                                                    const float2 *alpha, int64_t lda) {
+    extern __shared__ __align__(16) float2 smf[];
+    const int t = blockIdx.x, rhs = blockIdx.y;
+    const int c = tgt_cut[t], tl = tgt_leaf[t];
+    const int K = a.K, KK = K * K, Kb = a.Kbar, Kb2 = Kb * Kb;
+    float2 *al = smf;              // Kb2   alpha[m][n]
+    float2 *Tx = al + Kb2;         // K*Kb  T_m at the target x nodes
+    float2 *Ty = Tx + K * Kb;      // K*Kb
+    float2 *G = Ty + K * Kb;       // Kb*K
+    const float2 *ag = alpha + rhs * lda + (int64_t)c * Kb2;
+    for (int e = threadIdx.x; e < Kb2; e += blockDim.x) al[e] = ag[e];
+    const int leaf = a.cut_leaf[c];
+    const double sS = ldexp(1.0, -a.leaf_level[leaf]);
+    const double cxS = -0.5 + (a.leaf_ix[leaf] + 0.5) * sS, cyS = -0.5 + (a.leaf_iy[leaf] + 0.5) * sS;
+    const double r = 1.5 * sS;   // half side of Sbar
+    const double sT = ldexp(1.0, -a.leaf_level[tl]);
+    const double cxT = -0.5 + (a.leaf_ix[tl] + 0.5) * sT, cyT = -0.5 + (a.leaf_iy[tl] + 0.5) * sT;
+    // Chebyshev values at the target coordinates (FP64 recurrence, 2K x Kb values)
+    for (int e = threadIdx.x; e < 2 * K; e += blockDim.x) {
+        const int i = e % K;
+        const double z = (e < K) ? (cxT - cxS + 0.5 * sT * a.tnodes[i]) / r : (cyT - cyS + 0.5 * sT * a.tnodes[i]) / r;
+        float2 *T = (e < K) ? Tx + i * Kb : Ty + i * Kb;
+        double tp = 1.0, tc = z;   // T_{m-1}, T_m
+        T[0] = st_df(df_split(1.0));
+        if (Kb > 1) T[1] = st_df(df_split_bits(z));
+        for (int m = 2; m < Kb; ++m) {
+            const double tn = 2.0 * z * tc - tp;
+            tp = tc;
+            tc = tn;
+            T[m] = st_df(df_split_bits(tn));
+        }
+    }
+    __syncthreads();
+    // G[n][ax] = sum_m alpha[m][n] Tx[ax][m]
+    for (int e = threadIdx.x; e < Kb * K; e += blockDim.x) {
+        const int n = e / K, ax = e % K;
+        df32 s{0.f, 0.f};
+        for (int m = 0; m + n < Kb; ++m) df_mac(s, ld_df(al + m * Kb + n), ld_df(Tx + ax * Kb + m));
+        G[n * K + ax] = st_df(df_norm(s));
+    }
+    __syncthreads();
+    const double *f = a.f + rhs * a.ldf + a.stencil_off[c];
+    double *out = a.fe + rhs * a.ldfe + (int64_t)tl * KK;
+    const int32_t *ns = a.node_src + (size_t)c * KK;
+    const bool self = tl == leaf;
+    for (int j = threadIdx.x; j < KK; j += blockDim.x) {
+        const int ax = j % K, by = j / K;
+        if (self && ns[j] >= 0) {
+            out[j] = f[ns[j]];
+        } else {
+            df32 s{0.f, 0.f};
+            for (int n = 0; n < Kb; ++n) df_mac(s, ld_df(Ty + by * Kb + n), ld_df(G + n * K + ax));
+            out[j] = df_to_f64_scaled(df_norm(s), 0);
+        }
+    }
+}
+
+static size_t alpha_smem(int Kb) { return sizeof(float2) * 3 * (size_t)Kb * Kb; }
+static size_t eval_smem(int K, int Kb) { return sizeof(float2) * ((size_t)Kb * Kb + 3 * (size_t)K * Kb); }
+
+void extend_df_prepare(int max_interior, int K, int Kbar) {
+    const size_t s1 = sizeof(float2) * (size_t)max_interior;
+    if (s1 > 48 * 1024)
+        VPX_CUDA(cudaFuncSetAttribute(k_ext_coeff_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s1));
+    if (alpha_smem(Kbar) > 48 * 1024)
+        VPX_CUDA(cudaFuncSetAttribute(k_ext_alpha_df, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)alpha_smem(Kbar)));
+    if (eval_smem(K, Kbar) > 48 * 1024)
+        VPX_CUDA(cudaFuncSetAttribute(k_ext_eval_df, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)eval_smem(K, Kbar)));
+}
+
+void launch_ext_coeff_df(const ExtArgs &a, int ncut, int max_interior, int nrhs, double *cbuf, int64_t ldc,
+                         cudaStream_t s) {
+    const int nrb = (a.NG + 7) / 8;
+    k_ext_coeff_df<<<dim3(ncut * nrb, nrhs), 256, sizeof(float2) * (size_t)max_interior, s>>>(a, nrb, cbuf, ldc);
+    VPX_LAUNCH("k_ext_coeff_df");
+}
+
+void launch_ext_eval_df(const ExtArgs &a, int ncut, int n_tgt, const int32_t *tgt_cut, const int32_t *tgt_leaf,
+                        const double *Fall, int64_t ldF, float2 *alpha, int nrhs, cudaStream_t s) {
+    const int64_t lda = (int64_t)ncut * a.Kbar * a.Kbar;
+    k_ext_alpha_df<<<dim3(ncut, nrhs), 256, alpha_smem(a.Kbar), s>>>(a, Fall, ldF, alpha, lda);
+    VPX_LAUNCH("k_ext_alpha_df");
+    k_ext_eval_df<<<dim3(n_tgt, nrhs), 256, eval_smem(a.K, a.Kbar), s>>>(a, tgt_cut, tgt_leaf, alpha, lda);
+    VPX_LAUNCH("k_ext_eval_df");
+}
+
+}  // namespace vpx

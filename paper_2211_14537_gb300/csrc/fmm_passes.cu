@@ -33,30 +33,33 @@ typedef std::complex<double> cd;
 
 // ------------------------------------------------------- constant terms
 
-// local[b][0] += log(L_b) sum_{list i} a_0(src) + sum_{list i+} log(H_src) a_0(src)
-__global__ void k_local_const(int first, int count, int P, const int32_t *vlist, const int32_t *xlist,
+// local[b][0] += log(L_b) sum_{list i} a_0(src) + sum_{list i+} log(H_src) a_0(src).
+// One warp per box, lanes over the list slots; log of a box side 2^-l is -l ln 2.
+__global__ void k_local_const(int first, int count, int P, double ln2, const int32_t *vlist, const int32_t *xlist,
                               const int32_t *box_level, const int32_t *leaf_level, const int32_t *leaf_box,
                               const double *mpole, double *local, int64_t ldm) {
-    const int bi = blockIdx.x * blockDim.x + threadIdx.x, rhs = blockIdx.y;
+    const int bi = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31, rhs = blockIdx.y;
     if (bi >= count) return;
     const int b = first + bi;
     const double *mp = mpole + rhs * ldm;
     double sv = 0.0, sx = 0.0;
-    for (int s = 0; s < kVSlots; ++s) {
-        int src = vlist[(size_t)b * kVSlots + s];
+    for (int s = lane; s < kVSlots; s += 32) {
+        const int src = vlist[(size_t)b * kVSlots + s];
         if (src >= 0) sv += mp[(int64_t)src * 2 * P];
     }
-    for (int s = 0; s < kXSlots; ++s) {
-        int src = xlist[(size_t)b * kXSlots + s];
-        if (src >= 0) sx += log(0.5 * ldexp(1.0, -leaf_level[src])) * mp[(int64_t)leaf_box[src] * 2 * P];
+    if (lane < kXSlots) {
+        const int src = xlist[(size_t)b * kXSlots + lane];
+        if (src >= 0) sx = -(double)(leaf_level[src] + 1) * ln2 * mp[(int64_t)leaf_box[src] * 2 * P];
     }
-    local[rhs * ldm + (int64_t)b * 2 * P] += log(ldexp(1.0, -box_level[b])) * sv + sx;
+    double c = -(double)box_level[b] * ln2 * sv + sx;
+    for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (lane == 0) local[rhs * ldm + (int64_t)b * 2 * P] += c;
 }
 
 // V[t][i] += (1/2pi) [sum_near log(h_s) a_0(s) + sum_{list i-} log(L_W) a_0(W)], all i
-__global__ void k_leaf_const(int KK, int P, const int32_t *near, const int32_t *wlist, const int32_t *leaf_level,
-                             const int32_t *leaf_box, const int32_t *box_level, const double *mpole, int64_t ldm,
-                             double *v, int64_t ldv) {
+__global__ void k_leaf_const(int KK, int P, double ln2, const int32_t *near, const int32_t *wlist,
+                             const int32_t *leaf_level, const int32_t *leaf_box, const int32_t *box_level,
+                             const double *mpole, int64_t ldm, double *v, int64_t ldv) {
     const int t = blockIdx.x, rhs = blockIdx.y;
     __shared__ double s_c;
     if (threadIdx.x < 32) {
@@ -64,11 +67,11 @@ __global__ void k_leaf_const(int KK, int P, const int32_t *near, const int32_t *
         double c = 0.0;
         for (int s = threadIdx.x; s < kNearConfigs + kWSlots; s += 32) {
             if (s < kNearConfigs) {
-                int src = near[(size_t)t * kNearConfigs + s];
-                if (src >= 0) c += log(0.5 * ldexp(1.0, -leaf_level[src])) * mp[(int64_t)leaf_box[src] * 2 * P];
+                const int src = near[(size_t)t * kNearConfigs + s];
+                if (src >= 0) c -= (double)(leaf_level[src] + 1) * ln2 * mp[(int64_t)leaf_box[src] * 2 * P];
             } else {
-                int wb = wlist[(size_t)t * kWSlots + (s - kNearConfigs)];
-                if (wb >= 0) c += log(ldexp(1.0, -box_level[wb])) * mp[(int64_t)wb * 2 * P];
+                const int wb = wlist[(size_t)t * kWSlots + (s - kNearConfigs)];
+                if (wb >= 0) c -= (double)box_level[wb] * ln2 * mp[(int64_t)wb * 2 * P];
             }
         }
         for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
@@ -249,7 +252,7 @@ void setup_passes(vpx_plan *p) {
                 tg.push_back({0, GPair{i, 0, (int64_t)leaf_box[i] * P2, h * h}});
             }
         gemm_pass_upload_tables(F.l2m, l2m, 1, P2, KK, mixed);
-        F.l2m.add = 0;
+        F.l2m.add = 1;   // into the zeroed multipoles (the inner dimension may be split)
         gemm_pass_set_pairs(F.l2m, tg);
     }
     // M2M per parent level, L2L per child level
@@ -271,6 +274,10 @@ void setup_passes(vpx_plan *p) {
         gemm_pass_set_pairs(F.m2m[l], tm);
         gemm_pass_upload_tables(F.l2l[l], l2l, 4, P2, P2, mixed);
         gemm_pass_set_pairs(F.l2l[l], tl);
+        if (mixed) {   // the level chains: double-float row engine
+            gemm_pass_use_rows(F.m2m[l], m2m);
+            gemm_pass_use_rows(F.l2l[l], l2l);
+        }
     }
     // M2L and S2L
     {
@@ -326,15 +333,13 @@ void setup_passes(vpx_plan *p) {
         F.near.slices = s_near;
         for (GemmPass *g : {&F.l2m, &F.m2l, &F.s2l, &F.l2t, &F.m2t}) g->slices = s_far;
         for (int l = 0; l <= kMaxLevel; ++l) F.m2m[l].slices = F.l2l[l].slices = s_far;
-        gemm_prepare_device();
         gemm_tc_prepare_device();
+        gemm_frag_prepare_device();
         const int kp_f = (KK + 31) / 32 * 32, kp_m = (P2 + 31) / 32 * 32;
         F.fe_sl = dev_alloc<uint16_t>((size_t)p->opt.max_rhs * nl * kSlicesS * kp_f);
         F.fe_ex = dev_alloc<int32_t>((size_t)p->opt.max_rhs * nl);
         F.mp_sl = dev_alloc<uint16_t>((size_t)p->opt.max_rhs * nb * kSlicesS * kp_m);
         F.mp_ex = dev_alloc<int32_t>((size_t)p->opt.max_rhs * nb);
-        F.lo_sl = dev_alloc<uint16_t>((size_t)p->opt.max_rhs * nb * kSlicesS * kp_m);
-        F.lo_ex = dev_alloc<int32_t>((size_t)p->opt.max_rhs * nb);
     }
     for (GemmPass *g : {&F.l2m, &F.m2l, &F.s2l, &F.l2t, &F.m2t, &F.near}) g->status = p->wk.status;
     for (int l = 0; l <= kMaxLevel; ++l) F.m2m[l].status = F.l2l[l].status = p->wk.status;
@@ -357,8 +362,6 @@ void free_passes(vpx_plan *p) {
     dev_free(F.fe_ex);
     dev_free(F.mp_sl);
     dev_free(F.mp_ex);
-    dev_free(F.lo_sl);
-    dev_free(F.lo_ex);
 }
 
 // ------------------------------------------------------------ execute
@@ -378,9 +381,13 @@ void run_potential_passes(vpx_plan *p, const double *fe, int64_t ldfe, int nrhs,
     const int64_t ldm = (int64_t)nb * P2;
     const int kp_f = (KK + 31) / 32 * 32, kp_m = (P2 + 31) / 32 * 32;
     FmmPasses &F = p->fmm;
-    VecSet vf{fe, ldfe, KK, F.fe_sl, F.fe_ex, nl};
-    VecSet vm{mp, ldm, P2, F.mp_sl, F.mp_ex, nb};
-    VecSet vl{lo, ldm, P2, F.lo_sl, F.lo_ex, nb};
+    VecSet vf{fe, ldfe, KK, F.fe_sl, F.fe_ex, nl, kp_f};
+    // expansions along the level chains are sliced by the pass that reads them;
+    // the final multipoles once, for lists i and i-
+    VecSet vm{mp, ldm, P2, nullptr, nullptr, nb, 0};
+    VecSet vl{lo, ldm, P2, nullptr, nullptr, nb, 0};
+    VecSet vmf{mp, ldm, P2, F.mp_sl, F.mp_ex, nb, kp_m};
+    if (!mixed) vmf = vm;
     cudaStream_t aux = (cudaStream_t)p->aux_stream;
     ev_record_pass(p, 1, s);
     VPX_CUDA(cudaMemsetAsync(mp, 0, sizeof(double) * ldm * nrhs, s));
@@ -396,35 +403,31 @@ void run_potential_passes(vpx_plan *p, const double *fe, int64_t ldfe, int nrhs,
     // main stream: upward pass
     gemm_run(F.l2m, vf, mp, ldm, nrhs, mixed, s);
     ev_record_pass(p, 2, s);
-    for (int l = d.n_levels - 1; l >= 2; --l) {
-        if (mixed) slice_vectors(vm, d.level_start[l], d.level_start[l + 1] - d.level_start[l], P2, kp_m, nrhs, s);
-        if (l - 1 >= 2) gemm_run(F.m2m[l - 1], vm, mp, ldm, nrhs, mixed, s);
-    }
+    for (int l = d.n_levels - 1; l >= 3; --l) gemm_run(F.m2m[l - 1], vm, mp, ldm, nrhs, mixed, s);
+    if (mixed) slice_vectors(vmf, 0, nb, P2, kp_m, nrhs, s);
     // list i- on the auxiliary stream once the multipoles are final
     VPX_CUDA(cudaEventRecord((cudaEvent_t)p->ev_up, s));
     VPX_CUDA(cudaStreamWaitEvent(aux, (cudaEvent_t)p->ev_up, 0));
-    gemm_run(F.m2t, vm, v, ldv, nrhs, mixed, aux);
+    gemm_run(F.m2t, vmf, v, ldv, nrhs, mixed, aux);
     VPX_CUDA(cudaEventRecord((cudaEvent_t)p->ev_join, aux));
     ev_record_pass(p, 3, s);
-    gemm_run(F.m2l, vm, lo, ldm, nrhs, mixed, s);
+    gemm_run(F.m2l, vmf, lo, ldm, nrhs, mixed, s);
     gemm_run(F.s2l, vf, lo, ldm, nrhs, mixed, s);
     {
         int first = d.level_start[std::min(2, d.n_levels)], count = nb - first;
         if (count > 0) {
-            k_local_const<<<dim3((count + 127) / 128, nrhs), 128, 0, s>>>(first, count, P, d.vlist, d.xlist, d.box_level,
-                                                                           p->ext.leaf_level, d.leaf_box, mp, lo, ldm);
+            k_local_const<<<dim3((count + 7) / 8, nrhs), 256, 0, s>>>(first, count, P, std::log(2.0), d.vlist, d.xlist,
+                                                                       d.box_level, p->ext.leaf_level, d.leaf_box, mp,
+                                                                       lo, ldm);
             VPX_LAUNCH("k_local_const");
         }
     }
     ev_record_pass(p, 4, s);
-    for (int l = 2; l < d.n_levels; ++l) {
-        if (mixed) slice_vectors(vl, d.level_start[l], d.level_start[l + 1] - d.level_start[l], P2, kp_m, nrhs, s);
-        if (l + 1 < d.n_levels) gemm_run(F.l2l[l], vl, lo, ldm, nrhs, mixed, s);
-    }
+    for (int l = 2; l + 1 < d.n_levels; ++l) gemm_run(F.l2l[l], vl, lo, ldm, nrhs, mixed, s);
     ev_record_pass(p, 5, s);
     gemm_run(F.l2t, vl, v, ldv, nrhs, mixed, s);
-    k_leaf_const<<<dim3(nl, nrhs), 128, 0, s>>>(KK, P, d.near, d.wlist, p->ext.leaf_level, d.leaf_box, d.box_level, mp,
-                                                ldm, v, ldv);
+    k_leaf_const<<<dim3(nl, nrhs), 128, 0, s>>>(KK, P, std::log(2.0), d.near, d.wlist, p->ext.leaf_level, d.leaf_box,
+                                                d.box_level, mp, ldm, v, ldv);
     VPX_LAUNCH("k_leaf_const");
     ev_record_pass(p, 6, s);
     VPX_CUDA(cudaStreamWaitEvent(s, (cudaEvent_t)p->ev_join, 0));

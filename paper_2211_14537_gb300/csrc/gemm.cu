@@ -1,18 +1,20 @@
-// gemm.cu -- the two engines of the grouped table GEMM (see gemm.cuh).
+// gemm.cu -- the grouped table GEMM (gemm.cuh): FP64 engine, slicing of
+// vectors and tables for the exact-slice engines, pass setup and dispatch.
 //
 // FP64 form: 64 x 64 output tile per CTA, 4 x 4 FP64 register tile per thread,
 // 16-deep k stages in shared memory.
 //
 // Mixed form (exact bf16 slices): each table row i is scaled by 2^-e_i and
-// split into S = 5 or 6 integer slices of 7 bits (|a_1| <= 128, |a_k| <= 64), each
-// source vector likewise with its own exponent.  A product of two slices is
-// an integer of at most 14 bits; for an inner dimension <= 256 the sum of all
-// products of the same order d = k + l stays below 2^24, so the tensor core's
-// fp32 accumulation of each order is exact.  The orders are combined in
-// double-float fp32 (exact 2^-7 steps, TwoSum), converted once to FP64 and
-// scaled by scale_p 2^{e_i + e_v - 14}.  Truncation error ~ 2^-7S relative to
-// max|row| max|vector| (order sums stay below 8 * 2^20 < 2^24 for S <= 6).  Operand tiles are staged with cp.async (16-byte
-// copies, two stages); products use mma.sync m16n8k16 bf16 -> fp32.
+// split into S = 5 or 6 integer slices of 7 bits (|a_1| <= 128, |a_k| <= 64),
+// each source vector likewise with its own exponent (slice_math.cuh).  A
+// product of two slices is an integer; per inner index the products of one
+// order d = k + l sum to at most 2 * 128 * 64 + (S - 2) * 64^2 <= 2^15, so for
+// an inner dimension <= 512 every order sum stays below 2^24 and the tensor
+// cores' fp32 accumulation of it is exact.  The orders are combined in
+// double-float fp32 and scaled by scale_p 2^{e_i + e_v - 14}; the truncation
+// error is about 2^-7S relative to max|row| max|vector|.  Two engines run it:
+// tcgen05 with TMEM accumulators (gemm_tc.cu, the near field) and mma.sync
+// with tables in fragment order (gemm_frag.cu, every other pass).
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -21,7 +23,7 @@
 
 #include "dev_common.cuh"
 #include "gemm.cuh"
-#include "slice_epilogue.cuh"
+#include "slice_math.cuh"
 
 namespace vpx {
 
@@ -82,157 +84,6 @@ __global__ void __launch_bounds__(256) k_gemm_fp64(int M, int Kd, const double *
     }
 }
 
-// ------------------------------------------------------- exact bf16 engine
-
-constexpr int X_M = 64, X_N = 64, X_K = 32;
-constexpr int X_LD = X_K + 8;   // smem pitch (bf16): 80 bytes, 16-byte aligned rows, conflict-free fragments
-constexpr int X_STAGE = kSlicesS * (X_M + X_N) * X_LD;   // bf16 elements per stage (room for 6 slices)
-
-__device__ inline void cp_async16(void *smem, const void *gmem, int bytes) {
-    unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(bytes));
-}
-__device__ inline void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-__device__ inline void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
-__device__ inline void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::); }
-
-__device__ inline void mma16816(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
-        "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
-struct SlicedArgs {
-    int M, Mpad, Kpad, nvec;
-    const uint16_t *tslices;   // [ntab][S][Mpad][Kpad]
-    const int32_t *texpo;      // [ntab][Mpad]
-    const GTile *tiles;
-    const GPair *pairs;
-    const uint16_t *vslices;   // [rhs][nvec][S][Kpad]
-    const int32_t *vexpo;      // [rhs][nvec]
-    double *out;
-    int64_t ldo;
-    int add;
-};
-
-// 256 threads = 8 warps: 4 along M (16 rows) x 2 along N (32 pairs).  S slices used.
-template <int S>
-__global__ void __launch_bounds__(256) k_gemm_sliced(SlicedArgs a) {
-    extern __shared__ __align__(16) uint16_t xs[];
-    const GTile tile = a.tiles[blockIdx.x];
-    const int m0 = blockIdx.y * X_M, rhs = blockIdx.z;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int wm = warp & 3, wn = warp >> 2;
-    const int g = lane >> 2, tq = lane & 3;
-    const uint16_t *T = a.tslices + (size_t)tile.tab * kSlicesS * a.Mpad * a.Kpad;
-    const uint16_t *VS = a.vslices + (size_t)rhs * a.nvec * kSlicesS * a.Kpad;
-    // staging: 5 slices x 64 rows x 32 k of A and of B = 2 x 1280 16-byte chunks
-    auto stage = [&](int buf, int k0) {
-        uint16_t *As = xs + buf * X_STAGE;
-        uint16_t *Bs = As + kSlicesS * X_M * X_LD;
-        for (int c = threadIdx.x; c < S * X_M * 4; c += 256) {
-            int s = c / (X_M * 4), rem = c % (X_M * 4), r = rem >> 2, q = rem & 3;
-            int gr = m0 + r;
-            const uint16_t *src = T + ((size_t)s * a.Mpad + (gr < a.Mpad ? gr : 0)) * a.Kpad + k0 + q * 8;
-            cp_async16(As + (s * X_M + r) * X_LD + q * 8, src, gr < a.Mpad ? 16 : 0);
-        }
-        for (int c = threadIdx.x; c < S * X_N * 4; c += 256) {
-            int s = c / (X_N * 4), rem = c % (X_N * 4), n = rem >> 2, q = rem & 3;
-            bool ok = n < tile.count;
-            int v = ok ? a.pairs[tile.first + n].src : 0;
-            const uint16_t *src = VS + ((size_t)v * kSlicesS + s) * a.Kpad + k0 + q * 8;
-            cp_async16(Bs + (s * X_N + n) * X_LD + q * 8, src, ok ? 16 : 0);
-        }
-        cp_async_commit();
-    };
-    float acc[S][4][4];
-#pragma unroll
-    for (int d = 0; d < S; ++d)
-#pragma unroll
-        for (int t = 0; t < 4; ++t)
-#pragma unroll
-            for (int r = 0; r < 4; ++r) acc[d][t][r] = 0.f;
-    const int nk = a.Kpad / X_K;
-    stage(0, 0);
-    for (int kt = 0; kt < nk; ++kt) {
-        if (kt + 1 < nk) {
-            stage((kt + 1) & 1, (kt + 1) * X_K);
-            cp_async_wait1();
-        } else {
-            cp_async_wait0();
-        }
-        __syncthreads();
-        const uint16_t *As = xs + (kt & 1) * X_STAGE;
-        const uint16_t *Bs = As + kSlicesS * X_M * X_LD;
-#pragma unroll
-        for (int kk = 0; kk < X_K; kk += 16) {
-            uint32_t af[S][4];
-            const int ar = wm * 16 + g;
-#pragma unroll
-            for (int s = 0; s < S; ++s) {
-                const uint16_t *Ar = As + (s * X_M + ar) * X_LD + kk + tq * 2;
-                af[s][0] = *reinterpret_cast<const uint32_t *>(Ar);
-                af[s][1] = *reinterpret_cast<const uint32_t *>(Ar + 8 * X_LD);
-                af[s][2] = *reinterpret_cast<const uint32_t *>(Ar + 8);
-                af[s][3] = *reinterpret_cast<const uint32_t *>(Ar + 8 * X_LD + 8);
-            }
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                const int bn = wn * 32 + t * 8 + g;
-#pragma unroll
-                for (int l = 0; l < S; ++l) {
-                    const uint16_t *Br = Bs + (l * X_N + bn) * X_LD + kk + tq * 2;
-                    uint32_t bf[2];
-                    bf[0] = *reinterpret_cast<const uint32_t *>(Br);
-                    bf[1] = *reinterpret_cast<const uint32_t *>(Br + 8);
-#pragma unroll
-                    for (int s = 0; s < S; ++s)
-                        if (s + l < S) mma16816(acc[s + l][t], af[s], bf);
-                }
-            }
-        }
-        __syncthreads();
-    }
-    // epilogue
-    SliceScale pscale[4][2];
-    int64_t pdst[4][2];
-#pragma unroll
-    for (int t = 0; t < 4; ++t)
-#pragma unroll
-        for (int half = 0; half < 2; ++half) {
-            const int n = wn * 32 + t * 8 + tq * 2 + half;
-            pdst[t][half] = -1;
-            pscale[t][half] = SliceScale{0.f, 0.f, 0};
-            if (n < tile.count) {
-                const GPair pr = a.pairs[tile.first + n];
-                pscale[t][half] = slice_pair_scale(pr.scale, a.vexpo[(size_t)rhs * a.nvec + pr.src] - 2 * kSliceBitsB);
-                pdst[t][half] = rhs * a.ldo + pr.dst;
-            }
-        }
-#pragma unroll
-    for (int rr = 0; rr < 2; ++rr) {
-        const int i = m0 + wm * 16 + g + rr * 8;
-        if (i >= a.M) continue;
-        const int row_e = a.texpo[(size_t)tile.tab * a.Mpad + i];
-#pragma unroll
-        for (int t = 0; t < 4; ++t)
-#pragma unroll
-            for (int half = 0; half < 2; ++half) {
-                if (pdst[t][half] < 0) continue;
-                float acc_d[S], hi, lo;
-#pragma unroll
-                for (int d = 0; d < S; ++d) acc_d[d] = acc[d][t][rr * 2 + half];
-                slice_recombine<S>(acc_d, hi, lo);
-                const double val = slice_output(hi, lo, pscale[t][half], row_e);
-                double *o = a.out + pdst[t][half] + i;
-                if (a.add) atomicAdd(o, val);
-                else *o = val;
-            }
-    }
-}
-
 // ------------------------------------------------------------ slicing
 
 __device__ __host__ inline int slice_expo(double amax) {
@@ -242,35 +93,27 @@ __device__ __host__ inline int slice_expo(double amax) {
     return e;
 }
 
-// one block per (vector, rhs): exponent of max|v| and S slices over Kpad (zero padded)
-__global__ void k_slice_vec(const double *vbase, int64_t vld, int vstride, int first, int Kd, int Kpad, int nvec,
-                            uint16_t *slices, int32_t *expo) {
-    const int v = first + blockIdx.x, rhs = blockIdx.y;
+// One warp per (vector, rhs): exponent and slices (slice_math.cuh), zero padded to Kpad.
+__global__ void k_slice_vec(const double *vbase, int64_t vld, int vstride, int first, int count, int Kd, int Kpad,
+                            int nvec, uint16_t *slices, int32_t *expo) {
+    const int vi = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31, rhs = blockIdx.y;
+    if (vi >= count) return;
+    const int v = first + vi;
     const double *x = vbase + rhs * vld + (int64_t)v * vstride;
-    __shared__ double s_max[32];
-    double m = 0.0;
-    for (int j = threadIdx.x; j < Kd; j += blockDim.x) m = fmax(m, fabs(x[j]));
-    for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = m;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double mm = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mm = fmax(mm, s_max[w]);
-        s_max[0] = mm;
+    uint64_t mb = 0;
+    for (int j = lane; j < Kd; j += 32) {
+        const uint64_t t = slice_abs_bits(x[j]);
+        mb = t > mb ? t : mb;
     }
-    __syncthreads();
-    const int e = slice_expo(s_max[0]);
-    __nv_bfloat16 *out = reinterpret_cast<__nv_bfloat16 *>(slices) + ((size_t)rhs * nvec + v) * kSlicesS * Kpad;
-    for (int j = threadIdx.x; j < Kpad; j += blockDim.x) {
-        double y = (j < Kd) ? ldexp(x[j], -e) : 0.0;
-        for (int k = 0; k < kSlicesS; ++k) {
-            y = ldexp(y, kSliceBitsB);
-            double q = rint(y);
-            y -= q;
-            out[(size_t)k * Kpad + j] = __double2bfloat16(q);
-        }
+    const int e = slice_warp_expo(mb);
+    uint16_t *out = slices + ((size_t)rhs * nvec + v) * kSlicesS * Kpad;
+    for (int j = lane; j < Kpad; j += 32) {
+        uint16_t d[kSlicesS];
+        slice_digits((j < Kd) ? slice_fixed_point(x[j], e) : 0, d);
+#pragma unroll
+        for (int k = 0; k < kSlicesS; ++k) out[(size_t)k * Kpad + j] = d[k];
     }
-    if (threadIdx.x == 0) expo[(size_t)rhs * nvec + v] = e;
+    if (lane == 0) expo[(size_t)rhs * nvec + v] = e;
 }
 
 // ------------------------------------------------------------------ host
@@ -279,21 +122,32 @@ void gemm_pass_set_pairs(GemmPass &g, std::vector<std::pair<int, GPair>> &tagged
     std::stable_sort(tagged.begin(), tagged.end(),
                      [](const std::pair<int, GPair> &x, const std::pair<int, GPair> &y) { return x.first < y.first; });
     std::vector<GPair> pr;
-    std::vector<GTile> tl;
+    std::vector<GTile> tl, tf, tr;
+    const size_t npf = tagged.size() >= (size_t)kFragBigPass ? 32 : 8;
     size_t i = 0;
     while (i < tagged.size()) {
         size_t j = i;
         while (j < tagged.size() && tagged[j].first == tagged[i].first) ++j;
+        const int32_t base = (int32_t)pr.size();
         for (size_t k = i; k < j; k += kGemmTileN)
-            tl.push_back({tagged[i].first, (int32_t)(pr.size() + (k - i)), (int32_t)std::min<size_t>(kGemmTileN, j - k), 0});
+            tl.push_back({tagged[i].first, base + (int32_t)(k - i), (int32_t)std::min<size_t>(kGemmTileN, j - k), 0});
+        for (size_t k = i; k < j; k += npf)
+            tf.push_back({tagged[i].first, base + (int32_t)(k - i), (int32_t)std::min<size_t>(npf, j - k), 0});
+        for (size_t k = i; k < j; k += kRowsTileN)
+            tr.push_back({tagged[i].first, base + (int32_t)(k - i), (int32_t)std::min<size_t>(kRowsTileN, j - k), 0});
         for (size_t k = i; k < j; ++k) pr.push_back(tagged[k].second);
         i = j;
     }
     g.h_pairs = pr;
     g.n_pairs = (int)pr.size();
     g.n_tiles = (int)tl.size();
+    g.n_tiles_f = (int)tf.size();
+    g.n_tiles_r = (int)tr.size();
+    g.np_f = (int)npf;
     g.pairs = dev_upload(pr);
     g.tiles = dev_upload(tl);
+    g.tiles_f = dev_upload(tf);
+    g.tiles_r = dev_upload(tr);
 }
 
 static uint16_t bf16_bits_exact(double q) {
@@ -331,13 +185,48 @@ void gemm_pass_upload_tables(GemmPass &g, const std::vector<double> &tab, int nt
         }
     g.tslices = dev_upload(sl);
     g.texpo = dev_upload(ex);
+    // the same slices in mma.sync m16n8k16 A-fragment order: lane (g, q) of the
+    // fragment (m16 block mb, k16 block kb) holds rows mb*16+g, +8 and columns
+    // kb*16+2q, +1, +8, +9, two bf16 per 32-bit register (lower column low)
+    const int MB = g.Mpad / 16, KB = g.Kpad / 16;
+    std::vector<uint32_t> fr((size_t)ntab * kSlicesS * MB * KB * 32 * 4);
+    auto at = [&](int t, int s, int r, int c) -> uint32_t {
+        return sl[(((size_t)t * kSlicesS + s) * g.Mpad + r) * g.Kpad + c];
+    };
+    size_t o = 0;
+    for (int t = 0; t < ntab; ++t)
+        for (int s = 0; s < kSlicesS; ++s)
+            for (int mb = 0; mb < MB; ++mb)
+                for (int kb = 0; kb < KB; ++kb)
+                    for (int lane = 0; lane < 32; ++lane) {
+                        const int r0 = mb * 16 + (lane >> 2), c0 = kb * 16 + 2 * (lane & 3);
+                        fr[o++] = at(t, s, r0, c0) | at(t, s, r0, c0 + 1) << 16;
+                        fr[o++] = at(t, s, r0 + 8, c0) | at(t, s, r0 + 8, c0 + 1) << 16;
+                        fr[o++] = at(t, s, r0, c0 + 8) | at(t, s, r0, c0 + 9) << 16;
+                        fr[o++] = at(t, s, r0 + 8, c0 + 8) | at(t, s, r0 + 8, c0 + 9) << 16;
+                    }
+    g.tfrag = dev_upload(fr);
 }
 
-// Opt the sliced engine into its dynamic shared memory (once per device, at setup).
-void gemm_prepare_device() {
-    const size_t smem = 2 * X_STAGE * sizeof(uint16_t);
-    VPX_CUDA(cudaFuncSetAttribute(k_gemm_sliced<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    VPX_CUDA(cudaFuncSetAttribute(k_gemm_sliced<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+void gemm_rows_prepare(const GemmPass &g);
+
+bool gemm_pass_use_rows(GemmPass &g, const std::vector<double> &tab) {
+    if (g.M > 96 || (size_t)g.Kd * g.M * 8 > 160 * 1024) return false;
+    for (const GPair &p : g.h_pairs) {
+        int e = 0;
+        if (std::frexp(p.scale, &e) != 0.5) return false;
+    }
+    std::vector<float2> t((size_t)g.ntab * g.Kd * g.M);
+    for (int q = 0; q < g.ntab; ++q)
+        for (int i = 0; i < g.M; ++i)
+            for (int k = 0; k < g.Kd; ++k) {
+                const double v = tab[((size_t)q * g.M + i) * g.Kd + k];
+                const float h = (float)v;
+                t[((size_t)q * g.Kd + k) * g.M + i] = make_float2(h, (float)(v - (double)h));
+            }
+    g.tdfT = dev_upload(t);
+    gemm_rows_prepare(g);
+    return true;
 }
 
 void gemm_pass_free(GemmPass &g) {
@@ -346,50 +235,44 @@ void gemm_pass_free(GemmPass &g) {
     dev_free(g.texpo);
     dev_free(g.pairs);
     dev_free(g.tiles);
-    g.n_pairs = g.n_tiles = 0;
+    dev_free(g.tfrag);
+    dev_free(g.tiles_f);
+    dev_free(g.tiles_r);
+    dev_free(g.tdfT);
+    g.n_pairs = g.n_tiles = g.n_tiles_f = g.n_tiles_r = 0;
 }
 
 void gemm_tc_run(const GemmPass &g, const VecSet &vs, double *out, int64_t ldo, int nrhs, int *status, void *s);
+bool gemm_frag_eligible(const GemmPass &g, const VecSet &vs);
+void gemm_rows_run(const GemmPass &g, const VecSet &vs, double *out, int64_t ldo, int nrhs, void *s);
+void gemm_frag_run(const GemmPass &g, const VecSet &vs, double *out, int64_t ldo, int nrhs, void *s);
 
 void gemm_run(const GemmPass &g, const VecSet &vs, double *out, int64_t ldo, int nrhs, bool mixed, void *sv) {
     if (g.n_tiles == 0) return;
     cudaStream_t s = (cudaStream_t)sv;
-    const bool no_tc = getenv("VPX_NO_TC") != nullptr;
-    if (mixed && !no_tc && gemm_tc_eligible(g)) {
-        gemm_tc_run(g, vs, out, ldo, nrhs, g.status, sv);
-        return;
-    }
     if (!mixed) {
         dim3 grid(g.n_tiles, (g.M + G_M - 1) / G_M, nrhs);
         k_gemm_fp64<<<grid, 256, 0, s>>>(g.M, g.Kd, g.tab, g.tiles, g.pairs, vs.base, vs.ld, vs.stride, out, ldo, g.add);
         VPX_LAUNCH("k_gemm_fp64");
         return;
     }
-    SlicedArgs a;
-    a.M = g.M;
-    a.Mpad = g.Mpad;
-    a.Kpad = g.Kpad;
-    a.nvec = vs.nvec;
-    a.tslices = g.tslices;
-    a.texpo = g.texpo;
-    a.tiles = g.tiles;
-    a.pairs = g.pairs;
-    a.vslices = vs.slices;
-    a.vexpo = vs.expo;
-    a.out = out;
-    a.ldo = ldo;
-    a.add = g.add;
-    const size_t smem = 2 * X_STAGE * sizeof(uint16_t);
-    dim3 grid(g.n_tiles, (g.M + X_M - 1) / X_M, nrhs);
-    if (g.slices >= 6) k_gemm_sliced<6><<<grid, 256, smem, s>>>(a);
-    else k_gemm_sliced<5><<<grid, 256, smem, s>>>(a);
-    VPX_LAUNCH("k_gemm_sliced");
+    if (g.tdfT) {
+        gemm_rows_run(g, vs, out, ldo, nrhs, sv);
+        return;
+    }
+    const bool no_tc = getenv("VPX_NO_TC") != nullptr;   // read per call: lets a test compare the engines
+    if (!no_tc && vs.slices && gemm_tc_eligible(g)) {
+        gemm_tc_run(g, vs, out, ldo, nrhs, g.status, sv);
+        return;
+    }
+    if (!gemm_frag_eligible(g, vs)) fail(VPX_ERR_ARG, "no exact-slice engine covers this pass shape");
+    gemm_frag_run(g, vs, out, ldo, nrhs, sv);
 }
 
 void slice_vectors(const VecSet &vs, int first, int count, int Kd, int Kpad, int nrhs, void *sv) {
     if (count <= 0) return;
-    k_slice_vec<<<dim3(count, nrhs), 128, 0, (cudaStream_t)sv>>>(vs.base, vs.ld, vs.stride, first, Kd, Kpad, vs.nvec,
-                                                                 vs.slices, vs.expo);
+    k_slice_vec<<<dim3((count + 7) / 8, nrhs), 256, 0, (cudaStream_t)sv>>>(vs.base, vs.ld, vs.stride, first, count, Kd,
+                                                                            Kpad, vs.nvec, vs.slices, vs.expo);
     VPX_LAUNCH("k_slice_vec");
 }
 

@@ -15,7 +15,9 @@
 
 namespace vpx {
 
-constexpr int kGemmTileN = 64;   // pairs per tile
+constexpr int kGemmTileN = 64;   // pairs per tile (FP64 and tcgen05 engines)
+constexpr int kFragBigPass = 4096;   // fragment engine: 32 pairs per tile from this many pairs on, else 8
+constexpr int kRowsTileN = 4;        // pairs per tile (double-float row engine)
 constexpr int kSlicesS = 6;      // bf16 slices stored per operand in the mixed form (a pass uses 5 or 6)
 constexpr int kSliceBitsB = 7;   // bits per slice
 
@@ -39,9 +41,13 @@ struct GemmPass {
     const double *tab = nullptr;       // [ntab][M][Kd] FP64 (row-major)
     const uint16_t *tslices = nullptr; // [ntab][S][Mpad][Kpad] bf16 bits (mixed form)
     const int32_t *texpo = nullptr;    // [ntab][Mpad] row exponents (mixed form)
+    const uint32_t *tfrag = nullptr;   // [ntab][S][Mpad/16][Kpad/16][32 lanes][4] mma.sync A fragments (mixed form)
     GPair *pairs = nullptr;
-    GTile *tiles = nullptr;
-    int n_pairs = 0, n_tiles = 0;
+    GTile *tiles = nullptr;            // kGemmTileN pairs each
+    GTile *tiles_f = nullptr;          // np_f pairs each (fragment engine)
+    GTile *tiles_r = nullptr;          // kRowsTileN pairs each (row engine)
+    const void *tdfT = nullptr;        // [ntab][Kd][M] double-float (float hi, lo): the row engine runs the pass
+    int n_pairs = 0, n_tiles = 0, n_tiles_f = 0, np_f = 8, n_tiles_r = 0;
     std::vector<GPair> h_pairs;        // host copy (setup)
 };
 
@@ -49,18 +55,23 @@ struct GemmPass {
 void gemm_pass_set_pairs(GemmPass &g, std::vector<std::pair<int, GPair>> &tagged);   // (table, pair)
 void gemm_pass_upload_tables(GemmPass &g, const std::vector<double> &tab, int ntab, int M, int Kd, bool mixed);
 void gemm_pass_free(GemmPass &g);
-void gemm_prepare_device();
+// Hand a mixed-form pass to the double-float row engine (gemm_rows.cu) when
+// its rows fit one CTA and every pair scale is a power of two; returns whether.
+bool gemm_pass_use_rows(GemmPass &g, const std::vector<double> &tab);
 // tcgen05 engine (gemm_tc.cu): 5-slice passes whose rows tile by 128
 bool gemm_tc_eligible(const GemmPass &g);
 void gemm_tc_prepare_device();
+// fragment engine (gemm_frag.cu)
+void gemm_frag_prepare_device();
 
 struct VecSet {                        // source vectors of a pass
     const double *base = nullptr;      // vector v of rhs r at base + r*ld + v*stride
     int64_t ld = 0;
     int stride = 0;
-    uint16_t *slices = nullptr;        // mixed form: [rhs][nvec][S][Kpad]
+    uint16_t *slices = nullptr;        // mixed form: [rhs][nvec][S][Kpad], or null: sliced where used
     int32_t *expo = nullptr;           // [rhs][nvec]
     int nvec = 0;
+    int kpad = 0;                      // inner length of the stored slices
 };
 
 // Launches (stream s): run a pass on nrhs right-hand sides.

@@ -19,7 +19,7 @@
 
 #include "dev_common.cuh"
 #include "gemm.cuh"
-#include "slice_epilogue.cuh"
+#include "slice_math.cuh"
 
 namespace vpx {
 

@@ -44,6 +44,14 @@ struct DevExt {
     double *pinv = nullptr;       // all P_S
     double *A_grid = nullptr;     // [Kbar^2][NG] rows of the universal A at X_Sbar
     double *cheb_inv = nullptr;   // [Kbar][Kbar]
+    // double-float copies (hi, lo float pairs) for the mixed form
+    struct DfPair { float hi, lo; };
+    DfPair *pinv_df = nullptr, *cheb_df = nullptr;
+    GemmPass grid_pass;                  // A_{X_Sbar,G} c for all cut leaves (one table)
+    int n_tgt = 0, max_interior = 0;
+    int32_t *tgt_cut = nullptr, *tgt_leaf = nullptr;   // extension targets: cut leaves, then their lists
+    double *cbuf = nullptr, *Fall = nullptr;           // [max_rhs][ncut][NG], [max_rhs][ncut][Kbar^2]
+    DfPair *alpha = nullptr;                           // [max_rhs][ncut][Kbar^2] truncated Chebyshev coefficients
     int32_t *leaf_level = nullptr, *leaf_ix = nullptr, *leaf_iy = nullptr;
     int32_t *owned_flag_dev = nullptr;   // [n_leaves] 1 if the leaf is in an extension list
 };
@@ -65,8 +73,8 @@ struct FmmPasses {                // every contraction of the box FMM as a group
     GemmPass l2m, m2l, s2l, l2t, m2t, near;
     GemmPass m2m[kMaxLevel + 1];  // parents at level l
     GemmPass l2l[kMaxLevel + 1];  // parents at level l
-    uint16_t *fe_sl = nullptr, *mp_sl = nullptr, *lo_sl = nullptr;   // exact bf16 slices (mixed form)
-    int32_t *fe_ex = nullptr, *mp_ex = nullptr, *lo_ex = nullptr;
+    uint16_t *fe_sl = nullptr, *mp_sl = nullptr;   // exact bf16 slices of leaf values, multipoles (mixed form)
+    int32_t *fe_ex = nullptr, *mp_ex = nullptr;
 };
 
 }  // namespace vpx

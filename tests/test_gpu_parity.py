@@ -198,10 +198,16 @@ def _extension_bounds(tree, dom, meta):
     return kappa
 
 
+@pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("name", ["disk_l3_k8", "disk_l4_k8", "disk_l3_k16", "starfish_k8_adaptive"])
-def test_extension_parity(V, name):
+def test_extension_parity(V, name, precision):
+    """FP64 form (precision 0) and the mixed form's double-float extension
+    (precision 1): within 64 unit roundoffs of the arithmetic times the
+    forward-error factor kappa.  Machine epsilon is 2^-52 in FP64; a
+    double-float pair carries 48 significant bits, epsilon 2^-47."""
     wl = CASES[name]()
-    plan = make_plan(V, wl)
+    plan = make_plan(V, wl, precision=precision)
+    eps = EPS if precision == 0 else 2.0 ** -47
     tree = O.build_tree(wl.domain, wl.opts, wl.sources[0])
     pts, meta = O.stencil_points(tree, wl.domain)
     f = wl.sources[0](pts)
@@ -220,7 +226,7 @@ def test_extension_parity(V, name):
         elif tree.cls[i] == O.EXTERIOR and tree.owner[i] < 0:
             assert np.all(got[i] == 0.0)
         else:
-            tol = 64 * EPS * max(kappa[i], 1.0) * fmax
+            tol = 64 * eps * max(kappa[i], 1.0) * fmax
             assert np.max(np.abs(got[i] - want[i, 0])) <= tol, (i, kappa[i])
 
 
