@@ -233,11 +233,13 @@ static void run_extension(vpx_plan *p, const double *f, int nrhs, int64_t ldf, d
             DevExt &x = p->ext;
             const int Kb2 = p->st.Kbar * p->st.Kbar;
             const int64_t ldc = (int64_t)x.ncut * p->st.NG, ldF = (int64_t)x.ncut * Kb2;
-            launch_ext_coeff_df(a, x.ncut, x.max_interior, nrhs, x.cbuf, ldc, s);
+            a.pinv_df_off = x.pinv_df_off;
+            launch_ext_coeff_df(a, x.ncut, x.max_interior, nrhs, x.cbuf, ldc, p->wk.status, s);
             VecSet vc{x.cbuf, ldc, p->st.NG, nullptr, nullptr, x.ncut, 0};
             gemm_run(x.grid_pass, vc, x.Fall, ldF, nrhs, true, s);
-            launch_ext_eval_df(a, x.ncut, x.n_tgt, x.tgt_cut, x.tgt_leaf, x.Fall, ldF,
-                               reinterpret_cast<float2 *>(x.alpha), nrhs, s);
+            launch_ext_eval_df(a, x.ncut, x.n_tgt, x.tgt_cut, x.tgt_leaf,
+                               reinterpret_cast<const ExtTgtGeo *>(x.tgt_geo), x.Fall, ldF,
+                               reinterpret_cast<float2 *>(x.alpha), nrhs, p->wk.status, s);
         } else {
             k_extend<<<dim3(p->ext.ncut, nrhs), 256, smem, s>>>(a);
             VPX_LAUNCH("k_extend");

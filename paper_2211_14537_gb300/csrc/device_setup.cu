@@ -479,10 +479,25 @@ void device_setup(vpx_plan *p) {
             const float h = (float)v;
             return DevExt::DfPair{h, (float)(v - (double)h)};
         };
-        std::vector<DevExt::DfPair> pd(st.pinv.size()), cd(st.cheb_inv.size());
-        for (size_t i = 0; i < st.pinv.size(); ++i) pd[i] = split(st.pinv[i]);
+        // A_I^+ rows padded to an even length so that every row block is 16-byte aligned
+        std::vector<int64_t> poff(st.cut_leaf.size(), 0);
+        size_t tot = 0;
+        for (size_t c = 0; c < st.cut_leaf.size(); ++c) {
+            poff[c] = (int64_t)tot;
+            tot += (size_t)st.NG * ((st.n_interior[c] + 1) & ~1);
+        }
+        // the Chebyshev transform padded to an even length (16-byte multiple) likewise
+        std::vector<DevExt::DfPair> pd(tot, DevExt::DfPair{0.f, 0.f}), cd((st.cheb_inv.size() + 1) & ~(size_t)1,
+                                                                           DevExt::DfPair{0.f, 0.f});
+        for (size_t c = 0; c < st.cut_leaf.size(); ++c) {
+            const int nI = st.n_interior[c], nIp = (nI + 1) & ~1;
+            for (int k = 0; k < st.NG; ++k)
+                for (int i = 0; i < nI; ++i)
+                    pd[poff[c] + (size_t)k * nIp + i] = split(st.pinv[st.pinv_off[c] + (size_t)k * nI + i]);
+        }
         for (size_t i = 0; i < st.cheb_inv.size(); ++i) cd[i] = split(st.cheb_inv[i]);
         x.pinv_df = dev_upload(pd);
+        x.pinv_df_off = dev_upload(poff);
         x.cheb_df = dev_upload(cd);
         // A_{X_Sbar,G} c of every cut leaf as one table pass; targets of the Chebyshev stage
         const int Kb2 = st.Kbar * st.Kbar;
@@ -507,10 +522,24 @@ void device_setup(vpx_plan *p) {
         x.n_tgt = (int)tc.size();
         x.tgt_cut = dev_upload(tc);
         x.tgt_leaf = dev_upload(tl);
+        // target geometry in the coordinates of the cut leaf's Sbar (half side r):
+        // z = offset + scale * t for the leaf nodes t on [-1, 1]
+        std::vector<double> geo((size_t)4 * x.n_tgt);
+        for (int t = 0; t < x.n_tgt; ++t) {
+            const Leaf &S = p->tree.leaves[st.cut_leaf[tc[t]]], &T = p->tree.leaves[tl[t]];
+            const double sS = std::ldexp(1.0, -S.level), sT = std::ldexp(1.0, -T.level), r = 1.5 * sS;
+            const double cxS = -0.5 + (S.ix + 0.5) * sS, cyS = -0.5 + (S.iy + 0.5) * sS;
+            const double cxT = -0.5 + (T.ix + 0.5) * sT, cyT = -0.5 + (T.iy + 0.5) * sT;
+            geo[4 * t] = (cxT - cxS) / r;
+            geo[4 * t + 1] = (cyT - cyS) / r;
+            geo[4 * t + 2] = 0.5 * sT / r;
+            geo[4 * t + 3] = (tl[t] == st.cut_leaf[tc[t]]) ? 1.0 : 0.0;
+        }
+        x.tgt_geo = dev_upload(geo);
         for (int c = 0; c < x.ncut; ++c) x.max_interior = std::max(x.max_interior, st.n_interior[c]);
         x.cbuf = dev_alloc<double>((size_t)p->opt.max_rhs * x.ncut * st.NG);
         x.Fall = dev_alloc<double>((size_t)p->opt.max_rhs * x.ncut * Kb2);
-        x.alpha = dev_alloc<DevExt::DfPair>((size_t)p->opt.max_rhs * x.ncut * Kb2);
+        x.alpha = dev_alloc<DevExt::DfPair>((size_t)p->opt.max_rhs * x.ncut * ((Kb2 + 1) & ~1));
     }
     // boundary
     p->wk.bdry_leaf = dev_upload(p->bdry_leaf);
@@ -522,6 +551,7 @@ void device_setup(vpx_plan *p) {
     w.mpole = dev_alloc<double>((size_t)w.max_rhs * d.n_boxes * 2 * p->P);
     w.local = dev_alloc<double>((size_t)w.max_rhs * d.n_boxes * 2 * p->P);
     w.status = dev_alloc<int>(1);
+    x.grid_pass.status = w.status;
     VPX_CUDA(cudaMemset(w.status, 0, sizeof(int)));
     setup_near_pairs(p);
     setup_passes(p);
@@ -544,7 +574,7 @@ void device_free(vpx_plan *p) {
     dev_free(x.cut_leaf); dev_free(x.n_interior); dev_free(x.grid_src); dev_free(x.node_src);
     dev_free(x.stencil_off); dev_free(x.pinv_off); dev_free(x.reg_leaf_off); dev_free(x.owned_off);
     dev_free(x.owned); dev_free(x.pinv); dev_free(x.A_grid); dev_free(x.cheb_inv);
-    dev_free(x.pinv_df); dev_free(x.cheb_df);
+    dev_free(x.pinv_df); dev_free(x.cheb_df); dev_free(x.pinv_df_off); dev_free(x.tgt_geo);
     gemm_pass_free(x.grid_pass);
     dev_free(x.tgt_cut); dev_free(x.tgt_leaf); dev_free(x.cbuf); dev_free(x.Fall); dev_free(x.alpha);
     dev_free(x.leaf_level); dev_free(x.leaf_ix); dev_free(x.leaf_iy); dev_free(x.owned_flag_dev);

@@ -9,12 +9,19 @@
 
 namespace vpx {
 
+// an extension target in the coordinates of its cut leaf's Sbar: node
+// coordinate z = (ox or oy) + sc * t for the leaf nodes t on [-1, 1]
+struct ExtTgtGeo {
+    double ox, oy, sc, self;   // self: 1 for the cut leaf itself
+};
+
 struct ExtArgs {
     int K, Kbar, NG;
     const int32_t *cut_leaf, *n_interior, *grid_src, *node_src, *owned_off, *owned;
     const int64_t *stencil_off, *pinv_off;
     const double *pinv, *A_grid, *cheb_inv, *tnodes;
-    const float2 *pinv_df;      // P_S as double-float (hi, lo), same layout as pinv
+    const float2 *pinv_df;      // P_S as double-float (hi, lo), rows padded to an even length
+    const int64_t *pinv_df_off; // start of each cut leaf's P_S in pinv_df (even)
     const float2 *cheb_df;      // [Kbar][Kbar] double-float
     const int32_t *leaf_level, *leaf_ix, *leaf_iy;
     const double *f;
@@ -28,8 +35,9 @@ struct ExtArgs {
 // stage for every target leaf (tgt_cut[t], tgt_leaf[t])
 void extend_df_prepare(int max_interior, int K, int Kbar);
 void launch_ext_coeff_df(const ExtArgs &a, int ncut, int max_interior, int nrhs, double *cbuf, int64_t ldc,
-                         cudaStream_t s);
+                         int *status, cudaStream_t s);
 void launch_ext_eval_df(const ExtArgs &a, int ncut, int n_tgt, const int32_t *tgt_cut, const int32_t *tgt_leaf,
-                        const double *Fall, int64_t ldF, float2 *alpha, int nrhs, cudaStream_t s);
+                        const ExtTgtGeo *geo, const double *Fall, int64_t ldF, float2 *alpha, int nrhs, int *status,
+                        cudaStream_t s);
 
 }  // namespace vpx

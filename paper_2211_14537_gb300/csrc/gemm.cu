@@ -216,13 +216,14 @@ bool gemm_pass_use_rows(GemmPass &g, const std::vector<double> &tab) {
         int e = 0;
         if (std::frexp(p.scale, &e) != 0.5) return false;
     }
-    std::vector<float2> t((size_t)g.ntab * g.Kd * g.M);
+    const size_t ts = ((size_t)g.Kd * g.M + 1) / 2 * 2;   // table stride: a multiple of 16 bytes
+    std::vector<float2> t((size_t)g.ntab * ts, make_float2(0.f, 0.f));
     for (int q = 0; q < g.ntab; ++q)
         for (int i = 0; i < g.M; ++i)
             for (int k = 0; k < g.Kd; ++k) {
                 const double v = tab[((size_t)q * g.M + i) * g.Kd + k];
                 const float h = (float)v;
-                t[((size_t)q * g.Kd + k) * g.M + i] = make_float2(h, (float)(v - (double)h));
+                t[q * ts + (size_t)k * g.M + i] = make_float2(h, (float)(v - (double)h));
             }
     g.tdfT = dev_upload(t);
     gemm_rows_prepare(g);

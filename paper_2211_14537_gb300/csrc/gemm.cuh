@@ -17,7 +17,7 @@ namespace vpx {
 
 constexpr int kGemmTileN = 64;   // pairs per tile (FP64 and tcgen05 engines)
 constexpr int kFragBigPass = 4096;   // fragment engine: 32 pairs per tile from this many pairs on, else 8
-constexpr int kRowsTileN = 4;        // pairs per tile (double-float row engine)
+constexpr int kRowsTileN = 1;        // pairs per tile (double-float row engine)
 constexpr int kSlicesS = 6;      // bf16 slices stored per operand in the mixed form (a pass uses 5 or 6)
 constexpr int kSliceBitsB = 7;   // bits per slice
 

@@ -20,6 +20,7 @@
 
 #include <algorithm>
 
+#include "bulk.cuh"
 #include "dev_common.cuh"
 #include "gemm.cuh"
 #include "slice_math.cuh"
@@ -46,6 +47,8 @@ struct FragArgs {
     double *out;
     int64_t ldo;
     int add;
+    int bulk;                      // on-the-fly vectors may be staged by TMA bulk copies (16-byte aligned)
+    int *status;
 };
 
 __device__ inline void frag_cp16(void *smem, const void *gmem, int bytes) {
@@ -70,6 +73,7 @@ __global__ void __launch_bounds__(192, 2) k_gemm_frag(FragArgs a) {
     __shared__ GPair s_pr[NP];
     __shared__ int s_ve[NP];
     __shared__ SliceScale s_ps[NP];
+    __shared__ __align__(8) uint64_t s_bar;
     const int per_tile = a.rb * a.ks;
     const int ti = blockIdx.x / per_tile, rem = blockIdx.x % per_tile;
     const int rbi = rem / a.ks, ksi = rem % a.ks;
@@ -86,32 +90,58 @@ __global__ void __launch_bounds__(192, 2) k_gemm_frag(FragArgs a) {
     uint4 af[S];
 #pragma unroll
     for (int s = 0; s < S; ++s) af[s] = __ldg(Af + s * sstride);
+    // the rows' exponents do not depend on the vectors either
+    int row_e[2];
+#pragma unroll
+    for (int rr = 0; rr < 2; ++rr) {
+        const int i = mb * 16 + (lane >> 2) + rr * 8;
+        row_e[rr] = (mb < a.MB && i < a.M) ? a.texpo[(size_t)tile.tab * a.Mpad + i] : 0;
+    }
     for (int n = threadIdx.x; n < NP; n += blockDim.x)
         s_pr[n] = (n < tile.count) ? a.pairs[tile.first + n] : GPair{0, 0, -1, 0.0};
+    if (FLY && threadIdx.x == 0) bulk_bar_init(&s_bar);
     __syncthreads();
 
     // ---- stage the source vectors' slices for k in [16 kb0, 16 (kb0 + nkb))
     if (FLY) {
-        // all threads fetch the NP vectors at once, then one warp per vector
-        // takes its exponent and slices from shared memory
+        // the NP vectors arrive at once (TMA bulk copies when aligned), then one
+        // warp per vector takes its exponent and slices from shared memory
         double *xs = reinterpret_cast<double *>(bs + (size_t)S * NP * ldb);
-        for (int c = threadIdx.x; c < NP * a.Kd; c += blockDim.x) {
-            const int n = c / a.Kd, j = c % a.Kd;
-            xs[c] = (n < tile.count) ? a.vbase[rhs * a.vld + (int64_t)s_pr[n].src * a.vstride + j] : 0.0;
+        bool ok = true;
+        if (a.bulk) {
+            if (threadIdx.x == 0) {
+                const uint32_t bytes = (uint32_t)(a.Kd * sizeof(double));
+                bulk_expect(&s_bar, bytes * tile.count);
+                for (int n = 0; n < tile.count; ++n)
+                    bulk_copy(xs + (size_t)n * a.Kd, a.vbase + rhs * a.vld + (int64_t)s_pr[n].src * a.vstride, bytes,
+                              &s_bar);
+            }
+            ok = __syncthreads_and(bulk_wait(&s_bar, 0));
+        } else {
+            for (int c = threadIdx.x; c < tile.count * a.Kd; c += blockDim.x) {
+                const int n = c / a.Kd, j = c % a.Kd;
+                xs[c] = a.vbase[rhs * a.vld + (int64_t)s_pr[n].src * a.vstride + j];
+            }
+            __syncthreads();
         }
-        __syncthreads();
+        if (!ok) {
+            if (threadIdx.x == 0) set_status(a.status, VPX_ERR_TIMEOUT);
+            return;
+        }
         for (int n = warp; n < NP; n += nwarp) {
+            const bool live = n < tile.count;
             const double *x = xs + (size_t)n * a.Kd;
             uint64_t m = 0;
-            for (int j = lane; j < a.Kd; j += 32) {
-                const uint64_t t = slice_abs_bits(x[j]);
-                m = t > m ? t : m;
-            }
+            if (live)
+                for (int j = lane; j < a.Kd; j += 32) {
+                    const uint64_t t = slice_abs_bits(x[j]);
+                    m = t > m ? t : m;
+                }
             const int e = slice_warp_expo(m);
             for (int j = lane; j < nkb * 16; j += 32) {
                 const int k = kb0 * 16 + j;
                 uint16_t d[kSlicesS];
-                slice_digits(k < a.Kd ? slice_fixed_point(x[k], e) : 0, d);
+                slice_digits((live && k < a.Kd) ? slice_fixed_point(x[k], e) : 0, d);
 #pragma unroll
                 for (int s = 0; s < S; ++s) bs[(s * NP + n) * ldb + j] = d[s];
             }
@@ -174,7 +204,6 @@ __global__ void __launch_bounds__(192, 2) k_gemm_frag(FragArgs a) {
     for (int rr = 0; rr < 2; ++rr) {
         const int i = mb * 16 + g + rr * 8;
         if (i >= a.M) continue;
-        const int row_e = a.texpo[(size_t)tile.tab * a.Mpad + i];
 #pragma unroll
         for (int t = 0; t < NT; ++t)
 #pragma unroll
@@ -186,7 +215,7 @@ __global__ void __launch_bounds__(192, 2) k_gemm_frag(FragArgs a) {
 #pragma unroll
                 for (int d = 0; d < S; ++d) acc_d[d] = acc[d][t][rr * 2 + half];
                 slice_recombine<S>(acc_d, hi, lo);
-                const double val = slice_output(hi, lo, s_ps[n], row_e);
+                const double val = slice_output(hi, lo, s_ps[n], row_e[rr]);
                 double *o = a.out + rhs * a.ldo + dst + i;
                 if (a.add) atomicAdd(o, val);
                 else *o = val;
@@ -257,6 +286,9 @@ void gemm_frag_run(const GemmPass &g, const VecSet &vs, double *out, int64_t ldo
     a.out = out;
     a.ldo = ldo;
     a.add = g.add;
+    a.status = g.status;
+    a.bulk = fly && (a.Kd % 2 == 0) && (vs.stride % 2 == 0) && (vs.ld % 2 == 0) &&
+             (reinterpret_cast<uintptr_t>(vs.base) % 16 == 0);
     if (a.ks > 1 && !a.add) fail(VPX_ERR_ARG, "a pass split along its inner dimension must accumulate");
     if (!fly && vs.kpad < g.Kpad) fail(VPX_ERR_ARG, "pre-sliced vectors shorter than the table's inner dimension");
     const int S = g.slices >= 6 ? 6 : 5;

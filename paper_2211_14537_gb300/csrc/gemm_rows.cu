@@ -8,6 +8,7 @@
 // share of the inner index, with one double-float accumulator per pair
 // (independent chains).  About 48 significant bits, more than the 42-bit
 // slices of the tensor-core passes keep.
+#include "bulk.cuh"
 #include "dev_common.cuh"
 #include "df32.cuh"
 #include "gemm.cuh"
@@ -15,37 +16,43 @@
 namespace vpx {
 
 constexpr int R_NPB = kRowsTileN;
+static_assert(R_NPB == 1, "the row engine takes one pair per CTA");
 constexpr int R_KG = 4;   // k groups per CTA (rows <= 96)
 
 // CTA = R_KG groups of ceil32(M) threads; group g sums k = g, g + R_KG, ...
-// for its row; the table and the source vectors are staged in shared memory
-// first (one coalesced copy each), the group partials are added at the end.
-__global__ void __launch_bounds__(384) k_gemm_rows_df(int M, int Kd, int kg, const float2 *tT, const GTile *tiles,
-                                                      const GPair *pairs, const double *vbase, int64_t vld,
-                                                      int vstride, double *out, int64_t ldo, int add) {
+// for its row.  The table arrives in shared memory by one TMA bulk copy while
+// the threads fetch and split the source vector; the group partials are added
+// at the end.
+__global__ void __launch_bounds__(384) k_gemm_rows_df(int M, int Kd, int kg, int64_t tstride, const float2 *tT,
+                                                      const GTile *tiles, const GPair *pairs, const double *vbase,
+                                                      int64_t vld, int vstride, double *out, int64_t ldo, int add,
+                                                      int *status) {
     extern __shared__ __align__(16) float2 rsm[];   // table [Kd][M], vectors [R_NPB][Kd], partials [kg][R_NPB][M]
-    __shared__ GPair s_pr[R_NPB];
+    __shared__ __align__(8) uint64_t s_bar;
     __shared__ int s_e[R_NPB];
-    float2 *Ts = rsm, *vsm = Ts + (size_t)Kd * M, *part = vsm + R_NPB * Kd;
-    const GTile tile = tiles[blockIdx.x];
+    float2 *Ts = rsm, *vsm = Ts + tstride, *part = vsm + R_NPB * Kd;
     const int rhs = blockIdx.y, nt = blockDim.x;
-    const float2 *T = tT + (size_t)tile.tab * Kd * M;
-    for (int c = threadIdx.x; c < Kd * M; c += nt) Ts[c] = __ldg(T + c);
-    if (threadIdx.x < R_NPB) {
-        const GPair pr = (threadIdx.x < tile.count) ? pairs[tile.first + threadIdx.x] : GPair{0, 0, -1, 0.0};
-        s_pr[threadIdx.x] = pr;
+    // one pair per CTA, pairs in tile order: the pair and its tile load side by side
+    const GPair pr = pairs[blockIdx.x];
+    const GTile tile = tiles[blockIdx.x];
+    if (threadIdx.x == 0) {
+        bulk_bar_init(&s_bar);
+        const uint32_t bytes = (uint32_t)(tstride * sizeof(float2));
+        bulk_expect(&s_bar, bytes);
+        bulk_copy(Ts, tT + (size_t)tile.tab * tstride, bytes, &s_bar);
         int e = 0;
         frexp(pr.scale, &e);   // the pair scales of these passes are powers of two: 2^(e-1)
-        s_e[threadIdx.x] = e - 1;
+        s_e[0] = e - 1;
+    }
+    for (int k = threadIdx.x; k < Kd; k += nt) {
+        const df32 v = df_split_bits(vbase[rhs * vld + (int64_t)pr.src * vstride + k]);
+        vsm[k] = make_float2(v.hi, v.lo);
     }
     __syncthreads();
-    for (int c = threadIdx.x; c < R_NPB * Kd; c += nt) {
-        const int n = c / Kd, k = c % Kd;
-        const double x = (n < tile.count) ? vbase[rhs * vld + (int64_t)s_pr[n].src * vstride + k] : 0.0;
-        const df32 v = df_split_bits(x);
-        vsm[c] = make_float2(v.hi, v.lo);
+    if (!__syncthreads_and(bulk_wait(&s_bar, 0))) {   // every thread leaves together on a timeout
+        if (threadIdx.x == 0) set_status(status, VPX_ERR_TIMEOUT);
+        return;
     }
-    __syncthreads();
     const int mr = nt / kg, g = threadIdx.x / mr, i = threadIdx.x % mr;
     if (i < M) {
         df32 acc[R_NPB];
@@ -68,21 +75,22 @@ __global__ void __launch_bounds__(384) k_gemm_rows_df(int M, int Kd, int kg, con
     __syncthreads();
     for (int c = threadIdx.x; c < R_NPB * M; c += nt) {
         const int j = c / M, r = c % M;
-        if (j >= tile.count) continue;
         df32 s{0.f, 0.f};
         for (int q = 0; q < kg; ++q) {
             const float2 v = part[((size_t)q * R_NPB + j) * M + r];
             s = df_add(s, df32{v.x, v.y});
         }
         const double val = df_to_f64_scaled(s, s_e[j]);
-        double *o = out + rhs * ldo + s_pr[j].dst + r;
+        double *o = out + rhs * ldo + pr.dst + r;
         if (add) atomicAdd(o, val);
         else *o = val;
     }
 }
 
+static int64_t rows_tstride(int M, int Kd) { return ((int64_t)Kd * M + 1) / 2 * 2; }   // 16-byte multiple
+
 static size_t rows_smem(int M, int Kd, int kg) {
-    return sizeof(float2) * ((size_t)Kd * M + (size_t)R_NPB * Kd + (size_t)kg * R_NPB * M);
+    return sizeof(float2) * ((size_t)rows_tstride(M, Kd) + (size_t)R_NPB * Kd + (size_t)kg * R_NPB * M);
 }
 
 void gemm_rows_prepare(const GemmPass &g) {
@@ -97,9 +105,10 @@ void gemm_rows_run(const GemmPass &g, const VecSet &vs, double *out, int64_t ldo
     const int kg = g.M <= 96 ? R_KG : 1;
     const int threads = (g.M + 31) / 32 * 32 * kg;
     if (threads > 384) fail(VPX_ERR_ARG, "row engine: too many table rows");
+    if (g.n_tiles_r != g.n_pairs) fail(VPX_ERR_ARG, "row engine: one pair per tile expected");
     k_gemm_rows_df<<<dim3(g.n_tiles_r, nrhs), threads, rows_smem(g.M, g.Kd, kg), (cudaStream_t)s>>>(
-        g.M, g.Kd, kg, reinterpret_cast<const float2 *>(g.tdfT), g.tiles_r, g.pairs, vs.base, vs.ld, vs.stride, out,
-        ldo, g.add);
+        g.M, g.Kd, kg, rows_tstride(g.M, g.Kd), reinterpret_cast<const float2 *>(g.tdfT), g.tiles_r, g.pairs, vs.base,
+        vs.ld, vs.stride, out, ldo, g.add, g.status);
     VPX_LAUNCH("k_gemm_rows_df");
 }
 

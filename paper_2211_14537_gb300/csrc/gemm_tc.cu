@@ -86,12 +86,14 @@ __global__ void __launch_bounds__(256, 1) k_gemm_tc(TcArgs a) {
     __shared__ int s_fail;
     __shared__ SliceScale s_ps[TC_N];
     __shared__ int64_t s_pdst[TC_N];
+    __shared__ int s_src[TC_N];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const GTile tile = a.tiles[blockIdx.x];
     const int m0 = blockIdx.y * TC_M, rhs = blockIdx.z;
     const uint16_t *T = a.tslices + (size_t)tile.tab * kSlicesS * a.Mpad * a.Kpad;
     const uint16_t *VS = a.vslices + (size_t)rhs * a.nvec * kSlicesS * a.Kpad;
 
+    if (tid < TC_N) s_src[tid] = (tid < tile.count) ? a.pairs[tile.first + tid].src : 0;
     if (tid == 0) {
         s_fail = 0;
         for (int i = 0; i < TC_STAGES; ++i)
@@ -122,8 +124,7 @@ __global__ void __launch_bounds__(256, 1) k_gemm_tc(TcArgs a) {
         for (int c = tid; c < TC_S * TC_N * 4; c += 256) {
             int s = c / (TC_N * 4), rem = c % (TC_N * 4), n = rem >> 2, q = rem & 3;
             bool ok = n < tile.count;
-            int v = ok ? a.pairs[tile.first + n].src : 0;
-            const uint16_t *src = VS + ((size_t)v * kSlicesS + s) * a.Kpad + k0 + q * 8;
+            const uint16_t *src = VS + ((size_t)s_src[n] * kSlicesS + s) * a.Kpad + k0 + q * 8;
             uint32_t dst = sb + (uint32_t)(TC_S * TC_A_SLICE * 2 + s * TC_B_SLICE * 2 + q * (TC_N * 16) +
                                            (n >> 3) * 128 + (n & 7) * 16);
             tc_cp16(dst, src, ok ? 16 : 0);

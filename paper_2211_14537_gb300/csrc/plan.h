@@ -46,12 +46,14 @@ struct DevExt {
     double *cheb_inv = nullptr;   // [Kbar][Kbar]
     // double-float copies (hi, lo float pairs) for the mixed form
     struct DfPair { float hi, lo; };
-    DfPair *pinv_df = nullptr, *cheb_df = nullptr;
+    DfPair *pinv_df = nullptr, *cheb_df = nullptr;   // pinv_df: rows padded to an even length
+    int64_t *pinv_df_off = nullptr;
+    double *tgt_geo = nullptr;                         // [n_tgt][4]: offset x, offset y, node scale, is-cut-leaf
     GemmPass grid_pass;                  // A_{X_Sbar,G} c for all cut leaves (one table)
     int n_tgt = 0, max_interior = 0;
     int32_t *tgt_cut = nullptr, *tgt_leaf = nullptr;   // extension targets: cut leaves, then their lists
     double *cbuf = nullptr, *Fall = nullptr;           // [max_rhs][ncut][NG], [max_rhs][ncut][Kbar^2]
-    DfPair *alpha = nullptr;                           // [max_rhs][ncut][Kbar^2] truncated Chebyshev coefficients
+    DfPair *alpha = nullptr;                           // [max_rhs][ncut][Kbar^2 rounded up to even] truncated Chebyshev coefficients
     int32_t *leaf_level = nullptr, *leaf_ix = nullptr, *leaf_iy = nullptr;
     int32_t *owned_flag_dev = nullptr;   // [n_leaves] 1 if the leaf is in an extension list
 };
