@@ -137,15 +137,34 @@ __global__ void k_extend(ExtArgs a) {
 
 // ---------------------------------------------------------------- boundary
 
-// one warp per boundary node: V(x) = sum_b w_y[b] sum_a w_x[a] V_leaf[b][a]
-__global__ void k_boundary(int nb, int K, const int32_t *bleaf, const double *bw, const double *v, int64_t ldv,
-                           double *vb, int64_t ldb) {
-    const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31, rhs = blockIdx.y;
-    if (k >= nb) return;
+// The last launch of the potential: blocks [0, nan_blocks) check V for
+// non-finite values (status VPX_ERR_NAN); the rest interpolate V at the
+// boundary nodes, one warp per node: V(x) = sum_b w_y[b] sum_a w_x[a] V_leaf[b][a].
+__global__ void k_finish(int64_t n_v, int nan_blocks, int nb, int K, const int32_t *bleaf, const double *bw,
+                         const double *v, int64_t ldv, double *vb, int64_t ldb, int *status) {
+    const int rhs = blockIdx.y;
+    if ((int)blockIdx.x < nan_blocks) {
+        const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        if (i < n_v && !isfinite(v[rhs * ldv + i])) set_status(status, VPX_ERR_NAN);
+        return;
+    }
+    const int k = (blockIdx.x - nan_blocks) * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (k >= nb || vb == nullptr) return;
     const double *w = bw + (size_t)k * 2 * K;
     const double *V = v + rhs * ldv + (int64_t)bleaf[k] * K * K;
+    constexpr int kMaxPerLane = kMaxK * kMaxK / 32;
+    double vv[kMaxPerLane], wx[kMaxPerLane], wy[kMaxPerLane];
+#pragma unroll
+    for (int q = 0; q < kMaxPerLane; ++q) {
+        const int j = lane + 32 * q;
+        const bool in = j < K * K;
+        vv[q] = in ? V[j] : 0.0;
+        wx[q] = in ? w[j % K] : 0.0;
+        wy[q] = in ? w[K + j / K] : 0.0;
+    }
     double s = 0.0;
-    for (int j = lane; j < K * K; j += 32) s += w[K + j / K] * w[j % K] * V[j];
+#pragma unroll
+    for (int q = 0; q < kMaxPerLane; ++q) s += wy[q] * wx[q] * vv[q];
     for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) vb[rhs * ldb + k] = s;
 }
@@ -255,11 +274,14 @@ void run_potential_passes(vpx_plan *p, const double *fe, int64_t ldfe, int nrhs,
 void run_potential_scratch(vpx_plan *p, const double *fe, int64_t ldfe, int nrhs, double *v, int64_t ldv, double *vb,
                            int64_t ldb, double *mp, double *lo, cudaStream_t s) {
     run_potential_passes(p, fe, ldfe, nrhs, v, ldv, vb, ldb, mp, lo, s);
-    const int nbd = (int)p->bdry_leaf.size();
-    if (vb && nbd > 0) {
-        k_boundary<<<dim3((nbd + 7) / 8, nrhs), 256, 0, s>>>(nbd, p->K, p->wk.bdry_leaf, p->wk.bdry_w, v, ldv, vb,
-                                                            ldb);
-        VPX_LAUNCH("k_boundary");
+    const int nbd = (vb != nullptr) ? (int)p->bdry_leaf.size() : 0;
+    const int64_t n_v = (int64_t)p->dt.n_leaves * p->KK;
+    const int nan_blocks = (int)((n_v + 255) / 256);
+    const int blocks = nan_blocks + (nbd + 7) / 8;
+    if (blocks > 0) {
+        k_finish<<<dim3(blocks, nrhs), 256, 0, s>>>(n_v, nan_blocks, nbd, p->K, p->wk.bdry_leaf, p->wk.bdry_w, v, ldv,
+                                                    vb, ldb, p->wk.status);
+        VPX_LAUNCH("k_finish");
     }
     ev_record(p, 8, s);
 }
@@ -337,6 +359,7 @@ int device_sync_status(vpx_plan *p) {
     VPX_CUDA(cudaStreamSynchronize(s));
     if (p->timing && p->events[0]) {
         VPX_CUDA(cudaStreamSynchronize((cudaStream_t)p->aux_stream));
+        VPX_CUDA(cudaStreamSynchronize((cudaStream_t)p->aux2_stream));
         for (int i = 0; i < VPX_N_PASSES; ++i) {
             float ms = 0.f;
             if (p->events[i] && p->events[i + 1] &&

@@ -389,12 +389,14 @@ void device_setup(vpx_plan *p) {
     cudaError_t e = cudaGetDeviceCount(&ndev);
     if (e != cudaSuccess || ndev == 0) fail(VPX_ERR_NODEV, "no CUDA device");
     VPX_CUDA(cudaGetDevice(&p->device));
-    cudaStream_t s, aux;
+    cudaStream_t s, aux, aux2;
     VPX_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
     p->stream = s;
     VPX_CUDA(cudaStreamCreateWithFlags(&aux, cudaStreamNonBlocking));
     p->aux_stream = aux;
-    for (void **e : {&p->ev_fork, &p->ev_up, &p->ev_join})
+    VPX_CUDA(cudaStreamCreateWithFlags(&aux2, cudaStreamNonBlocking));
+    p->aux2_stream = aux2;
+    for (void **e : {&p->ev_fork, &p->ev_up, &p->ev_join, &p->ev_s2l, &p->ev_join2})
         VPX_CUDA(cudaEventCreateWithFlags((cudaEvent_t *)e, cudaEventDisableTiming));
     DevTree &d = p->dt;
     d.n_leaves = (int)p->tree.leaves.size();
@@ -592,15 +594,16 @@ void device_free(vpx_plan *p) {
         cudaGraphExecDestroy((cudaGraphExec_t)p->graph_exec);
         p->graph_exec = nullptr;
     }
-    for (void **e : {&p->ev_fork, &p->ev_up, &p->ev_join})
+    for (void **e : {&p->ev_fork, &p->ev_up, &p->ev_join, &p->ev_s2l, &p->ev_join2})
         if (*e) {
             cudaEventDestroy((cudaEvent_t)*e);
             *e = nullptr;
         }
-    if (p->aux_stream) {
-        cudaStreamDestroy((cudaStream_t)p->aux_stream);
-        p->aux_stream = nullptr;
-    }
+    for (void **st : {&p->aux_stream, &p->aux2_stream})
+        if (*st) {
+            cudaStreamDestroy((cudaStream_t)*st);
+            *st = nullptr;
+        }
     if (p->stream) {
         cudaStreamDestroy((cudaStream_t)p->stream);
         p->stream = nullptr;

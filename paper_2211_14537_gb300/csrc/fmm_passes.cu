@@ -33,58 +33,27 @@ typedef std::complex<double> cd;
 
 // ------------------------------------------------------- constant terms
 
-// local[b][0] += log(L_b) sum_{list i} a_0(src) + sum_{list i+} log(H_src) a_0(src).
-// One warp per box, lanes over the list slots; log of a box side 2^-l is -l ln 2.
-__global__ void k_local_const(int first, int count, int P, double ln2, const int32_t *vlist, const int32_t *xlist,
-                              const int32_t *box_level, const int32_t *leaf_level, const int32_t *leaf_box,
-                              const double *mpole, double *local, int64_t ldm) {
-    const int bi = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31, rhs = blockIdx.y;
-    if (bi >= count) return;
-    const int b = first + bi;
+// The level-dependent real terms of the scaled expansions, as fixed gather
+// lists built at setup (row r: entries off[r] .. off[r+1] of (idx, coef)):
+//   local[b][0] += log(L_b) sum_{list i} a_0(src) + sum_{list i+} log(H_src) a_0(src)
+//   V[t][i]     += (1/2pi) [sum_near log(h_s) a_0(s) + sum_{list i-} log(L_W) a_0(W)]  (all i)
+// with log(2^-l) = -l ln 2 folded into coef.  One warp per row.
+__global__ void k_const_gather(int rows, int first, int P, const int32_t *off, const int32_t *idx,
+                               const double *coef, const double *mpole, int64_t ldm, double *out, int64_t ldo,
+                               int stride, int width) {
+    const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31, rhs = blockIdx.y;
+    if (r >= rows) return;
     const double *mp = mpole + rhs * ldm;
-    double sv = 0.0, sx = 0.0;
-    for (int s = lane; s < kVSlots; s += 32) {
-        const int src = vlist[(size_t)b * kVSlots + s];
-        if (src >= 0) sv += mp[(int64_t)src * 2 * P];
-    }
-    if (lane < kXSlots) {
-        const int src = xlist[(size_t)b * kXSlots + lane];
-        if (src >= 0) sx = -(double)(leaf_level[src] + 1) * ln2 * mp[(int64_t)leaf_box[src] * 2 * P];
-    }
-    double c = -(double)box_level[b] * ln2 * sv + sx;
+    const int e0 = off[r], e1 = off[r + 1];
+    double c = 0.0;
+    for (int e = e0 + lane; e < e1; e += 32) c += coef[e] * mp[(int64_t)idx[e] * 2 * P];
     for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-    if (lane == 0) local[rhs * ldm + (int64_t)b * 2 * P] += c;
-}
-
-// V[t][i] += (1/2pi) [sum_near log(h_s) a_0(s) + sum_{list i-} log(L_W) a_0(W)], all i
-__global__ void k_leaf_const(int KK, int P, double ln2, const int32_t *near, const int32_t *wlist,
-                             const int32_t *leaf_level, const int32_t *leaf_box, const int32_t *box_level,
-                             const double *mpole, int64_t ldm, double *v, int64_t ldv) {
-    const int t = blockIdx.x, rhs = blockIdx.y;
-    __shared__ double s_c;
-    if (threadIdx.x < 32) {
-        const double *mp = mpole + rhs * ldm;
-        double c = 0.0;
-        for (int s = threadIdx.x; s < kNearConfigs + kWSlots; s += 32) {
-            if (s < kNearConfigs) {
-                const int src = near[(size_t)t * kNearConfigs + s];
-                if (src >= 0) c -= (double)(leaf_level[src] + 1) * ln2 * mp[(int64_t)leaf_box[src] * 2 * P];
-            } else {
-                const int wb = wlist[(size_t)t * kWSlots + (s - kNearConfigs)];
-                if (wb >= 0) c -= (double)box_level[wb] * ln2 * mp[(int64_t)wb * 2 * P];
-            }
-        }
-        for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-        if (threadIdx.x == 0) s_c = c * 0.15915494309189533576888376337251;
+    double *o = out + rhs * ldo + (int64_t)(first + r) * stride;
+    if (width == 1) {
+        if (lane == 0) o[0] += c;
+    } else {
+        for (int i = lane; i < width; i += 32) atomicAdd(o + i, c);   // concurrent with the near field
     }
-    __syncthreads();
-    double *o = v + rhs * ldv + (int64_t)t * KK;
-    for (int i = threadIdx.x; i < KK; i += blockDim.x) atomicAdd(o + i, s_c);   // concurrent with the near field
-}
-
-__global__ void k_nan_check(const double *v, int64_t ldv, int64_t n, int *status) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n && !isfinite(v[blockIdx.y * ldv + i])) set_status(status, VPX_ERR_NAN);
 }
 
 // ------------------------------------------------------------ tables
@@ -325,6 +294,57 @@ void setup_passes(vpx_plan *p) {
         gemm_pass_upload_tables(F.near, near, kNearConfigs, KK, KK, mixed);
         gemm_pass_set_pairs(F.near, tn);
     }
+    // gather lists of the level-dependent constant terms
+    {
+        const double ln2 = std::log(2.0), inv2pi = 0.15915494309189533576888376337251;
+        std::vector<int32_t> off(1, 0), idx;
+        std::vector<double> coef;
+        F.lc_first = p->level_start[std::min(2, p->n_levels)];
+        for (int b = F.lc_first; b < nb; ++b) {
+            for (int s2 = 0; s2 < kVSlots; ++s2) {
+                const int src = p->vlist[(size_t)b * kVSlots + s2];
+                if (src >= 0) {
+                    idx.push_back(src);
+                    coef.push_back(-(double)p->box_level[b] * ln2);
+                }
+            }
+            for (int s2 = 0; s2 < kXSlots; ++s2) {
+                const int src = p->xlist[(size_t)b * kXSlots + s2];
+                if (src >= 0) {
+                    idx.push_back(leaf_box[src]);
+                    coef.push_back(-(double)(p->tree.leaves[src].level + 1) * ln2);
+                }
+            }
+            off.push_back((int32_t)idx.size());
+        }
+        F.lc_rows = nb - F.lc_first;
+        F.lc_off = dev_upload(off);
+        F.lc_idx = dev_upload(idx);
+        F.lc_coef = dev_upload(coef);
+        off.assign(1, 0);
+        idx.clear();
+        coef.clear();
+        for (int i = 0; i < nl; ++i) {
+            for (int c = 0; c < kNearConfigs; ++c) {
+                const int src = p->near[(size_t)i * kNearConfigs + c];
+                if (src >= 0) {
+                    idx.push_back(leaf_box[src]);
+                    coef.push_back(-(double)(p->tree.leaves[src].level + 1) * ln2 * inv2pi);
+                }
+            }
+            for (int s2 = 0; s2 < kWSlots; ++s2) {
+                const int wb = p->wlist[(size_t)i * kWSlots + s2];
+                if (wb >= 0) {
+                    idx.push_back(wb);
+                    coef.push_back(-(double)p->box_level[wb] * ln2 * inv2pi);
+                }
+            }
+            off.push_back((int32_t)idx.size());
+        }
+        F.tc_off = dev_upload(off);
+        F.tc_idx = dev_upload(idx);
+        F.tc_coef = dev_upload(coef);
+    }
     if (mixed) {
         // slices per pass: near field and far field separately (environment overrides for experiments)
         const char *sn = getenv("VPX_SLICES_NEAR"), *sf = getenv("VPX_SLICES_FAR");
@@ -360,6 +380,12 @@ void free_passes(vpx_plan *p) {
     }
     dev_free(F.fe_sl);
     dev_free(F.fe_ex);
+    dev_free(F.lc_off);
+    dev_free(F.lc_idx);
+    dev_free(F.lc_coef);
+    dev_free(F.tc_off);
+    dev_free(F.tc_idx);
+    dev_free(F.tc_coef);
     dev_free(F.mp_sl);
     dev_free(F.mp_ex);
 }
@@ -368,10 +394,11 @@ void free_passes(vpx_plan *p) {
 
 void ev_record_pass(vpx_plan *p, int i, cudaStream_t s);
 
-// Two streams: the near field and the list-i- evaluation (which need only the
-// leaf values and the finished multipoles) run on an auxiliary stream forked
-// from the main one, overlapping the level-by-level passes; both add into V
-// with atomics and the main stream joins before the NaN check.
+// Three streams forked from the main one: the near field (leaf values only)
+// on the second; list i+ (leaf values -> locals) and, once the multipoles are
+// final, list i- on the third.  They overlap the level-by-level passes of the
+// main stream, add into V or the locals with atomics, and are joined where
+// their results are read (the locals before L2L, V before the last launch).
 void run_potential_passes(vpx_plan *p, const double *fe, int64_t ldfe, int nrhs, double *v, int64_t ldv, double *vb,
                           int64_t ldb, double *mp, double *lo, cudaStream_t s) {
     const bool mixed = p->opt.precision == VPX_PREC_MIXED;
@@ -388,54 +415,52 @@ void run_potential_passes(vpx_plan *p, const double *fe, int64_t ldfe, int nrhs,
     VecSet vl{lo, ldm, P2, nullptr, nullptr, nb, 0};
     VecSet vmf{mp, ldm, P2, F.mp_sl, F.mp_ex, nb, kp_m};
     if (!mixed) vmf = vm;
-    cudaStream_t aux = (cudaStream_t)p->aux_stream;
+    cudaStream_t aux = (cudaStream_t)p->aux_stream, aux2 = (cudaStream_t)p->aux2_stream;
     ev_record_pass(p, 1, s);
     VPX_CUDA(cudaMemsetAsync(mp, 0, sizeof(double) * ldm * nrhs, s));
     VPX_CUDA(cudaMemsetAsync(lo, 0, sizeof(double) * ldm * nrhs, s));
     VPX_CUDA(cudaMemset2DAsync(v, sizeof(double) * ldv, 0, sizeof(double) * (size_t)nl * KK, nrhs, s));
     if (mixed) slice_vectors(vf, 0, nl, KK, kp_f, nrhs, s);
-    // fork: near field on the auxiliary stream
+    // fork: near field on the second stream, list i+ (leaf values -> local) on the third
     VPX_CUDA(cudaEventRecord((cudaEvent_t)p->ev_fork, s));
     VPX_CUDA(cudaStreamWaitEvent(aux, (cudaEvent_t)p->ev_fork, 0));
+    VPX_CUDA(cudaStreamWaitEvent(aux2, (cudaEvent_t)p->ev_fork, 0));
     ev_record_pass(p, VPX_N_PASSES + 1, aux);
     gemm_run(F.near, vf, v, ldv, nrhs, mixed, aux);
     ev_record_pass(p, VPX_N_PASSES + 2, aux);
+    VPX_CUDA(cudaEventRecord((cudaEvent_t)p->ev_join, aux));
+    gemm_run(F.s2l, vf, lo, ldm, nrhs, mixed, aux2);
+    VPX_CUDA(cudaEventRecord((cudaEvent_t)p->ev_s2l, aux2));
     // main stream: upward pass
     gemm_run(F.l2m, vf, mp, ldm, nrhs, mixed, s);
     ev_record_pass(p, 2, s);
     for (int l = d.n_levels - 1; l >= 3; --l) gemm_run(F.m2m[l - 1], vm, mp, ldm, nrhs, mixed, s);
     if (mixed) slice_vectors(vmf, 0, nb, P2, kp_m, nrhs, s);
-    // list i- on the auxiliary stream once the multipoles are final
+    // list i- on the third stream once the multipoles are final
     VPX_CUDA(cudaEventRecord((cudaEvent_t)p->ev_up, s));
-    VPX_CUDA(cudaStreamWaitEvent(aux, (cudaEvent_t)p->ev_up, 0));
-    gemm_run(F.m2t, vmf, v, ldv, nrhs, mixed, aux);
-    VPX_CUDA(cudaEventRecord((cudaEvent_t)p->ev_join, aux));
+    VPX_CUDA(cudaStreamWaitEvent(aux2, (cudaEvent_t)p->ev_up, 0));
+    gemm_run(F.m2t, vmf, v, ldv, nrhs, mixed, aux2);
+    VPX_CUDA(cudaEventRecord((cudaEvent_t)p->ev_join2, aux2));
     ev_record_pass(p, 3, s);
     gemm_run(F.m2l, vmf, lo, ldm, nrhs, mixed, s);
-    gemm_run(F.s2l, vf, lo, ldm, nrhs, mixed, s);
-    {
-        int first = d.level_start[std::min(2, d.n_levels)], count = nb - first;
-        if (count > 0) {
-            k_local_const<<<dim3((count + 7) / 8, nrhs), 256, 0, s>>>(first, count, P, std::log(2.0), d.vlist, d.xlist,
-                                                                       d.box_level, p->ext.leaf_level, d.leaf_box, mp,
-                                                                       lo, ldm);
-            VPX_LAUNCH("k_local_const");
-        }
+    if (F.lc_rows > 0) {
+        k_const_gather<<<dim3((F.lc_rows + 7) / 8, nrhs), 256, 0, s>>>(F.lc_rows, F.lc_first, P, F.lc_off, F.lc_idx,
+                                                                       F.lc_coef, mp, ldm, lo, ldm, P2, 1);
+        VPX_LAUNCH("k_const_gather");
     }
+    VPX_CUDA(cudaStreamWaitEvent(s, (cudaEvent_t)p->ev_s2l, 0));
     ev_record_pass(p, 4, s);
     for (int l = 2; l + 1 < d.n_levels; ++l) gemm_run(F.l2l[l], vl, lo, ldm, nrhs, mixed, s);
     ev_record_pass(p, 5, s);
     gemm_run(F.l2t, vl, v, ldv, nrhs, mixed, s);
-    k_leaf_const<<<dim3(nl, nrhs), 128, 0, s>>>(KK, P, std::log(2.0), d.near, d.wlist, p->ext.leaf_level, d.leaf_box,
-                                                d.box_level, mp, ldm, v, ldv);
-    VPX_LAUNCH("k_leaf_const");
+    if (nl > 0) {
+        k_const_gather<<<dim3((nl + 7) / 8, nrhs), 256, 0, s>>>(nl, 0, P, F.tc_off, F.tc_idx, F.tc_coef, mp, ldm, v,
+                                                                ldv, KK, KK);
+        VPX_LAUNCH("k_const_gather");
+    }
     ev_record_pass(p, 6, s);
     VPX_CUDA(cudaStreamWaitEvent(s, (cudaEvent_t)p->ev_join, 0));
-    {
-        const int64_t n = (int64_t)nl * KK;
-        k_nan_check<<<dim3((unsigned)((n + 255) / 256), nrhs), 256, 0, s>>>(v, ldv, n, p->wk.status);
-        VPX_LAUNCH("k_nan_check");
-    }
+    VPX_CUDA(cudaStreamWaitEvent(s, (cudaEvent_t)p->ev_join2, 0));
     ev_record_pass(p, 7, s);
 }
 

@@ -94,22 +94,34 @@ __device__ __host__ inline int slice_expo(double amax) {
 }
 
 // One warp per (vector, rhs): exponent and slices (slice_math.cuh), zero padded to Kpad.
+constexpr int kSliceMaxPerLane = 8;   // Kpad <= 256
+
 __global__ void k_slice_vec(const double *vbase, int64_t vld, int vstride, int first, int count, int Kd, int Kpad,
                             int nvec, uint16_t *slices, int32_t *expo) {
     const int vi = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31, rhs = blockIdx.y;
     if (vi >= count) return;
     const int v = first + vi;
     const double *x = vbase + rhs * vld + (int64_t)v * vstride;
+    double xv[kSliceMaxPerLane];
     uint64_t mb = 0;
-    for (int j = lane; j < Kd; j += 32) {
-        const uint64_t t = slice_abs_bits(x[j]);
+#pragma unroll
+    for (int q = 0; q < kSliceMaxPerLane; ++q) {   // all loads first
+        const int j = lane + 32 * q;
+        xv[q] = (j < Kd) ? x[j] : 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < kSliceMaxPerLane; ++q) {
+        const uint64_t t = slice_abs_bits(xv[q]);
         mb = t > mb ? t : mb;
     }
     const int e = slice_warp_expo(mb);
     uint16_t *out = slices + ((size_t)rhs * nvec + v) * kSlicesS * Kpad;
-    for (int j = lane; j < Kpad; j += 32) {
+#pragma unroll
+    for (int q = 0; q < kSliceMaxPerLane; ++q) {
+        const int j = lane + 32 * q;
+        if (j >= Kpad) break;
         uint16_t d[kSlicesS];
-        slice_digits((j < Kd) ? slice_fixed_point(x[j], e) : 0, d);
+        slice_digits(slice_fixed_point(xv[q], e), d);
 #pragma unroll
         for (int k = 0; k < kSlicesS; ++k) out[(size_t)k * Kpad + j] = d[k];
     }
@@ -272,6 +284,7 @@ void gemm_run(const GemmPass &g, const VecSet &vs, double *out, int64_t ldo, int
 
 void slice_vectors(const VecSet &vs, int first, int count, int Kd, int Kpad, int nrhs, void *sv) {
     if (count <= 0) return;
+    if (Kpad > 32 * kSliceMaxPerLane) fail(VPX_ERR_ARG, "slice_vectors: vectors longer than 256");
     k_slice_vec<<<dim3((count + 7) / 8, nrhs), 256, 0, (cudaStream_t)sv>>>(vs.base, vs.ld, vs.stride, first, count, Kd,
                                                                             Kpad, vs.nvec, vs.slices, vs.expo);
     VPX_LAUNCH("k_slice_vec");

@@ -76,6 +76,10 @@ struct FmmPasses {                // every contraction of the box FMM as a group
     GemmPass m2m[kMaxLevel + 1];  // parents at level l
     GemmPass l2l[kMaxLevel + 1];  // parents at level l
     uint16_t *fe_sl = nullptr, *mp_sl = nullptr;   // exact bf16 slices of leaf values, multipoles (mixed form)
+    // gather lists of the constant terms: boxes from lc_first on (locals), leaves (potentials)
+    int lc_first = 0, lc_rows = 0;
+    int32_t *lc_off = nullptr, *lc_idx = nullptr, *tc_off = nullptr, *tc_idx = nullptr;
+    double *lc_coef = nullptr, *tc_coef = nullptr;
     int32_t *fe_ex = nullptr, *mp_ex = nullptr;
 };
 
@@ -111,8 +115,9 @@ struct vpx_plan {
     vpx::FmmPasses fmm;
     bool timing = false;
     void *events[VPX_N_PASSES + 3] = {nullptr};   // pass boundaries on the main stream, near field on aux
-    void *aux_stream = nullptr;   // second stream of the execute graph (near field, list i-)
-    void *ev_fork = nullptr, *ev_up = nullptr, *ev_join = nullptr;
+    void *aux_stream = nullptr;   // second stream of the execute graph (near field)
+    void *aux2_stream = nullptr;  // third stream (lists i+ and i-)
+    void *ev_fork = nullptr, *ev_up = nullptr, *ev_join = nullptr, *ev_s2l = nullptr, *ev_join2 = nullptr;
     void *graph_exec = nullptr;   // captured vpx_execute sequence (cudaGraphExec_t)
     int64_t graph_key[10] = {0};
     double pass_ms[VPX_N_PASSES] = {0};
