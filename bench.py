@@ -40,7 +40,7 @@ def parse():
     ap.add_argument("--p", type=int, default=40)
     ap.add_argument("--precision", default="both", choices=["fp64", "mixed", "both"])
     ap.add_argument("--nrhs", type=int, default=1)
-    ap.add_argument("--oracle-sample", type=int, default=400)
+    ap.add_argument("--oracle-sample", type=int, default=10000)   # ~10-15 s of oracle work on 16 cores
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -101,17 +101,6 @@ class ClockSampler:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
                 "reasons": sorted(reasons)}
-
-
-def launches_per_step(n_levels, has_cut, has_bdry, form):
-    """Kernels of one vpx_execute: extension (2), L2M, M2M per level, M2L, S2L,
-    local constants, L2L per level, L2T, M2T, leaf constants, near, NaN check,
-    boundary; the mixed form adds one slicing kernel per vector level."""
-    lv = max(0, n_levels - 2)          # levels >= 2
-    n = 2 + 1 + max(0, lv - 1) + 3 + max(0, lv - 1) + 3 + 1 + 1 + (1 if has_bdry else 0)
-    if form == "mixed":
-        n += 1 + lv + lv               # leaf values, multipoles and locals per level
-    return n
 
 
 def run_gpu(args, rank, world, precision):
@@ -175,6 +164,7 @@ def run_gpu(args, rank, world, precision):
         import torch.distributed as dist
         dist.barrier()
     times = [ev0[i].elapsed_time(ev1[i]) for i in range(args.steps)]
+    graph_kernels = V.vpx_graph_kernel_count(plan)   # kernel launches of one replayed step
     ms = statistics.mean(times)
     # per-pass breakdown (separate short loop with the pass events enabled)
     V.vpx_set_timing(plan, True)
@@ -202,7 +192,7 @@ def run_gpu(args, rank, world, precision):
     near_ms = pass_ms.get("near", float("nan"))
     return dict(plan=plan, wl=wl, ms=ms, times=times, setup_s=setup_s, tg=tg, nt=nt, nb=nb, ns=ns,
                 n_leaves=n_leaves, lc=lc, pass_ms=pass_ms, near_flops=near_flops, near_ms=near_ms,
-                clocks=cl, e2e_s=e2e_s, v=v[0].cpu().numpy(), vh=vh, K=K)
+                clocks=cl, e2e_s=e2e_s, v=v[0].cpu().numpy(), vh=vh, K=K, graph_kernels=graph_kernels)
 
 
 def oracle_sample(wl, n_sample, seed=2213, nthreads=0):
@@ -264,8 +254,8 @@ def main():
         bf16_flops = 15 * r["near_flops"]
         achieved = bf16_flops / (r["near_ms"] * 1e-3) / 1e12
         peak = 1918.1
-        kname = ("k_gemm_sliced (near-field pass, exact bf16 slices on mma.sync)" if os.environ.get("VPX_NO_TC")
-                 else "k_gemm_tc (near-field pass, exact bf16 slices on tcgen05, accumulators in TMEM)")
+        kname = ("k_gemm_frag (near-field pass, exact bf16 slices on mma.sync)" if os.environ.get("VPX_NO_TC")
+                 else "k_gemm_ws (near-field pass, exact bf16 slices on tcgen05: TMA tables, TMEM accumulators)")
         roof = {"kernel": kname, "bound": "tensor",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst)",
@@ -294,7 +284,7 @@ def main():
                   for f in forms},
         "rel_err_vs_oracle": errs.get(head),
         "roofline": roof,
-        "gpu_launches": launches_per_step(r["lc"]["n_levels"], True, r["nb"] > 0, head) * args.steps,
+        "gpu_launches": r["graph_kernels"] * args.steps,
         "e2e": {"value": r["tg"] * world / r["e2e_s"], "unit": UNIT,
                 "h2d_bytes_per_step": 8 * r["ns"] * args.nrhs,
                 "d2h_bytes_per_step": 8 * (r["nt"] + r["nb"]) * args.nrhs},

@@ -195,6 +195,13 @@ int vpx_get_timings(vpx_plan_t plan, double *ms, int n);
 /* Names of the passes timed by vpx_get_timings, in order. */
 const char *vpx_pass_name(int i);
 
+/* Number of kernel launches in the CUDA graph that vpx_execute captured for
+ * its last buffer set (0 before the first captured call, or when the calls
+ * run without a graph).  The paper has no counterpart: it reports what one
+ * execute launches, for measurement.  Errors: VPX_ERR_ARG for a null
+ * argument. */
+int vpx_graph_kernel_count(vpx_plan_t plan, int64_t *kernels);
+
 const char *vpx_error_string(int code);
 const char *vpx_last_error_message(void);
 

@@ -410,6 +410,12 @@ int vpx_get_timings(vpx_plan_t p, double *ms, int n) {
     return VPX_OK;
 }
 
+int vpx_graph_kernel_count(vpx_plan_t p, int64_t *kernels) {
+    if (!p || !kernels) return VPX_ERR_ARG;
+    *kernels = p->graph_kernels;
+    return VPX_OK;
+}
+
 const char *vpx_pass_name(int i) {
     static const char *names[VPX_N_PASSES] = {"extension", "l2m", "m2m", "m2l_s2l", "l2l",
                                               "l2t_const", "near", "join_boundary"};

@@ -8,6 +8,7 @@
 // Leaf values are the K x K Gauss-Legendre node values of f^e on each leaf.
 #include <cmath>
 #include <cstdlib>
+#include <vector>
 
 #include "dev_common.cuh"
 #include "ext.cuh"
@@ -313,7 +314,7 @@ static void execute_sequence(vpx_plan *p, const double *f, int nrhs, int64_t ldf
     run_potential(p, p->wk.fe, ldfe, nrhs, v, ldv, vb, ldb, s);
 }
 
-// The whole sequence (about 35 launches) is captured into a CUDA graph on the
+// The whole sequence (about 25 kernels) is captured into a CUDA graph on the
 // first call with a given set of buffers, strides and nrhs, and replayed on
 // later calls; calls on the legacy default stream run the launches directly.
 void device_execute(vpx_plan *p, const double *f, int nrhs, int64_t ldf, double *v, int64_t ldv, double *vb,
@@ -344,6 +345,17 @@ void device_execute(vpx_plan *p, const double *f, int nrhs, int64_t ldf, double 
             throw;
         }
         VPX_CUDA(cudaStreamEndCapture(s, &graph));
+        size_t n_nodes = 0;
+        VPX_CUDA(cudaGraphGetNodes(graph, nullptr, &n_nodes));
+        std::vector<cudaGraphNode_t> nodes(n_nodes);
+        if (n_nodes) VPX_CUDA(cudaGraphGetNodes(graph, nodes.data(), &n_nodes));
+        int64_t nk = 0;
+        for (cudaGraphNode_t nd : nodes) {
+            cudaGraphNodeType t;
+            VPX_CUDA(cudaGraphNodeGetType(nd, &t));
+            if (t == cudaGraphNodeTypeKernel) ++nk;
+        }
+        p->graph_kernels = nk;
         cudaGraphExec_t exec = nullptr;
         cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
         cudaGraphDestroy(graph);

@@ -353,8 +353,9 @@ void setup_passes(vpx_plan *p) {
         F.near.slices = s_near;
         for (GemmPass *g : {&F.l2m, &F.m2l, &F.s2l, &F.l2t, &F.m2t}) g->slices = s_far;
         for (int l = 0; l <= kMaxLevel; ++l) F.m2m[l].slices = F.l2l[l].slices = s_far;
-        gemm_tc_prepare_device();
+        gemm_ws_prepare_device();
         gemm_frag_prepare_device();
+        for (GemmPass *g : {&F.near, &F.l2m, &F.m2l, &F.s2l, &F.l2t, &F.m2t}) gemm_ws_prepare(*g);
         const int kp_f = (KK + 31) / 32 * 32, kp_m = (P2 + 31) / 32 * 32;
         F.fe_sl = dev_alloc<uint16_t>((size_t)p->opt.max_rhs * nl * kSlicesS * kp_f);
         F.fe_ex = dev_alloc<int32_t>((size_t)p->opt.max_rhs * nl);

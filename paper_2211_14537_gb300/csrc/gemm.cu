@@ -13,8 +13,9 @@
 // cores' fp32 accumulation of it is exact.  The orders are combined in
 // double-float fp32 and scaled by scale_p 2^{e_i + e_v - 14}; the truncation
 // error is about 2^-7S relative to max|row| max|vector|.  Two engines run it:
-// tcgen05 with TMEM accumulators (gemm_tc.cu, the near field) and mma.sync
-// with tables in fragment order (gemm_frag.cu, every other pass).
+// warp-specialised tcgen05 with TMA and TMEM accumulators (gemm_ws.cu) and
+// mma.sync with tables in fragment order (gemm_frag.cu); a double-float
+// engine on the fp32 pipes (gemm_rows.cu) takes the short level chains.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -134,7 +135,7 @@ void gemm_pass_set_pairs(GemmPass &g, std::vector<std::pair<int, GPair>> &tagged
     std::stable_sort(tagged.begin(), tagged.end(),
                      [](const std::pair<int, GPair> &x, const std::pair<int, GPair> &y) { return x.first < y.first; });
     std::vector<GPair> pr;
-    std::vector<GTile> tl, tf, tr;
+    std::vector<GTile> tl, tf, tr, tp;
     const size_t npf = tagged.size() >= (size_t)kFragBigPass ? 32 : 8;
     size_t i = 0;
     while (i < tagged.size()) {
@@ -147,6 +148,8 @@ void gemm_pass_set_pairs(GemmPass &g, std::vector<std::pair<int, GPair>> &tagged
             tf.push_back({tagged[i].first, base + (int32_t)(k - i), (int32_t)std::min<size_t>(npf, j - k), 0});
         for (size_t k = i; k < j; k += kRowsTileN)
             tr.push_back({tagged[i].first, base + (int32_t)(k - i), (int32_t)std::min<size_t>(kRowsTileN, j - k), 0});
+        for (size_t k = i; k < j; k += kPairTileN)
+            tp.push_back({tagged[i].first, base + (int32_t)(k - i), (int32_t)std::min<size_t>(kPairTileN, j - k), 0});
         for (size_t k = i; k < j; ++k) pr.push_back(tagged[k].second);
         i = j;
     }
@@ -155,11 +158,13 @@ void gemm_pass_set_pairs(GemmPass &g, std::vector<std::pair<int, GPair>> &tagged
     g.n_tiles = (int)tl.size();
     g.n_tiles_f = (int)tf.size();
     g.n_tiles_r = (int)tr.size();
+    g.n_tiles_p = (int)tp.size();
     g.np_f = (int)npf;
     g.pairs = dev_upload(pr);
     g.tiles = dev_upload(tl);
     g.tiles_f = dev_upload(tf);
     g.tiles_r = dev_upload(tr);
+    g.tiles_p = dev_upload(tp);
 }
 
 static uint16_t bf16_bits_exact(double q) {
@@ -251,13 +256,16 @@ void gemm_pass_free(GemmPass &g) {
     dev_free(g.tfrag);
     dev_free(g.tiles_f);
     dev_free(g.tiles_r);
+    dev_free(g.tiles_p);
     dev_free(g.tdfT);
-    g.n_pairs = g.n_tiles = g.n_tiles_f = g.n_tiles_r = 0;
+    dev_free(g.tint);
+    g.n_pairs = g.n_tiles = g.n_tiles_f = g.n_tiles_r = g.n_tiles_p = 0;
 }
 
-void gemm_tc_run(const GemmPass &g, const VecSet &vs, double *out, int64_t ldo, int nrhs, int *status, void *s);
 bool gemm_frag_eligible(const GemmPass &g, const VecSet &vs);
 void gemm_rows_run(const GemmPass &g, const VecSet &vs, double *out, int64_t ldo, int nrhs, void *s);
+bool gemm_ws_eligible(const GemmPass &g, const VecSet &vs);
+void gemm_ws_run(const GemmPass &g, const VecSet &vs, double *out, int64_t ldo, int nrhs, void *s);
 void gemm_frag_run(const GemmPass &g, const VecSet &vs, double *out, int64_t ldo, int nrhs, void *s);
 
 void gemm_run(const GemmPass &g, const VecSet &vs, double *out, int64_t ldo, int nrhs, bool mixed, void *sv) {
@@ -274,8 +282,8 @@ void gemm_run(const GemmPass &g, const VecSet &vs, double *out, int64_t ldo, int
         return;
     }
     const bool no_tc = getenv("VPX_NO_TC") != nullptr;   // read per call: lets a test compare the engines
-    if (!no_tc && vs.slices && gemm_tc_eligible(g)) {
-        gemm_tc_run(g, vs, out, ldo, nrhs, g.status, sv);
+    if (!no_tc && gemm_ws_eligible(g, vs)) {
+        gemm_ws_run(g, vs, out, ldo, nrhs, sv);
         return;
     }
     if (!gemm_frag_eligible(g, vs)) fail(VPX_ERR_ARG, "no exact-slice engine covers this pass shape");

@@ -18,6 +18,7 @@ namespace vpx {
 constexpr int kGemmTileN = 64;   // pairs per tile (FP64 and tcgen05 engines)
 constexpr int kFragBigPass = 4096;   // fragment engine: 32 pairs per tile from this many pairs on, else 8
 constexpr int kRowsTileN = 1;        // pairs per tile (double-float row engine)
+constexpr int kPairTileN = 128;      // pairs per tile (tcgen05 with pairs on M)
 constexpr int kSlicesS = 6;      // bf16 slices stored per operand in the mixed form (a pass uses 5 or 6)
 constexpr int kSliceBitsB = 7;   // bits per slice
 
@@ -46,8 +47,11 @@ struct GemmPass {
     GTile *tiles = nullptr;            // kGemmTileN pairs each
     GTile *tiles_f = nullptr;          // np_f pairs each (fragment engine)
     GTile *tiles_r = nullptr;          // kRowsTileN pairs each (row engine)
+    GTile *tiles_p = nullptr;          // kPairTileN pairs each (tcgen05, pairs on M)
     const void *tdfT = nullptr;        // [ntab][Kd][M] double-float (float hi, lo): the row engine runs the pass
-    int n_pairs = 0, n_tiles = 0, n_tiles_f = 0, np_f = 8, n_tiles_r = 0;
+    const uint16_t *tint = nullptr;    // [ntab][S][Kpad/8][Mpad][8] slices, column chunks interleaved (tcgen05 engine)
+    int ws_kind = 0;                   // 0: not on that engine; 1: table rows on M; 2: pairs on M
+    int n_pairs = 0, n_tiles = 0, n_tiles_f = 0, np_f = 8, n_tiles_r = 0, n_tiles_p = 0;
     std::vector<GPair> h_pairs;        // host copy (setup)
 };
 
@@ -58,11 +62,11 @@ void gemm_pass_free(GemmPass &g);
 // Hand a mixed-form pass to the double-float row engine (gemm_rows.cu) when
 // its rows fit one CTA and every pair scale is a power of two; returns whether.
 bool gemm_pass_use_rows(GemmPass &g, const std::vector<double> &tab);
-// tcgen05 engine (gemm_tc.cu): 5-slice passes whose rows tile by 128
-bool gemm_tc_eligible(const GemmPass &g);
-void gemm_tc_prepare_device();
 // fragment engine (gemm_frag.cu)
 void gemm_frag_prepare_device();
+// warp-specialised tcgen05 engine (gemm_ws.cu): interleaved table copy of a mixed-form pass
+void gemm_ws_prepare(GemmPass &g);
+void gemm_ws_prepare_device();
 
 struct VecSet {                        // source vectors of a pass
     const double *base = nullptr;      // vector v of rhs r at base + r*ld + v*stride

@@ -211,11 +211,10 @@ __global__ void __launch_bounds__(192, 2) k_gemm_frag(FragArgs a) {
                 const int n = t * 8 + tq * 2 + half;
                 const int64_t dst = s_pr[n].dst;
                 if (dst < 0) continue;
-                float acc_d[S], hi, lo;
+                float acc_d[S];
 #pragma unroll
                 for (int d = 0; d < S; ++d) acc_d[d] = acc[d][t][rr * 2 + half];
-                slice_recombine<S>(acc_d, hi, lo);
-                const double val = slice_output(hi, lo, s_ps[n], row_e[rr]);
+                const double val = slice_output<S>(acc_d, s_ps[n], row_e[rr]);
                 double *o = a.out + rhs * a.ldo + dst + i;
                 if (a.add) atomicAdd(o, val);
                 else *o = val;

@@ -117,6 +117,7 @@ struct vpx_plan {
     void *events[VPX_N_PASSES + 3] = {nullptr};   // pass boundaries on the main stream, near field on aux
     void *aux_stream = nullptr;   // second stream of the execute graph (near field)
     void *aux2_stream = nullptr;  // third stream (lists i+ and i-)
+    int64_t graph_kernels = 0;    // kernel nodes of the captured execute graph
     void *ev_fork = nullptr, *ev_up = nullptr, *ev_join = nullptr, *ev_s2l = nullptr, *ev_join2 = nullptr;
     void *graph_exec = nullptr;   // captured vpx_execute sequence (cudaGraphExec_t)
     int64_t graph_key[10] = {0};

@@ -1,5 +1,5 @@
 // slice_math.cuh -- device arithmetic of the exact-slice table GEMM shared by
-// its engines (gemm.cu, gemm_frag.cu: mma.sync; gemm_tc.cu: tcgen05): splitting
+// its engines (gemm_frag.cu: mma.sync; gemm_ws.cu: tcgen05): splitting
 // an FP64 vector into bf16 integer slices, and the epilogue.
 //
 // Slicing.  e = exponent of max|v| (frexp convention); every element becomes the
@@ -8,28 +8,18 @@
 // [-64, 63], the top digit (the remainder) in [-128, 128].  Integer arithmetic
 // on the bit pattern only, apart from the exact digit -> bf16 conversion.
 //
-// Epilogue.
-// An output of the sliced GEMM is held as S fp32 order sums acc_d (each exact,
-// an integer), worth  sum_d acc_d 2^{-7d} * 2^{e_row} * scale_p * 2^{e_vec - 14}.
-// FP64 issues at about 2 operations per clock per SM on this part, 1/64 of the
-// fp32 rate, so the epilogue keeps every step it can in fp32 and integer
-// arithmetic:
-//   1. recombine the orders into a double-float (hi, lo) with TwoSum in fp32
-//      (hi + lo carries about 48 bits; both lie on the grid 2^{-7(S-1)}, so
-//      neither is subnormal unless zero);
-//   2. multiply by the pair scale held as a double-float mantissa (ph + pl in
-//      [0.5, 1)) with an integer exponent, error-free product by fma;
-//   3. build the two fp64 halves by writing the fp32 sign, exponent + the row
-//      and pair exponents, and mantissa into an IEEE binary64 bit pattern
-//      (integer operations only), then one fp64 add.
-// Relative error per output is below 2^-46 of that output's own magnitude.
+// Epilogue.  Each order sum acc_d is an exact integer below 2^24 held in fp32:
+// it converts exactly to int32, and N = sum_d acc_d 128^{S-1-d} is an exact
+// int64 (|N| < 2^60).  The output N 2^{e_row + e_pair + e_vec - 14 - 7(S-1)}
+// m_pair is then one rounding of the exact slice-product sum: the int64 ->
+// FP64 conversion, the power of two applied to the exponent field, and one
+// FP64 multiply only for a pair scale that is not a power of two.
 #pragma once
 
 #include <cuda_bf16.h>
 
 #include <cstdint>
 
-#include "df32.cuh"   // f32_scaled_to_f64
 #include "gemm.cuh"   // kSlicesS (slices stored per operand), kSliceBitsB (bits per slice)
 
 namespace vpx {
@@ -77,47 +67,38 @@ __device__ inline void slice_digits(int64_t n, uint16_t (&d)[kSlicesS]) {
 }
 
 struct SliceScale {
-    float hi, lo;   // mantissa of the pair scale, hi + lo in [0.5, 1)
+    double mul;     // pair scale / 2^e (1 when the scale is a power of two, else in [1, 2))
     int e;          // its exponent, including the vector's exponent and 2^-14
 };
 
 __device__ inline SliceScale slice_pair_scale(double scale, int extra_e) {
     SliceScale s;
     int e = 0;
-    const double m = frexp(scale, &e);
-    s.hi = (float)m;
-    s.lo = (float)(m - (double)s.hi);
-    s.e = e + extra_e;
+    const double m = frexp(scale, &e);   // scale = m 2^e, |m| in [0.5, 1)
+    s.mul = (m == 0.5) ? 1.0 : 2.0 * m;
+    s.e = e - 1 + extra_e;
     return s;
 }
 
-// acc[0] is the most significant order.  Returns the exact sum as hi + lo.
-template <int S>
-__device__ inline void slice_recombine(const float (&acc)[S], float &hi, float &lo) {
-    hi = acc[S - 1];
-    lo = 0.f;
-#pragma unroll
-    for (int d = S - 2; d >= 0; --d) {
-        hi *= 0x1p-7f;
-        lo *= 0x1p-7f;
-        const float b = acc[d];
-        const float sm = hi + b, bb = sm - hi;
-        const float er = (hi - (sm - bb)) + (b - bb);
-        hi = sm;
-        lo += er;
-        const float s2 = hi + lo;
-        lo = lo - (s2 - hi);
-        hi = s2;
-    }
+// n 2^e as a double: one rounding (the conversion), the scaling exact
+__device__ inline double slice_i64_scaled(int64_t n, int e) {
+    const double v = (double)n;
+    const uint64_t b = (uint64_t)__double_as_longlong(v);
+    const int ex = (int)((b >> 52) & 0x7ff);
+    if (ex == 0) return v;   // zero
+    const int ne = ex + e;
+    if (ne <= 0 || ne >= 2047) return ldexp(v, e);
+    return __longlong_as_double((long long)(b + ((uint64_t)(int64_t)e << 52)));
 }
 
-__device__ inline double slice_output(float hi, float lo, const SliceScale &ps, int row_e) {
-    const float p = __fmul_rn(hi, ps.hi);   // kept a rounded product: q below is its exact error
-    float q = fmaf(hi, ps.hi, -p);
-    q = fmaf(hi, ps.lo, q);
-    q = fmaf(lo, ps.hi, q);
-    const int E = row_e + ps.e;
-    return f32_scaled_to_f64(p, E) + f32_scaled_to_f64(q, E);
+// acc[0] is the most significant order
+template <int S>
+__device__ inline double slice_output(const float (&acc)[S], const SliceScale &ps, int row_e) {
+    int64_t n = __float2int_rn(acc[0]);
+#pragma unroll
+    for (int d = 1; d < S; ++d) n = n * 128 + __float2int_rn(acc[d]);
+    const double v = slice_i64_scaled(n, row_e + ps.e - kSliceBitsB * (S - 1));
+    return ps.mul == 1.0 ? v : v * ps.mul;
 }
 
 }  // namespace vpx

@@ -47,7 +47,7 @@ EXPORTED = [
     "vpx_default_options", "vpx_plan_create", "vpx_plan_sizes", "vpx_plan_leaves", "vpx_stencil_points",
     "vpx_leaf_nodes", "vpx_boundary_nodes", "vpx_plan_list_counts", "vpx_plan_lists", "vpx_plan_near_tables", "vpx_execute",
     "vpx_extend", "vpx_potential", "vpx_potential_static", "vpx_execute_host", "vpx_sync_status", "vpx_set_timing",
-    "vpx_get_timings", "vpx_pass_name", "vpx_error_string", "vpx_last_error_message", "vpx_plan_destroy",
+    "vpx_get_timings", "vpx_pass_name", "vpx_graph_kernel_count", "vpx_error_string", "vpx_last_error_message", "vpx_plan_destroy",
 ]
 
 _lib = None
@@ -82,6 +82,7 @@ def load_library(path: str = LIB_PATH):
     L.vpx_sync_status.argtypes = [vp]
     L.vpx_set_timing.argtypes = [vp, ctypes.c_int]
     L.vpx_get_timings.argtypes = [vp, P(d), ctypes.c_int]
+    L.vpx_graph_kernel_count.argtypes = [vp, P(ctypes.c_int64)]
     L.vpx_pass_name.argtypes = [ctypes.c_int]
     L.vpx_pass_name.restype = ctypes.c_char_p
     L.vpx_error_string.argtypes = [ctypes.c_int]
@@ -290,6 +291,13 @@ def vpx_sync_status(plan: Plan) -> int:
 
 def vpx_set_timing(plan: Plan, enable: bool = True):
     _check(load_library().vpx_set_timing(plan.handle, int(bool(enable))))
+
+
+def vpx_graph_kernel_count(plan: Plan) -> int:
+    """Kernel launches in the graph that vpx_execute captured (0 before it)."""
+    n = ctypes.c_int64(0)
+    _check(load_library().vpx_graph_kernel_count(plan.handle, ctypes.byref(n)))
+    return int(n.value)
 
 
 def vpx_get_timings(plan: Plan):

@@ -59,6 +59,7 @@ CASES = {
     "disk_l3_k8": lambda: W.disk_sincos(level=3, K=8),
     "disk_l4_k8": lambda: W.disk_sincos(level=4, K=8),
     "disk_l3_k16": lambda: W.disk_sincos(level=3, K=16),
+    "disk_l3_k6": lambda: W.disk_sincos(level=3, K=6),   # Kbar = 9: odd grid, padded copies
     "starfish_k8_adaptive": lambda: W.starfish_gaussian(K=8, tol=1e-8, max_level=8),
     "lshape_k8_adaptive": lambda: W.lshape_expsin(K=8, base_level=3, max_level=8, corner_levels=5),
 }
@@ -199,7 +200,7 @@ def _extension_bounds(tree, dom, meta):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-@pytest.mark.parametrize("name", ["disk_l3_k8", "disk_l4_k8", "disk_l3_k16", "starfish_k8_adaptive"])
+@pytest.mark.parametrize("name", ["disk_l3_k8", "disk_l4_k8", "disk_l3_k16", "disk_l3_k6", "starfish_k8_adaptive"])
 def test_extension_parity(V, name, precision):
     """FP64 form (precision 0) and the mixed form's double-float extension
     (precision 1): within 64 unit roundoffs of the arithmetic times the
@@ -313,7 +314,8 @@ def test_full_size_adaptive_sampled(V):
     assert err <= 1e-12, err
 
 
-@pytest.mark.parametrize("name", ["disk_l3_k8", "disk_l3_k16", "starfish_k8_adaptive", "lshape_k8_adaptive"])
+@pytest.mark.parametrize("name", ["disk_l3_k8", "disk_l3_k16", "disk_l3_k6", "starfish_k8_adaptive",
+                                  "lshape_k8_adaptive"])
 def test_potential_parity_mixed(V, name):
     """Mixed form (near field on the tensor cores with exact bf16 slices):
     relative max-norm error <= 1e-9 against the FP64 oracle."""
@@ -354,8 +356,11 @@ def test_mixed_full_size_sampled(V):
 
 
 def test_tcgen05_engine_matches_mma_engine(V):
-    """The tcgen05 (tensor-memory) engine and the mma.sync engine compute the
-    same exact slice products: their potentials agree to rounding."""
+    """The tcgen05 (tensor-memory) engines and the mma.sync engine compute the
+    same exact slice-order sums; they differ only where a pass's inner
+    dimension is split (the mma.sync engine rounds each 64-deep chunk's pair
+    value, about 2^-46 relative, then adds the chunks).  Their potentials agree
+    a thousand times closer than the mixed form's error bound of 1e-9."""
     import os
     wl = CASES["disk_l3_k16"]()
     plan = make_plan(V, wl, precision=1)
@@ -377,4 +382,4 @@ def test_tcgen05_engine_matches_mma_engine(V):
     scale = float(v_mma.abs().max())
     diff = float((v_tc - v_mma).abs().max())
     print("tcgen05 vs mma.sync max diff %.3e (scale %.3e)" % (diff, scale))
-    assert diff <= 1e-14 * scale
+    assert diff <= 1e-12 * scale
