@@ -202,6 +202,14 @@ const char *vpx_pass_name(int i);
  * argument. */
 int vpx_graph_kernel_count(vpx_plan_t plan, int64_t *kernels);
 
+/* Exercise the bounded-wait path of the tensor-core engines on device 0's
+ * current context: a kernel waits on a barrier that nothing completes, gives up
+ * after 20 ms of wall-clock time and latches VPX_ERR_TIMEOUT, which is
+ * returned in *status (VPX_ERR_TIMEOUT expected).  The paper has no
+ * counterpart; this is the failure-detection check of the build.  Errors:
+ * VPX_ERR_ARG for a null argument, VPX_ERR_CUDA / VPX_ERR_NODEV. */
+int vpx_check_bounded_wait(int *status);
+
 const char *vpx_error_string(int code);
 const char *vpx_last_error_message(void);
 

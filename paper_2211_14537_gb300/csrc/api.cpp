@@ -410,6 +410,11 @@ int vpx_get_timings(vpx_plan_t p, double *ms, int n) {
     return VPX_OK;
 }
 
+int vpx_check_bounded_wait(int *status) {
+    if (!status) return VPX_ERR_ARG;
+    return guarded([&] { return vpx::device_check_bounded_wait(status); });
+}
+
 int vpx_graph_kernel_count(vpx_plan_t p, int64_t *kernels) {
     if (!p || !kernels) return VPX_ERR_ARG;
     *kernels = p->graph_kernels;

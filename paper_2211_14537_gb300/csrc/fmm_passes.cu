@@ -267,30 +267,33 @@ void setup_passes(vpx_plan *p) {
         gemm_pass_upload_tables(F.m2l, m2l, kVSlots, P2, P2, mixed);
         gemm_pass_set_pairs(F.m2l, tv);
         gemm_pass_upload_tables(F.s2l, s2l, kXSlots, P2, KK, mixed);
-        gemm_pass_set_pairs(F.s2l, tx);
+        gemm_pass_set_pairs(F.s2l, tx, 32);   // third stream: fewer, fuller CTAs leave the main chain room
     }
-    // L2T, M2T, near
+    // L2T, M2T, near: the factor 1/2pi of the kernel is folded into the tables, so
+    // that every pair scale of every pass is a power of two (h^2 or 1)
     {
         const double inv2pi = 0.15915494309189533576888376337251;
+        for (std::vector<double> *t : {&l2t, &m2t, &near})
+            for (double &x : *t) x *= inv2pi;
         Tagged tt, tw, tn;
         for (int i = 0; i < nl; ++i) {
-            if (p->tree.leaves[i].level >= 2) tt.push_back({0, GPair{leaf_box[i], 0, (int64_t)i * KK, inv2pi}});
+            if (p->tree.leaves[i].level >= 2) tt.push_back({0, GPair{leaf_box[i], 0, (int64_t)i * KK, 1.0}});
             for (int s = 0; s < kWSlots; ++s) {
                 int wb = p->wlist[(size_t)i * kWSlots + s];
-                if (wb >= 0) tw.push_back({s, GPair{wb, 0, (int64_t)i * KK, inv2pi}});
+                if (wb >= 0) tw.push_back({s, GPair{wb, 0, (int64_t)i * KK, 1.0}});
             }
             for (int c = 0; c < kNearConfigs; ++c) {
                 int src = p->near[(size_t)i * kNearConfigs + c];
                 if (src >= 0) {
                     double h = 0.5 * lvl_side(p->tree.leaves[src].level);
-                    tn.push_back({c, GPair{src, 0, (int64_t)i * KK, h * h * inv2pi}});
+                    tn.push_back({c, GPair{src, 0, (int64_t)i * KK, h * h}});
                 }
             }
         }
         gemm_pass_upload_tables(F.l2t, l2t, 1, KK, P2, mixed);
         gemm_pass_set_pairs(F.l2t, tt);
         gemm_pass_upload_tables(F.m2t, m2t, kWSlots, KK, P2, mixed);
-        gemm_pass_set_pairs(F.m2t, tw);
+        gemm_pass_set_pairs(F.m2t, tw, 32);
         gemm_pass_upload_tables(F.near, near, kNearConfigs, KK, KK, mixed);
         gemm_pass_set_pairs(F.near, tn);
     }

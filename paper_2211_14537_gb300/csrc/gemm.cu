@@ -131,12 +131,12 @@ __global__ void k_slice_vec(const double *vbase, int64_t vld, int vstride, int f
 
 // ------------------------------------------------------------------ host
 
-void gemm_pass_set_pairs(GemmPass &g, std::vector<std::pair<int, GPair>> &tagged) {
+void gemm_pass_set_pairs(GemmPass &g, std::vector<std::pair<int, GPair>> &tagged, int frag_np) {
     std::stable_sort(tagged.begin(), tagged.end(),
                      [](const std::pair<int, GPair> &x, const std::pair<int, GPair> &y) { return x.first < y.first; });
     std::vector<GPair> pr;
     std::vector<GTile> tl, tf, tr, tp;
-    const size_t npf = tagged.size() >= (size_t)kFragBigPass ? 32 : 8;
+    const size_t npf = frag_np == 8 || frag_np == 32 ? (size_t)frag_np : tagged.size() >= (size_t)kFragBigPass ? 32 : 8;
     size_t i = 0;
     while (i < tagged.size()) {
         size_t j = i;

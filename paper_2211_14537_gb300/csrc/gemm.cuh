@@ -56,7 +56,8 @@ struct GemmPass {
 };
 
 // Host helpers
-void gemm_pass_set_pairs(GemmPass &g, std::vector<std::pair<int, GPair>> &tagged);   // (table, pair)
+// (table, pair); frag_np: pairs per fragment-engine tile (8 or 32; 0: by pass size)
+void gemm_pass_set_pairs(GemmPass &g, std::vector<std::pair<int, GPair>> &tagged, int frag_np = 0);
 void gemm_pass_upload_tables(GemmPass &g, const std::vector<double> &tab, int ntab, int M, int Kd, bool mixed);
 void gemm_pass_free(GemmPass &g);
 // Hand a mixed-form pass to the double-float row engine (gemm_rows.cu) when

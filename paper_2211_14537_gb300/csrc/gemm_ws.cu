@@ -31,6 +31,7 @@
 
 #include <cstdlib>
 
+#include "bulk.cuh"
 #include "dev_common.cuh"
 #include "gemm.cuh"
 #include "slice_math.cuh"
@@ -40,7 +41,6 @@ namespace vpx {
 constexpr int TW_M = 128, TW_K = 32, TW_STAGES = 3, TW_THREADS = 256, TW_PROD0 = 64;   // producers: threads 64..255
 constexpr int TW_NPROD = TW_THREADS - TW_PROD0;
 constexpr uint32_t TW_TMEM_COLS = 512;
-constexpr long long TW_SPIN = 1ll << 26;
 
 __device__ inline uint32_t tw_smem(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -54,19 +54,7 @@ __device__ inline uint64_t tw_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
 }
 
 __device__ inline bool tw_wait(uint64_t *bar, uint32_t parity) {
-    const uint32_t a = tw_smem(bar);
-    for (long long it = 0; it < TW_SPIN; ++it) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}\n"
-            : "=r"(done)
-            : "r"(a), "r"(parity)
-            : "memory");
-        if (done) return true;
-    }
-    return false;
+    return mbar_wait_bounded(tw_smem(bar), parity, kWaitLimitNs, 0);
 }
 
 struct WsArgs {
@@ -260,21 +248,8 @@ __global__ void __launch_bounds__(TW_THREADS, 1) k_gemm_ws(WsArgs a) {
     }
     // ---- epilogue (all warps) once every product is in tensor memory
     __syncwarp();
-    bool ok = !s_fail;
-    if (ok) {
-        ok = false;
-        for (long long it = 0; it < TW_SPIN / 64 && !ok; ++it) {   // idle threads: poll gently
-            uint32_t d;
-            asm volatile(
-                "{\n\t.reg .pred p;\n\t"
-                "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
-                "selp.u32 %0, 1, 0, p;\n\t}\n"
-                : "=r"(d)
-                : "r"(tw_smem(&done))
-                : "memory");
-            if (!(ok = d != 0)) __nanosleep(64);
-        }
-    }
+    // idle threads poll gently
+    const bool ok = !s_fail && mbar_wait_bounded(tw_smem(&done), 0, kWaitLimitNs, 64);
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     if (__syncthreads_and(ok)) {
         const int q4 = warp & 3, half = warp >> 2;

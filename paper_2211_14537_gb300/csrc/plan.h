@@ -137,6 +137,7 @@ void device_potential(vpx_plan *p, const double *fe_in, int64_t ldfe, int nrhs, 
 void device_execute(vpx_plan *p, const double *f, int nrhs, int64_t ldf, double *v, int64_t ldv, double *vb,
                     int64_t ldb, void *stream);
 int device_sync_status(vpx_plan *p);
+int device_check_bounded_wait(int *status_out);   // selftest.cu
 void device_copy_near_tables(vpx_plan *p, double *out);
 void device_potential_static(vpx_plan *p, const double *fe_in, int64_t ldfe, int nrhs, double *v, int64_t ldv,
                              double *vb, int64_t ldb, void *stream);

@@ -17,6 +17,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libvpx.so")
 
 VPX_OK = 0
+VPX_ERR_TIMEOUT = -7
+VPX_ERR_NAN = -8
 VPX_PREC_FP64 = 0
 VPX_PREC_MIXED = 1
 VPX_PLAN_HOST_ONLY = 1
@@ -47,7 +49,7 @@ EXPORTED = [
     "vpx_default_options", "vpx_plan_create", "vpx_plan_sizes", "vpx_plan_leaves", "vpx_stencil_points",
     "vpx_leaf_nodes", "vpx_boundary_nodes", "vpx_plan_list_counts", "vpx_plan_lists", "vpx_plan_near_tables", "vpx_execute",
     "vpx_extend", "vpx_potential", "vpx_potential_static", "vpx_execute_host", "vpx_sync_status", "vpx_set_timing",
-    "vpx_get_timings", "vpx_pass_name", "vpx_graph_kernel_count", "vpx_error_string", "vpx_last_error_message", "vpx_plan_destroy",
+    "vpx_get_timings", "vpx_pass_name", "vpx_graph_kernel_count", "vpx_check_bounded_wait", "vpx_error_string", "vpx_last_error_message", "vpx_plan_destroy",
 ]
 
 _lib = None
@@ -83,6 +85,7 @@ def load_library(path: str = LIB_PATH):
     L.vpx_set_timing.argtypes = [vp, ctypes.c_int]
     L.vpx_get_timings.argtypes = [vp, P(d), ctypes.c_int]
     L.vpx_graph_kernel_count.argtypes = [vp, P(ctypes.c_int64)]
+    L.vpx_check_bounded_wait.argtypes = [P(ctypes.c_int)]
     L.vpx_pass_name.argtypes = [ctypes.c_int]
     L.vpx_pass_name.restype = ctypes.c_char_p
     L.vpx_error_string.argtypes = [ctypes.c_int]
@@ -291,6 +294,13 @@ def vpx_sync_status(plan: Plan) -> int:
 
 def vpx_set_timing(plan: Plan, enable: bool = True):
     _check(load_library().vpx_set_timing(plan.handle, int(bool(enable))))
+
+
+def vpx_check_bounded_wait() -> int:
+    """Run the bounded-wait probe; returns the latched status (VPX_ERR_TIMEOUT expected)."""
+    st = ctypes.c_int(0)
+    _check(load_library().vpx_check_bounded_wait(ctypes.byref(st)))
+    return int(st.value)
 
 
 def vpx_graph_kernel_count(plan: Plan) -> int:

@@ -275,6 +275,23 @@ def test_execute_host_matches_device(V):
     assert np.max(np.abs(bh[0] - vb.cpu().numpy())) <= 1e-14 * np.max(np.abs(vh))
 
 
+def test_bounded_wait_reports_timeout_and_context_survives(V):
+    """A device wait that can never complete (a barrier nothing arrives on) gives
+    up after its wall-clock limit and latches VPX_ERR_TIMEOUT; the context stays
+    usable: a plan built and executed afterwards is correct."""
+    import time
+    t0 = time.perf_counter()
+    assert V.vpx_check_bounded_wait() == V.VPX_ERR_TIMEOUT
+    assert time.perf_counter() - t0 < 30.0
+    wl = W.disk_sincos(level=3, K=8)
+    plan = make_plan(V, wl, precision=1)
+    fs = torch.tensor(wl.sources[0](plan.stencil_points()), dtype=torch.float64, device="cuda")
+    v = torch.empty(plan.sizes()[1], dtype=torch.float64, device="cuda")
+    V.vpx_execute(plan, fs, v)
+    assert V.vpx_sync_status(plan) == 0
+    assert bool(torch.isfinite(v).all())
+
+
 def test_nan_input_is_reported(V):
     """Fault injection on the host: a NaN in f must come back as VPX_ERR_NAN."""
     wl = W.disk_sincos(level=3, K=8)
