@@ -400,3 +400,90 @@ def test_tcgen05_engine_matches_mma_engine(V):
     diff = float((v_tc - v_mma).abs().max())
     print("tcgen05 vs mma.sync max diff %.3e (scale %.3e)" % (diff, scale))
     assert diff <= 1e-12 * scale
+
+
+def _oracle_leaf_values(wl, tree, srcs):
+    pts, meta = O.stencil_points(tree, wl.domain)
+    F = np.stack([src(pts) for src in srcs], axis=1)
+    vals, _ = O.leaf_values(tree, wl.domain, F, meta)
+    return vals
+
+
+def test_c3_sixty_four_rhs_mixed_per_rhs(V):
+    """Config C3: 64 Gaussian-mixture right-hand sides on the uniform disk tree
+    (level 4, K = 8) in one call of the mixed form: potential of the oracle's
+    extended leaf values, every RHS against the FP64 oracle on a seeded sample
+    of targets; relative max-norm error per RHS <= 1e-9 (reported)."""
+    wl = W.disk_multi_rhs(64)
+    nrhs = len(wl.sources)
+    plan = make_plan(V, wl, max_rhs=nrhs, precision=1)
+    tree = O.build_tree(wl.domain, wl.opts, wl.sources[0])
+    vals = _oracle_leaf_values(wl, tree, wl.sources)
+    nodes = O.all_leaf_nodes(tree)
+    sub = _subset(len(nodes), 200, 31)
+    want = O.volume_potential(tree, vals, nodes[sub])          # (targets, rhs)
+    nt = len(nodes)
+    fe = torch.tensor(np.ascontiguousarray(vals.transpose(1, 0, 2).reshape(nrhs, nt)), dtype=torch.float64,
+                      device="cuda")
+    v = torch.empty((nrhs, nt), dtype=torch.float64, device="cuda")
+    V.vpx_potential(plan, fe, v)
+    assert V.vpx_sync_status(plan) == 0
+    got = v.cpu().numpy()[:, sub].T
+    err = np.max(np.abs(got - want), axis=0) / np.max(np.abs(want), axis=0)
+    print("C3 64 RHS mixed: rel err per RHS max %.3e median %.3e" % (err.max(), np.median(err)))
+    assert np.all(err <= 1e-9), err
+
+
+def test_c3_sixty_four_rhs_execute_matches_single_rhs(V):
+    """The 64-RHS execute (extension + potential, one graph) gives every column
+    what single-RHS executes give."""
+    wl = W.disk_multi_rhs(64)
+    nrhs = len(wl.sources)
+    plan = make_plan(V, wl, max_rhs=nrhs, precision=1)
+    sp = plan.stencil_points()
+    fs = torch.tensor(np.stack([src(sp) for src in wl.sources]), dtype=torch.float64, device="cuda")
+    nt = plan.sizes()[1]
+    v = torch.empty((nrhs, nt), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.Stream()
+    V.vpx_execute(plan, fs, v, stream=stream)
+    assert V.vpx_sync_status(plan) == 0
+    one = make_plan(V, wl, max_rhs=1, precision=1)
+    for r in (0, 17, 63):
+        v1 = torch.empty(nt, dtype=torch.float64, device="cuda")
+        V.vpx_execute(one, fs[r].contiguous(), v1)
+        assert V.vpx_sync_status(one) == 0
+        d = float((v[r] - v1).abs().max()) / float(v1.abs().max())
+        assert d <= 1e-12, (r, d)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_c4_lshape_full_size_sampled(V, precision):
+    """Config C4: the L-shape with corners refined to level 14 (5,407 leaves,
+    1.38 M leaf targets); sampled targets (seeded, plus those nearest the
+    re-entrant corner) against the oracle's potential of its own extended leaf
+    values: <= 1e-12 (FP64 form) or 1e-9 (mixed).  End to end, where the
+    extension's conditioning enters, the error is reported (<= 1e-6)."""
+    wl = W.lshape_expsin()
+    plan = make_plan(V, wl, p=50, precision=precision)
+    tree = O.build_tree(wl.domain, wl.opts, wl.sources[0])
+    assert tree.n_leaves == plan.sizes()[0]
+    vals = _oracle_leaf_values(wl, tree, wl.sources)
+    nodes = O.all_leaf_nodes(tree)
+    rng = np.random.Generator(np.random.PCG64(2214))
+    r0 = np.hypot(nodes[:, 0], nodes[:, 1])
+    sub = np.unique(np.concatenate([rng.choice(len(nodes), 120, replace=False), np.argsort(r0)[:30]]))
+    want = O.volume_potential(tree, vals, nodes[sub])[:, 0]
+    fe = torch.tensor(vals[:, 0, :].ravel(), dtype=torch.float64, device="cuda")
+    v = torch.empty(len(nodes), dtype=torch.float64, device="cuda")
+    V.vpx_potential(plan, fe, v)
+    assert V.vpx_sync_status(plan) == 0
+    err = np.max(np.abs(v.cpu().numpy()[sub] - want)) / np.max(np.abs(want))
+    print("C4 L-shape potential (precision %d) rel err %.3e" % (precision, err))
+    assert err <= (1e-12 if precision == 0 else 1e-9), err
+    fs = torch.tensor(wl.sources[0](plan.stencil_points()), dtype=torch.float64, device="cuda")
+    ve = torch.empty(len(nodes), dtype=torch.float64, device="cuda")
+    V.vpx_execute(plan, fs, ve)
+    assert V.vpx_sync_status(plan) == 0
+    e2e = np.max(np.abs(ve.cpu().numpy()[sub] - want)) / np.max(np.abs(want))
+    print("C4 L-shape end to end (precision %d) rel err %.3e" % (precision, e2e))
+    assert e2e <= 1e-6, e2e
