@@ -152,6 +152,22 @@ int vpx_plan_near_tables(vpx_plan_t plan, double *out);
 int vpx_execute(vpx_plan_t plan, const double *f_stencil, int nrhs, int64_t ld_f,
                 double *v_leaf, int64_t ld_v, double *v_bdry, int64_t ld_b, void *stream);
 
+/*
+ * Many trees at once (uneven batches): vpx_execute for n plans, captured into
+ * one CUDA graph on `stream` and replayed while the plans and buffers stay the
+ * same.  Each plan's passes run on that plan's own streams, forked from and
+ * joined back to `stream`, so small and large trees overlap.  Arrays have n
+ * entries each; entry i has the meaning of the same argument of vpx_execute
+ * for plans[i] (v_bdry[i] may be NULL).  The paper solves one tree at a time;
+ * batching is this library's.  Errors: VPX_ERR_ARG (null arrays, n < 1, a plan
+ * listed twice, a bad entry: nothing is launched), VPX_ERR_STATE (host-only
+ * plan), VPX_ERR_CUDA.  A NULL stream runs the plans one after the other
+ * without a graph.
+ */
+int vpx_execute_batch(int n, vpx_plan_t const *plans, const double *const *f_stencil, const int *nrhs,
+                      const int64_t *ld_f, double *const *v_leaf, const int64_t *ld_v, double *const *v_bdry,
+                      const int64_t *ld_b, void *stream);
+
 /* Extension only: f^e at all leaf nodes (device, nrhs columns, ld_fe >= n_leaf_nodes). */
 int vpx_extend(vpx_plan_t plan, const double *f_stencil, int nrhs, int64_t ld_f,
                double *fe_leaf, int64_t ld_fe, void *stream);

@@ -1,5 +1,6 @@
 // api.cpp -- the extern "C" entry points declared in include/vpx.h.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -228,6 +229,8 @@ int vpx_plan_create(const vpx_options *opt, int n_panels, vpx_curve_cb curve, vp
         if (n_panels < 0 || (n_panels > 0 && !curve) || !inside || !refine_f)
             fail(VPX_ERR_ARG, "missing callback");
         p = new vpx_plan();
+        static std::atomic<uint64_t> next_uid{1};
+        p->uid = next_uid++;
         p->opt = *opt;
         p->host_only = (flags & VPX_PLAN_HOST_ONLY) != 0;
         p->K = opt->K;
@@ -238,13 +241,9 @@ int vpx_plan_create(const vpx_options *opt, int n_panels, vpx_curve_cb curve, vp
         build_stencil(p->opt, cb, p->tree, p->stencil_xy, p->st, !p->host_only);
         build_leaf_and_boundary_nodes(p, cb);
         build_boxes(p);
-        if (p->host_only) {
-            build_lists_host(p);
-            count_lists(p);
-        } else {
-            device_setup(p);   // lists are built on the device and copied back
-            count_lists(p);
-        }
+        build_lists_host(p);
+        count_lists(p);
+        if (!p->host_only) device_setup(p);
     });
     if (rc != VPX_OK) {
         if (p) {
@@ -343,6 +342,27 @@ int vpx_execute(vpx_plan_t p, const double *f, int nrhs, int64_t ld_f, double *v
         if (nrhs < 1 || nrhs > p->opt.max_rhs) fail(VPX_ERR_ARG, "nrhs out of range");
         if ((ns && !f) || !v || ld_f < ns || ld_v < nt || (vb && ld_b < nbd)) fail(VPX_ERR_ARG, "bad buffer");
         device_execute(p, f, nrhs, ld_f, v, ld_v, vb, ld_b, stream);
+    });
+}
+
+int vpx_execute_batch(int n, vpx_plan_t const *plans, const double *const *f, const int *nrhs, const int64_t *ld_f,
+                      double *const *v, const int64_t *ld_v, double *const *vb, const int64_t *ld_b, void *stream) {
+    return guarded([&] {
+        if (n < 1 || !plans || !f || !nrhs || !ld_f || !v || !ld_v || !vb || !ld_b) fail(VPX_ERR_ARG, "null batch array");
+        for (int i = 0; i < n; ++i) {
+            vpx_plan *p = plans[i];
+            if (!p) fail(VPX_ERR_ARG, "null plan in batch");
+            for (int j = 0; j < i; ++j)
+                if (plans[j] == p) fail(VPX_ERR_ARG, "a plan appears twice in a batch");
+            int64_t ns = (int64_t)p->stencil_xy.size() / 2, nt = (int64_t)p->leaf_xy.size() / 2;
+            int64_t nbd = (int64_t)p->bdry_xy.size() / 2;
+            if (nrhs[i] < 1 || nrhs[i] > p->opt.max_rhs) fail(VPX_ERR_ARG, "nrhs out of range in batch");
+            if ((ns && !f[i]) || !v[i] || ld_f[i] < ns || ld_v[i] < nt || (vb[i] && ld_b[i] < nbd))
+                fail(VPX_ERR_ARG, "bad buffer in batch");
+        }
+        for (int i = 0; i < n; ++i)
+            if (plans[i]->host_only) fail(VPX_ERR_STATE, "host-only plan in batch");
+        device_execute_batch(n, plans, f, nrhs, ld_f, v, ld_v, vb, ld_b, stream);
     });
 }
 

@@ -8,6 +8,7 @@
 // Leaf values are the K x K Gauss-Legendre node values of f^e on each leaf.
 #include <cmath>
 #include <cstdlib>
+#include <mutex>
 #include <vector>
 
 #include "dev_common.cuh"
@@ -364,6 +365,67 @@ void device_execute(vpx_plan *p, const double *f, int nrhs, int64_t ldf, double 
         for (int i = 0; i < 10; ++i) p->graph_key[i] = key[i];
     }
     VPX_CUDA(cudaGraphLaunch((cudaGraphExec_t)p->graph_exec, s));
+}
+
+// A batch of plans in one graph.  One cached graph per process (the last
+// batch key); the key holds every plan's unique id, so a destroyed plan whose
+// address is reused never matches.
+static std::mutex g_batch_mu;
+static std::vector<int64_t> g_batch_key;
+static cudaGraphExec_t g_batch_exec = nullptr;
+
+void device_execute_batch(int n, vpx_plan *const *plans, const double *const *f, const int *nrhs, const int64_t *ldf,
+                          double *const *v, const int64_t *ldv, double *const *vb, const int64_t *ldb, void *stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    bool direct = s == nullptr || getenv("VPX_NO_GRAPH") != nullptr;
+    for (int i = 0; i < n; ++i) direct = direct || plans[i]->timing;
+    if (direct) {
+        for (int i = 0; i < n; ++i) {
+            plans[i]->last_stream = stream;
+            execute_sequence(plans[i], f[i], nrhs[i], ldf[i], v[i], ldv[i], vb[i], ldb[i], s);
+        }
+        return;
+    }
+    std::vector<int64_t> key = {n, (int64_t)(uintptr_t)s};
+    for (int i = 0; i < n; ++i) {
+        const int64_t k[8] = {(int64_t)plans[i]->uid, (int64_t)(uintptr_t)f[i], nrhs[i], ldf[i],
+                              (int64_t)(uintptr_t)v[i], ldv[i], (int64_t)(uintptr_t)vb[i], ldb[i]};
+        key.insert(key.end(), k, k + 8);
+    }
+    std::lock_guard<std::mutex> lock(g_batch_mu);
+    if (key != g_batch_key || !g_batch_exec) {
+        if (g_batch_exec) {
+            cudaGraphExecDestroy(g_batch_exec);
+            g_batch_exec = nullptr;
+        }
+        g_batch_key.clear();
+        cudaGraph_t graph = nullptr;
+        VPX_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        try {
+            for (int i = 0; i < n; ++i) {
+                vpx_plan *p = plans[i];
+                cudaStream_t ps = (cudaStream_t)p->stream;
+                VPX_CUDA(cudaEventRecord((cudaEvent_t)p->ev_bfork, s));
+                VPX_CUDA(cudaStreamWaitEvent(ps, (cudaEvent_t)p->ev_bfork, 0));
+                execute_sequence(p, f[i], nrhs[i], ldf[i], v[i], ldv[i], vb[i], ldb[i], ps);
+                VPX_CUDA(cudaEventRecord((cudaEvent_t)p->ev_bjoin, ps));
+                VPX_CUDA(cudaStreamWaitEvent(s, (cudaEvent_t)p->ev_bjoin, 0));
+            }
+        } catch (...) {
+            cudaStreamEndCapture(s, &graph);
+            if (graph) cudaGraphDestroy(graph);
+            throw;
+        }
+        VPX_CUDA(cudaStreamEndCapture(s, &graph));
+        cudaGraphExec_t exec = nullptr;
+        cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        VPX_CUDA(e);
+        g_batch_exec = exec;
+        g_batch_key = key;
+    }
+    VPX_CUDA(cudaGraphLaunch(g_batch_exec, s));
+    for (int i = 0; i < n; ++i) plans[i]->last_stream = stream;
 }
 
 int device_sync_status(vpx_plan *p) {

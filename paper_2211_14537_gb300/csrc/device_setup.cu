@@ -1,24 +1,13 @@
-// device_setup.cu -- per-geometry setup on the GPU: interaction lists (one
-// thread per box), near-field tables (polar quadrature), S2L tables, and the
-// small expansion/translation tables computed on the host.
+// device_setup.cu -- per-geometry setup on the GPU: near-field tables (polar
+// quadrature), S2L tables, the small expansion/translation tables computed on
+// the host, and the upload of the tree and its interaction lists.
 #include <algorithm>
 #include <cmath>
 #include <complex>
 
 #include "dev_common.cuh"
-#include "lists.h"
 
 namespace vpx {
-
-// ------------------------------------------------------------------ lists
-
-__global__ void k_build_lists(ListView v, int n_boxes, int32_t *near, int32_t *vlist, int32_t *xlist, int32_t *wlist) {
-    int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= n_boxes) return;
-    int lf = v.box_leaf[b];
-    lv_build_box(v, b, lf >= 0 ? near + (size_t)lf * kNearConfigs : nullptr, vlist + (size_t)b * kVSlots,
-                 xlist + (size_t)b * kXSlots, lf >= 0 ? wlist + (size_t)lf * kWSlots : nullptr);
-}
 
 // ------------------------------------------------------ near-field tables
 //
@@ -396,7 +385,7 @@ void device_setup(vpx_plan *p) {
     p->aux_stream = aux;
     VPX_CUDA(cudaStreamCreateWithFlags(&aux2, cudaStreamNonBlocking));
     p->aux2_stream = aux2;
-    for (void **e : {&p->ev_fork, &p->ev_up, &p->ev_join, &p->ev_s2l, &p->ev_join2})
+    for (void **e : {&p->ev_fork, &p->ev_up, &p->ev_join, &p->ev_s2l, &p->ev_join2, &p->ev_bfork, &p->ev_bjoin})
         VPX_CUDA(cudaEventCreateWithFlags((cudaEvent_t *)e, cudaEventDisableTiming));
     DevTree &d = p->dt;
     d.n_leaves = (int)p->tree.leaves.size();
@@ -426,35 +415,11 @@ void device_setup(vpx_plan *p) {
     p->ext.leaf_level = dev_upload(llev);
     p->ext.leaf_ix = dev_upload(lix);
     p->ext.leaf_iy = dev_upload(liy);
-    // lists on the device
-    std::vector<int32_t> ls(p->level_start, p->level_start + kMaxLevel + 2);
-    int32_t *dls = dev_upload(ls);
-    d.near = dev_alloc<int32_t>((size_t)d.n_leaves * kNearConfigs);
-    d.vlist = dev_alloc<int32_t>((size_t)d.n_boxes * kVSlots);
-    d.xlist = dev_alloc<int32_t>((size_t)d.n_boxes * kXSlots);
-    d.wlist = dev_alloc<int32_t>((size_t)d.n_leaves * kWSlots);
-    ListView v;
-    v.n_levels = d.n_levels;
-    v.level_start = dls;
-    v.morton = d.box_morton;
-    v.box_level = d.box_level;
-    v.box_ix = d.box_ix;
-    v.box_iy = d.box_iy;
-    v.box_child0 = d.box_child0;
-    v.box_leaf = d.box_leaf;
-    v.box_nz = d.box_nz;
-    v.leaf_nz = d.leaf_nz;
-    k_build_lists<<<(d.n_boxes + 127) / 128, 128>>>(v, d.n_boxes, d.near, d.vlist, d.xlist, d.wlist);
-    VPX_LAUNCH("k_build_lists");
-    p->near.resize((size_t)d.n_leaves * kNearConfigs);
-    p->vlist.resize((size_t)d.n_boxes * kVSlots);
-    p->xlist.resize((size_t)d.n_boxes * kXSlots);
-    p->wlist.resize((size_t)d.n_leaves * kWSlots);
-    VPX_CUDA(cudaMemcpy(p->near.data(), d.near, p->near.size() * 4, cudaMemcpyDeviceToHost));
-    VPX_CUDA(cudaMemcpy(p->vlist.data(), d.vlist, p->vlist.size() * 4, cudaMemcpyDeviceToHost));
-    VPX_CUDA(cudaMemcpy(p->xlist.data(), d.xlist, p->xlist.size() * 4, cudaMemcpyDeviceToHost));
-    VPX_CUDA(cudaMemcpy(p->wlist.data(), d.wlist, p->wlist.size() * 4, cudaMemcpyDeviceToHost));
-    dev_free(dls);
+    // interaction lists (built on the host, once per geometry)
+    d.near = dev_upload(p->near);
+    d.vlist = dev_upload(p->vlist);
+    d.xlist = dev_upload(p->xlist);
+    d.wlist = dev_upload(p->wlist);
     setup_tables(p);
     // extension data
     const StencilInfo &st = p->st;
@@ -594,7 +559,7 @@ void device_free(vpx_plan *p) {
         cudaGraphExecDestroy((cudaGraphExec_t)p->graph_exec);
         p->graph_exec = nullptr;
     }
-    for (void **e : {&p->ev_fork, &p->ev_up, &p->ev_join, &p->ev_s2l, &p->ev_join2})
+    for (void **e : {&p->ev_fork, &p->ev_up, &p->ev_join, &p->ev_s2l, &p->ev_join2, &p->ev_bfork, &p->ev_bjoin})
         if (*e) {
             cudaEventDestroy((cudaEvent_t)*e);
             *e = nullptr;

@@ -25,7 +25,6 @@
 
 #include "dev_common.cuh"
 #include "gemm.cuh"
-#include "lists.h"
 
 namespace vpx {
 

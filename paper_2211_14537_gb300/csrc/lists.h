@@ -1,7 +1,7 @@
 // lists.h -- interaction lists of the adaptive box FMM, one box at a time.
 //
-// The same routine runs as a CUDA kernel (one thread per box, lists built on
-// the device) and on the host (host-only plans and CPU tests).
+// Built on the host once per geometry (milliseconds for 1e5 boxes) and
+// uploaded; the passes only read the resulting slot arrays.
 //
 // For a box B at level l (Section 4, Fig. tree_levels):
 //  - near list (leaves only): colleagues that are leaves (incl. B itself),
@@ -19,12 +19,6 @@
 
 #include <cstdint>
 
-#ifdef __CUDACC__
-#define VPX_HD __host__ __device__
-#else
-#define VPX_HD
-#endif
-
 namespace vpx {
 
 struct ListView {
@@ -35,7 +29,7 @@ struct ListView {
     const uint8_t *box_nz, *leaf_nz;
 };
 
-VPX_HD inline uint32_t lv_morton(uint32_t ix, uint32_t iy) {
+inline uint32_t lv_morton(uint32_t ix, uint32_t iy) {
     uint32_t k = 0;
     for (int b = 0; b < 16; ++b) {
         k |= ((ix >> b) & 1u) << (2 * b);
@@ -45,7 +39,7 @@ VPX_HD inline uint32_t lv_morton(uint32_t ix, uint32_t iy) {
 }
 
 // box index at (level, ix, iy) or -1
-VPX_HD inline int32_t lv_find(const ListView &v, int l, int ix, int iy) {
+inline int32_t lv_find(const ListView &v, int l, int ix, int iy) {
     if (l < 0 || l >= v.n_levels) return -1;
     int n = 1 << l;
     if (ix < 0 || iy < 0 || ix >= n || iy >= n) return -1;
@@ -62,7 +56,7 @@ VPX_HD inline int32_t lv_find(const ListView &v, int l, int ix, int iy) {
 }
 
 // index (0..11) of position (rx, ry) in {-1,0,1,2}^2 \ {0,1}^2, row-major
-VPX_HD inline int lv_ring12(int rx, int ry) {
+inline int lv_ring12(int rx, int ry) {
     int idx = 0;
     for (int y = -1; y <= 2; ++y)
         for (int x = -1; x <= 2; ++x) {
@@ -74,7 +68,7 @@ VPX_HD inline int lv_ring12(int rx, int ry) {
 }
 
 // index (0..19) of position (rx, ry) in {-2..3}^2 \ {-1..2}^2, row-major
-VPX_HD inline int lv_ring20(int rx, int ry) {
+inline int lv_ring20(int rx, int ry) {
     int idx = 0;
     for (int y = -2; y <= 3; ++y)
         for (int x = -2; x <= 3; ++x) {
@@ -86,7 +80,7 @@ VPX_HD inline int lv_ring20(int rx, int ry) {
 }
 
 // index (0..39) of offset (dx, dy) in [-3,3]^2 \ [-1,1]^2, row-major
-VPX_HD inline int lv_ring40(int dx, int dy) {
+inline int lv_ring40(int dx, int dy) {
     int idx = 0;
     for (int y = -3; y <= 3; ++y)
         for (int x = -3; x <= 3; ++x) {
@@ -97,7 +91,7 @@ VPX_HD inline int lv_ring40(int dx, int dy) {
     return -1;
 }
 
-VPX_HD inline bool lv_touch(int l1, int x1, int y1, int l2, int x2, int y2) {
+inline bool lv_touch(int l1, int x1, int y1, int l2, int x2, int y2) {
     // closed boxes touch: compare on the finer grid
     int L = l1 > l2 ? l1 : l2;
     int a0 = x1 << (L - l1), a1 = (x1 + 1) << (L - l1), b0 = x2 << (L - l2), b1 = (x2 + 1) << (L - l2);
@@ -105,7 +99,7 @@ VPX_HD inline bool lv_touch(int l1, int x1, int y1, int l2, int x2, int y2) {
     return a0 <= b1 && b0 <= a1 && c0 <= d1 && d0 <= c1;
 }
 
-VPX_HD inline void lv_build_box(const ListView &v, int b, int32_t *near /*33 or null*/, int32_t *vl /*40*/,
+inline void lv_build_box(const ListView &v, int b, int32_t *near /*33 or null*/, int32_t *vl /*40*/,
                                 int32_t *xl /*20*/, int32_t *wl /*20 or null*/) {
     const int l = v.box_level[b], ix = v.box_ix[b], iy = v.box_iy[b];
     const int leaf = v.box_leaf[b];

@@ -86,6 +86,7 @@ struct FmmPasses {                // every contraction of the box FMM as a group
 }  // namespace vpx
 
 struct vpx_plan {
+    uint64_t uid = 0;             // unique per plan of the process (keys of cached batch graphs)
     vpx_options opt{};
     bool host_only = false;
     int K = 0, KK = 0, P = 0;
@@ -119,6 +120,7 @@ struct vpx_plan {
     void *aux2_stream = nullptr;  // third stream (lists i+ and i-)
     int64_t graph_kernels = 0;    // kernel nodes of the captured execute graph
     void *ev_fork = nullptr, *ev_up = nullptr, *ev_join = nullptr, *ev_s2l = nullptr, *ev_join2 = nullptr;
+    void *ev_bfork = nullptr, *ev_bjoin = nullptr;   // batch fork / join on the plan's own stream
     void *graph_exec = nullptr;   // captured vpx_execute sequence (cudaGraphExec_t)
     int64_t graph_key[10] = {0};
     double pass_ms[VPX_N_PASSES] = {0};
@@ -138,6 +140,8 @@ void device_execute(vpx_plan *p, const double *f, int nrhs, int64_t ldf, double 
                     int64_t ldb, void *stream);
 int device_sync_status(vpx_plan *p);
 int device_check_bounded_wait(int *status_out);   // selftest.cu
+void device_execute_batch(int n, vpx_plan *const *plans, const double *const *f, const int *nrhs, const int64_t *ldf,
+                          double *const *v, const int64_t *ldv, double *const *vb, const int64_t *ldb, void *stream);
 void device_copy_near_tables(vpx_plan *p, double *out);
 void device_potential_static(vpx_plan *p, const double *fe_in, int64_t ldfe, int nrhs, double *v, int64_t ldv,
                              double *vb, int64_t ldb, void *stream);

@@ -17,8 +17,17 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libvpx.so")
 
 VPX_OK = 0
+VPX_ERR_ARG = -1
+VPX_ERR_CUDA = -2
+VPX_ERR_NOMEM = -3
+VPX_ERR_STENCIL = -4
+VPX_ERR_DOMAIN = -5
+VPX_ERR_LEVEL = -6
 VPX_ERR_TIMEOUT = -7
 VPX_ERR_NAN = -8
+VPX_ERR_CALLBACK = -9
+VPX_ERR_STATE = -10
+VPX_ERR_NODEV = -11
 VPX_PREC_FP64 = 0
 VPX_PREC_MIXED = 1
 VPX_PLAN_HOST_ONLY = 1
@@ -48,6 +57,7 @@ CURVE_CB = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_
 EXPORTED = [
     "vpx_default_options", "vpx_plan_create", "vpx_plan_sizes", "vpx_plan_leaves", "vpx_stencil_points",
     "vpx_leaf_nodes", "vpx_boundary_nodes", "vpx_plan_list_counts", "vpx_plan_lists", "vpx_plan_near_tables", "vpx_execute",
+    "vpx_execute_batch",
     "vpx_extend", "vpx_potential", "vpx_potential_static", "vpx_execute_host", "vpx_sync_status", "vpx_set_timing",
     "vpx_get_timings", "vpx_pass_name", "vpx_graph_kernel_count", "vpx_check_bounded_wait", "vpx_error_string", "vpx_last_error_message", "vpx_plan_destroy",
 ]
@@ -78,6 +88,8 @@ def load_library(path: str = LIB_PATH):
     L.vpx_plan_near_tables.argtypes = [vp, P(d)]
     L.vpx_execute.argtypes = [vp, vp, ctypes.c_int, i64, vp, i64, vp, i64, vp]
     L.vpx_extend.argtypes = [vp, vp, ctypes.c_int, i64, vp, i64, vp]
+    L.vpx_execute_batch.argtypes = [ctypes.c_int, P(vp), P(vp), P(ctypes.c_int), P(i64), P(vp), P(i64), P(vp), P(i64),
+                                    vp]
     L.vpx_potential.argtypes = [vp, vp, ctypes.c_int, i64, vp, i64, vp, i64, vp]
     L.vpx_potential_static.argtypes = [vp, vp, ctypes.c_int, i64, vp, i64, vp, i64, vp]
     L.vpx_execute_host.argtypes = [vp, P(d), ctypes.c_int, P(d), P(d)]
@@ -249,6 +261,33 @@ def vpx_execute(plan: Plan, f_stencil, v_leaf, v_bdry=None, stream=None):
     if v_bdry is not None and v_bdry.numel() > 0:
         bp, _, ldb = _cols(v_bdry)
     _check(load_library().vpx_execute(plan.handle, fp, nrhs, ldf, vp_, ldv, bp, ldb, _stream_handle(stream)))
+
+
+def vpx_execute_batch(plans, f_stencils, v_leaves, v_bdrys=None, stream=None):
+    """vpx_execute for every (plan, f, v[, v_bdry]) of the lists, in one captured graph."""
+    n = len(plans)
+    vp = ctypes.c_void_p
+
+    def raw(x):
+        return x.value if isinstance(x, vp) else x
+
+    fps, nrs, ldfs, vps, ldvs, bps, ldbs = [], [], [], [], [], [], []
+    for i in range(n):
+        fp, nrhs, ldf = _cols(f_stencils[i])
+        vq, _, ldv = _cols(v_leaves[i])
+        bp, ldb = vp(0), 1
+        if v_bdrys is not None and v_bdrys[i] is not None and v_bdrys[i].numel() > 0:
+            bp, _, ldb = _cols(v_bdrys[i])
+        fps.append(raw(fp)); nrs.append(nrhs); ldfs.append(ldf)
+        vps.append(raw(vq)); ldvs.append(ldv); bps.append(raw(bp)); ldbs.append(ldb)
+
+    def arr(t, xs):
+        return (t * n)(*xs)
+
+    hs = [raw(p.handle) for p in plans]
+    _check(load_library().vpx_execute_batch(n, arr(vp, hs), arr(vp, fps), arr(ctypes.c_int, nrs),
+                                            arr(ctypes.c_int64, ldfs), arr(vp, vps), arr(ctypes.c_int64, ldvs),
+                                            arr(vp, bps), arr(ctypes.c_int64, ldbs), _stream_handle(stream)))
 
 
 def vpx_extend(plan: Plan, f_stencil, fe_leaf, stream=None):

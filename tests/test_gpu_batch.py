@@ -1,0 +1,147 @@
+"""Uneven batch of trees in one captured graph (vpx_execute_batch): 32 random
+star domains, each with its own Gaussian mixture and its own adaptive tree
+(deepest level drawn from {4..6}: 1.4e4 to 1.4e5 leaf targets per tree), in
+the mixed form.
+
+The batch must give every tree what a single vpx_execute gives (the same
+kernels on the same data), and sampled targets of several trees are checked
+end to end against the oracle: the oracle's extension (Section 3) followed by
+the oracle's direct quadrature of the volume potential (Eq. 2).
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def V():
+    import __graft_entry__ as g
+    g.build_library()
+    from paper_2211_14537_gb300 import vpx
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return vpx
+
+
+def _plan(V, wl, precision=1):
+    o = V.vpx_default_options(K=wl.opts.K, min_level=wl.opts.min_level, max_level=wl.opts.max_level,
+                              refine_tol=wl.opts.refine_tol, f_scale=wl.opts.f_scale, p=40, precision=precision)
+    return V.vpx_plan_create(o, wl.domain, wl.sources[0])
+
+
+@pytest.fixture(scope="module")
+def batch(V):
+    wls = W.star_batch(32)
+    plans = [_plan(V, wl) for wl in wls]
+    sizes = [p.sizes() for p in plans]
+    fs = [torch.tensor(wl.sources[0](p.stencil_points()), dtype=torch.float64, device="cuda")
+          for wl, p in zip(wls, plans)]
+    return wls, plans, sizes, fs
+
+
+def _outputs(sizes):
+    vs = [torch.full((sz[1],), float("nan"), dtype=torch.float64, device="cuda") for sz in sizes]
+    vbs = [torch.full((sz[3],), float("nan"), dtype=torch.float64, device="cuda") for sz in sizes]
+    return vs, vbs
+
+
+def test_c5_batch_matches_single_executes(V, batch):
+    wls, plans, sizes, fs = batch
+    npts = [sz[1] for sz in sizes]
+    assert min(npts) < 20000 and max(npts) > 100000          # uneven
+    stream = torch.cuda.Stream()
+    vs, vbs = _outputs(sizes)
+    V.vpx_execute_batch(plans, fs, vs, vbs, stream=stream)
+    for p in plans:
+        assert V.vpx_sync_status(p) == 0
+    # replay of the cached graph on fresh contents of the same buffers
+    for v in vs:
+        v.fill_(float("nan"))
+    V.vpx_execute_batch(plans, fs, vs, vbs, stream=stream)
+    stream.synchronize()
+    worst = 0.0
+    for i, p in enumerate(plans):
+        v1 = torch.empty(sizes[i][1], dtype=torch.float64, device="cuda")
+        vb1 = torch.empty(sizes[i][3], dtype=torch.float64, device="cuda")
+        V.vpx_execute(p, fs[i], v1, vb1, stream=stream)
+        assert V.vpx_sync_status(p) == 0
+        assert torch.isfinite(vs[i]).all() and torch.isfinite(vbs[i]).all()
+        d = max(float((vs[i] - v1).abs().max()) / float(v1.abs().max()),
+                float((vbs[i] - vb1).abs().max()) / float(vb1.abs().max()))
+        worst = max(worst, d)
+    print("C5 batch vs single executes: max rel diff %.3e over %d trees" % (worst, len(plans)))
+    assert worst == 0.0
+
+
+def test_c5_batch_sampled_against_oracle(V, batch):
+    wls, plans, sizes, fs = batch
+    stream = torch.cuda.Stream()
+    vs, vbs = _outputs(sizes)
+    V.vpx_execute_batch(plans, fs, vs, vbs, stream=stream)
+    for p in plans:
+        assert V.vpx_sync_status(p) == 0
+    order = np.argsort([sz[1] for sz in sizes])
+    picks = [int(order[0]), int(order[len(order) // 2]), int(order[-1])]
+    for i in picks:
+        wl = wls[i]
+        tree = O.build_tree(wl.domain, wl.opts, wl.sources[0])
+        assert tree.n_leaves == sizes[i][0]
+        pts, meta = O.stencil_points(tree, wl.domain)
+        vals, _ = O.leaf_values(tree, wl.domain, wl.sources[0](pts)[:, None], meta)
+        nodes = O.all_leaf_nodes(tree)
+        bnodes = plans[i].boundary_nodes()
+        rng = np.random.Generator(np.random.PCG64(2215 + i))
+        sub = np.sort(rng.choice(len(nodes), 60, replace=False))
+        bsub = np.sort(rng.choice(len(bnodes), 20, replace=False))
+        want = O.volume_potential(tree, vals, nodes[sub])[:, 0]
+        wantb = O.volume_potential(tree, vals, bnodes[bsub])[:, 0]
+        scale = max(np.max(np.abs(want)), np.max(np.abs(wantb)))
+        err = np.max(np.abs(vs[i].cpu().numpy()[sub] - want)) / scale
+        errb = np.max(np.abs(vbs[i].cpu().numpy()[bsub] - wantb)) / scale
+        print("C5 tree %s (%d leaf targets): rel err leaf %.3e boundary %.3e" % (wl.name, sizes[i][1], err, errb))
+        assert err <= 1e-9 and errb <= 1e-9, (wl.name, err, errb)
+
+
+def test_c5_batch_graph_follows_its_arguments(V, batch):
+    """A different selection or order of plans, or other buffers, is a new
+    graph; the results do not depend on the batch the tree is in."""
+    wls, plans, sizes, fs = batch
+    stream = torch.cuda.Stream()
+    sel = [5, 1, 23]
+    vs, vbs = _outputs([sizes[i] for i in sel])
+    V.vpx_execute_batch([plans[i] for i in sel], [fs[i] for i in sel], vs, vbs, stream=stream)
+    ref = []
+    for k, i in enumerate(sel):
+        assert V.vpx_sync_status(plans[i]) == 0
+        v1 = torch.empty(sizes[i][1], dtype=torch.float64, device="cuda")
+        V.vpx_execute(plans[i], fs[i], v1, stream=stream)
+        assert V.vpx_sync_status(plans[i]) == 0
+        assert torch.equal(vs[k], v1)
+        ref.append(v1)
+    rev = sel[::-1]
+    vs2, _ = _outputs([sizes[i] for i in rev])
+    V.vpx_execute_batch([plans[i] for i in rev], [fs[i] for i in rev], vs2, None, stream=stream)
+    for k, i in enumerate(rev):
+        assert V.vpx_sync_status(plans[i]) == 0
+        assert torch.equal(vs2[k], ref[len(sel) - 1 - k])
+    # a plan created after the cached graph was captured
+    extra = _plan(V, wls[1])
+    f_extra = torch.tensor(wls[1].sources[0](extra.stencil_points()), dtype=torch.float64, device="cuda")
+    vs3, _ = _outputs([sizes[1]])
+    V.vpx_execute_batch([extra], [f_extra], vs3, None, stream=stream)
+    assert V.vpx_sync_status(extra) == 0
+    assert torch.equal(vs3[0], ref[1])
+
+
+def test_c5_batch_rejects_bad_arguments(V, batch):
+    wls, plans, sizes, fs = batch
+    vs, vbs = _outputs(sizes[:2])
+    with pytest.raises(V.VpxError):
+        V.vpx_execute_batch([plans[0], plans[0]], [fs[0], fs[0]], [vs[0], vs[0]], None)
+    with pytest.raises(V.VpxError):
+        V.vpx_execute_batch([plans[0], plans[1]], [fs[0], fs[1]], [vs[1], vs[0]], None)   # short buffers

@@ -146,3 +146,21 @@ def test_lists_cover_every_pair_exactly_once(V, name):
             s = near[t, c]
             if s >= 0:
                 assert lv["level"][s] == lv["level"][t] + 1
+
+
+def test_batch_refuses_host_only_plans_and_bad_arrays(V):
+    """vpx_execute_batch validates every entry before anything is launched:
+    a host-only plan is a state error, a plan listed twice an argument error."""
+    wls = W.star_batch(2)
+    plans = [_plan(V, wl) for wl in wls]
+    torch = pytest.importorskip("torch")
+    f = [torch.zeros(p.sizes()[2], dtype=torch.float64) for p in plans]
+    v = [torch.zeros(p.sizes()[1], dtype=torch.float64) for p in plans]
+    with pytest.raises(V.VpxError) as e:
+        V.vpx_execute_batch(plans, f, v, None, stream=0)
+    assert e.value.code == V.VPX_ERR_STATE
+    with pytest.raises(V.VpxError) as e:
+        V.vpx_execute_batch([plans[0], plans[0]], f, v, None, stream=0)
+    assert e.value.code == V.VPX_ERR_ARG
+    L = V.load_library()
+    assert L.vpx_execute_batch(0, None, None, None, None, None, None, None, None, None) == V.VPX_ERR_ARG
