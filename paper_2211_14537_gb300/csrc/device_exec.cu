@@ -402,15 +402,17 @@ void device_execute_batch(int n, vpx_plan *const *plans, const double *const *f,
         cudaGraph_t graph = nullptr;
         VPX_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
         try {
+            // every tree forks from one point of `stream` and joins back at the
+            // end, so the trees' passes are independent branches of the graph
+            VPX_CUDA(cudaEventRecord((cudaEvent_t)plans[0]->ev_bfork, s));
             for (int i = 0; i < n; ++i) {
                 vpx_plan *p = plans[i];
                 cudaStream_t ps = (cudaStream_t)p->stream;
-                VPX_CUDA(cudaEventRecord((cudaEvent_t)p->ev_bfork, s));
-                VPX_CUDA(cudaStreamWaitEvent(ps, (cudaEvent_t)p->ev_bfork, 0));
+                VPX_CUDA(cudaStreamWaitEvent(ps, (cudaEvent_t)plans[0]->ev_bfork, 0));
                 execute_sequence(p, f[i], nrhs[i], ldf[i], v[i], ldv[i], vb[i], ldb[i], ps);
                 VPX_CUDA(cudaEventRecord((cudaEvent_t)p->ev_bjoin, ps));
-                VPX_CUDA(cudaStreamWaitEvent(s, (cudaEvent_t)p->ev_bjoin, 0));
             }
+            for (int i = 0; i < n; ++i) VPX_CUDA(cudaStreamWaitEvent(s, (cudaEvent_t)plans[i]->ev_bjoin, 0));
         } catch (...) {
             cudaStreamEndCapture(s, &graph);
             if (graph) cudaGraphDestroy(graph);

@@ -322,22 +322,21 @@ def lshape_expsin(K: int = 16, base_level: int = 6, max_level: int = 14, corner_
                     [f_exp_sin], "L-shape side 0.8, f=-3e^x sin2y, base level %d, corners to level %d" % (base_level, max_level))
 
 
-def star_batch(n_domains: int = 32, K: int = 8, tol: float = 1e-10, max_level: Optional[int] = None):
+def star_batch(n_domains: int = 32, K: int = 8, tol: Optional[float] = None, max_level: int = 11):
     """Uneven batch: random star domains r = .35(1 + sum_{k=2..8} a_k cos(k t + phi_k)),
     a_k ~ U[0, .04], phi_k ~ U[0, 2 pi), each with its own Gaussian mixture.
-    Without ``max_level`` each domain draws its deepest level from {4..6}
-    (level 4 is the coarsest whose cut-leaf extension squares stay inside D
-    for every such star), so the trees range from about 200 leaves (1.5e4
-    points at K = 8) to about two thousand (1.3e5 points)."""
+    Without ``tol`` each domain draws its refinement tolerance log-uniformly
+    from [1e-8, 1e-3], so every tree resolves its own f and the trees range
+    from about 300 leaves (1.8e4 points at K = 8) to about 6,000 (3.8e5)."""
     rng = np.random.Generator(np.random.PCG64(2211 + 5))
     out = []
     for d in range(n_domains):
         modes = [(k, rng.uniform(0.0, 0.04), rng.uniform(0.0, TWO_PI)) for k in range(2, 9)]
         dom = StarDomain(0.35, modes)
         f, _ = random_mixture(dom, rng)
-        ml = int(rng.integers(4, 7)) if max_level is None else int(max_level)
+        t = 10.0 ** rng.uniform(-8.0, -3.0) if tol is None else float(tol)
         out.append(Workload("star%02d" % d, 5, dom,
-                            TreeOptions(K=K, min_level=2, max_level=ml, refine_tol=tol, f_scale=1.0),
+                            TreeOptions(K=K, min_level=2, max_level=max_level, refine_tol=t, f_scale=1.0),
                             [f], "random star %d" % d))
     return out
 
