@@ -42,6 +42,10 @@ def parse():
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--oracle-sample", type=int, default=10000)   # ~10-15 s of oracle work on 16 cores
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default engine / tile choices")
+    ap.add_argument("--workload", default="starfish", choices=["starfish", "star-batch"],
+                    help="star-batch: the uneven batch of 32 star domains in one graph (mixed form), "
+                         "against the same trees run one after another in both forms")
     return ap.parse_args()
 
 
@@ -132,6 +136,9 @@ def run_gpu(args, rank, world, precision):
     def step():
         V.vpx_execute(plan, f, v, vb if nb else None, stream=stream)
 
+    tune = (0, 0)
+    if precision == "mixed" and not args.no_autotune:
+        tune = V.vpx_autotune(plan, f, stream=stream)   # engine / tile choices on this plan's data
     V.vpx_set_timing(plan, False)
     for _ in range(max(args.warmup, 3)):
         step()
@@ -192,7 +199,106 @@ def run_gpu(args, rank, world, precision):
     near_ms = pass_ms.get("near", float("nan"))
     return dict(plan=plan, wl=wl, ms=ms, times=times, setup_s=setup_s, tg=tg, nt=nt, nb=nb, ns=ns,
                 n_leaves=n_leaves, lc=lc, pass_ms=pass_ms, near_flops=near_flops, near_ms=near_ms,
-                clocks=cl, e2e_s=e2e_s, v=v[0].cpu().numpy(), vh=vh, K=K, graph_kernels=graph_kernels)
+                clocks=cl, e2e_s=e2e_s, v=v[0].cpu().numpy(), vh=vh, K=K, graph_kernels=graph_kernels, tune=tune)
+
+
+def run_batch(args):
+    """Uneven batch: 32 random star domains, each with its own mixture and tree,
+    in one vpx_execute_batch graph (mixed form), against the same trees run one
+    after another (mixed, and FP64 as in a plain sequential solver)."""
+    import torch
+    import workloads as W
+    from paper_2211_14537_gb300 import vpx as V
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    wls = W.star_batch(32)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def make(prec):
+        t0 = time.perf_counter()
+        plans = []
+        for wl in wls:
+            o = V.vpx_default_options(K=wl.opts.K, min_level=wl.opts.min_level, max_level=wl.opts.max_level,
+                                      refine_tol=wl.opts.refine_tol, f_scale=wl.opts.f_scale, p=args.p,
+                                      precision=prec)
+            plans.append(V.vpx_plan_create(o, wl.domain, wl.sources[0]))
+        return plans, time.perf_counter() - t0
+
+    def timed(step, steps):
+        for _ in range(max(args.warmup, 3)):
+            step()
+        torch.cuda.synchronize(dev)
+        e0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        e1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        for i in range(steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(float(i))
+                e0[i].record(stream)
+            step()
+            with torch.cuda.stream(stream):
+                e1[i].record(stream)
+        torch.cuda.synchronize(dev)
+        return statistics.mean([e0[i].elapsed_time(e1[i]) for i in range(steps)])
+
+    mixed, setup_mixed = make(V.VPX_PREC_MIXED)
+    sizes = [p.sizes() for p in mixed]
+    fs = [torch.tensor(wl.sources[0](p.stencil_points()), dtype=torch.float64, device=dev)
+          for wl, p in zip(wls, mixed)]
+    vs = [torch.empty(sz[1], dtype=torch.float64, device=dev) for sz in sizes]
+    vbs = [torch.empty(sz[3], dtype=torch.float64, device=dev) for sz in sizes]
+    targets = sum(sz[1] + sz[3] for sz in sizes)
+    tuned = [0, 0]
+    if not args.no_autotune:
+        t0 = time.perf_counter()
+        tuned = list(V.vpx_autotune_batch(mixed, fs, stream=stream))   # one choice per pass role, on the batch graph
+        tune_s = time.perf_counter() - t0
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    time.sleep(0.3)
+    ms_batch = timed(lambda: V.vpx_execute_batch(mixed, fs, vs, vbs, stream=stream), args.steps)
+    time.sleep(0.15)
+    cl = clocks.stop()
+    for p in mixed:
+        if V.vpx_sync_status(p) != 0:
+            raise RuntimeError("device status error in the batch")
+
+    def sequence(plans):
+        def step():
+            for i, p in enumerate(plans):
+                V.vpx_execute(p, fs[i], vs[i], vbs[i], stream=stream)
+        return step
+
+    ms_seq_mixed = timed(sequence(mixed), max(args.steps // 4, 5))
+    kernels = sum(V.vpx_graph_kernel_count(p) for p in mixed)
+    del mixed
+    fp64, setup_fp64 = make(V.VPX_PREC_FP64)
+    ms_seq_fp64 = timed(sequence(fp64), 5)
+    for p in fp64:
+        if V.vpx_sync_status(p) != 0:
+            raise RuntimeError("device status error in the FP64 sequence")
+    rate = lambda ms: targets / (ms * 1e-3)
+    out = {
+        "metric": METRIC, "value": rate(ms_batch), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": ms_batch, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16 (exact 7-bit slices) + f64",
+        "data": "synthetic (32 seeded random star domains, each with its own Gaussian mixture)",
+        "config": {"workload": "star_batch_32", "K": 8, "p": args.p, "trees": len(sizes),
+                   "leaf_targets": sum(sz[1] for sz in sizes), "boundary_targets": sum(sz[3] for sz in sizes),
+                   "leaf_targets_min": min(sz[1] for sz in sizes), "leaf_targets_max": max(sz[1] for sz in sizes),
+                   "l2": "flushed between timed steps (256 MB write, outside the events)",
+                   "graph": "one vpx_execute_batch graph replay per step",
+                   "setup_s": {"mixed": round(setup_mixed, 2), "fp64": round(setup_fp64, 2)},
+                   "autotune": {"passes_tuned": tuned[0], "passes_changed": tuned[1],
+                                "seconds": round(tune_s, 2) if not args.no_autotune else 0.0}},
+        "forms": {"mixed_batch": {"value": rate(ms_batch), "ms_per_step": ms_batch},
+                  "mixed_sequential": {"value": rate(ms_seq_mixed), "ms_per_step": ms_seq_mixed},
+                  "fp64_sequential": {"value": rate(ms_seq_fp64), "ms_per_step": ms_seq_fp64}},
+        "gpu_launches": kernels * args.steps,
+        "clocks": cl,
+    }
+    print(json.dumps(out), flush=True)
 
 
 def oracle_sample(wl, n_sample, seed=2213, nthreads=0):
@@ -221,6 +327,11 @@ def main():
     if args.impl == "reference":
         if rank == 0:
             run_reference(args, world)
+        return
+    if args.workload == "star-batch":
+        if world > 1:
+            raise SystemExit("--workload star-batch runs on one GPU")
+        run_batch(args)
         return
     forms = ["fp64", "mixed"] if args.precision == "both" else [args.precision]
     res = {f: run_gpu(args, rank, world, f) for f in forms}
@@ -278,7 +389,8 @@ def main():
                    "s2l_pairs": r["lc"]["s2l"], "m2t_pairs": r["lc"]["m2t"], "levels": r["lc"]["n_levels"],
                    "l2": "flushed between timed steps (256 MB write, outside the events)",
                    "graph": "vpx_execute replays a captured CUDA graph",
-                   "setup_s": round(r["setup_s"], 3), "parallelism": "replicas" if world > 1 else "single"},
+                   "setup_s": round(r["setup_s"], 3), "parallelism": "replicas" if world > 1 else "single",
+                   "autotune": {"passes_tuned": r["tune"][0], "passes_changed": r["tune"][1]}},
         "forms": {f: {"value": res[f]["tg"] * world / (res[f]["ms"] * 1e-3), "ms_per_step": res[f]["ms"],
                       "rel_err_vs_oracle": errs.get(f), "pass_ms": {k: round(x, 5) for k, x in res[f]["pass_ms"].items()}}
                   for f in forms},

@@ -168,6 +168,38 @@ int vpx_execute_batch(int n, vpx_plan_t const *plans, const double *const *f_ste
                       const int64_t *ld_f, double *const *v_leaf, const int64_t *ld_v, double *const *v_bdry,
                       const int64_t *ld_b, void *stream);
 
+/*
+ * Autotuner: picks, for every mixed-form pass that two engines or two tile
+ * widths can run, the choice that makes the whole step fastest on this
+ * plan's own data (the near field on tcgen05 or on mma.sync; 8 or 32 pairs per
+ * mma.sync tile).  It runs one execute on f_stencil (device, nrhs columns,
+ * ld_f) into internal buffers and records the pass calls.  It checks every
+ * candidate against the default choice to 1e-12 of the maximum, with outputs
+ * in scratch memory.  Then, pass by pass, it times replays of the captured
+ * execute graph under each candidate and keeps the fastest (one sweep of
+ * coordinate descent; a candidate replaces the current choice only if its step
+ * is at least 3 % shorter).  Choices are cached per pass-shape signature for the
+ * process, and later executes and graphs use them.  Synchronises `stream`;
+ * allocates and frees device scratch.  *n_passes and *n_changed (either may
+ * be NULL) receive the passes tuned and those whose choice differs from the
+ * default.  The paper has no counterpart: schedules and tile shapes are this
+ * library's.  Errors: VPX_ERR_ARG; VPX_ERR_STATE (a host-only plan, or a
+ * candidate that disagrees with the default, in which case the defaults are
+ * kept); VPX_ERR_CUDA; VPX_ERR_NOMEM.  An FP64-form plan has nothing to tune
+ * (VPX_OK, 0 passes).
+ */
+int vpx_autotune(vpx_plan_t plan, const double *f_stencil, int nrhs, int64_t ld_f, void *stream, int *n_passes,
+                 int *n_changed);
+
+/*
+ * The same for a batch (arrays of n entries, as in vpx_execute_batch): each
+ * pass role, meaning the same pass of every plan (near field, M2L, ...), gets
+ * one choice for all plans.  The choice is timed on replays of the batch
+ * graph, so that it suits trees that run side by side.  Not cached.
+ */
+int vpx_autotune_batch(int n, vpx_plan_t const *plans, const double *const *f_stencil, const int *nrhs,
+                       const int64_t *ld_f, void *stream, int *n_passes, int *n_changed);
+
 /* Extension only: f^e at all leaf nodes (device, nrhs columns, ld_fe >= n_leaf_nodes). */
 int vpx_extend(vpx_plan_t plan, const double *f_stencil, int nrhs, int64_t ld_f,
                double *fe_leaf, int64_t ld_fe, void *stream);

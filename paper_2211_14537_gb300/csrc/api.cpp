@@ -366,6 +366,36 @@ int vpx_execute_batch(int n, vpx_plan_t const *plans, const double *const *f, co
     });
 }
 
+int vpx_autotune(vpx_plan_t p, const double *f, int nrhs, int64_t ld_f, void *stream, int *n_passes, int *n_changed) {
+    return guarded([&] {
+        if (!p) fail(VPX_ERR_ARG, "null plan");
+        if (p->host_only) fail(VPX_ERR_STATE, "host-only plan");
+        const int64_t ns = (int64_t)p->stencil_xy.size() / 2;
+        if (nrhs < 1 || nrhs > p->opt.max_rhs) fail(VPX_ERR_ARG, "nrhs out of range");
+        if ((ns && !f) || ld_f < ns) fail(VPX_ERR_ARG, "bad stencil buffer");
+        device_autotune(1, &p, &f, &nrhs, &ld_f, stream, n_passes, n_changed);
+    });
+}
+
+int vpx_autotune_batch(int n, vpx_plan_t const *plans, const double *const *f, const int *nrhs, const int64_t *ld_f,
+                       void *stream, int *n_passes, int *n_changed) {
+    return guarded([&] {
+        if (n < 1 || !plans || !f || !nrhs || !ld_f) fail(VPX_ERR_ARG, "null batch array");
+        for (int i = 0; i < n; ++i) {
+            vpx_plan *p = plans[i];
+            if (!p) fail(VPX_ERR_ARG, "null plan in batch");
+            for (int j = 0; j < i; ++j)
+                if (plans[j] == p) fail(VPX_ERR_ARG, "a plan appears twice in a batch");
+            const int64_t ns = (int64_t)p->stencil_xy.size() / 2;
+            if (nrhs[i] < 1 || nrhs[i] > p->opt.max_rhs) fail(VPX_ERR_ARG, "nrhs out of range in batch");
+            if ((ns && !f[i]) || ld_f[i] < ns) fail(VPX_ERR_ARG, "bad stencil buffer in batch");
+        }
+        for (int i = 0; i < n; ++i)
+            if (plans[i]->host_only) fail(VPX_ERR_STATE, "host-only plan in batch");
+        device_autotune(n, plans, f, nrhs, ld_f, stream, n_passes, n_changed);
+    });
+}
+
 int vpx_extend(vpx_plan_t p, const double *f, int nrhs, int64_t ld_f, double *fe, int64_t ld_fe, void *stream) {
     return guarded([&] {
         if (!p) fail(VPX_ERR_ARG, "null plan");

@@ -6,8 +6,11 @@
 //   local      Psi(z) = sum_{l>=0} bt_l ((z - c) / L)^l
 //   V(x) = (1/2pi) Re Phi  (the complex log kernel; G = (1/2pi) log|x - y|).
 // Leaf values are the K x K Gauss-Legendre node values of f^e on each leaf.
+#include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdlib>
+#include <map>
 #include <mutex>
 #include <vector>
 
@@ -328,7 +331,7 @@ void device_execute(vpx_plan *p, const double *f, int nrhs, int64_t ldf, double 
         return;
     }
     const int64_t key[10] = {(int64_t)(uintptr_t)f, ldf, (int64_t)(uintptr_t)v, ldv, (int64_t)(uintptr_t)vb, ldb,
-                             nrhs, p->timing ? 1 : 0, (int64_t)(uintptr_t)s, 1};
+                             nrhs, p->timing ? 1 : 0, (int64_t)(uintptr_t)s, p->tune_epoch};
     bool hit = p->graph_exec != nullptr;
     for (int i = 0; i < 10 && hit; ++i) hit = key[i] == p->graph_key[i];
     if (!hit) {
@@ -388,9 +391,9 @@ void device_execute_batch(int n, vpx_plan *const *plans, const double *const *f,
     }
     std::vector<int64_t> key = {n, (int64_t)(uintptr_t)s};
     for (int i = 0; i < n; ++i) {
-        const int64_t k[8] = {(int64_t)plans[i]->uid, (int64_t)(uintptr_t)f[i], nrhs[i], ldf[i],
-                              (int64_t)(uintptr_t)v[i], ldv[i], (int64_t)(uintptr_t)vb[i], ldb[i]};
-        key.insert(key.end(), k, k + 8);
+        const int64_t k[9] = {(int64_t)plans[i]->uid, plans[i]->tune_epoch, (int64_t)(uintptr_t)f[i], nrhs[i],
+                              ldf[i], (int64_t)(uintptr_t)v[i], ldv[i], (int64_t)(uintptr_t)vb[i], ldb[i]};
+        key.insert(key.end(), k, k + 9);
     }
     std::lock_guard<std::mutex> lock(g_batch_mu);
     if (key != g_batch_key || !g_batch_exec) {
@@ -428,6 +431,252 @@ void device_execute_batch(int n, vpx_plan *const *plans, const double *const *f,
     }
     VPX_CUDA(cudaGraphLaunch(g_batch_exec, s));
     for (int i = 0; i < n; ++i) plans[i]->last_stream = stream;
+}
+
+// ------------------------------------------------------------------ autotuner
+//
+// The mixed-form passes that two engines or two tile widths can run (the near
+// field on tcgen05 or mma.sync; 8 or 32 pairs per mma.sync tile) are tuned on
+// the plans' own data.  One execute per plan records every pass call; each
+// candidate then replays the call into scratch memory and must agree with the
+// default choice to 1e-12 of the maximum (the candidates differ only in how
+// the exact order sums are split).  The choice is made by timing the whole
+// step -- the captured graph of the plan, or of the batch -- because a pass
+// timed alone favours wide tiles (fewer table reads), while inside the step
+// it shares the GPU with the passes on the other streams.  One sweep of
+// coordinate descent over the pass roles (the same member of every plan:
+// near field, M2L, ...) keeps, role by role, the candidate with the shortest
+// step if it beats the current choice by 3 %.  Single-plan results are cached
+// per pass-shape signature.
+
+bool gemm_frag_eligible(const GemmPass &g, const VecSet &vs);
+bool gemm_ws_eligible(const GemmPass &g, const VecSet &vs);
+
+static std::mutex g_tune_mu;
+static std::map<std::vector<int64_t>, std::vector<GemmChoice>> g_tune_cache;
+
+static void shape_key(const GemmCall &c, std::vector<int64_t> &key) {
+    const GemmPass &g = *c.g;
+    int64_t lg = 0;
+    while ((int64_t(1) << lg) < (int64_t)g.n_pairs) ++lg;
+    const int64_t k[10] = {g.M, g.Kd, g.Kpad, g.ntab, g.slices, lg, c.nrhs, c.vs.slices != nullptr ? 1 : 0,
+                           gemm_ws_eligible(g, c.vs) ? 1 : 0, g.add};
+    key.insert(key.end(), k, k + 10);
+}
+
+// elements from `out` that one call may write: (nrhs - 1) ldo + max dst + M
+static int64_t call_footprint(const GemmCall &c) {
+    int64_t mx = 0;
+    for (const GPair &q : c.g->h_pairs) mx = std::max<int64_t>(mx, q.dst);
+    return (int64_t)(c.nrhs - 1) * c.ldo + mx + c.g->M;
+}
+
+struct TunePass {
+    GemmCall call;
+    size_t role;                      // byte offset of the pass inside its plan
+    GemmChoice dflt;
+    std::vector<GemmChoice> cand;     // candidates that agree with the default
+};
+
+// np_f 0 means "any width": the tcgen05 engine does not use the fragment tiles
+static bool same_choice(GemmChoice a, GemmChoice b) {
+    return a.engine == b.engine && (a.np_f == b.np_f || a.np_f == 0 || b.np_f == 0);
+}
+
+void device_autotune(int n, vpx_plan *const *plans, const double *const *f, const int *nrhs, const int64_t *ldf,
+                     void *stream, int *n_passes, int *n_changed) {
+    cudaStream_t s = (cudaStream_t)stream;
+    int tuned = 0, changed = 0;
+    bool any_mixed = false;
+    for (int i = 0; i < n; ++i) any_mixed = any_mixed || plans[i]->opt.precision == VPX_PREC_MIXED;
+    if (!any_mixed) {
+        if (n_passes) *n_passes = 0;
+        if (n_changed) *n_changed = 0;
+        return;
+    }
+    std::vector<double *> v(n, nullptr), vb(n, nullptr);
+    std::vector<int64_t> ldv(n), ldb(n);
+    double *scratch = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    auto release = [&] {
+        gemm_set_recorder(nullptr);
+        dev_free(scratch);
+        for (int i = 0; i < n; ++i) {
+            dev_free(v[i]);
+            dev_free(vb[i]);
+        }
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    };
+    try {
+        // 1. record the pass calls of every plan (one execute each)
+        std::vector<TunePass> tp;
+        for (int i = 0; i < n; ++i) {
+            vpx_plan *p = plans[i];
+            ldv[i] = std::max<int64_t>((int64_t)p->dt.n_leaves * p->KK, 1);
+            ldb[i] = std::max<int64_t>((int64_t)p->bdry_xy.size() / 2, 1);
+            v[i] = dev_alloc<double>((size_t)ldv[i] * nrhs[i]);
+            vb[i] = p->bdry_xy.empty() ? nullptr : dev_alloc<double>((size_t)ldb[i] * nrhs[i]);
+            if (p->opt.precision != VPX_PREC_MIXED) continue;
+            std::vector<GemmCall> calls;
+            gemm_set_recorder(&calls);
+            execute_sequence(p, f[i], nrhs[i], ldf[i], v[i], ldv[i], vb[i], ldb[i], s);
+            gemm_set_recorder(nullptr);
+            std::vector<const GemmPass *> seen;
+            for (const GemmCall &c : calls) {
+                if (std::find(seen.begin(), seen.end(), c.g) != seen.end()) continue;   // first call of a pass
+                seen.push_back(c.g);
+                if (!gemm_frag_eligible(*c.g, c.vs)) continue;
+                const size_t role = (size_t)((const char *)c.g - (const char *)p);
+                if (role >= sizeof(vpx_plan)) continue;
+                TunePass t{c, role, gemm_choice(*c.g), {}};
+                // engine 0 routes to tcgen05 where eligible, else to the fragment engine;
+                // engine 1 forces the fragment engine (a distinct choice only where tcgen05 is eligible)
+                const int frag_engine = gemm_ws_eligible(*c.g, c.vs) ? 1 : 0;
+                if (frag_engine == 1) t.cand.push_back(GemmChoice{0, 0});
+                t.cand.push_back(GemmChoice{frag_engine, 8});
+                t.cand.push_back(GemmChoice{frag_engine, 32});
+                bool has_default = false;
+                for (const GemmChoice &x : t.cand) has_default = has_default || same_choice(x, t.dflt);
+                if (!has_default) fail(VPX_ERR_STATE, "autotune: the default choice is not a candidate");
+                tp.push_back(t);
+            }
+        }
+        VPX_CUDA(cudaStreamSynchronize(s));
+        // 2. every candidate must reproduce the default choice's output
+        int64_t fp = 1;
+        for (const TunePass &t : tp) fp = std::max(fp, call_footprint(t.call));
+        scratch = dev_alloc<double>((size_t)fp);
+        std::vector<double> ref, got;
+        for (TunePass &t : tp) {
+            GemmPass &g = *t.call.g;
+            const size_t m = (size_t)call_footprint(t.call);
+            for (int pass = 0; pass < 2; ++pass) {   // pass 0: the default, pass 1: the others
+                for (const GemmChoice &c : t.cand) {
+                    if (same_choice(c, t.dflt) != (pass == 0)) continue;
+                    gemm_set_choice(g, c);
+                    VPX_CUDA(cudaMemsetAsync(scratch, 0, m * sizeof(double), s));
+                    gemm_run(g, t.call.vs, scratch, t.call.ldo, t.call.nrhs, true, s);
+                    got.resize(m);
+                    VPX_CUDA(cudaMemcpyAsync(got.data(), scratch, m * sizeof(double), cudaMemcpyDeviceToHost, s));
+                    VPX_CUDA(cudaStreamSynchronize(s));
+                    if (pass == 0) {
+                        ref = got;
+                        continue;
+                    }
+                    if (ref.size() != m) fail(VPX_ERR_STATE, "autotune: no reference output for a pass");
+                    double mx = 0.0, d = 0.0;
+                    for (size_t i = 0; i < m; ++i) {
+                        mx = std::max(mx, std::fabs(ref[i]));
+                        d = std::max(d, std::fabs(got[i] - ref[i]));
+                    }
+                    if (!(d <= 1e-12 * mx)) {
+                        gemm_set_choice(g, t.dflt);
+                        fail(VPX_ERR_STATE, "autotune: an engine variant disagrees with the default");
+                    }
+                }
+            }
+            gemm_set_choice(g, t.dflt);
+        }
+        dev_free(scratch);
+        // 3. roles in call order; candidates common to every pass of a role
+        std::vector<size_t> roles;
+        for (const TunePass &t : tp)
+            if (std::find(roles.begin(), roles.end(), t.role) == roles.end()) roles.push_back(t.role);
+        std::vector<int64_t> sig;
+        if (n == 1) {
+            for (const TunePass &t : tp) shape_key(t.call, sig);
+            std::lock_guard<std::mutex> lock(g_tune_mu);
+            auto it = g_tune_cache.find(sig);
+            if (it != g_tune_cache.end() && it->second.size() == tp.size()) {
+                for (size_t k = 0; k < tp.size(); ++k) {
+                    gemm_set_choice(*tp[k].call.g, it->second[k]);
+                    changed += !same_choice(it->second[k], tp[k].dflt);
+                }
+                tuned = (int)tp.size();
+                sig.clear();
+                roles.clear();   // nothing left to time
+            }
+        }
+        // 4. coordinate descent on the time of the whole step
+        VPX_CUDA(cudaEventCreate(&e0));
+        VPX_CUDA(cudaEventCreate(&e1));
+        auto step = [&] {
+            if (n == 1) device_execute(plans[0], f[0], nrhs[0], ldf[0], v[0], ldv[0], vb[0], ldb[0], s);
+            else device_execute_batch(n, plans, f, nrhs, ldf, v.data(), ldv.data(), vb.data(), ldb.data(), s);
+        };
+        auto step_ms = [&] {
+            for (int i = 0; i < n; ++i) ++plans[i]->tune_epoch;   // recapture with the current choices
+            step();
+            step();
+            float best = 1e30f;
+            for (int rep = 0; rep < 3; ++rep) {
+                VPX_CUDA(cudaEventRecord(e0, s));
+                for (int r = 0; r < 5; ++r) step();
+                VPX_CUDA(cudaEventRecord(e1, s));
+                VPX_CUDA(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                VPX_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                best = std::min(best, ms);
+            }
+            return best;
+        };
+        for (size_t role : roles) {
+            std::vector<GemmChoice> common;
+            bool first = true;
+            for (const TunePass &t : tp) {
+                if (t.role != role) continue;
+                if (first) {
+                    common = t.cand;
+                    first = false;
+                    continue;
+                }
+                std::vector<GemmChoice> keep;
+                for (const GemmChoice &c : common)
+                    for (const GemmChoice &d : t.cand)
+                        if (same_choice(c, d)) keep.push_back(c);
+                common = keep;
+            }
+            // the current choices first; another wins only by 3 % (replay-to-replay noise is ~1-2 %)
+            std::vector<std::pair<TunePass *, GemmChoice>> current;
+            for (TunePass &t : tp)
+                if (t.role == role) current.push_back({&t, gemm_choice(*t.call.g)});
+            const float cur_ms = step_ms();
+            float best_ms = cur_ms;
+            GemmChoice best{-1, 0};
+            for (const GemmChoice &c : common) {
+                for (TunePass &t : tp)
+                    if (t.role == role) gemm_set_choice(*t.call.g, c);
+                const float ms = step_ms();
+                if (ms < 0.97f * cur_ms && ms < best_ms) {
+                    best_ms = ms;
+                    best = c;
+                }
+            }
+            for (auto &pc : current) gemm_set_choice(*pc.first->call.g, best.engine >= 0 ? best : pc.second);
+        }
+        if (!roles.empty()) {
+            std::vector<GemmChoice> chosen;
+            for (const TunePass &t : tp) {
+                const GemmChoice c = gemm_choice(*t.call.g);
+                chosen.push_back(c);
+                changed += !same_choice(c, t.dflt);
+            }
+            tuned = (int)tp.size();
+            if (n == 1) {
+                std::lock_guard<std::mutex> lock(g_tune_mu);
+                g_tune_cache[sig] = chosen;
+            }
+        }
+        VPX_CUDA(cudaStreamSynchronize(s));
+    } catch (...) {
+        release();
+        throw;
+    }
+    release();
+    for (int i = 0; i < n; ++i) ++plans[i]->tune_epoch;   // later executes capture with the choices
+    if (n_passes) *n_passes = tuned;
+    if (n_changed) *n_changed = changed;
 }
 
 int device_sync_status(vpx_plan *p) {

@@ -135,8 +135,9 @@ void gemm_pass_set_pairs(GemmPass &g, std::vector<std::pair<int, GPair>> &tagged
     std::stable_sort(tagged.begin(), tagged.end(),
                      [](const std::pair<int, GPair> &x, const std::pair<int, GPair> &y) { return x.first < y.first; });
     std::vector<GPair> pr;
-    std::vector<GTile> tl, tf, tr, tp;
+    std::vector<GTile> tl, tf, tfa, tr, tp;
     const size_t npf = frag_np == 8 || frag_np == 32 ? (size_t)frag_np : tagged.size() >= (size_t)kFragBigPass ? 32 : 8;
+    const size_t npa = npf == 8 ? 32 : 8;
     size_t i = 0;
     while (i < tagged.size()) {
         size_t j = i;
@@ -146,6 +147,8 @@ void gemm_pass_set_pairs(GemmPass &g, std::vector<std::pair<int, GPair>> &tagged
             tl.push_back({tagged[i].first, base + (int32_t)(k - i), (int32_t)std::min<size_t>(kGemmTileN, j - k), 0});
         for (size_t k = i; k < j; k += npf)
             tf.push_back({tagged[i].first, base + (int32_t)(k - i), (int32_t)std::min<size_t>(npf, j - k), 0});
+        for (size_t k = i; k < j; k += npa)
+            tfa.push_back({tagged[i].first, base + (int32_t)(k - i), (int32_t)std::min<size_t>(npa, j - k), 0});
         for (size_t k = i; k < j; k += kRowsTileN)
             tr.push_back({tagged[i].first, base + (int32_t)(k - i), (int32_t)std::min<size_t>(kRowsTileN, j - k), 0});
         for (size_t k = i; k < j; k += kPairTileN)
@@ -160,6 +163,9 @@ void gemm_pass_set_pairs(GemmPass &g, std::vector<std::pair<int, GPair>> &tagged
     g.n_tiles_r = (int)tr.size();
     g.n_tiles_p = (int)tp.size();
     g.np_f = (int)npf;
+    g.n_tiles_f_alt = (int)tfa.size();
+    g.np_f_alt = (int)npa;
+    g.tiles_f_alt = dev_upload(tfa);
     g.pairs = dev_upload(pr);
     g.tiles = dev_upload(tl);
     g.tiles_f = dev_upload(tf);
@@ -255,12 +261,28 @@ void gemm_pass_free(GemmPass &g) {
     dev_free(g.tiles);
     dev_free(g.tfrag);
     dev_free(g.tiles_f);
+    dev_free(g.tiles_f_alt);
     dev_free(g.tiles_r);
     dev_free(g.tiles_p);
     dev_free(g.tdfT);
     dev_free(g.tint);
-    g.n_pairs = g.n_tiles = g.n_tiles_f = g.n_tiles_r = g.n_tiles_p = 0;
+    g.n_pairs = g.n_tiles = g.n_tiles_f = g.n_tiles_f_alt = g.n_tiles_r = g.n_tiles_p = 0;
 }
+
+GemmChoice gemm_choice(const GemmPass &g) { return GemmChoice{g.engine, g.np_f}; }
+
+void gemm_set_choice(GemmPass &g, GemmChoice c) {
+    g.engine = c.engine;
+    if (c.np_f != 0 && c.np_f != g.np_f && c.np_f == g.np_f_alt) {   // np_f 0: keep the current width
+        std::swap(g.tiles_f, g.tiles_f_alt);
+        std::swap(g.n_tiles_f, g.n_tiles_f_alt);
+        std::swap(g.np_f, g.np_f_alt);
+    }
+}
+
+static thread_local std::vector<GemmCall> *t_recorder = nullptr;
+
+void gemm_set_recorder(std::vector<GemmCall> *rec) { t_recorder = rec; }
 
 bool gemm_frag_eligible(const GemmPass &g, const VecSet &vs);
 void gemm_rows_run(const GemmPass &g, const VecSet &vs, double *out, int64_t ldo, int nrhs, void *s);
@@ -281,8 +303,9 @@ void gemm_run(const GemmPass &g, const VecSet &vs, double *out, int64_t ldo, int
         gemm_rows_run(g, vs, out, ldo, nrhs, sv);
         return;
     }
+    if (t_recorder) t_recorder->push_back(GemmCall{const_cast<GemmPass *>(&g), vs, out, ldo, nrhs});
     const bool no_tc = getenv("VPX_NO_TC") != nullptr;   // read per call: lets a test compare the engines
-    if (!no_tc && gemm_ws_eligible(g, vs)) {
+    if (!no_tc && g.engine == 0 && gemm_ws_eligible(g, vs)) {
         gemm_ws_run(g, vs, out, ldo, nrhs, sv);
         return;
     }

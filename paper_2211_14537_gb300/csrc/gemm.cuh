@@ -33,6 +33,16 @@ struct GTile {
     int32_t tab, first, count, pad;
 };
 
+struct VecSet {                        // source vectors of a pass
+    const double *base = nullptr;      // vector v of rhs r at base + r*ld + v*stride
+    int64_t ld = 0;
+    int stride = 0;
+    uint16_t *slices = nullptr;        // mixed form: [rhs][nvec][S][Kpad], or null: sliced where used
+    int32_t *expo = nullptr;           // [rhs][nvec]
+    int nvec = 0;
+    int kpad = 0;                      // inner length of the stored slices
+};
+
 // One pass on the device.
 struct GemmPass {
     int M = 0, Kd = 0, Kpad = 0, Mpad = 0, ntab = 0;
@@ -52,8 +62,31 @@ struct GemmPass {
     const uint16_t *tint = nullptr;    // [ntab][S][Kpad/8][Mpad][8] slices, column chunks interleaved (tcgen05 engine)
     int ws_kind = 0;                   // 0: not on that engine; 1: table rows on M; 2: pairs on M
     int n_pairs = 0, n_tiles = 0, n_tiles_f = 0, np_f = 8, n_tiles_r = 0, n_tiles_p = 0;
+    // the fragment engine's other tile width (8 <-> 32 pairs), for the autotuner
+    GTile *tiles_f_alt = nullptr;
+    int n_tiles_f_alt = 0, np_f_alt = 32;
+    int engine = 0;                    // 0: default routing; 1: fragment engine even where tcgen05 is eligible
     std::vector<GPair> h_pairs;        // host copy (setup)
 };
+
+// The schedule choices of one mixed-form pass that the autotuner may change.
+struct GemmChoice {
+    int engine;   // 0: default routing (tcgen05 where eligible), 1: fragment engine
+    int np_f;     // fragment-engine pairs per tile (8 or 32; 0: keep the current width)
+};
+GemmChoice gemm_choice(const GemmPass &g);
+void gemm_set_choice(GemmPass &g, GemmChoice c);
+
+// One recorded call of gemm_run (the autotuner replays recorded calls).
+struct GemmCall {
+    GemmPass *g;
+    VecSet vs;
+    double *out;
+    int64_t ldo;
+    int nrhs;
+};
+// While non-null, gemm_run appends every mixed-form call it makes on this thread.
+void gemm_set_recorder(std::vector<GemmCall> *rec);
 
 // Host helpers
 // (table, pair); frag_np: pairs per fragment-engine tile (8 or 32; 0: by pass size)
@@ -69,15 +102,6 @@ void gemm_frag_prepare_device();
 void gemm_ws_prepare(GemmPass &g);
 void gemm_ws_prepare_device();
 
-struct VecSet {                        // source vectors of a pass
-    const double *base = nullptr;      // vector v of rhs r at base + r*ld + v*stride
-    int64_t ld = 0;
-    int stride = 0;
-    uint16_t *slices = nullptr;        // mixed form: [rhs][nvec][S][Kpad], or null: sliced where used
-    int32_t *expo = nullptr;           // [rhs][nvec]
-    int nvec = 0;
-    int kpad = 0;                      // inner length of the stored slices
-};
 
 // Launches (stream s): run a pass on nrhs right-hand sides.
 void gemm_run(const GemmPass &g, const VecSet &vs, double *out, int64_t ldo, int nrhs, bool mixed, void *s);

@@ -87,6 +87,7 @@ struct FmmPasses {                // every contraction of the box FMM as a group
 
 struct vpx_plan {
     uint64_t uid = 0;             // unique per plan of the process (keys of cached batch graphs)
+    int64_t tune_epoch = 0;       // bumped whenever the autotuner changes a pass (keys of cached graphs)
     vpx_options opt{};
     bool host_only = false;
     int K = 0, KK = 0, P = 0;
@@ -143,6 +144,8 @@ int device_check_bounded_wait(int *status_out);   // selftest.cu
 void device_execute_batch(int n, vpx_plan *const *plans, const double *const *f, const int *nrhs, const int64_t *ldf,
                           double *const *v, const int64_t *ldv, double *const *vb, const int64_t *ldb, void *stream);
 void device_copy_near_tables(vpx_plan *p, double *out);
+void device_autotune(int n, vpx_plan *const *plans, const double *const *f, const int *nrhs, const int64_t *ldf,
+                     void *stream, int *n_passes, int *n_changed);
 void device_potential_static(vpx_plan *p, const double *fe_in, int64_t ldfe, int nrhs, double *v, int64_t ldv,
                              double *vb, int64_t ldb, void *stream);
 void device_execute_host(vpx_plan *p, const double *f, int nrhs, double *v, double *vb);

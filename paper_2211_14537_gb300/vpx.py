@@ -57,7 +57,7 @@ CURVE_CB = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_
 EXPORTED = [
     "vpx_default_options", "vpx_plan_create", "vpx_plan_sizes", "vpx_plan_leaves", "vpx_stencil_points",
     "vpx_leaf_nodes", "vpx_boundary_nodes", "vpx_plan_list_counts", "vpx_plan_lists", "vpx_plan_near_tables", "vpx_execute",
-    "vpx_execute_batch",
+    "vpx_execute_batch", "vpx_autotune", "vpx_autotune_batch",
     "vpx_extend", "vpx_potential", "vpx_potential_static", "vpx_execute_host", "vpx_sync_status", "vpx_set_timing",
     "vpx_get_timings", "vpx_pass_name", "vpx_graph_kernel_count", "vpx_check_bounded_wait", "vpx_error_string", "vpx_last_error_message", "vpx_plan_destroy",
 ]
@@ -91,6 +91,9 @@ def load_library(path: str = LIB_PATH):
     L.vpx_execute_batch.argtypes = [ctypes.c_int, P(vp), P(vp), P(ctypes.c_int), P(i64), P(vp), P(i64), P(vp), P(i64),
                                     vp]
     L.vpx_potential.argtypes = [vp, vp, ctypes.c_int, i64, vp, i64, vp, i64, vp]
+    L.vpx_autotune.argtypes = [vp, vp, ctypes.c_int, i64, vp, P(ctypes.c_int), P(ctypes.c_int)]
+    L.vpx_autotune_batch.argtypes = [ctypes.c_int, P(vp), P(vp), P(ctypes.c_int), P(i64), vp, P(ctypes.c_int),
+                                     P(ctypes.c_int)]
     L.vpx_potential_static.argtypes = [vp, vp, ctypes.c_int, i64, vp, i64, vp, i64, vp]
     L.vpx_execute_host.argtypes = [vp, P(d), ctypes.c_int, P(d), P(d)]
     L.vpx_sync_status.argtypes = [vp]
@@ -288,6 +291,30 @@ def vpx_execute_batch(plans, f_stencils, v_leaves, v_bdrys=None, stream=None):
     _check(load_library().vpx_execute_batch(n, arr(vp, hs), arr(vp, fps), arr(ctypes.c_int, nrs),
                                             arr(ctypes.c_int64, ldfs), arr(vp, vps), arr(ctypes.c_int64, ldvs),
                                             arr(vp, bps), arr(ctypes.c_int64, ldbs), _stream_handle(stream)))
+
+
+def vpx_autotune(plan: Plan, f_stencil, stream=None):
+    """Time the engine / tile-width candidates of the plan's mixed-form passes on
+    its own data and keep the fastest; returns (passes tuned, passes changed)."""
+    fp, nrhs, ldf = _cols(f_stencil)
+    npass, nchg = ctypes.c_int(), ctypes.c_int()
+    _check(load_library().vpx_autotune(plan.handle, fp, nrhs, ldf, _stream_handle(stream), ctypes.byref(npass),
+                                       ctypes.byref(nchg)))
+    return npass.value, nchg.value
+
+
+def vpx_autotune_batch(plans, f_stencils, stream=None):
+    """vpx_autotune for a batch: one choice per pass role, timed on the batch graph."""
+    n = len(plans)
+    vp = ctypes.c_void_p
+    raw = lambda x: x.value if isinstance(x, vp) else x
+    cols = [_cols(t) for t in f_stencils]
+    npass, nchg = ctypes.c_int(), ctypes.c_int()
+    _check(load_library().vpx_autotune_batch(n, (vp * n)(*[raw(p.handle) for p in plans]),
+                                             (vp * n)(*[raw(c[0]) for c in cols]), (ctypes.c_int * n)(*[c[1] for c in cols]),
+                                             (ctypes.c_int64 * n)(*[c[2] for c in cols]), _stream_handle(stream),
+                                             ctypes.byref(npass), ctypes.byref(nchg)))
+    return npass.value, nchg.value
 
 
 def vpx_extend(plan: Plan, f_stencil, fe_leaf, stream=None):

@@ -187,3 +187,23 @@ def test_c5_batch_rejects_bad_arguments(V, batch):
         V.vpx_execute_batch([plans[0], plans[0]], [fs[0], fs[0]], [vs[0], vs[0]], None)
     with pytest.raises(V.VpxError):
         V.vpx_execute_batch([plans[0], plans[1]], [fs[0], fs[1]], [vs[1], vs[0]], None)   # short buffers
+
+
+def test_c5_batch_autotune_keeps_results(V, batch):
+    """The batch autotuner (one engine / tile choice per pass role, timed on the
+    batch graph) leaves every tree's result unchanged to 1e-12."""
+    wls, plans, sizes, fs = batch
+    stream = torch.cuda.Stream()
+    vs, vbs = _outputs(sizes)
+    V.vpx_execute_batch(plans, fs, vs, vbs, stream=stream)
+    stream.synchronize()
+    npass, nchg = V.vpx_autotune_batch(plans, fs, stream=stream)
+    print("C5 batch autotune: %d passes tuned, %d changed" % (npass, nchg))
+    assert npass >= 4 * len(plans)
+    vs2, vbs2 = _outputs(sizes)
+    V.vpx_execute_batch(plans, fs, vs2, vbs2, stream=stream)
+    for i, p in enumerate(plans):
+        assert V.vpx_sync_status(p) == 0
+        scale = float(vs[i].abs().max())
+        assert float((vs2[i] - vs[i]).abs().max()) <= 1e-12 * scale
+        assert float((vbs2[i] - vbs[i]).abs().max()) <= 1e-12 * scale

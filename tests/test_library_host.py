@@ -164,3 +164,13 @@ def test_batch_refuses_host_only_plans_and_bad_arrays(V):
     assert e.value.code == V.VPX_ERR_ARG
     L = V.load_library()
     assert L.vpx_execute_batch(0, None, None, None, None, None, None, None, None, None) == V.VPX_ERR_ARG
+
+
+def test_autotune_refuses_host_only_plan(V):
+    torch = pytest.importorskip("torch")
+    wl = W.disk_sincos(level=3)
+    plan = _plan(V, wl)
+    f = torch.zeros(plan.sizes()[2], dtype=torch.float64)
+    with pytest.raises(V.VpxError) as e:
+        V.vpx_autotune(plan, f, stream=0)
+    assert e.value.code == V.VPX_ERR_STATE
