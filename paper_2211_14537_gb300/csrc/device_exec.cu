@@ -219,11 +219,17 @@ static void run_extension(vpx_plan *p, const double *f, int nrhs, int64_t ldf, d
                           cudaStream_t s) {
     const int nl = p->dt.n_leaves, KK = p->KK;
     const int64_t n = (int64_t)nl * KK;
+    // regular and unowned exterior leaves on the second stream, beside the
+    // extension (which writes only the cut leaves and their extension lists)
+    cudaStream_t aux = (cudaStream_t)p->aux_stream;
     if (n > 0) {
+        VPX_CUDA(cudaEventRecord((cudaEvent_t)p->ev_lvf, s));
+        VPX_CUDA(cudaStreamWaitEvent(aux, (cudaEvent_t)p->ev_lvf, 0));
         dim3 g((unsigned)((n + 255) / 256), nrhs);
-        k_leafvals<<<g, 256, 0, s>>>(nl, KK, p->dt.leaf_cls, p->ext.owned_flag_dev, p->ext.reg_leaf_off, f, ldf, fe,
-                                     ldfe);
+        k_leafvals<<<g, 256, 0, aux>>>(nl, KK, p->dt.leaf_cls, p->ext.owned_flag_dev, p->ext.reg_leaf_off, f, ldf, fe,
+                                       ldfe);
         VPX_LAUNCH("k_leafvals");
+        VPX_CUDA(cudaEventRecord((cudaEvent_t)p->ev_lv, aux));
     }
     if (p->ext.ncut > 0) {
         const StencilInfo &st = p->st;
@@ -269,6 +275,7 @@ static void run_extension(vpx_plan *p, const double *f, int nrhs, int64_t ldf, d
             VPX_LAUNCH("k_extend");
         }
     }
+    if (n > 0) VPX_CUDA(cudaStreamWaitEvent(s, (cudaEvent_t)p->ev_lv, 0));
 }
 
 void run_potential_passes(vpx_plan *p, const double *fe, int64_t ldfe, int nrhs, double *v, int64_t ldv, double *vb,

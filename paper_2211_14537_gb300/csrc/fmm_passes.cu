@@ -47,12 +47,9 @@ __global__ void k_const_gather(int rows, int first, int P, const int32_t *off, c
     double c = 0.0;
     for (int e = e0 + lane; e < e1; e += 32) c += coef[e] * mp[(int64_t)idx[e] * 2 * P];
     for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    // atomic: the locals take M2L at the same time, V the near field and L2T
     double *o = out + rhs * ldo + (int64_t)(first + r) * stride;
-    if (width == 1) {
-        if (lane == 0) o[0] += c;
-    } else {
-        for (int i = lane; i < width; i += 32) atomicAdd(o + i, c);   // concurrent with the near field
-    }
+    for (int i = lane; i < width; i += 32) atomicAdd(o + i, c);
 }
 
 // ------------------------------------------------------------ tables
@@ -412,6 +409,9 @@ void run_potential_passes(vpx_plan *p, const double *fe, int64_t ldfe, int nrhs,
     const int kp_f = (KK + 31) / 32 * 32, kp_m = (P2 + 31) / 32 * 32;
     FmmPasses &F = p->fmm;
     VecSet vf{fe, ldfe, KK, F.fe_sl, F.fe_ex, nl, kp_f};
+    // L2M reads every leaf once: it slices the leaf values itself, so it need
+    // not wait for the slicing that the near field and list i+ share
+    VecSet vf_fly{fe, ldfe, KK, nullptr, nullptr, nl, 0};
     // expansions along the level chains are sliced by the pass that reads them;
     // the final multipoles once, for lists i and i-
     VecSet vm{mp, ldm, P2, nullptr, nullptr, nb, 0};
@@ -423,44 +423,48 @@ void run_potential_passes(vpx_plan *p, const double *fe, int64_t ldfe, int nrhs,
     VPX_CUDA(cudaMemsetAsync(mp, 0, sizeof(double) * ldm * nrhs, s));
     VPX_CUDA(cudaMemsetAsync(lo, 0, sizeof(double) * ldm * nrhs, s));
     VPX_CUDA(cudaMemset2DAsync(v, sizeof(double) * ldv, 0, sizeof(double) * (size_t)nl * KK, nrhs, s));
-    if (mixed) slice_vectors(vf, 0, nl, KK, kp_f, nrhs, s);
-    // fork: near field on the second stream, list i+ (leaf values -> local) on the third
+    // fork: leaf-value slices and the near field on the second stream; list i+
+    // (leaf values -> local), then the constant terms and list i- on the third
     VPX_CUDA(cudaEventRecord((cudaEvent_t)p->ev_fork, s));
     VPX_CUDA(cudaStreamWaitEvent(aux, (cudaEvent_t)p->ev_fork, 0));
     VPX_CUDA(cudaStreamWaitEvent(aux2, (cudaEvent_t)p->ev_fork, 0));
     ev_record_pass(p, VPX_N_PASSES + 1, aux);
+    if (mixed) slice_vectors(vf, 0, nl, KK, kp_f, nrhs, aux);
+    VPX_CUDA(cudaEventRecord((cudaEvent_t)p->ev_sl, aux));
     gemm_run(F.near, vf, v, ldv, nrhs, mixed, aux);
     ev_record_pass(p, VPX_N_PASSES + 2, aux);
     VPX_CUDA(cudaEventRecord((cudaEvent_t)p->ev_join, aux));
+    VPX_CUDA(cudaStreamWaitEvent(aux2, (cudaEvent_t)p->ev_sl, 0));
     gemm_run(F.s2l, vf, lo, ldm, nrhs, mixed, aux2);
-    VPX_CUDA(cudaEventRecord((cudaEvent_t)p->ev_s2l, aux2));
     // main stream: upward pass
-    gemm_run(F.l2m, vf, mp, ldm, nrhs, mixed, s);
+    gemm_run(F.l2m, mixed ? vf_fly : vf, mp, ldm, nrhs, mixed, s);
     ev_record_pass(p, 2, s);
     for (int l = d.n_levels - 1; l >= 3; --l) gemm_run(F.m2m[l - 1], vm, mp, ldm, nrhs, mixed, s);
     if (mixed) slice_vectors(vmf, 0, nb, P2, kp_m, nrhs, s);
-    // list i- on the third stream once the multipoles are final
+    // the final multipoles feed the constant terms and list i- on the third
+    // stream, beside M2L on this one (all accumulate into distinct sums)
     VPX_CUDA(cudaEventRecord((cudaEvent_t)p->ev_up, s));
     VPX_CUDA(cudaStreamWaitEvent(aux2, (cudaEvent_t)p->ev_up, 0));
+    if (F.lc_rows > 0) {
+        k_const_gather<<<dim3((F.lc_rows + 7) / 8, nrhs), 256, 0, aux2>>>(
+            F.lc_rows, F.lc_first, P, F.lc_off, F.lc_idx, F.lc_coef, mp, ldm, lo, ldm, P2, 1);
+        VPX_LAUNCH("k_const_gather");
+    }
+    VPX_CUDA(cudaEventRecord((cudaEvent_t)p->ev_lc, aux2));   // list i+ and local constants done
     gemm_run(F.m2t, vmf, v, ldv, nrhs, mixed, aux2);
+    if (nl > 0) {
+        k_const_gather<<<dim3((nl + 7) / 8, nrhs), 256, 0, aux2>>>(nl, 0, P, F.tc_off, F.tc_idx, F.tc_coef, mp, ldm,
+                                                                   v, ldv, KK, KK);
+        VPX_LAUNCH("k_const_gather");
+    }
     VPX_CUDA(cudaEventRecord((cudaEvent_t)p->ev_join2, aux2));
     ev_record_pass(p, 3, s);
     gemm_run(F.m2l, vmf, lo, ldm, nrhs, mixed, s);
-    if (F.lc_rows > 0) {
-        k_const_gather<<<dim3((F.lc_rows + 7) / 8, nrhs), 256, 0, s>>>(F.lc_rows, F.lc_first, P, F.lc_off, F.lc_idx,
-                                                                       F.lc_coef, mp, ldm, lo, ldm, P2, 1);
-        VPX_LAUNCH("k_const_gather");
-    }
-    VPX_CUDA(cudaStreamWaitEvent(s, (cudaEvent_t)p->ev_s2l, 0));
+    VPX_CUDA(cudaStreamWaitEvent(s, (cudaEvent_t)p->ev_lc, 0));
     ev_record_pass(p, 4, s);
     for (int l = 2; l + 1 < d.n_levels; ++l) gemm_run(F.l2l[l], vl, lo, ldm, nrhs, mixed, s);
     ev_record_pass(p, 5, s);
     gemm_run(F.l2t, vl, v, ldv, nrhs, mixed, s);
-    if (nl > 0) {
-        k_const_gather<<<dim3((nl + 7) / 8, nrhs), 256, 0, s>>>(nl, 0, P, F.tc_off, F.tc_idx, F.tc_coef, mp, ldm, v,
-                                                                ldv, KK, KK);
-        VPX_LAUNCH("k_const_gather");
-    }
     ev_record_pass(p, 6, s);
     VPX_CUDA(cudaStreamWaitEvent(s, (cudaEvent_t)p->ev_join, 0));
     VPX_CUDA(cudaStreamWaitEvent(s, (cudaEvent_t)p->ev_join2, 0));

@@ -28,7 +28,8 @@
 namespace vpx {
 
 constexpr int F_KC_PRE = 4;        // k16 blocks per CTA chunk for pre-sliced vectors
-constexpr int F_MAX_KB_FLY = 8;    // on-the-fly slicing: Kpad <= 128
+constexpr int F_MAX_KB_FLY = 16;   // on-the-fly slicing: Kpad <= 256 (32 pairs x 256 doubles staged: 166 KB)
+constexpr int F_MAX_KB_WHOLE = 8;  // pre-sliced vectors up to this many k16 blocks are staged whole
 constexpr int F_MAX_WARPS = 6;     // m16 blocks (warps) per CTA: 96 rows, two CTAs per SM
 
 struct FragArgs {
@@ -269,7 +270,7 @@ void gemm_frag_run(const GemmPass &g, const VecSet &vs, double *out, int64_t ldo
     a.wm = std::min(F_MAX_WARPS, a.MB);
     a.rb = (a.MB + a.wm - 1) / a.wm;
     const bool fly = vs.slices == nullptr;
-    a.kc = (fly || a.KB <= F_MAX_KB_FLY) ? a.KB : F_KC_PRE;
+    a.kc = (fly || a.KB <= F_MAX_KB_WHOLE) ? a.KB : F_KC_PRE;
     a.ks = (a.KB + a.kc - 1) / a.kc;
     a.tfrag = reinterpret_cast<const uint4 *>(g.tfrag);
     a.texpo = g.texpo;
