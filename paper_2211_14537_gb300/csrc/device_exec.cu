@@ -27,6 +27,7 @@ __device__ inline double box_side_d(int level) { return ldexp(1.0, -level); }
 // regular leaves: copy data; exterior leaves outside every extension list: 0
 __global__ void k_leafvals(int n_leaves, int KK, const int32_t *leaf_cls, const int32_t *owner_flag,
                            const int64_t *reg_off, const double *f, int64_t ldf, double *fe, int64_t ldfe) {
+    pdl_entry();
     const int rhs = blockIdx.y;
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (int64_t)n_leaves * KK) return;
@@ -43,6 +44,7 @@ __global__ void k_leafvals(int n_leaves, int KK, const int32_t *leaf_cls, const 
 // chebexpbarS) are evaluated at the cut leaf's exterior nodes and at all nodes
 // of the exterior leaves in its extension list.
 __global__ void k_extend(ExtArgs a) {
+    pdl_entry();
     extern __shared__ double sm[];
     const int c = blockIdx.x, rhs = blockIdx.y;
     const int K = a.K, KK = K * K, Kb = a.Kbar, Kb2 = Kb * Kb, NG = a.NG;
@@ -147,6 +149,7 @@ __global__ void k_extend(ExtArgs a) {
 // boundary nodes, one warp per node: V(x) = sum_b w_y[b] sum_a w_x[a] V_leaf[b][a].
 __global__ void k_finish(int64_t n_v, int nan_blocks, int nb, int K, const int32_t *bleaf, const double *bw,
                          const double *v, int64_t ldv, double *vb, int64_t ldb, int *status) {
+    pdl_entry();
     const int rhs = blockIdx.y;
     if ((int)blockIdx.x < nan_blocks) {
         const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -226,8 +229,8 @@ static void run_extension(vpx_plan *p, const double *f, int nrhs, int64_t ldf, d
         VPX_CUDA(cudaEventRecord((cudaEvent_t)p->ev_lvf, s));
         VPX_CUDA(cudaStreamWaitEvent(aux, (cudaEvent_t)p->ev_lvf, 0));
         dim3 g((unsigned)((n + 255) / 256), nrhs);
-        k_leafvals<<<g, 256, 0, aux>>>(nl, KK, p->dt.leaf_cls, p->ext.owned_flag_dev, p->ext.reg_leaf_off, f, ldf, fe,
-                                       ldfe);
+        launch_pdl(k_leafvals, g, dim3(256), 0, aux, nl, KK, p->dt.leaf_cls, p->ext.owned_flag_dev, p->ext.reg_leaf_off, f,
+                   ldf, fe, ldfe);
         VPX_LAUNCH("k_leafvals");
         VPX_CUDA(cudaEventRecord((cudaEvent_t)p->ev_lv, aux));
     }
@@ -271,7 +274,7 @@ static void run_extension(vpx_plan *p, const double *f, int nrhs, int64_t ldf, d
                                reinterpret_cast<const ExtTgtGeo *>(x.tgt_geo), x.Fall, ldF,
                                reinterpret_cast<float2 *>(x.alpha), nrhs, p->wk.status, s);
         } else {
-            k_extend<<<dim3(p->ext.ncut, nrhs), 256, smem, s>>>(a);
+            launch_pdl(k_extend, dim3(p->ext.ncut, nrhs), dim3(256), smem, s, a);
             VPX_LAUNCH("k_extend");
         }
     }
@@ -291,7 +294,7 @@ void run_potential_scratch(vpx_plan *p, const double *fe, int64_t ldfe, int nrhs
     const int nan_blocks = (int)((n_v + 255) / 256);
     const int blocks = nan_blocks + (nbd + 7) / 8;
     if (blocks > 0) {
-        k_finish<<<dim3(blocks, nrhs), 256, 0, s>>>(n_v, nan_blocks, nbd, p->K, p->wk.bdry_leaf, p->wk.bdry_w, v, ldv,
+        launch_pdl(k_finish, dim3(blocks, nrhs), dim3(256), 0, s, n_v, nan_blocks, nbd, p->K, p->wk.bdry_leaf, p->wk.bdry_w, v, ldv,
                                                     vb, ldb, p->wk.status);
         VPX_LAUNCH("k_finish");
     }

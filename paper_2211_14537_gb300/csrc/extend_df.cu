@@ -39,6 +39,7 @@ __device__ inline float2 st_df(df32 v) { return make_float2(v.hi, v.lo); }
 // A_I^+ (contiguous, rows padded to an even length) arrive by one TMA bulk copy
 // while the threads split f_I.
 __global__ void __launch_bounds__(256) k_ext_coeff_df(ExtArgs a, int nrb, double *cbuf, int64_t ldc, int *status) {
+    pdl_entry();
     extern __shared__ __align__(16) float2 csm[];
     __shared__ __align__(8) uint64_t s_bar;
     const int c = blockIdx.x / nrb, rb = blockIdx.x % nrb, rhs = blockIdx.y;
@@ -73,6 +74,7 @@ constexpr int kExtPerThread = 4;   // grid points per thread in k_ext_alpha_df (
 // points and A_{X_Sbar,G} c elsewhere; alpha = C F C^T truncated to m + n < Kbar
 __global__ void __launch_bounds__(256) k_ext_alpha_df(ExtArgs a, const double *Fall, int64_t ldF, float2 *alpha,
                                                      int64_t lda, int *status) {
+    pdl_entry();
     extern __shared__ __align__(16) float2 smf[];
     __shared__ __align__(8) uint64_t s_bar;
     const int c = blockIdx.x, rhs = blockIdx.y;
@@ -136,6 +138,7 @@ __global__ void __launch_bounds__(256) k_ext_alpha_df(ExtArgs a, const double *F
 __global__ void __launch_bounds__(256) k_ext_eval_df(ExtArgs a, const int32_t *tgt_cut, const int32_t *tgt_leaf,
                                                     const ExtTgtGeo *geo, const float2 *alpha, int64_t lda,
                                                     int *status) {
+    pdl_entry();
     extern __shared__ __align__(16) float2 smf[];
     __shared__ __align__(8) uint64_t s_bar;
     const int t = blockIdx.x, rhs = blockIdx.y;
@@ -220,7 +223,7 @@ void extend_df_prepare(int max_interior, int K, int Kbar) {
 void launch_ext_coeff_df(const ExtArgs &a, int ncut, int max_interior, int nrhs, double *cbuf, int64_t ldc,
                          int *status, cudaStream_t s) {
     const int nrb = (a.NG + 7) / 8;
-    k_ext_coeff_df<<<dim3(ncut * nrb, nrhs), 256, coeff_smem(max_interior), s>>>(a, nrb, cbuf, ldc, status);
+    launch_pdl(k_ext_coeff_df, dim3(ncut * nrb, nrhs), dim3(256), coeff_smem(max_interior), s, a, nrb, cbuf, ldc, status);
     VPX_LAUNCH("k_ext_coeff_df");
 }
 
@@ -229,9 +232,9 @@ void launch_ext_eval_df(const ExtArgs &a, int ncut, int n_tgt, const int32_t *tg
                         cudaStream_t s) {
     if (a.Kbar * a.Kbar > kExtPerThread * 256) fail(VPX_ERR_ARG, "extension grid larger than one block covers");
     const int64_t lda = (int64_t)ncut * kb2p(a.Kbar);
-    k_ext_alpha_df<<<dim3(ncut, nrhs), 256, alpha_smem(a.Kbar), s>>>(a, Fall, ldF, alpha, lda, status);
+    launch_pdl(k_ext_alpha_df, dim3(ncut, nrhs), dim3(256), alpha_smem(a.Kbar), s, a, Fall, ldF, alpha, lda, status);
     VPX_LAUNCH("k_ext_alpha_df");
-    k_ext_eval_df<<<dim3(n_tgt, nrhs), 256, eval_smem(a.K, a.Kbar), s>>>(a, tgt_cut, tgt_leaf, geo, alpha, lda,
+    launch_pdl(k_ext_eval_df, dim3(n_tgt, nrhs), dim3(256), eval_smem(a.K, a.Kbar), s, a, tgt_cut, tgt_leaf, geo, alpha, lda,
                                                                           status);
     VPX_LAUNCH("k_ext_eval_df");
 }

@@ -40,6 +40,7 @@ typedef std::complex<double> cd;
 __global__ void k_const_gather(int rows, int first, int P, const int32_t *off, const int32_t *idx,
                                const double *coef, const double *mpole, int64_t ldm, double *out, int64_t ldo,
                                int stride, int width) {
+    pdl_entry();
     const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31, rhs = blockIdx.y;
     if (r >= rows) return;
     const double *mp = mpole + rhs * ldm;
@@ -446,14 +447,14 @@ void run_potential_passes(vpx_plan *p, const double *fe, int64_t ldfe, int nrhs,
     VPX_CUDA(cudaEventRecord((cudaEvent_t)p->ev_up, s));
     VPX_CUDA(cudaStreamWaitEvent(aux2, (cudaEvent_t)p->ev_up, 0));
     if (F.lc_rows > 0) {
-        k_const_gather<<<dim3((F.lc_rows + 7) / 8, nrhs), 256, 0, aux2>>>(
+        launch_pdl(k_const_gather, dim3((F.lc_rows + 7) / 8, nrhs), dim3(256), 0, aux2, 
             F.lc_rows, F.lc_first, P, F.lc_off, F.lc_idx, F.lc_coef, mp, ldm, lo, ldm, P2, 1);
         VPX_LAUNCH("k_const_gather");
     }
     VPX_CUDA(cudaEventRecord((cudaEvent_t)p->ev_lc, aux2));   // list i+ and local constants done
     gemm_run(F.m2t, vmf, v, ldv, nrhs, mixed, aux2);
     if (nl > 0) {
-        k_const_gather<<<dim3((nl + 7) / 8, nrhs), 256, 0, aux2>>>(nl, 0, P, F.tc_off, F.tc_idx, F.tc_coef, mp, ldm,
+        launch_pdl(k_const_gather, dim3((nl + 7) / 8, nrhs), dim3(256), 0, aux2, nl, 0, P, F.tc_off, F.tc_idx, F.tc_coef, mp, ldm,
                                                                    v, ldv, KK, KK);
         VPX_LAUNCH("k_const_gather");
     }

@@ -35,6 +35,7 @@ constexpr int G_M = 64, G_N = 64, G_K = 16;
 __global__ void __launch_bounds__(256) k_gemm_fp64(int M, int Kd, const double *tab, const GTile *tiles,
                                                    const GPair *pairs, const double *vbase, int64_t vld,
                                                    int vstride, double *out, int64_t ldo, int add) {
+    pdl_entry();
     __shared__ double As[G_K][G_M + 1];
     __shared__ double Bs[G_K][G_N + 1];
     const GTile tile = tiles[blockIdx.x];
@@ -99,6 +100,7 @@ constexpr int kSliceMaxPerLane = 8;   // Kpad <= 256
 
 __global__ void k_slice_vec(const double *vbase, int64_t vld, int vstride, int first, int count, int Kd, int Kpad,
                             int nvec, uint16_t *slices, int32_t *expo) {
+    pdl_entry();
     const int vi = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31, rhs = blockIdx.y;
     if (vi >= count) return;
     const int v = first + vi;
@@ -282,6 +284,11 @@ void gemm_set_choice(GemmPass &g, GemmChoice c) {
 
 static thread_local std::vector<GemmCall> *t_recorder = nullptr;
 
+bool pdl_enabled() {
+    static const bool on = getenv("VPX_NO_PDL") == nullptr;
+    return on;
+}
+
 void gemm_set_recorder(std::vector<GemmCall> *rec) { t_recorder = rec; }
 
 bool gemm_frag_eligible(const GemmPass &g, const VecSet &vs);
@@ -295,7 +302,8 @@ void gemm_run(const GemmPass &g, const VecSet &vs, double *out, int64_t ldo, int
     cudaStream_t s = (cudaStream_t)sv;
     if (!mixed) {
         dim3 grid(g.n_tiles, (g.M + G_M - 1) / G_M, nrhs);
-        k_gemm_fp64<<<grid, 256, 0, s>>>(g.M, g.Kd, g.tab, g.tiles, g.pairs, vs.base, vs.ld, vs.stride, out, ldo, g.add);
+        launch_pdl(k_gemm_fp64, grid, dim3(256), 0, s, g.M, g.Kd, g.tab, g.tiles, g.pairs, vs.base, vs.ld, vs.stride, out, ldo,
+                   g.add);
         VPX_LAUNCH("k_gemm_fp64");
         return;
     }
@@ -316,7 +324,7 @@ void gemm_run(const GemmPass &g, const VecSet &vs, double *out, int64_t ldo, int
 void slice_vectors(const VecSet &vs, int first, int count, int Kd, int Kpad, int nrhs, void *sv) {
     if (count <= 0) return;
     if (Kpad > 32 * kSliceMaxPerLane) fail(VPX_ERR_ARG, "slice_vectors: vectors longer than 256");
-    k_slice_vec<<<dim3((count + 7) / 8, nrhs), 256, 0, (cudaStream_t)sv>>>(vs.base, vs.ld, vs.stride, first, count, Kd,
+    launch_pdl(k_slice_vec, dim3((count + 7) / 8, nrhs), dim3(256), 0, (cudaStream_t)sv, vs.base, vs.ld, vs.stride, first, count, Kd,
                                                                             Kpad, vs.nvec, vs.slices, vs.expo);
     VPX_LAUNCH("k_slice_vec");
 }

@@ -69,6 +69,7 @@ __device__ inline void frag_mma(float (&c)[4], const uint4 &a, uint32_t b0, uint
 // (8 NT pairs) per CTA
 template <int S, bool FLY, int NT>
 __global__ void __launch_bounds__(192, 2) k_gemm_frag(FragArgs a) {
+    pdl_entry();
     constexpr int NP = 8 * NT;
     extern __shared__ __align__(16) uint16_t bs[];   // [S][NP][ldb] slices, then (FLY) [NP][Kd] doubles
     __shared__ GPair s_pr[NP];
@@ -254,8 +255,8 @@ bool gemm_frag_eligible(const GemmPass &g, const VecSet &vs) {
 
 template <int S, bool FLY>
 static void frag_launch(int np, dim3 grid, int threads, size_t smem, cudaStream_t st, const FragArgs &a) {
-    if (np == 8) k_gemm_frag<S, FLY, 1><<<grid, threads, smem, st>>>(a);
-    else k_gemm_frag<S, FLY, 4><<<grid, threads, smem, st>>>(a);
+    if (np == 8) launch_pdl(k_gemm_frag<S, FLY, 1>, grid, dim3(threads), smem, st, a);
+    else launch_pdl(k_gemm_frag<S, FLY, 4>, grid, dim3(threads), smem, st, a);
 }
 
 void gemm_frag_run(const GemmPass &g, const VecSet &vs, double *out, int64_t ldo, int nrhs, void *s) {

@@ -27,6 +27,7 @@ __global__ void __launch_bounds__(384) k_gemm_rows_df(int M, int Kd, int kg, int
                                                       const GTile *tiles, const GPair *pairs, const double *vbase,
                                                       int64_t vld, int vstride, double *out, int64_t ldo, int add,
                                                       int *status) {
+    pdl_entry();
     extern __shared__ __align__(16) float2 rsm[];   // table [Kd][M], vectors [R_NPB][Kd], partials [kg][R_NPB][M]
     __shared__ __align__(8) uint64_t s_bar;
     __shared__ int s_e[R_NPB];
@@ -106,7 +107,7 @@ void gemm_rows_run(const GemmPass &g, const VecSet &vs, double *out, int64_t ldo
     const int threads = (g.M + 31) / 32 * 32 * kg;
     if (threads > 384) fail(VPX_ERR_ARG, "row engine: too many table rows");
     if (g.n_tiles_r != g.n_pairs) fail(VPX_ERR_ARG, "row engine: one pair per tile expected");
-    k_gemm_rows_df<<<dim3(g.n_tiles_r, nrhs), threads, rows_smem(g.M, g.Kd, kg), (cudaStream_t)s>>>(
+    launch_pdl(k_gemm_rows_df, dim3(g.n_tiles_r, nrhs), dim3(threads), rows_smem(g.M, g.Kd, kg), (cudaStream_t)s,
         g.M, g.Kd, kg, rows_tstride(g.M, g.Kd), reinterpret_cast<const float2 *>(g.tdfT), g.tiles_r, g.pairs, vs.base,
         vs.ld, vs.stride, out, ldo, g.add, g.status);
     VPX_LAUNCH("k_gemm_rows_df");

@@ -88,6 +88,7 @@ struct WsShape {
 // grid: x = tile of pairs, y = block of table rows, z = rhs
 template <bool TM, int S, int NB>
 __global__ void __launch_bounds__(TW_THREADS, 1) k_gemm_ws(WsArgs a) {
+    pdl_entry();
     typedef WsShape<TM, S, NB> Sh;
     extern __shared__ __align__(1024) uint16_t wsm[];
     __shared__ __align__(8) uint64_t full[TW_STAGES], empty[TW_STAGES], done;
@@ -410,14 +411,14 @@ void gemm_ws_run(const GemmPass &g, const VecSet &vs, double *out, int64_t ldo, 
         if (g.n_tiles == 0) return;
         a.tiles = g.tiles;
         dim3 grid(g.n_tiles, g.Mpad / TW_M, nrhs);
-        k_gemm_ws<true, 5, 64><<<grid, TW_THREADS, WsShape<true, 5, 64>::SMEM, st>>>(a);
+        launch_pdl(k_gemm_ws<true, 5, 64>, grid, dim3(TW_THREADS), WsShape<true, 5, 64>::SMEM, st, a);
     } else {
         if (g.n_tiles_p == 0) return;
         a.tiles = g.tiles_p;
         const int nb = ws_rows_n(g);
         dim3 grid(g.n_tiles_p, (g.M + nb - 1) / nb, nrhs);
-        if (nb == 48) k_gemm_ws<false, 6, 48><<<grid, TW_THREADS, WsShape<false, 6, 48>::SMEM, st>>>(a);
-        else k_gemm_ws<false, 6, 64><<<grid, TW_THREADS, WsShape<false, 6, 64>::SMEM, st>>>(a);
+        if (nb == 48) launch_pdl(k_gemm_ws<false, 6, 48>, grid, dim3(TW_THREADS), WsShape<false, 6, 48>::SMEM, st, a);
+        else launch_pdl(k_gemm_ws<false, 6, 64>, grid, dim3(TW_THREADS), WsShape<false, 6, 64>::SMEM, st, a);
     }
     VPX_LAUNCH("k_gemm_ws");
 }
