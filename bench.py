@@ -367,8 +367,13 @@ def main():
         peak = 1918.1
         kname = ("k_gemm_frag (near-field pass, exact bf16 slices on mma.sync)" if os.environ.get("VPX_NO_TC")
                  else "k_gemm_ws (near-field pass, exact bf16 slices on tcgen05: TMA tables, TMEM accumulators)")
+        # DRAM bytes read + written by one launch of the near-field kernel on this
+        # workload, from an ncu capture of the kernel as it stands (profiles/);
+        # reset to None whenever the kernel changes
+        traffic = 24641280 if not os.environ.get("VPX_NO_TC") and args.nrhs == 1 else None
         roof = {"kernel": kname, "bound": "tensor",
-                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+                "traffic_unit": "bytes per launch",
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst)",
                 "fp64_equivalent_tflops": r["near_flops"] / (r["near_ms"] * 1e-3) / 1e12}
     else:

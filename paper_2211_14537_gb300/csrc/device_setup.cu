@@ -385,7 +385,7 @@ void device_setup(vpx_plan *p) {
     p->aux_stream = aux;
     VPX_CUDA(cudaStreamCreateWithFlags(&aux2, cudaStreamNonBlocking));
     p->aux2_stream = aux2;
-    for (void **e : {&p->ev_fork, &p->ev_up, &p->ev_join, &p->ev_join2, &p->ev_sl, &p->ev_lc, &p->ev_lvf, &p->ev_lv,
+    for (void **e : {&p->ev_fork, &p->ev_up, &p->ev_join, &p->ev_join2, &p->ev_lc, &p->ev_lvf, &p->ev_lv,
                      &p->ev_bfork, &p->ev_bjoin})
         VPX_CUDA(cudaEventCreateWithFlags((cudaEvent_t *)e, cudaEventDisableTiming));
     DevTree &d = p->dt;
@@ -560,7 +560,7 @@ void device_free(vpx_plan *p) {
         cudaGraphExecDestroy((cudaGraphExec_t)p->graph_exec);
         p->graph_exec = nullptr;
     }
-    for (void **e : {&p->ev_fork, &p->ev_up, &p->ev_join, &p->ev_join2, &p->ev_sl, &p->ev_lc, &p->ev_lvf, &p->ev_lv,
+    for (void **e : {&p->ev_fork, &p->ev_up, &p->ev_join, &p->ev_join2, &p->ev_lc, &p->ev_lvf, &p->ev_lv,
                      &p->ev_bfork, &p->ev_bjoin})
         if (*e) {
             cudaEventDestroy((cudaEvent_t)*e);

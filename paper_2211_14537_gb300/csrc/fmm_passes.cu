@@ -410,9 +410,6 @@ void run_potential_passes(vpx_plan *p, const double *fe, int64_t ldfe, int nrhs,
     const int kp_f = (KK + 31) / 32 * 32, kp_m = (P2 + 31) / 32 * 32;
     FmmPasses &F = p->fmm;
     VecSet vf{fe, ldfe, KK, F.fe_sl, F.fe_ex, nl, kp_f};
-    // L2M reads every leaf once: it slices the leaf values itself, so it need
-    // not wait for the slicing that the near field and list i+ share
-    VecSet vf_fly{fe, ldfe, KK, nullptr, nullptr, nl, 0};
     // expansions along the level chains are sliced by the pass that reads them;
     // the final multipoles once, for lists i and i-
     VecSet vm{mp, ldm, P2, nullptr, nullptr, nb, 0};
@@ -424,21 +421,21 @@ void run_potential_passes(vpx_plan *p, const double *fe, int64_t ldfe, int nrhs,
     VPX_CUDA(cudaMemsetAsync(mp, 0, sizeof(double) * ldm * nrhs, s));
     VPX_CUDA(cudaMemsetAsync(lo, 0, sizeof(double) * ldm * nrhs, s));
     VPX_CUDA(cudaMemset2DAsync(v, sizeof(double) * ldv, 0, sizeof(double) * (size_t)nl * KK, nrhs, s));
-    // fork: leaf-value slices and the near field on the second stream; list i+
-    // (leaf values -> local), then the constant terms and list i- on the third
+    // the leaf-value slices serve L2M, the near field and list i+ (slicing L2M's
+    // 256-long vectors on the fly took longer than slicing once before it)
+    if (mixed) slice_vectors(vf, 0, nl, KK, kp_f, nrhs, s);
+    // fork: the near field on the second stream; list i+ (leaf values ->
+    // local), then the constant terms and list i- on the third
     VPX_CUDA(cudaEventRecord((cudaEvent_t)p->ev_fork, s));
     VPX_CUDA(cudaStreamWaitEvent(aux, (cudaEvent_t)p->ev_fork, 0));
     VPX_CUDA(cudaStreamWaitEvent(aux2, (cudaEvent_t)p->ev_fork, 0));
     ev_record_pass(p, VPX_N_PASSES + 1, aux);
-    if (mixed) slice_vectors(vf, 0, nl, KK, kp_f, nrhs, aux);
-    VPX_CUDA(cudaEventRecord((cudaEvent_t)p->ev_sl, aux));
     gemm_run(F.near, vf, v, ldv, nrhs, mixed, aux);
     ev_record_pass(p, VPX_N_PASSES + 2, aux);
     VPX_CUDA(cudaEventRecord((cudaEvent_t)p->ev_join, aux));
-    VPX_CUDA(cudaStreamWaitEvent(aux2, (cudaEvent_t)p->ev_sl, 0));
     gemm_run(F.s2l, vf, lo, ldm, nrhs, mixed, aux2);
     // main stream: upward pass
-    gemm_run(F.l2m, mixed ? vf_fly : vf, mp, ldm, nrhs, mixed, s);
+    gemm_run(F.l2m, vf, mp, ldm, nrhs, mixed, s);
     ev_record_pass(p, 2, s);
     for (int l = d.n_levels - 1; l >= 3; --l) gemm_run(F.m2m[l - 1], vm, mp, ldm, nrhs, mixed, s);
     if (mixed) slice_vectors(vmf, 0, nb, P2, kp_m, nrhs, s);

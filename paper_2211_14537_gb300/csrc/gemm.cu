@@ -158,6 +158,11 @@ void gemm_pass_set_pairs(GemmPass &g, std::vector<std::pair<int, GPair>> &tagged
         for (size_t k = i; k < j; ++k) pr.push_back(tagged[k].second);
         i = j;
     }
+    // largest tiles first: CTAs start in tile order, so a pass of more than one
+    // wave ends with its smallest tiles (stable: full tiles keep their table
+    // order).  The row engine pairs tile i with pair i and keeps its order.
+    auto by_count = [](const GTile &x, const GTile &y) { return x.count > y.count; };
+    for (std::vector<GTile> *v : {&tl, &tf, &tfa, &tp}) std::stable_sort(v->begin(), v->end(), by_count);
     g.h_pairs = pr;
     g.n_pairs = (int)pr.size();
     g.n_tiles = (int)tl.size();

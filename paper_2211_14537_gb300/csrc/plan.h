@@ -121,7 +121,6 @@ struct vpx_plan {
     void *aux2_stream = nullptr;  // third stream (lists i+ and i-)
     int64_t graph_kernels = 0;    // kernel nodes of the captured execute graph
     void *ev_fork = nullptr, *ev_up = nullptr, *ev_join = nullptr, *ev_join2 = nullptr;
-    void *ev_sl = nullptr;    // leaf-value slices done (second stream)
     void *ev_lc = nullptr;    // list i+ and the local constant terms done (third stream)
     void *ev_lvf = nullptr, *ev_lv = nullptr;   // leaf values beside the extension: fork / done
     void *ev_bfork = nullptr, *ev_bjoin = nullptr;   // batch fork / join on the plan's own stream

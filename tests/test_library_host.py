@@ -174,3 +174,18 @@ def test_autotune_refuses_host_only_plan(V):
     with pytest.raises(V.VpxError) as e:
         V.vpx_autotune(plan, f, stream=0)
     assert e.value.code == V.VPX_ERR_STATE
+
+
+def test_boundary_targets_follow_section6(V):
+    """16 Gauss-Legendre nodes per boundary panel (Section 6), as in the
+    oracle and the golden fixture."""
+    import os
+    n_q = None
+    with open(os.path.join(ROOT, "tests", "golden", "discretization_section6.txt")) as fh:
+        for line in fh:
+            w = line.split("#", 1)[0].split()
+            if w and w[0] == "N_q":
+                n_q = int(w[1])
+    for wl in (W.disk_sincos(level=3), W.starfish_gaussian(K=8, tol=1e-6, max_level=6)):
+        plan = _plan(V, wl)
+        assert plan.sizes()[3] == n_q * wl.domain.n_panels

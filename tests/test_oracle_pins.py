@@ -384,3 +384,30 @@ def test_single_basis_integral_green_identity(K, a, b, where):
     L.orc_leaf_basis_integrals(K, O._ptr(np.ascontiguousarray(t)), cx, cy, h, x[0], x[1], O._ptr(I))
     want = _green_area_integral(q, gq, np.array(x), -1.0, 1.0, -1.0, 1.0)
     assert abs(I[b * K + a] - want) <= 1e-11 * max(1.0, abs(want)), (I[b * K + a], want)
+
+
+def _golden(name):
+    import os
+    vals = {}
+    with open(os.path.join(os.path.dirname(__file__), "golden", name)) as fh:
+        for line in fh:
+            line = line.split("#", 1)[0].split()
+            if line:
+                vals[line[0]] = int(line[1])
+    return vals
+
+
+def test_discretization_matches_section6():
+    """The oracle's stencil and boundary rule take the sizes Section 6 states
+    for K = 8: 66 Gaussians (points of G, columns of the universal operator),
+    Kbar = 12 on the extension region, 16 Gauss-Legendre nodes per panel."""
+    g = _golden("discretization_section6.txt")
+    q, Kbar, NG = O.stencil_params(g["K"])
+    assert (Kbar, NG) == (g["Kbar"], g["N_G"])
+    assert len(O.padua_points(q)) == g["N_G"]
+    A = O.universal_matrix(g["K"])
+    assert A.shape[1] == g["N_G"]
+    assert A.shape[0] == g["K"] ** 2 + g["Kbar"] ** 2 + g["N_G"]   # X = X_S u X_Sbar u G
+    assert O.NQ_BOUNDARY == g["N_q"]
+    dom = W.disk_sincos(level=3).domain
+    assert len(O.boundary_nodes(dom)) == g["N_q"] * dom.n_panels
