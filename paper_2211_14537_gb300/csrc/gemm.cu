@@ -30,26 +30,33 @@ namespace vpx {
 
 // ------------------------------------------------------------ FP64 engine
 
-constexpr int G_M = 64, G_N = 64, G_K = 16;
+constexpr int G_M = 64, G_K = 16;
 
+// One CTA: G_M table rows x GN pairs, 256 threads as TY x TX with RI rows and NJ
+// pairs each.  GN = 64 for passes that fill the GPU; GN = 8 for the small ones
+// (the level chains), whose few wide tiles would leave most SMs idle at the
+// FP64 rate.  Each output sums over k in the same order for every GN.
+template <int GN>
 __global__ void __launch_bounds__(256) k_gemm_fp64(int M, int Kd, const double *tab, const GTile *tiles,
                                                    const GPair *pairs, const double *vbase, int64_t vld,
                                                    int vstride, double *out, int64_t ldo, int add) {
     pdl_entry();
+    constexpr int TX = GN < 16 ? GN : 16, TY = 256 / TX, RI = G_M / TY, NJ = GN / TX;
+    static_assert(TX * TY == 256 && RI * TY == G_M && NJ * TX == GN, "thread layout");
     __shared__ double As[G_K][G_M + 1];
-    __shared__ double Bs[G_K][G_N + 1];
+    __shared__ double Bs[G_K][GN + 1];
     const GTile tile = tiles[blockIdx.x];
     const int m0 = blockIdx.y * G_M, rhs = blockIdx.z;
     const double *A = tab + (size_t)tile.tab * M * Kd;
     const double *V = vbase + rhs * vld;
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    double acc[4][4] = {};
+    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+    double acc[RI][NJ] = {};
     for (int k0 = 0; k0 < Kd; k0 += G_K) {
         for (int e = threadIdx.x; e < G_M * G_K; e += 256) {
             int r = e / G_K, k = e % G_K;
             As[k][r] = (m0 + r < M && k0 + k < Kd) ? A[(size_t)(m0 + r) * Kd + k0 + k] : 0.0;
         }
-        for (int e = threadIdx.x; e < G_N * G_K; e += 256) {
+        for (int e = threadIdx.x; e < GN * G_K; e += 256) {
             int n = e / G_K, k = e % G_K;
             Bs[k][n] = (n < tile.count && k0 + k < Kd)
                            ? V[(int64_t)pairs[tile.first + n].src * vstride + k0 + k]
@@ -58,27 +65,27 @@ __global__ void __launch_bounds__(256) k_gemm_fp64(int M, int Kd, const double *
         __syncthreads();
 #pragma unroll
         for (int k = 0; k < G_K; ++k) {
-            double ar[4], br[4];
+            double ar[RI], br[NJ];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) ar[i] = As[k][ty * 4 + i];
+            for (int i = 0; i < RI; ++i) ar[i] = As[k][ty * RI + i];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) br[j] = Bs[k][tx + 16 * j];
+            for (int j = 0; j < NJ; ++j) br[j] = Bs[k][tx + TX * j];
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < RI; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] += ar[i] * br[j];
+                for (int j = 0; j < NJ; ++j) acc[i][j] += ar[i] * br[j];
         }
         __syncthreads();
     }
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        int n = tx + 16 * j;
+    for (int j = 0; j < NJ; ++j) {
+        int n = tx + TX * j;
         if (n >= tile.count) continue;
         const GPair pr = pairs[tile.first + n];
         double *o = out + rhs * ldo + pr.dst;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            int r = m0 + ty * 4 + i;
+        for (int i = 0; i < RI; ++i) {
+            int r = m0 + ty * RI + i;
             if (r >= M) continue;
             if (add) atomicAdd(o + r, pr.scale * acc[i][j]);
             else o[r] = pr.scale * acc[i][j];
@@ -306,9 +313,23 @@ void gemm_run(const GemmPass &g, const VecSet &vs, double *out, int64_t ldo, int
     if (g.n_tiles == 0) return;
     cudaStream_t s = (cudaStream_t)sv;
     if (!mixed) {
-        dim3 grid(g.n_tiles, (g.M + G_M - 1) / G_M, nrhs);
-        launch_pdl(k_gemm_fp64, grid, dim3(256), 0, s, g.M, g.Kd, g.tab, g.tiles, g.pairs, vs.base, vs.ld, vs.stride, out, ldo,
-                   g.add);
+        // 64-pair tiles when they give at least two CTAs per SM, else the 8-pair
+        // tiles of the fragment engine (one of its two widths is 8)
+        static int sms = 0;
+        if (!sms) {
+            int dev = 0;
+            VPX_CUDA(cudaGetDevice(&dev));
+            VPX_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        }
+        const int mb = (g.M + G_M - 1) / G_M;
+        const GTile *t8 = g.np_f == 8 ? g.tiles_f : g.tiles_f_alt;
+        const int n8 = g.np_f == 8 ? g.n_tiles_f : g.n_tiles_f_alt;
+        if ((int64_t)g.n_tiles * mb * nrhs < 2 * sms && t8 && n8 > 0)
+            launch_pdl(k_gemm_fp64<8>, dim3(n8, mb, nrhs), dim3(256), 0, s, g.M, g.Kd, g.tab, (const GTile *)t8,
+                       (const GPair *)g.pairs, vs.base, vs.ld, vs.stride, out, ldo, g.add);
+        else
+            launch_pdl(k_gemm_fp64<64>, dim3(g.n_tiles, mb, nrhs), dim3(256), 0, s, g.M, g.Kd, g.tab,
+                       (const GTile *)g.tiles, (const GPair *)g.pairs, vs.base, vs.ld, vs.stride, out, ldo, g.add);
         VPX_LAUNCH("k_gemm_fp64");
         return;
     }
