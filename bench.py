@@ -202,17 +202,56 @@ def run_gpu(args, rank, world, precision):
                 clocks=cl, e2e_s=e2e_s, v=v[0].cpu().numpy(), vh=vh, K=K, graph_kernels=graph_kernels, tune=tune)
 
 
-def run_batch(args):
+def shard_by_size(sizes, world):
+    """Trees to ranks for the batch: largest first, each to the rank with the
+    least work so far (ties: the lower rank).  Returns one sorted index list
+    per rank; every tree lands on exactly one rank."""
+    load = [0] * world
+    out = [[] for _ in range(world)]
+    for i in sorted(range(len(sizes)), key=lambda i: (-sizes[i], i)):
+        r = min(range(world), key=lambda q: (load[q], q))
+        out[r].append(i)
+        load[r] += sizes[i]
+    return [sorted(x) for x in out]
+
+
+def reduce_over_ranks(ms, units, device, world):
+    """(max of ms, sum of units) over the ranks: the job's time is its slowest
+    rank's, its work all ranks' work.  No collective on one rank."""
+    if world == 1:
+        return float(ms), float(units)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+def run_batch(args, rank=0, world=1):
     """Uneven batch: 32 random star domains, each with its own mixture and tree,
     in one vpx_execute_batch graph (mixed form), against the same trees run one
-    after another (mixed, and FP64 as in a plain sequential solver)."""
+    after another (mixed, and FP64 as in a plain sequential solver).  On N
+    ranks each takes a size-balanced share of the trees (no collective on the
+    data path); value = all ranks' targets / the slowest rank's time."""
     import torch
     import workloads as W
     from paper_2211_14537_gb300 import vpx as V
 
-    dev = torch.device("cuda", 0)
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
-    wls = W.star_batch(32)
+    wls_all = W.star_batch(32)
+    shard = list(range(len(wls_all)))
+    if world > 1:
+        # tree sizes from host-only plans (no device work), then the share of this rank
+        sizes_all = []
+        for wl in wls_all:
+            o = V.vpx_default_options(K=wl.opts.K, min_level=wl.opts.min_level, max_level=wl.opts.max_level,
+                                      refine_tol=wl.opts.refine_tol, f_scale=wl.opts.f_scale, p=args.p)
+            sizes_all.append(V.vpx_plan_create(o, wl.domain, wl.sources[0], host_only=True).sizes()[1])
+        shard = shard_by_size(sizes_all, world)[rank]
+    wls = [wls_all[i] for i in shard]
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
@@ -230,6 +269,9 @@ def run_batch(args):
         for _ in range(max(args.warmup, 3)):
             step()
         torch.cuda.synchronize(dev)
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
         e0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
         e1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
         for i in range(steps):
@@ -240,7 +282,8 @@ def run_batch(args):
             with torch.cuda.stream(stream):
                 e1[i].record(stream)
         torch.cuda.synchronize(dev)
-        return statistics.mean([e0[i].elapsed_time(e1[i]) for i in range(steps)])
+        ms = statistics.mean([e0[i].elapsed_time(e1[i]) for i in range(steps)])
+        return reduce_over_ranks(ms, 0, dev, world)[0]
 
     mixed, setup_mixed = make(V.VPX_PREC_MIXED)
     sizes = [p.sizes() for p in mixed]
@@ -248,7 +291,7 @@ def run_batch(args):
           for wl, p in zip(wls, mixed)]
     vs = [torch.empty(sz[1], dtype=torch.float64, device=dev) for sz in sizes]
     vbs = [torch.empty(sz[3], dtype=torch.float64, device=dev) for sz in sizes]
-    targets = sum(sz[1] + sz[3] for sz in sizes)
+    targets = reduce_over_ranks(0.0, sum(sz[1] + sz[3] for sz in sizes), dev, world)[1]
     tuned = [0, 0]
     if not args.no_autotune:
         t0 = time.perf_counter()
@@ -279,14 +322,21 @@ def run_batch(args):
         if V.vpx_sync_status(p) != 0:
             raise RuntimeError("device status error in the FP64 sequence")
     rate = lambda ms: targets / (ms * 1e-3)
+    leaf_all = reduce_over_ranks(0.0, sum(sz[1] for sz in sizes), dev, world)[1]
+    bdry_all = reduce_over_ranks(0.0, sum(sz[3] for sz in sizes), dev, world)[1]
+    kernels = reduce_over_ranks(0.0, kernels, dev, world)[1]
+    if rank != 0:
+        return
     out = {
-        "metric": METRIC, "value": rate(ms_batch), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "metric": METRIC, "value": rate(ms_batch), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": ms_batch, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16 (exact 7-bit slices) + f64",
         "data": "synthetic (32 seeded random star domains, each with its own Gaussian mixture)",
-        "config": {"workload": "star_batch_32", "K": 8, "p": args.p, "trees": len(sizes),
-                   "leaf_targets": sum(sz[1] for sz in sizes), "boundary_targets": sum(sz[3] for sz in sizes),
-                   "leaf_targets_min": min(sz[1] for sz in sizes), "leaf_targets_max": max(sz[1] for sz in sizes),
+        "config": {"workload": "star_batch_32", "K": 8, "p": args.p, "trees": len(wls_all),
+                   "trees_per_rank": "size-balanced shares" if world > 1 else "all",
+                   "leaf_targets": int(leaf_all), "boundary_targets": int(bdry_all),
+                   "leaf_targets_min_rank0": min(sz[1] for sz in sizes),
+                   "leaf_targets_max_rank0": max(sz[1] for sz in sizes),
                    "l2": "flushed between timed steps (256 MB write, outside the events)",
                    "graph": "one vpx_execute_batch graph replay per step",
                    "setup_s": {"mixed": round(setup_mixed, 2), "fp64": round(setup_fp64, 2)},
@@ -295,7 +345,7 @@ def run_batch(args):
         "forms": {"mixed_batch": {"value": rate(ms_batch), "ms_per_step": ms_batch},
                   "mixed_sequential": {"value": rate(ms_seq_mixed), "ms_per_step": ms_seq_mixed},
                   "fp64_sequential": {"value": rate(ms_seq_fp64), "ms_per_step": ms_seq_fp64}},
-        "gpu_launches": kernels * args.steps,
+        "gpu_launches": int(kernels) * args.steps,
         "clocks": cl,
     }
     print(json.dumps(out), flush=True)
@@ -329,9 +379,7 @@ def main():
             run_reference(args, world)
         return
     if args.workload == "star-batch":
-        if world > 1:
-            raise SystemExit("--workload star-batch runs on one GPU")
-        run_batch(args)
+        run_batch(args, rank, world)
         return
     forms = ["fp64", "mixed"] if args.precision == "both" else [args.precision]
     res = {f: run_gpu(args, rank, world, f) for f in forms}
@@ -352,14 +400,8 @@ def main():
     ok = [f for f in forms if errs.get(f, 0.0) <= 1e-10]
     head = min(ok or forms, key=lambda f: res[f]["ms"])
     r = res[head]
-    ms_max = r["ms"]
-    if world > 1:
-        import torch
-        import torch.distributed as dist
-        t = torch.tensor([r["ms"]], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-    value = r["tg"] * world / (ms_max * 1e-3)
+    ms_max, tg_all = reduce_over_ranks(r["ms"], r["tg"], "cuda", world)   # replicas: every rank one tree
+    value = tg_all / (ms_max * 1e-3)
     if head == "mixed":
         # exact bf16 slice products: 15 slice pairs per near-field product
         bf16_flops = 15 * r["near_flops"]
