@@ -189,3 +189,19 @@ def test_boundary_targets_follow_section6(V):
     for wl in (W.disk_sincos(level=3), W.starfish_gaussian(K=8, tol=1e-6, max_level=6)):
         plan = _plan(V, wl)
         assert plan.sizes()[3] == n_q * wl.domain.n_panels
+
+
+def test_star_batch_is_seeded_and_uneven(V):
+    """The uneven batch: 32 domains, the same on every call; each draws its own
+    refinement tolerance in [1e-8, 1e-3]; the trees (host-only plans) span more
+    than a factor of ten in leaf targets."""
+    a, b = W.star_batch(32), W.star_batch(32)
+    assert len(a) == 32
+    xy = np.random.Generator(np.random.PCG64(3)).uniform(-0.3, 0.3, size=(50, 2))
+    for wa, wb in zip(a, b):
+        assert wa.opts.refine_tol == wb.opts.refine_tol
+        assert 1e-8 <= wa.opts.refine_tol <= 1e-3
+        assert np.array_equal(wa.sources[0](xy), wb.sources[0](xy))
+        assert np.array_equal(wa.domain.inside(xy), wb.domain.inside(xy))
+    sizes = [_plan(V, wl).sizes()[1] for wl in a[:8]]
+    assert max(sizes) > 10 * min(sizes)
