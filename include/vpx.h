@@ -94,7 +94,8 @@ int vpx_default_options(vpx_options *opt);
  * restriction), leaf classification and extension lists, the universal
  * stencil of every cut leaf and its least-squares extension operator
  * (Section 3.2), the near-field, expansion and translation tables of the box
- * FMM, the interaction lists (built on the device), and the boundary nodes.
+ * FMM, the interaction lists (built on the host and uploaded), and the
+ * boundary nodes.
  * n_panels may be 0 (no boundary: every leaf must then be regular).
  * flags: 0 or VPX_PLAN_HOST_ONLY.  On success *out owns all resources.
  */
@@ -143,11 +144,20 @@ int vpx_plan_lists(vpx_plan_t plan, int32_t *near, int32_t *vlist, int32_t *xlis
 int vpx_plan_near_tables(vpx_plan_t plan, double *out);
 
 /*
- * The hot path.  f_stencil: device, nrhs columns of n_stencil values (ld_f >= n_stencil).
- * v_leaf: device, nrhs columns of n_leaf_nodes values (ld_v >= n_leaf_nodes).
- * v_bdry: device, nrhs columns of n_bdry values (ld_b >= n_bdry); may be NULL.
- * Computes f^e on all leaves (extension) and V[f^e] at all targets.
- * Asynchronous on `stream`.  nrhs <= opt.max_rhs.
+ * The hot path: the extension of Section 3.2 on the cut leaves and their
+ * extension lists (f^e at every leaf node), then the box FMM of Section 4.1,
+ * V[f^e] (eq. volinte) at every leaf node and boundary node.
+ * f_stencil: device, nrhs columns of n_stencil values in vpx_stencil_points
+ * order (ld_f >= n_stencil).  v_leaf: device, nrhs columns of n_leaf_nodes
+ * values, leaf-major (ld_v >= n_leaf_nodes).  v_bdry: device, nrhs columns of
+ * n_bdry values (ld_b >= n_bdry); may be NULL.  The caller owns all three.
+ * Asynchronous on `stream`; the first call with a given set of pointers,
+ * strides, nrhs and stream captures a CUDA graph, later calls replay it.
+ * Errors: VPX_ERR_ARG (null plan or buffer, nrhs outside 1..opt.max_rhs,
+ * short leading dimension; nothing is launched), VPX_ERR_STATE (host-only
+ * plan), VPX_ERR_CUDA.  Non-finite output (VPX_ERR_NAN) and a bounded wait
+ * that gave up (VPX_ERR_TIMEOUT) are latched on the device and returned by
+ * vpx_sync_status.
  */
 int vpx_execute(vpx_plan_t plan, const double *f_stencil, int nrhs, int64_t ld_f,
                 double *v_leaf, int64_t ld_v, double *v_bdry, int64_t ld_b, void *stream);
@@ -200,12 +210,15 @@ int vpx_autotune(vpx_plan_t plan, const double *f_stencil, int nrhs, int64_t ld_
 int vpx_autotune_batch(int n, vpx_plan_t const *plans, const double *const *f_stencil, const int *nrhs,
                        const int64_t *ld_f, void *stream, int *n_passes, int *n_changed);
 
-/* Extension only: f^e at all leaf nodes (device, nrhs columns, ld_fe >= n_leaf_nodes). */
+/* Extension only (Section 3.2): f^e at all leaf nodes (device, nrhs columns,
+ * ld_fe >= n_leaf_nodes; f_stencil as in vpx_execute).  Errors as in vpx_execute. */
 int vpx_extend(vpx_plan_t plan, const double *f_stencil, int nrhs, int64_t ld_f,
                double *fe_leaf, int64_t ld_fe, void *stream);
 
-/* Volume potential only (the box FMM of Section 4.1) for given leaf-node
- * values fe_leaf (device, nrhs columns of n_leaf_nodes values). */
+/* Volume potential only (the box FMM of Section 4.1, eq. volinte) for given
+ * leaf-node values fe_leaf (device, nrhs columns of n_leaf_nodes values,
+ * leaf-major, ld_fe >= n_leaf_nodes); outputs as in vpx_execute.  Errors as in
+ * vpx_execute. */
 int vpx_potential(vpx_plan_t plan, const double *fe_leaf, int nrhs, int64_t ld_fe,
                   double *v_leaf, int64_t ld_v, double *v_bdry, int64_t ld_b, void *stream);
 
@@ -225,8 +238,11 @@ int vpx_potential(vpx_plan_t plan, const double *fe_leaf, int nrhs, int64_t ld_f
 int vpx_potential_static(vpx_plan_t plan, const double *fe_leaf, int nrhs, int64_t ld_fe,
                          double *v_leaf, int64_t ld_v, double *v_bdry, int64_t ld_b, void *stream);
 
-/* End to end with HOST buffers (contiguous columns): copies f in, runs
- * vpx_execute on the plan's own stream, copies V out, synchronises. */
+/* End to end with HOST buffers (contiguous columns of n_stencil, n_leaf_nodes
+ * and n_bdry doubles; v_bdry_host may be NULL): copies f in, runs vpx_execute
+ * on the plan's own stream, copies V out and synchronises.  Errors as in
+ * vpx_execute; the latched device status (VPX_ERR_NAN, VPX_ERR_TIMEOUT) is
+ * read by a following vpx_sync_status. */
 int vpx_execute_host(vpx_plan_t plan, const double *f_stencil_host, int nrhs,
                      double *v_leaf_host, double *v_bdry_host);
 
@@ -254,7 +270,7 @@ int vpx_graph_kernel_count(vpx_plan_t plan, int64_t *kernels);
  * current context: a kernel waits on a barrier that nothing completes, gives up
  * after 20 ms of wall-clock time and latches VPX_ERR_TIMEOUT, which is
  * returned in *status (VPX_ERR_TIMEOUT expected).  The paper has no
- * counterpart; this is the failure-detection check of the build.  Errors:
+ * counterpart; it is the library's self-check of its failure detection.  Errors:
  * VPX_ERR_ARG for a null argument, VPX_ERR_CUDA / VPX_ERR_NODEV. */
 int vpx_check_bounded_wait(int *status);
 
