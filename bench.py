@@ -464,8 +464,17 @@ def run_reference(args, world):
     pts, meta = O.stencil_points(tree, wl.domain)
     vals, _ = O.leaf_values(tree, wl.domain, wl.sources[0](pts)[:, None], meta)
     nodes = O.all_leaf_nodes(tree)
-    n = min(args.oracle_sample // 4 or 1, len(nodes))
     rng = np.random.Generator(np.random.PCG64(2214))
+    # per-step sample sized so that warm-up + timed steps take about 150 s of
+    # oracle work whatever --steps / --warmup are (calibrated on 64 targets),
+    # but at least 64 targets: the oracle parallelises over targets, and a
+    # target's singular quadrature alone takes a large part of a second
+    t0 = time.perf_counter()
+    O.volume_potential(tree, vals, nodes[rng.choice(len(nodes), 64, replace=False)])
+    per_target = (time.perf_counter() - t0) / 64
+    budget_s = 150.0
+    n = int(budget_s / (max(args.steps + args.warmup, 1) * per_target))
+    n = max(64, min(n, args.oracle_sample // 4 or 1, len(nodes)))
     for _ in range(args.warmup):
         O.volume_potential(tree, vals, nodes[rng.choice(len(nodes), n, replace=False)])
     t0 = time.perf_counter()
@@ -480,7 +489,8 @@ def run_reference(args, world):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": wl.name, "K": wl.opts.K, "sample_targets_per_step": n},
         "cpu_baseline": {"value": val, "unit": UNIT, "cores": thr, "kind": "oracle",
-                         "sample": "%d seeded leaf nodes per step, direct quadrature" % n},
+                         "sample": "%d seeded leaf nodes per step (sized for about %.0f s of oracle work over "
+                                   "the run), direct quadrature" % (n, budget_s)},
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
