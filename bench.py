@@ -40,7 +40,7 @@ def parse():
     ap.add_argument("--p", type=int, default=40)
     ap.add_argument("--precision", default="both", choices=["fp64", "mixed", "both"])
     ap.add_argument("--nrhs", type=int, default=1)
-    ap.add_argument("--oracle-sample", type=int, default=10000)   # ~10-15 s of oracle work on 16 cores
+    ap.add_argument("--oracle-sample", type=int, default=12000)   # ~10 s of oracle work on 16 cores
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default engine / tile choices")
     ap.add_argument("--workload", default="starfish", choices=["starfish", "star-batch"],
@@ -474,7 +474,7 @@ def run_reference(args, world):
     per_target = (time.perf_counter() - t0) / 64
     budget_s = 150.0
     n = int(budget_s / (max(args.steps + args.warmup, 1) * per_target))
-    n = max(64, min(n, args.oracle_sample // 4 or 1, len(nodes)))
+    n = max(64, min(n, 2500, len(nodes)))
     for _ in range(args.warmup):
         O.volume_potential(tree, vals, nodes[rng.choice(len(nodes), n, replace=False)])
     t0 = time.perf_counter()
