@@ -149,6 +149,38 @@ def universal_matrix(K: int):
     return _universal_A[K]
 
 
+def universal_matrix_finite_eps(K: int, eps: float) -> np.ndarray:
+    """A_{X,G} = Phi_{X,G} Phi_{G,G}^{-1} (eq. defA) for Gaussians
+    exp(-eps^2 |x - g|^2) of finite shape parameter eps on the reference square
+    [-1,1]^2, the points X and G of universal_matrix.  Phi_{G,G} has condition
+    number ~ eps^{-2q}, so the matrices are formed and the system solved in
+    multiprecision (mpmath, 30 + 2q log10(1/eps) digits) and the result rounded
+    to FP64.  As eps -> 0 this tends to the flat-limit operator of
+    universal_matrix, the paper's operator at its small eps (Section 3.1,
+    Section 6).  Slow (seconds); for checking the flat-limit reading only."""
+    import mpmath as mp
+    q, Kbar, NG = stencil_params(K)
+    t, _ = gauss_legendre(K)
+    XS = np.stack(np.meshgrid(t / 3.0, t / 3.0, indexing="xy"), axis=-1).reshape(-1, 2)
+    tc = chebyshev1_nodes(Kbar)
+    XSb = np.stack(np.meshgrid(tc, tc, indexing="xy"), axis=-1).reshape(-1, 2)
+    G = padua_points(q)
+    X = np.concatenate([XS, XSb, G])
+    with mp.workdps(30 + int(math.ceil(2 * q * math.log10(1.0 / eps)))):
+        e2 = mp.mpf(eps) ** 2
+        Gm = [(mp.mpf(float(a)), mp.mpf(float(b))) for a, b in G]
+        Xm = [(mp.mpf(float(a)), mp.mpf(float(b))) for a, b in X]
+        phi = lambda p, g: mp.exp(-e2 * ((p[0] - g[0]) ** 2 + (p[1] - g[1]) ** 2))
+        PGG = mp.matrix([[phi(gi, gj) for gj in Gm] for gi in Gm])
+        W = mp.inverse(PGG)                       # Phi_GG is symmetric: A = Phi_XG W
+        A = np.empty((len(Xm), len(Gm)))
+        for i, x in enumerate(Xm):
+            row = [phi(x, gj) for gj in Gm]
+            for j in range(len(Gm)):
+                A[i, j] = float(mp.fsum(row[k] * W[k, j] for k in range(len(Gm))))
+    return A
+
+
 def pseudo_inverse(M: np.ndarray, rcond: float = PINV_RCOND) -> np.ndarray:
     """Moore-Penrose pseudo-inverse by the SVD (numpy/LAPACK), singular values
     <= rcond * largest treated as zero."""

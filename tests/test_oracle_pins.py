@@ -411,3 +411,18 @@ def test_discretization_matches_section6():
     assert O.NQ_BOUNDARY == g["N_q"]
     dom = W.disk_sincos(level=3).domain
     assert len(O.boundary_nodes(dom)) == g["N_q"] * dom.n_panels
+
+
+@pytest.mark.slow
+def test_flat_limit_reading_against_finite_eps_operator():
+    """The extension operator is read in the flat limit of the Gaussian basis
+    (the Lagrange basis of P_10 at G).  The paper's operator has eps = 1e-5
+    (Section 3.1, Section 6).  Formed in multiprecision, the finite-eps
+    operator converges to the flat-limit one as eps^2 and differs from it by
+    2.3e-11 in max norm at eps = 1e-5 (entries of order 1)."""
+    pytest.importorskip("mpmath")
+    A0 = O.universal_matrix(8)
+    d3 = np.abs(O.universal_matrix_finite_eps(8, 1e-3) - A0).max()
+    d5 = np.abs(O.universal_matrix_finite_eps(8, 1e-5) - A0).max()
+    assert d5 <= 1e-10
+    assert abs(d3 / d5 / 1e4 - 1.0) < 0.05      # eps^2 convergence
