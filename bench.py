@@ -43,15 +43,18 @@ def parse():
     ap.add_argument("--oracle-sample", type=int, default=12000)   # ~10 s of oracle work on 16 cores
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default engine / tile choices")
-    ap.add_argument("--workload", default="starfish", choices=["starfish", "star-batch"],
-                    help="star-batch: the uneven batch of 32 star domains in one graph (mixed form), "
-                         "against the same trees run one after another in both forms")
+    ap.add_argument("--workload", default="starfish", choices=["starfish", "lshape", "star-batch"],
+                    help="lshape: the L-shape refined to level 14 (1.4 M targets); star-batch: the uneven "
+                         "batch of 32 star domains in one graph (mixed form), against the same trees run one "
+                         "after another in both forms")
     return ap.parse_args()
 
 
-def workload():
+def workload(name="starfish"):
+    """The single-tree workloads: the adaptive starfish (the default line) and
+    the L-shape refined to level 14 toward its corners (1.4 M targets)."""
     import workloads as W
-    return W.starfish_gaussian(K=16)
+    return W.lshape_expsin() if name == "lshape" else W.starfish_gaussian(K=16)
 
 
 class ClockSampler:
@@ -113,7 +116,7 @@ def run_gpu(args, rank, world, precision):
 
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
-    wl = workload()
+    wl = workload(args.workload)
     t0 = time.perf_counter()
     o = V.vpx_default_options(K=wl.opts.K, min_level=wl.opts.min_level, max_level=wl.opts.max_level,
                               refine_tol=wl.opts.refine_tol, f_scale=wl.opts.f_scale, p=args.p,
@@ -412,7 +415,8 @@ def main():
         # DRAM bytes read + written by one launch of the near-field kernel on this
         # workload, from an ncu capture of the kernel as it stands (profiles/);
         # reset to None whenever the kernel changes
-        traffic = 24641280 if not os.environ.get("VPX_NO_TC") and args.nrhs == 1 else None
+        traffic = (24641280 if not os.environ.get("VPX_NO_TC") and args.nrhs == 1 and args.workload == "starfish"
+                   else None)
         roof = {"kernel": kname, "bound": "tensor",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
                 "traffic_unit": "bytes per launch",
@@ -427,10 +431,9 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if head == "fp64" else "bf16 (exact 7-bit slices) + f64",
-        "data": "synthetic (seeded analytic source on the starfish domain)",
-        "config": {"workload": r["wl"].name, "domain": "starfish r=0.35(1+0.3cos5t)",
-                   "source": "exp(-|x-(0.1,0.05)|^2/0.02^2)", "K": r["K"], "p": args.p,
-                   "refine_tol": 1e-10, "n_leaves": r["n_leaves"], "leaf_targets": r["nt"],
+        "data": "synthetic (seeded analytic source on the %s domain)" % ("L-shape" if args.workload == "lshape" else "starfish"),
+        "config": {"workload": r["wl"].name, "description": r["wl"].description, "K": r["K"], "p": args.p,
+                   "refine_tol": r["wl"].opts.refine_tol, "n_leaves": r["n_leaves"], "leaf_targets": r["nt"],
                    "boundary_targets": r["nb"], "stencil_points": r["ns"], "nrhs": args.nrhs,
                    "precision": head, "near_pairs": r["lc"]["near"], "m2l_pairs": r["lc"]["m2l"],
                    "s2l_pairs": r["lc"]["s2l"], "m2t_pairs": r["lc"]["m2t"], "levels": r["lc"]["n_levels"],

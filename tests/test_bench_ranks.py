@@ -54,3 +54,35 @@ def test_reduce_over_two_gloo_ranks():
 
 def test_reduce_on_one_rank_is_identity():
     assert bench.reduce_over_ranks(3.0, 7, "cpu", 1) == (3.0, 7.0)
+
+
+def test_bench_line_carries_the_contract_keys(monkeypatch, capsys):
+    """bench.main() on one rank, the GPU run and the oracle sample replaced by
+    fixed results: one JSON line with the keys of the benchmark contract."""
+    import json
+    import sys
+    import numpy as np
+
+    def fake_run_gpu(args, rank, world, prec):
+        return dict(wl=bench.workload(args.workload), ms=0.2 if prec == "mixed" else 1.5, setup_s=0.6,
+                    tg=184832, nt=182272, nb=2560, ns=129619, n_leaves=712,
+                    lc={"near": 4900, "m2l": 14104, "s2l": 822, "m2t": 1112, "n_levels": 7},
+                    pass_ms={"near": 0.05}, near_flops=6.4e8, near_ms=0.05, clocks={"sm_mhz": 2070.0},
+                    e2e_s=3e-4, v=np.ones(182272), K=16, graph_kernels=24, tune=(7, 0))
+
+    monkeypatch.setattr(bench, "run_gpu", fake_run_gpu)
+    monkeypatch.setattr(bench, "oracle_sample", lambda wl, n, **k: (np.arange(10), np.ones(10), 1.0, 16))
+    monkeypatch.setattr(sys, "argv", ["bench.py"])
+    bench.main()
+    d = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "roofline", "cpu_baseline", "e2e",
+              "gpu_launches", "clocks"):
+        assert k in d, k
+    assert d["n_gpus"] == 1 and d["warmup"] >= 3 and d["config"]["workload"]
+    assert d["value"] == pytest.approx(184832 / 0.2e-3)                      # the faster form that meets 1e-10
+    assert set(d["roofline"]) >= {"bound", "achieved", "peak", "unit", "frac", "traffic"}
+    assert d["roofline"]["frac"] == pytest.approx(d["roofline"]["achieved"] / d["roofline"]["peak"])
+    assert set(d["e2e"]) >= {"value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step"}
+    assert d["e2e"]["h2d_bytes_per_step"] == 8 * 129619 and d["gpu_launches"] == 24 * d["steps"]
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 16
