@@ -45,6 +45,7 @@ WORKLOADS = {
     "disk_l3_k16": lambda: W.disk_sincos(level=3, K=16),
     "starfish_k8": lambda: W.starfish_gaussian(K=8, tol=1e-8, max_level=8),
     "lshape_small": lambda: W.lshape_expsin(K=8, base_level=4, max_level=8, corner_levels=5),
+    "star_batch_03": lambda: W.star_batch(4)[3],   # adaptive K = 8 star of the uneven batch (3,844 leaves)
 }
 
 
