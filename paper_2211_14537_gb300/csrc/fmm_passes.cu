@@ -397,9 +397,10 @@ void ev_record_pass(vpx_plan *p, int i, cudaStream_t s);
 
 // Three streams forked from the main one: the near field (leaf values only)
 // on the second; list i+ (leaf values -> locals) and, once the multipoles are
-// final, list i- on the third.  They overlap the level-by-level passes of the
-// main stream, add into V or the locals with atomics, and are joined where
-// their results are read (the locals before L2L, V before the last launch).
+// final, the a_0 log terms of the locals and of V and list i- on the third.
+// They overlap the level-by-level passes of the main stream, add into V or the
+// locals with atomics, and are joined where their results are read (the
+// locals before L2L, V before the last launch).
 void run_potential_passes(vpx_plan *p, const double *fe, int64_t ldfe, int nrhs, double *v, int64_t ldv, double *vb,
                           int64_t ldb, double *mp, double *lo, cudaStream_t s) {
     const bool mixed = p->opt.precision == VPX_PREC_MIXED;
