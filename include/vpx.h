@@ -69,6 +69,9 @@ typedef struct {
     int    precision;    /* VPX_PREC_FP64 or VPX_PREC_MIXED */
     int    max_rhs;      /* largest nrhs a later vpx_execute may pass */
     int    n_quad_bdry;  /* Gauss-Legendre nodes per boundary panel (default 16) */
+    double rbf_eps;      /* shape parameter of the Gaussians on the unit box (Section 3.1): 0 (default)
+                            = their flat limit, the polynomial interpolant at G; up to 1e-3 otherwise
+                            (the paper uses ~1e-5), K = 6, 8 or 16 */
 } vpx_options;
 
 /* ---------------------------------------------------------------- callbacks
@@ -136,6 +139,16 @@ int vpx_plan_list_counts(vpx_plan_t plan, int64_t *near, int64_t *m2l, int64_t *
  * (level, ix, iy, leaf index or -1), n_boxes each.  Any pointer may be NULL. */
 int vpx_plan_lists(vpx_plan_t plan, int32_t *near, int32_t *vlist, int32_t *xlist, int32_t *wlist,
                    int32_t *box_level, int32_t *box_ix, int32_t *box_iy, int32_t *box_leaf);
+
+/* The universal extension operator A_{X,G} = Phi_{X,G} Phi_{G,G}^{-1}
+ * (Section 3.1, eq. defA) that plans of leaf order K and shape parameter
+ * rbf_eps use, on the reference extension square [-1,1]^2: *nx x *ng doubles,
+ * row-major (rows X_S, X_Sbar, G; columns G), written to `out` when non-NULL.
+ * rbf_eps = 0 is the flat limit; rbf_eps > 0 adds (rbf_eps / 2)^2 A2, the
+ * eps^2 term of the Gaussian operator, from a table precomputed in
+ * multiprecision (unit box of side 1 = half the reference square).  Host only;
+ * no plan needed.  Errors: VPX_ERR_ARG (bad K or rbf_eps, null nx / ng). */
+int vpx_universal_matrix(int K, double rbf_eps, double *out, int64_t *nx, int64_t *ng);
 
 /* Host copy of the near-field tables (33 x K*K x K*K doubles): entry
  * [c][i][j] = int over the source box [-1,1]^2 of log|x_i - y| l_j(y) dy, x_i the

@@ -181,6 +181,19 @@ def universal_matrix_finite_eps(K: int, eps: float) -> np.ndarray:
     return A
 
 
+_finite_eps_cache = {}
+
+
+def _finite_eps_A(K: int, rbf_eps: float) -> np.ndarray:
+    """The universal operator for Gaussians of shape parameter rbf_eps on the
+    unit box: the extension square maps to [-1,1]^2, twice the unit box's side,
+    so the reference-square parameter is rbf_eps / 2."""
+    key = (K, float(rbf_eps))
+    if key not in _finite_eps_cache:
+        _finite_eps_cache[key] = universal_matrix_finite_eps(K, 0.5 * rbf_eps)
+    return _finite_eps_cache[key]
+
+
 def pseudo_inverse(M: np.ndarray, rcond: float = PINV_RCOND) -> np.ndarray:
     """Moore-Penrose pseudo-inverse by the SVD (numpy/LAPACK), singular values
     <= rcond * largest treated as zero."""
@@ -549,7 +562,7 @@ def legendre_total_degree_vander(z: np.ndarray, q: int) -> np.ndarray:
     return np.stack(cols, axis=1)
 
 
-def extend_cut_leaf(b, K, t, masks, fI: np.ndarray, targets: np.ndarray):
+def extend_cut_leaf(b, K, t, masks, fI: np.ndarray, targets: np.ndarray, rbf_eps: float = 0.0):
     """Section 3.2 + 4.1 for one cut leaf, flat-limit reading.
 
     fI: (N_I, nrhs) data at the interior stencil points (X_S^I, X_Sbar^I, G^I).
@@ -563,7 +576,7 @@ def extend_cut_leaf(b, K, t, masks, fI: np.ndarray, targets: np.ndarray):
     XS, XSb, G = cut_leaf_stencil(b, K, t)
     cx, cy = box_center(b)
     r = 1.5 * box_side(b[0])
-    A = universal_matrix(K)
+    A = universal_matrix(K) if rbf_eps == 0.0 else _finite_eps_A(K, rbf_eps)
     nS = K * K
     interior = np.concatenate(masks)
     AI = A[interior]
@@ -597,11 +610,12 @@ def extend_cut_leaf(b, K, t, masks, fI: np.ndarray, targets: np.ndarray):
     return out, cond
 
 
-def leaf_values(tree: OracleTree, dom, f_stencil: np.ndarray, meta):
+def leaf_values(tree: OracleTree, dom, f_stencil: np.ndarray, meta, rbf_eps: float = 0.0):
     """f^e at every leaf node, shape (n_leaves, nrhs, K*K): data on regular
     leaves and on interior nodes of cut leaves, the extension on exterior
     nodes of cut leaves and on owned exterior leaves, zero elsewhere
-    (Section 4.1)."""
+    (Section 4.1).  rbf_eps > 0: Gaussians of that shape parameter on the unit
+    box (Section 3.1) instead of their flat limit."""
     K = tree.K
     f_stencil = np.asarray(f_stencil, dtype=np.float64)
     if f_stencil.ndim == 1:
@@ -627,7 +641,7 @@ def leaf_values(tree: OracleTree, dom, f_stencil: np.ndarray, meta):
         for j in owned.get(i, []):
             tg.append(leaf_nodes(tree.leaves[j], tree.t))
         targets = np.concatenate(tg)
-        vals, cond = extend_cut_leaf(b, K, tree.t, masks, fI, targets)
+        vals, cond = extend_cut_leaf(b, K, tree.t, masks, fI, targets, rbf_eps)
         conds[i] = cond
         nE = int((~masks[0]).sum())
         v = np.zeros((K * K, nrhs))

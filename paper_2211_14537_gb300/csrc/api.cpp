@@ -196,6 +196,7 @@ static void check_options(const vpx_options *o) {
     if (o->precision != VPX_PREC_FP64 && o->precision != VPX_PREC_MIXED) fail(VPX_ERR_ARG, "bad precision");
     if (o->max_rhs < 1) fail(VPX_ERR_ARG, "max_rhs >= 1 required");
     if (o->n_quad_bdry < 1 || o->n_quad_bdry > 64) fail(VPX_ERR_ARG, "n_quad_bdry in 1..64");
+    check_rbf_eps(o->K, o->rbf_eps);
 }
 
 }  // namespace vpx
@@ -203,6 +204,20 @@ static void check_options(const vpx_options *o) {
 using namespace vpx;
 
 extern "C" {
+
+int vpx_universal_matrix(int K, double rbf_eps, double *out, int64_t *nx, int64_t *ng) {
+    return guarded([&] {
+        if (!nx || !ng) fail(VPX_ERR_ARG, "null size pointer");
+        if (K < 4 || K > kMaxK || (K % 2)) fail(VPX_ERR_ARG, "K must be even, 4..16");
+        check_rbf_eps(K, rbf_eps);
+        std::vector<double> A;
+        int NX = 0, NG = 0;
+        universal_operator(K, rbf_eps, A, NX, NG);
+        *nx = NX;
+        *ng = NG;
+        if (out) std::copy(A.begin(), A.end(), out);
+    });
+}
 
 int vpx_default_options(vpx_options *opt) {
     if (!opt) return VPX_ERR_ARG;

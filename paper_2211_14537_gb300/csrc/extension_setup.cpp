@@ -7,9 +7,11 @@
 // values at X; for each cut leaf the rows of the interior points give A_I and
 // the extension is f_{X_Sbar^E} = A_{X_Sbar^E,G} A_I^+ f_I.
 //
-// Our reading of the Gaussian basis is its flat limit (shape parameter -> 0):
-// with G unisolvent for the polynomials P_q of total degree <= q and
-// N_G = dim P_q, A is the Lagrange interpolation matrix of P_q at G.  G is
+// By default the Gaussian basis is read in its flat limit (shape parameter ->
+// 0): with G unisolvent for the polynomials P_q of total degree <= q and
+// N_G = dim P_q, A is the Lagrange interpolation matrix of P_q at G.  With a
+// positive shape parameter the eps^2 term of the Gaussian operator is added
+// from a table precomputed in multiprecision (universal_operator).  G is
 // the Padua point set of degree q = 10 (N_G = 66, Section 6), Kbar = 3K/2.  A is formed with the
 // well-conditioned tensor Chebyshev basis T_m T_n (m + n <= q), and A_I^+ (the
 // Moore-Penrose pseudo-inverse) by Householder QR plus a one-sided Jacobi SVD
@@ -215,6 +217,68 @@ void pseudo_inverse(int m, int n, const double *AI, double *P, double *cond, dou
 
 }  // namespace
 
+void check_rbf_eps(int K, double rbf_eps) {
+    if (!(rbf_eps >= 0.0) || rbf_eps > 1e-3) fail(VPX_ERR_ARG, "rbf_eps must lie in [0, 1e-3]");
+    const double *a2 = nullptr;
+    int nx = 0, ng = 0;
+    if (rbf_eps > 0.0 && !rbf_eps2_table(K, &a2, &nx, &ng))
+        fail(VPX_ERR_ARG, "rbf_eps > 0 needs K = 6, 8 or 16 (no Gaussian table for this K)");
+}
+
+// A = Phi_X Phi_G^{-1} in the flat limit (the Lagrange basis of P_q at G,
+// formed with the tensor Chebyshev basis), plus (rbf_eps / 2)^2 A2 for
+// Gaussians of shape parameter rbf_eps on the unit box: the extension square
+// maps to [-1,1]^2, whose side is twice the unit box's, and the remainder of
+// the series is O(rbf_eps^4), below 1e-13 for rbf_eps <= 1e-3.
+void universal_operator(int K, double rbf_eps, std::vector<double> &A, int &NX, int &NG) {
+    const int q = 10, Kb = 3 * K / 2, KK = K * K, KbKb = Kb * Kb;
+    NG = (q + 1) * (q + 2) / 2;
+    NX = KK + KbKb + NG;
+    std::vector<double> t, tw;
+    gauss_legendre(K, t, tw);
+    std::vector<double> tc = chebyshev1(Kb);
+    std::vector<double> px, py;
+    padua(q, px, py);
+    if ((int)px.size() != NG) fail(VPX_ERR_ARG, "Padua point count mismatch");
+    std::vector<double> xy(2 * (size_t)NX);
+    for (int b = 0; b < K; ++b)
+        for (int a = 0; a < K; ++a) {
+            xy[2 * (b * K + a)] = t[a] / 3.0;
+            xy[2 * (b * K + a) + 1] = t[b] / 3.0;
+        }
+    for (int b = 0; b < Kb; ++b)
+        for (int a = 0; a < Kb; ++a) {
+            xy[2 * (KK + b * Kb + a)] = tc[a];
+            xy[2 * (KK + b * Kb + a) + 1] = tc[b];
+        }
+    for (int g = 0; g < NG; ++g) {
+        xy[2 * (KK + KbKb + g)] = px[g];
+        xy[2 * (KK + KbKb + g) + 1] = py[g];
+    }
+    // solve Phi_G^T Y = Phi_X^T, A = Y^T
+    std::vector<double> PhiG((size_t)NG * NG), B((size_t)NG * NX), row(NG);
+    for (int g = 0; g < NG; ++g) {
+        phi_row(q, px[g], py[g], row.data());
+        for (int k = 0; k < NG; ++k) PhiG[(size_t)k * NG + g] = row[k];   // transpose
+    }
+    for (int j = 0; j < NX; ++j) {
+        phi_row(q, xy[2 * j], xy[2 * j + 1], row.data());
+        for (int k = 0; k < NG; ++k) B[(size_t)k * NX + j] = row[k];
+    }
+    lu_solve(NG, PhiG, B, NX);
+    A.assign((size_t)NX * NG, 0.0);
+    for (int j = 0; j < NX; ++j)
+        for (int k = 0; k < NG; ++k) A[(size_t)j * NG + k] = B[(size_t)k * NX + j];
+    if (rbf_eps > 0.0) {
+        const double *a2 = nullptr;
+        int nx = 0, ng = 0;
+        if (!rbf_eps2_table(K, &a2, &nx, &ng) || nx != NX || ng != NG)
+            fail(VPX_ERR_ARG, "no Gaussian table matching this universal stencil");
+        const double e = 0.5 * rbf_eps, e2 = e * e;
+        for (size_t i = 0; i < A.size(); ++i) A[i] += e2 * a2[i];
+    }
+}
+
 void build_stencil(const vpx_options &opt, const Callbacks &cb, const HostTree &tree,
                    std::vector<double> &stencil_xy, StencilInfo &st, bool compute_operators) {
     const int K = opt.K, KK = K * K;
@@ -330,21 +394,12 @@ void build_stencil(const vpx_options &opt, const Callbacks &cb, const HostTree &
     }
     if (!compute_operators) return;
 
-    // universal A = Phi_X Phi_G^{-1}: solve Phi_G^T Y = Phi_X^T, A = Y^T
-    std::vector<double> PhiG((size_t)NG * NG), B((size_t)NG * NX);
-    std::vector<double> row(NG);
-    for (int g = 0; g < NG; ++g) {
-        phi_row(st.q, px[g], py[g], row.data());
-        for (int k = 0; k < NG; ++k) PhiG[(size_t)k * NG + g] = row[k];   // transpose
+    // the universal A (flat limit, plus the Gaussian eps^2 term when rbf_eps > 0)
+    {
+        int nx = 0, ng = 0;
+        universal_operator(K, opt.rbf_eps, st.A, nx, ng);
+        if (nx != NX || ng != NG) fail(VPX_ERR_ARG, "universal stencil size mismatch");
     }
-    for (int j = 0; j < NX; ++j) {
-        phi_row(st.q, st.ref_xy[2 * j], st.ref_xy[2 * j + 1], row.data());
-        for (int k = 0; k < NG; ++k) B[(size_t)k * NX + j] = row[k];
-    }
-    lu_solve(NG, PhiG, B, NX);
-    st.A.assign((size_t)NX * NG, 0.0);
-    for (int j = 0; j < NX; ++j)
-        for (int k = 0; k < NG; ++k) st.A[(size_t)j * NG + k] = B[(size_t)k * NX + j];
 
     st.pinv_off.assign(ncut, 0);
     size_t tot = 0;

@@ -85,6 +85,13 @@ struct StencilInfo {
     double max_pinv_norm = 0.0, max_cond = 0.0;
 };
 
+// The universal operator of leaf order K on [-1,1]^2 (rows X_S, X_Sbar, G),
+// flat limit plus (rbf_eps / 2)^2 A2 for rbf_eps > 0.
+void universal_operator(int K, double rbf_eps, std::vector<double> &A, int &NX, int &NG);
+// A2 of the Gaussian operator for leaf order K (rbf_eps2_tables.cpp); false if K has no table.
+bool rbf_eps2_table(int K, const double **a2, int *nx, int *ng);
+// rbf_eps in [0, 1e-3], and a table for K when positive; else VPX_ERR_ARG.
+void check_rbf_eps(int K, double rbf_eps);
 void build_stencil(const vpx_options &opt, const Callbacks &cb, const HostTree &tree,
                    std::vector<double> &stencil_xy, StencilInfo &st, bool compute_operators);
 

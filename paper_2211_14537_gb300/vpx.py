@@ -44,7 +44,8 @@ class VpxError(RuntimeError):
 class vpx_options(ctypes.Structure):
     _fields_ = [("K", ctypes.c_int), ("min_level", ctypes.c_int), ("max_level", ctypes.c_int),
                 ("refine_tol", ctypes.c_double), ("f_scale", ctypes.c_double), ("p", ctypes.c_int),
-                ("precision", ctypes.c_int), ("max_rhs", ctypes.c_int), ("n_quad_bdry", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("max_rhs", ctypes.c_int), ("n_quad_bdry", ctypes.c_int),
+                ("rbf_eps", ctypes.c_double)]
 
 
 POINTS_CB = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_int64,
@@ -56,7 +57,8 @@ CURVE_CB = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_
 
 EXPORTED = [
     "vpx_default_options", "vpx_plan_create", "vpx_plan_sizes", "vpx_plan_leaves", "vpx_stencil_points",
-    "vpx_leaf_nodes", "vpx_boundary_nodes", "vpx_plan_list_counts", "vpx_plan_lists", "vpx_plan_near_tables", "vpx_execute",
+    "vpx_leaf_nodes", "vpx_boundary_nodes", "vpx_plan_list_counts", "vpx_plan_lists", "vpx_plan_near_tables",
+    "vpx_universal_matrix", "vpx_execute",
     "vpx_execute_batch", "vpx_autotune", "vpx_autotune_batch",
     "vpx_extend", "vpx_potential", "vpx_potential_static", "vpx_execute_host", "vpx_sync_status", "vpx_set_timing",
     "vpx_get_timings", "vpx_pass_name", "vpx_graph_kernel_count", "vpx_check_bounded_wait", "vpx_error_string", "vpx_last_error_message", "vpx_plan_destroy",
@@ -92,6 +94,7 @@ def load_library(path: str = LIB_PATH):
                                     vp]
     L.vpx_potential.argtypes = [vp, vp, ctypes.c_int, i64, vp, i64, vp, i64, vp]
     L.vpx_autotune.argtypes = [vp, vp, ctypes.c_int, i64, vp, P(ctypes.c_int), P(ctypes.c_int)]
+    L.vpx_universal_matrix.argtypes = [ctypes.c_int, ctypes.c_double, P(ctypes.c_double), P(i64), P(i64)]
     L.vpx_autotune_batch.argtypes = [ctypes.c_int, P(vp), P(vp), P(ctypes.c_int), P(i64), vp, P(ctypes.c_int),
                                      P(ctypes.c_int)]
     L.vpx_potential_static.argtypes = [vp, vp, ctypes.c_int, i64, vp, i64, vp, i64, vp]
@@ -188,6 +191,17 @@ class Plan:
         _check(load_library().vpx_plan_lists(self.handle, *[_iptr(x) for x in a]))
         return dict(near=a[0].reshape(nl, N_NEAR), vlist=a[1].reshape(nb, N_V), xlist=a[2].reshape(nb, N_X),
                     wlist=a[3].reshape(nl, N_W), box_level=a[4], box_ix=a[5], box_iy=a[6], box_leaf=a[7])
+
+
+def vpx_universal_matrix(K: int, rbf_eps: float = 0.0) -> np.ndarray:
+    """The universal extension operator (rows X_S, X_Sbar, G; columns G) that
+    plans of leaf order K and shape parameter rbf_eps use (host)."""
+    L = load_library()
+    nx, ng = ctypes.c_int64(), ctypes.c_int64()
+    _check(L.vpx_universal_matrix(K, rbf_eps, None, ctypes.byref(nx), ctypes.byref(ng)))
+    out = np.zeros((nx.value, ng.value))
+    _check(L.vpx_universal_matrix(K, rbf_eps, _dptr(out), ctypes.byref(nx), ctypes.byref(ng)))
+    return out
 
 
 def vpx_plan_near_tables(plan: "Plan") -> np.ndarray:

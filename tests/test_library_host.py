@@ -206,3 +206,35 @@ def test_star_batch_is_seeded_and_uneven(V):
         assert np.array_equal(wa.domain.inside(xy), wb.domain.inside(xy))
     sizes = [_plan(V, wl).sizes()[1] for wl in a[:8]]
     assert max(sizes) > 10 * min(sizes)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("K", [6, 8])
+def test_universal_operator_matches_oracle(V, K):
+    """The library's universal operator (flat limit + the tabulated eps^2 term
+    of the Gaussian operator) against the oracle's, formed independently (its
+    own basis; the finite-eps operator directly in multiprecision): the flat
+    limit to 1e-13; at the paper's eps = 1e-5 on the unit box to 1e-13; the
+    eps^2 term at eps = 1e-3 to 1e-5 of its size (the O(eps^4) remainder)."""
+    pytest.importorskip("mpmath")
+    from oracle import oracle as O
+    A0 = V.vpx_universal_matrix(K)
+    assert np.abs(A0 - O.universal_matrix(K)).max() <= 1e-13
+    A5 = V.vpx_universal_matrix(K, 1e-5)
+    assert np.abs(A5 - O.universal_matrix_finite_eps(K, 0.5e-5)).max() <= 1e-13
+    D_lib = V.vpx_universal_matrix(K, 1e-3) - A0
+    D_orc = O.universal_matrix_finite_eps(K, 0.5e-3) - O.universal_matrix(K)
+    assert np.abs(D_lib - D_orc).max() <= 1e-5 * np.abs(D_orc).max()
+
+
+def test_rbf_eps_option_is_checked(V):
+    with pytest.raises(V.VpxError):
+        V.vpx_universal_matrix(10, 1e-5)          # no Gaussian table for K = 10
+    with pytest.raises(V.VpxError):
+        V.vpx_universal_matrix(8, -1e-5)
+    with pytest.raises(V.VpxError):
+        V.vpx_universal_matrix(8, 2e-3)
+    wl = W.disk_sincos(level=3)
+    o = V.vpx_default_options(K=10, min_level=3, max_level=3, rbf_eps=1e-5)
+    with pytest.raises(V.VpxError):
+        V.vpx_plan_create(o, wl.domain, wl.sources[0], host_only=True)
