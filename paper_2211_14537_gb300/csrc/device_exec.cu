@@ -518,9 +518,9 @@ void device_autotune(int n, vpx_plan *const *plans, const double *const *f, cons
         if (e0) cudaEventDestroy(e0);
         if (e1) cudaEventDestroy(e1);
     };
+    std::vector<TunePass> tp;
     try {
         // 1. record the pass calls of every plan (one execute each)
-        std::vector<TunePass> tp;
         for (int i = 0; i < n; ++i) {
             vpx_plan *p = plans[i];
             ldv[i] = std::max<int64_t>((int64_t)p->dt.n_leaves * p->KK, 1);
@@ -680,6 +680,9 @@ void device_autotune(int n, vpx_plan *const *plans, const double *const *f, cons
         }
         VPX_CUDA(cudaStreamSynchronize(s));
     } catch (...) {
+        // an error part-way leaves every pass on its default choice
+        for (TunePass &t : tp) gemm_set_choice(*t.call.g, t.dflt);
+        for (int i = 0; i < n; ++i) ++plans[i]->tune_epoch;
         release();
         throw;
     }
