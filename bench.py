@@ -205,6 +205,33 @@ def run_gpu(args, rank, world, precision):
                 clocks=cl, e2e_s=e2e_s, v=v[0].cpu().numpy(), vh=vh, K=K, graph_kernels=graph_kernels, tune=tune)
 
 
+def latency_floor_us(device="cuda"):
+    """Replay time of a captured graph holding one trivial kernel: the floor
+    under any captured pipeline on this GPU (CUDA events over 200 replays).
+    None when it cannot be measured; it never stops the benchmark line."""
+    try:
+        import torch
+        x = torch.zeros(1, device=device)
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream(device=device)
+        with torch.cuda.stream(s):
+            x.add_(1.0)                       # warm-up outside the capture
+            torch.cuda.synchronize(device)
+            with torch.cuda.graph(g, stream=s):
+                x.add_(1.0)
+            for _ in range(10):
+                g.replay()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            for _ in range(200):
+                g.replay()
+            e1.record(s)
+        torch.cuda.synchronize(device)
+        return e0.elapsed_time(e1) / 200 * 1e3
+    except Exception:   # noqa: BLE001 - a measurement aid only
+        return None
+
+
 def shard_by_size(sizes, world):
     """Trees to ranks for the batch: largest first, each to the rank with the
     least work so far (ties: the lower rank).  Returns one sorted index list
@@ -442,6 +469,7 @@ def main():
                    "setup_s": round(r["setup_s"], 3), "parallelism": "replicas" if world > 1 else "single",
                    "autotune": {"passes_tuned": r["tune"][0], "passes_changed": r["tune"][1]}},
         "forms": {f: {"value": res[f]["tg"] * world / (res[f]["ms"] * 1e-3), "ms_per_step": res[f]["ms"],
+                      "median_ms_per_step": statistics.median(res[f]["times"]) if res[f].get("times") else None,
                       "rel_err_vs_oracle": errs.get(f), "pass_ms": {k: round(x, 5) for k, x in res[f]["pass_ms"].items()}}
                   for f in forms},
         "rel_err_vs_oracle": errs.get(head),
@@ -451,6 +479,7 @@ def main():
                 "h2d_bytes_per_step": 8 * r["ns"] * args.nrhs,
                 "d2h_bytes_per_step": 8 * (r["nt"] + r["nb"]) * args.nrhs},
         "clocks": r["clocks"],
+        "latency_floor_us": latency_floor_us() if rank == 0 else None,
     }
     if cpu is not None:
         out["cpu_baseline"] = cpu

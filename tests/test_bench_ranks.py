@@ -68,7 +68,7 @@ def test_bench_line_carries_the_contract_keys(monkeypatch, capsys):
                     tg=184832, nt=182272, nb=2560, ns=129619, n_leaves=712,
                     lc={"near": 4900, "m2l": 14104, "s2l": 822, "m2t": 1112, "n_levels": 7},
                     pass_ms={"near": 0.05}, near_flops=6.4e8, near_ms=0.05, clocks={"sm_mhz": 2070.0},
-                    e2e_s=3e-4, v=np.ones(182272), K=16, graph_kernels=24, tune=(7, 0))
+                    e2e_s=3e-4, v=np.ones(182272), K=16, graph_kernels=24, tune=(7, 0), times=[0.2, 0.21, 0.19])
 
     monkeypatch.setattr(bench, "run_gpu", fake_run_gpu)
     monkeypatch.setattr(bench, "oracle_sample", lambda wl, n, **k: (np.arange(10), np.ones(10), 1.0, 16))
@@ -86,3 +86,5 @@ def test_bench_line_carries_the_contract_keys(monkeypatch, capsys):
     assert set(d["e2e"]) >= {"value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step"}
     assert d["e2e"]["h2d_bytes_per_step"] == 8 * 129619 and d["gpu_launches"] == 24 * d["steps"]
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 16
+    assert d["forms"]["mixed"]["median_ms_per_step"] == pytest.approx(0.2)
+    assert "latency_floor_us" in d                                             # None without a GPU
