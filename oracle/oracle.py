@@ -552,6 +552,159 @@ def stencil_points(tree: OracleTree, dom):
     return (np.concatenate(pts) if pts else np.zeros((0, 2))), meta
 
 
+# --------------------------------------------------------------------------- extension along lines
+
+FH_DEGREE = 3        # Floater-Hormann blending degree d (the text leaves it open)
+N_RAY_NODES = 8      # interior data points per ray (Section 6.4)
+
+
+def fh_weights(x: np.ndarray, d: int) -> np.ndarray:
+    """Floater-Hormann barycentric weights of degree d for the nodes x_0..x_n:
+    w_k = (-1)^(k-d) sum over i in J_k of prod_{j=i..i+d, j != k} 1/|x_k - x_j|,
+    J_k = {i : 0 <= i <= n-d, k-d <= i <= k}."""
+    n = len(x) - 1
+    w = np.zeros(n + 1)
+    for k in range(n + 1):
+        tot = 0.0
+        for i in range(max(0, k - d), min(k, n - d) + 1):
+            p = 1.0
+            for j in range(i, i + d + 1):
+                if j != k:
+                    p /= abs(x[k] - x[j])
+            tot += p
+        w[k] = (-1.0) ** (k - d) * tot
+    return w
+
+
+def fh_eval(x: np.ndarray, f: np.ndarray, w: np.ndarray, z: float) -> float:
+    """The barycentric rational interpolant sum w_k f_k/(z-x_k) / sum w_k/(z-x_k)."""
+    dz = z - x
+    hit = np.nonzero(dz == 0.0)[0]
+    if len(hit):
+        return float(f[hit[0]])
+    c = w / dz
+    return float(np.dot(c, f) / np.sum(c))
+
+
+def ray_nodes(dom, p, L: float, n: int = N_RAY_NODES):
+    """The data points for extending to p along the line through the star's
+    centre c and p (Section 6.4): with r_b the boundary radius in the direction
+    of p, the n points at radii r_b - j L / n, j = 1..n, inside Omega.
+    Returns (points (n, 2), their radii, the radius of p)."""
+    cx, cy = dom.center
+    th = math.atan2(p[1] - cy, p[0] - cx)
+    rb = float(dom.r(np.array([th]))[0])
+    radii = rb - L * np.arange(1, n + 1) / n
+    if radii[-1] <= 0.0:
+        raise ValueError("ray nodes reach the centre")
+    u = np.array([math.cos(th), math.sin(th)])
+    return np.array([cx, cy]) + radii[:, None] * u, radii, math.hypot(p[0] - cx, p[1] - cy)
+
+
+def stencil_points_lines(tree: OracleTree, dom):
+    """Points where f is supplied for the extension along lines: the K*K nodes
+    of each regular leaf, then per cut leaf X_S^I, X_Sbar^I and, for every
+    exterior point of its Kbar x Kbar grid (grid order), the N_RAY_NODES ray
+    points.  Returns (points, per-leaf metadata)."""
+    K = tree.K
+    pts, meta = [], {}
+    off = 0
+    for i, b in enumerate(tree.leaves):
+        if tree.cls[i] == REGULAR:
+            p = leaf_nodes(b, tree.t)
+            meta[i] = (off, len(p))
+            pts.append(p)
+            off += len(p)
+    for i, b in enumerate(tree.leaves):
+        if tree.cls[i] == CUT:
+            XS, XSb, _ = cut_leaf_stencil(b, K, tree.t)
+            m = [dom.inside(XS), dom.inside(XSb)]
+            L = box_side(b[0])
+            rays = [ray_nodes(dom, XSb[e], L)[0] for e in np.nonzero(~m[1])[0]]
+            p = np.concatenate([XS[m[0]], XSb[m[1]]] + rays)
+            meta[i] = (off, len(p), m)
+            pts.append(p)
+            off += len(p)
+    return (np.concatenate(pts) if pts else np.zeros((0, 2))), meta
+
+
+def extend_cut_leaf_lines(b, K, t, dom, masks, fI: np.ndarray, targets: np.ndarray):
+    """Extension along lines for cut leaf b (Section 6.4): the exterior points
+    of the Kbar x Kbar grid take the Floater-Hormann interpolant (degree
+    FH_DEGREE) of the data at their ray points, evaluated at their own radius;
+    the interior grid points keep the data; then the truncated Chebyshev
+    expansion of the grid (m + n < Kbar, eq. chebexpbarS) is evaluated at the
+    targets, as in extend_cut_leaf.
+    fI: (N, nrhs) data in the order of stencil_points_lines for this leaf."""
+    q, Kbar, NG = stencil_params(K)
+    _, XSb, _ = cut_leaf_stencil(b, K, t)
+    cx, cy = box_center(b)
+    r = 1.5 * box_side(b[0])
+    L = box_side(b[0])
+    nI_S, nI_Sb = int(masks[0].sum()), int(masks[1].sum())
+    grid = np.zeros((Kbar * Kbar, fI.shape[1]))
+    grid[masks[1]] = fI[nI_S:nI_S + nI_Sb]
+    pos = nI_S + nI_Sb
+    for e in np.nonzero(~masks[1])[0]:
+        _, radii, rx = ray_nodes(dom, XSb[e], L)
+        order = np.argsort(radii)
+        w = fh_weights(radii[order], FH_DEGREE)
+        for rr in range(fI.shape[1]):
+            grid[e, rr] = fh_eval(radii[order], fI[pos:pos + N_RAY_NODES, rr][order], w, rx)
+        pos += N_RAY_NODES
+    tc = chebyshev1_nodes(Kbar)
+    T = npcheb.chebvander(tc, Kbar - 1)
+    Tinv = np.linalg.inv(T)
+    zt = (targets - np.array([cx, cy])) / r
+    TX = npcheb.chebvander(zt[:, 0], Kbar - 1)
+    TY = npcheb.chebvander(zt[:, 1], Kbar - 1)
+    mm, nn = np.meshgrid(np.arange(Kbar), np.arange(Kbar), indexing="ij")
+    keep = (mm + nn) < Kbar
+    out = np.zeros((len(targets), fI.shape[1]))
+    for rr in range(fI.shape[1]):
+        Fb = grid[:, rr].reshape(Kbar, Kbar).T
+        alpha = np.where(keep, Tinv @ Fb @ Tinv.T, 0.0)
+        out[:, rr] = np.einsum("im,mn,in->i", TX, alpha, TY)
+    return out
+
+
+def leaf_values_lines(tree: OracleTree, dom, f_stencil: np.ndarray, meta):
+    """f^e at every leaf node with the extension along lines (Section 6.4) in
+    place of the universal stencil; otherwise as leaf_values."""
+    K = tree.K
+    f_stencil = np.asarray(f_stencil, dtype=np.float64)
+    if f_stencil.ndim == 1:
+        f_stencil = f_stencil[:, None]
+    nrhs = f_stencil.shape[1]
+    out = np.zeros((tree.n_leaves, nrhs, K * K))
+    owned: Dict[int, List[int]] = {}
+    for i, o in enumerate(tree.owner):
+        if o >= 0:
+            owned.setdefault(o, []).append(i)
+    for i, b in enumerate(tree.leaves):
+        if tree.cls[i] == REGULAR:
+            off, n = meta[i]
+            out[i] = f_stencil[off:off + n].T
+    for i, b in enumerate(tree.leaves):
+        if tree.cls[i] != CUT:
+            continue
+        off, n, masks = meta[i]
+        fI = f_stencil[off:off + n]
+        own_nodes = leaf_nodes(b, tree.t)
+        tg = [own_nodes[~masks[0]]] + [leaf_nodes(tree.leaves[j], tree.t) for j in owned.get(i, [])]
+        vals = extend_cut_leaf_lines(b, K, tree.t, dom, masks, fI, np.concatenate(tg))
+        nE = int((~masks[0]).sum())
+        v = np.zeros((K * K, nrhs))
+        v[masks[0]] = fI[:int(masks[0].sum())]
+        v[~masks[0]] = vals[:nE]
+        out[i] = v.T
+        pos = nE
+        for j in owned.get(i, []):
+            out[j] = vals[pos:pos + K * K].T
+            pos += K * K
+    return out
+
+
 # --------------------------------------------------------------------------- extension
 
 def legendre_total_degree_vander(z: np.ndarray, q: int) -> np.ndarray:

@@ -1,0 +1,69 @@
+"""Mutation checks of the oracle's pins: each test plants one plausible mistake
+in the CPU oracle (on the CPU, by replacing one of its functions for the test)
+and requires the pin that guards that part to fail.  A pin that passed with the
+mistake in place would not be a pin."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+import test_oracle_pins as P
+
+
+def test_dropped_two_pi_in_the_potential_is_caught(monkeypatch):
+    real = O.volume_potential
+    monkeypatch.setattr(O, "volume_potential", lambda *a, **k: real(*a, **k) * (2 * np.pi))
+    with pytest.raises(AssertionError):
+        P.test_potential_of_unit_source_on_D()
+    with pytest.raises(AssertionError):
+        P.test_potential_of_gaussian_matches_closed_form()
+
+
+def test_leaf_centre_off_by_half_a_side_is_caught(monkeypatch):
+    real = O.box_center
+    monkeypatch.setattr(O, "box_center", lambda b: tuple(c + 0.5 * O.box_side(b[0]) for c in real(b)))
+    with pytest.raises(AssertionError):
+        P.test_potential_of_unit_source_on_D()
+
+
+def test_transposed_grid_order_in_the_operator_is_caught(monkeypatch):
+    """The rows of the Kbar x Kbar grid taken y-fastest instead of x-fastest.
+    (Reordering the columns, the support points G, would be no mistake: the
+    least-squares extension A_E A_I^+ does not depend on the basis order.)"""
+    real = O.universal_matrix
+
+    def transposed(K):
+        A = real(K).copy()
+        nS, Kb = K * K, O.stencil_params(K)[1]
+        blk = A[nS:nS + Kb * Kb].reshape(Kb, Kb, -1)
+        A[nS:nS + Kb * Kb] = blk.transpose(1, 0, 2).reshape(Kb * Kb, -1)
+        return A
+    monkeypatch.setattr(O, "universal_matrix", transposed)
+    with pytest.raises(AssertionError):
+        P.test_extension_reproduces_total_degree_q_polynomials("disk_l3_k8")
+
+
+def test_swapped_interpolation_axes_are_caught(monkeypatch):
+    def swapped(tree, Vleaf, pts):
+        K, t = tree.K, tree.t
+        out = np.zeros((len(pts), Vleaf.shape[2]))
+        for k, p in enumerate(pts):
+            i = O.locate_leaf(tree, p)
+            cx, cy = O.box_center(tree.leaves[i])
+            h = 0.5 * O.box_side(tree.leaves[i][0])
+            u, v = (p[0] - cx) / h, (p[1] - cy) / h
+            la = np.array([np.prod([(u - t[m]) / (t[a] - t[m]) for m in range(K) if m != a]) for a in range(K)])
+            lb = np.array([np.prod([(v - t[m]) / (t[a] - t[m]) for m in range(K) if m != a]) for a in range(K)])
+            out[k] = np.outer(la, lb).ravel() @ Vleaf[i]      # planted: x and y weights exchanged
+        return out
+    monkeypatch.setattr(O, "interpolate_at", swapped)
+    with pytest.raises(AssertionError):
+        P.test_interpolation_exact_for_tensor_polynomials()
+
+
+def test_dropped_sign_in_the_rational_weights_is_caught(monkeypatch):
+    real = O.fh_weights
+    monkeypatch.setattr(O, "fh_weights", lambda x, d: np.abs(real(x, d)))
+    with pytest.raises(AssertionError):
+        P.test_fh_reproduces_polynomials_of_degree_d()
+    with pytest.raises(AssertionError):
+        P.test_line_extension_exact_for_quadratic_along_rays()

@@ -426,3 +426,78 @@ def test_flat_limit_reading_against_finite_eps_operator():
     d5 = np.abs(O.universal_matrix_finite_eps(8, 1e-5) - A0).max()
     assert d5 <= 1e-10
     assert abs(d3 / d5 / 1e4 - 1.0) < 0.05      # eps^2 convergence
+
+
+# ---------------------------------------------------------------- extension along lines (Section 6.4)
+
+def test_fh_of_full_degree_is_polynomial_interpolation():
+    """Floater-Hormann with d = n is the polynomial interpolant (textbook
+    special case): against numpy's polynomial fit through the same nodes."""
+    rng = np.random.Generator(np.random.PCG64(41))
+    x = np.sort(rng.uniform(0.0, 1.0, 8))
+    f = np.sin(3 * x) + x ** 2
+    w = O.fh_weights(x, 7)
+    c = np.polyfit(x, f, 7)
+    for z in (0.05, 0.5, 0.97, 1.1, 1.25):
+        assert abs(O.fh_eval(x, f, w, z) - np.polyval(c, z)) <= 1e-9 * max(1.0, abs(np.polyval(c, z)))
+
+
+def test_fh_reproduces_polynomials_of_degree_d():
+    """The Floater-Hormann interpolant of degree d reproduces polynomials of
+    degree <= d, inside the nodes and beyond them."""
+    rng = np.random.Generator(np.random.PCG64(42))
+    x = np.sort(rng.uniform(0.2, 0.45, 8))
+    for d in (0, 1, 2, 3):
+        c = rng.standard_normal(d + 1)
+        w = O.fh_weights(x, d)
+        for z in (0.25, 0.33, 0.5, 0.6):
+            assert abs(O.fh_eval(x, np.polyval(c, x), w, z) - np.polyval(c, z)) <= 1e-11 * np.abs(c).sum()
+
+
+def test_fh_weights_on_equispaced_nodes_match_the_binomial_form():
+    """On equispaced nodes the weights are, up to one common factor,
+    (-1)^k sum_{i in J_k} binom(d, k - i)."""
+    from math import comb
+    x = 0.3 + 0.01 * np.arange(8)
+    for d in (1, 2, 3, 4):
+        w = O.fh_weights(x, d)
+        ref = np.array([(-1.0) ** k * sum(comb(d, k - i) for i in range(max(0, k - d), min(k, 7 - d) + 1))
+                        for k in range(8)])
+        ratio = w / ref
+        assert np.allclose(ratio, ratio[0], rtol=1e-12, atol=0)
+
+
+def _star_workload(f):
+    dom = W.StarDomain(0.35, [(3, 0.1, 0.3), (5, 0.05, 1.0)])
+    return W.Workload("star_lines", 9, dom, W.TreeOptions(K=8, min_level=4, max_level=4), [f])
+
+
+def _line_extension_error(f):
+    wl = _star_workload(f)
+    tree = O.build_tree(wl.domain, wl.opts, f)
+    pts, meta = O.stencil_points_lines(tree, wl.domain)
+    vals = O.leaf_values_lines(tree, wl.domain, f(pts), meta)
+    err = 0.0
+    for i, b in enumerate(tree.leaves):
+        if tree.cls[i] == O.CUT or tree.owner[i] >= 0:
+            nodes = O.leaf_nodes(b, tree.t)
+            err = max(err, np.max(np.abs(vals[i, 0] - f(nodes))))
+    return err, len(tree.cut_leaves())
+
+
+def test_line_extension_exact_for_quadratic_along_rays():
+    """f = x^2 + y^2 is quadratic along every line through the centre, so the
+    degree-3 rational extension reproduces it at the exterior grid points, and
+    the truncated Chebyshev expansion of a quadratic is exact: f^e = f at every
+    node of every cut and extension-list leaf (Section 6.4 with the readings
+    FH degree 3, 8 ray points over one leaf side)."""
+    err, ncut = _line_extension_error(lambda xy: xy[:, 0] ** 2 + xy[:, 1] ** 2)
+    assert ncut > 0 and err <= 1e-11
+
+
+def test_line_extension_extrapolates_rather_than_sampling_f():
+    """Along rays f = (x^2 + y^2)^3 is of degree 6 in the radius: the degree-3
+    extension is no longer exact (so the exact case above is not f sampled
+    outside Omega); the error stays below the size of f there (about 8e-3)."""
+    err, _ = _line_extension_error(lambda xy: (xy[:, 0] ** 2 + xy[:, 1] ** 2) ** 3)
+    assert 1e-10 < err < 1e-2
