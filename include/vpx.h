@@ -72,6 +72,11 @@ typedef struct {
     double rbf_eps;      /* shape parameter of the Gaussians on the unit box (Section 3.1): 0 (default)
                             = their flat limit, the polynomial interpolant at G; up to 1e-3 otherwise
                             (the paper uses ~1e-5), K = 6, 8 or 16 */
+    int    ext_mode;     /* 0 (default): universal-stencil extension (Section 3.2); 1: extension along
+                            lines through the origin (Section 6.4: Floater-Hormann, degree 3, eight
+                            points per line over one leaf side); Omega must be star-shaped about the
+                            origin.  Mode 1 has its stencil on the host (VPX_PLAN_HOST_ONLY) and no
+                            device path yet: device plans with it return VPX_ERR_ARG */
 } vpx_options;
 
 /* ---------------------------------------------------------------- callbacks

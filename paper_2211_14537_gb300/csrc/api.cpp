@@ -197,6 +197,8 @@ static void check_options(const vpx_options *o) {
     if (o->max_rhs < 1) fail(VPX_ERR_ARG, "max_rhs >= 1 required");
     if (o->n_quad_bdry < 1 || o->n_quad_bdry > 64) fail(VPX_ERR_ARG, "n_quad_bdry in 1..64");
     check_rbf_eps(o->K, o->rbf_eps);
+    if (o->ext_mode != 0 && o->ext_mode != 1) fail(VPX_ERR_ARG, "ext_mode must be 0 or 1");
+    if (o->ext_mode == 1 && o->rbf_eps != 0.0) fail(VPX_ERR_ARG, "rbf_eps applies to the universal stencil only");
 }
 
 }  // namespace vpx
@@ -248,6 +250,8 @@ int vpx_plan_create(const vpx_options *opt, int n_panels, vpx_curve_cb curve, vp
         p->uid = next_uid++;
         p->opt = *opt;
         p->host_only = (flags & VPX_PLAN_HOST_ONLY) != 0;
+        if (opt->ext_mode == 1 && !p->host_only)
+            fail(VPX_ERR_ARG, "the extension along lines has no device path yet (host-only plans)");
         p->K = opt->K;
         p->KK = opt->K * opt->K;
         p->P = opt->p + 1;

@@ -217,6 +217,76 @@ void pseudo_inverse(int m, int n, const double *AI, double *P, double *cond, dou
 
 }  // namespace
 
+// Stencil of the extension along lines (Section 6.4): per cut leaf its interior
+// leaf nodes X_S^I and grid points X_Sbar^I, then for each exterior grid point
+// (grid order) the kRayNodes points at radii r_b - j L / kRayNodes, j = 1..,
+// on the line from the origin through it, where r_b is the boundary radius in
+// that direction and L the leaf side.  r_b is found by bisection on the inside
+// test between the origin (inside: Omega is star-shaped about it) and the grid
+// point (outside), all lines at once, one callback per step.
+constexpr int kRayNodes = 8;
+
+void ray_stencil(const vpx_options &opt, const Callbacks &cb, const HostTree &tree, StencilInfo &st,
+                 const std::vector<double> &cxy, const std::vector<uint8_t> &ins, int NX, int KK, int KbKb,
+                 std::vector<double> &stencil_xy) {
+    const int ncut = (int)st.cut_leaf.size();
+    std::vector<double> ux, uy, rp, lside;
+    std::vector<int> owner_c;
+    for (int c = 0; c < ncut; ++c) {
+        const double L = std::ldexp(1.0, -tree.leaves[st.cut_leaf[c]].level);
+        for (int e = 0; e < KbKb; ++e) {
+            const size_t j = (size_t)c * NX + KK + e;
+            if (ins[j]) continue;
+            const double x = cxy[2 * j], y = cxy[2 * j + 1], r = std::hypot(x, y);
+            if (!(r > 0.0)) fail(VPX_ERR_STENCIL, "a grid point at the origin");
+            ux.push_back(x / r);
+            uy.push_back(y / r);
+            rp.push_back(r);
+            lside.push_back(L);
+            owner_c.push_back(c);
+        }
+    }
+    const size_t nr = rp.size();
+    std::vector<double> lo(nr, 0.0), hi = rp, pts(2 * nr);
+    std::vector<uint8_t> in(nr);
+    for (int it = 0; it < 64 && nr; ++it) {
+        for (size_t k = 0; k < nr; ++k) {
+            const double m = 0.5 * (lo[k] + hi[k]);
+            pts[2 * k] = m * ux[k];
+            pts[2 * k + 1] = m * uy[k];
+        }
+        if (cb.inside(pts.data(), (int64_t)nr, in.data(), cb.ctx) != 0) fail(VPX_ERR_CALLBACK, "inside callback failed");
+        for (size_t k = 0; k < nr; ++k) {
+            const double m = 0.5 * (lo[k] + hi[k]);
+            (in[k] ? lo[k] : hi[k]) = m;
+        }
+    }
+    st.stencil_off.assign(ncut, 0);
+    st.n_interior.assign(ncut, 0);
+    size_t k = 0;
+    for (int c = 0; c < ncut; ++c) {
+        st.stencil_off[c] = (int64_t)(stencil_xy.size() / 2);
+        int cnt = 0;
+        for (int j = 0; j < KK + KbKb; ++j) {
+            if (!ins[(size_t)c * NX + j]) continue;
+            stencil_xy.push_back(cxy[2 * ((size_t)c * NX + j)]);
+            stencil_xy.push_back(cxy[2 * ((size_t)c * NX + j) + 1]);
+            ++cnt;
+        }
+        for (; k < nr && owner_c[k] == c; ++k) {
+            for (int q = 1; q <= kRayNodes; ++q) {
+                const double rad = lo[k] - lside[k] * q / kRayNodes;
+                if (!(rad > 0.0)) fail(VPX_ERR_STENCIL, "ray points reach the origin");
+                stencil_xy.push_back(rad * ux[k]);
+                stencil_xy.push_back(rad * uy[k]);
+            }
+            cnt += kRayNodes;
+        }
+        st.n_interior[c] = cnt;
+    }
+    (void)opt;
+}
+
 void check_rbf_eps(int K, double rbf_eps) {
     if (!(rbf_eps >= 0.0) || rbf_eps > 1e-3) fail(VPX_ERR_ARG, "rbf_eps must lie in [0, 1e-3]");
     const double *a2 = nullptr;
@@ -352,6 +422,10 @@ void build_stencil(const vpx_options &opt, const Callbacks &cb, const HostTree &
     std::vector<uint8_t> ins((size_t)ncut * NX, 0);
     if (ncut && cb.inside(cxy.data(), (int64_t)ins.size(), ins.data(), cb.ctx) != 0)
         fail(VPX_ERR_CALLBACK, "inside callback failed");
+    if (opt.ext_mode == 1) {   // extension along lines (Section 6.4): no support set G in the stencil
+        ray_stencil(opt, cb, tree, st, cxy, ins, NX, KK, KbKb, stencil_xy);
+        return;
+    }
     st.stencil_off.assign(ncut, 0);
     st.n_interior.assign(ncut, 0);
     st.grid_src.assign((size_t)ncut * KbKb, -1);

@@ -45,7 +45,7 @@ class vpx_options(ctypes.Structure):
     _fields_ = [("K", ctypes.c_int), ("min_level", ctypes.c_int), ("max_level", ctypes.c_int),
                 ("refine_tol", ctypes.c_double), ("f_scale", ctypes.c_double), ("p", ctypes.c_int),
                 ("precision", ctypes.c_int), ("max_rhs", ctypes.c_int), ("n_quad_bdry", ctypes.c_int),
-                ("rbf_eps", ctypes.c_double)]
+                ("rbf_eps", ctypes.c_double), ("ext_mode", ctypes.c_int)]
 
 
 POINTS_CB = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_int64,

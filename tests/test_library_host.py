@@ -238,3 +238,32 @@ def test_rbf_eps_option_is_checked(V):
     o = V.vpx_default_options(K=10, min_level=3, max_level=3, rbf_eps=1e-5)
     with pytest.raises(V.VpxError):
         V.vpx_plan_create(o, wl.domain, wl.sources[0], host_only=True)
+
+
+def test_ray_stencil_matches_oracle(V):
+    """Extension along lines (Section 6.4), host part: the points where f is
+    needed -- interior leaf nodes and grid points of each cut leaf, then eight
+    points per exterior grid point on its line through the origin -- equal the
+    oracle's (the library finds the boundary radius by bisection on the inside
+    test, the oracle takes it from the analytic r(theta))."""
+    from oracle import oracle as O
+    f = lambda xy: xy[:, 0] ** 2 + xy[:, 1] ** 2
+    dom = W.StarDomain(0.35, [(3, 0.1, 0.3), (5, 0.05, 1.0)])
+    wl = W.Workload("star_lines", 9, dom, W.TreeOptions(K=8, min_level=4, max_level=4), [f])
+    o = V.vpx_default_options(K=8, min_level=4, max_level=4, ext_mode=1)
+    plan = V.vpx_plan_create(o, wl.domain, f, host_only=True)
+    lib = plan.stencil_points()
+    tree = O.build_tree(dom, wl.opts, f)
+    orc, _ = O.stencil_points_lines(tree, dom)
+    assert lib.shape == orc.shape and np.abs(lib - orc).max() <= 1e-14
+
+
+def test_line_extension_mode_is_host_only_for_now(V):
+    wl = W.disk_sincos(level=3)
+    o = V.vpx_default_options(K=8, min_level=3, max_level=3, ext_mode=1)
+    with pytest.raises(V.VpxError) as e:
+        V.vpx_plan_create(o, wl.domain, wl.sources[0])
+    assert e.value.code == V.VPX_ERR_ARG
+    o = V.vpx_default_options(K=8, min_level=3, max_level=3, ext_mode=1, rbf_eps=1e-5)
+    with pytest.raises(V.VpxError):
+        V.vpx_plan_create(o, wl.domain, wl.sources[0], host_only=True)
