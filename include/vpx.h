@@ -75,8 +75,7 @@ typedef struct {
     int    ext_mode;     /* 0 (default): universal-stencil extension (Section 3.2); 1: extension along
                             lines through the origin (Section 6.4: Floater-Hormann, degree 3, eight
                             points per line over one leaf side); Omega must be star-shaped about the
-                            origin.  Mode 1 has its stencil on the host (VPX_PLAN_HOST_ONLY) and no
-                            device path yet: device plans with it return VPX_ERR_ARG */
+                            origin */
 } vpx_options;
 
 /* ---------------------------------------------------------------- callbacks
@@ -154,6 +153,16 @@ int vpx_plan_lists(vpx_plan_t plan, int32_t *near, int32_t *vlist, int32_t *xlis
  * multiprecision (unit box of side 1 = half the reference square).  Host only;
  * no plan needed.  Errors: VPX_ERR_ARG (bad K or rbf_eps, null nx / ng). */
 int vpx_universal_matrix(int K, double rbf_eps, double *out, int64_t *nx, int64_t *ng);
+
+/* The operator of the extension along lines (ext_mode 1, Section 6.4), for
+ * inspection and tests: one entry per exterior grid point of every cut leaf,
+ * *n_ray in all.  ray_c: the cut leaf's index among the cut leaves; ray_g: the
+ * grid index by*Kbar + ax; ray_src: position of the first of its eight line
+ * points in the f column; coef (8 per entry): the grid value is
+ * sum_q coef[q] f[ray_src + q].  Pass NULL arrays to get *n_ray first.
+ * Errors: VPX_ERR_ARG (null plan or n_ray), VPX_ERR_STATE (ext_mode 0). */
+int vpx_plan_ray_operator(vpx_plan_t plan, int64_t *n_ray, int32_t *ray_c, int32_t *ray_g, int64_t *ray_src,
+                          double *coef);
 
 /* Host copy of the near-field tables (33 x K*K x K*K doubles): entry
  * [c][i][j] = int over the source box [-1,1]^2 of log|x_i - y| l_j(y) dy, x_i the

@@ -221,6 +221,20 @@ int vpx_universal_matrix(int K, double rbf_eps, double *out, int64_t *nx, int64_
     });
 }
 
+int vpx_plan_ray_operator(vpx_plan_t p, int64_t *n_ray, int32_t *ray_c, int32_t *ray_g, int64_t *ray_src,
+                          double *coef) {
+    return guarded([&] {
+        if (!p || !n_ray) fail(VPX_ERR_ARG, "null argument");
+        const StencilInfo &st = p->st;
+        if (st.mode != 1) fail(VPX_ERR_STATE, "the plan extends with the universal stencil");
+        *n_ray = (int64_t)st.ray_c.size();
+        if (ray_c) std::copy(st.ray_c.begin(), st.ray_c.end(), ray_c);
+        if (ray_g) std::copy(st.ray_g.begin(), st.ray_g.end(), ray_g);
+        if (ray_src) std::copy(st.ray_src.begin(), st.ray_src.end(), ray_src);
+        if (coef) std::copy(st.ray_coef.begin(), st.ray_coef.end(), coef);
+    });
+}
+
 int vpx_default_options(vpx_options *opt) {
     if (!opt) return VPX_ERR_ARG;
     std::memset(opt, 0, sizeof(*opt));
@@ -250,8 +264,6 @@ int vpx_plan_create(const vpx_options *opt, int n_panels, vpx_curve_cb curve, vp
         p->uid = next_uid++;
         p->opt = *opt;
         p->host_only = (flags & VPX_PLAN_HOST_ONLY) != 0;
-        if (opt->ext_mode == 1 && !p->host_only)
-            fail(VPX_ERR_ARG, "the extension along lines has no device path yet (host-only plans)");
         p->K = opt->K;
         p->KK = opt->K * opt->K;
         p->P = opt->p + 1;

@@ -38,6 +38,23 @@ __global__ void k_leafvals(int n_leaves, int KK, const int32_t *leaf_cls, const 
     else if (cls == kExterior && owner_flag[leaf] == 0) *o = 0.0;
 }
 
+// Extension along lines (Section 6.4): the value at each exterior grid point
+// is the Floater-Hormann interpolant of the data at its eight line points,
+// sum_q coef[q] f[src + q] with the coefficients from the host.  One thread
+// per (exterior grid point, rhs).
+__global__ void k_ext_rays(int n_ray, int Kb2, const int32_t *ray_c, const int32_t *ray_g, const int64_t *ray_src,
+                           const double *ray_coef, const double *f, int64_t ldf, double *F, int64_t ldF) {
+    pdl_entry();
+    const int k = blockIdx.x * blockDim.x + threadIdx.x, rhs = blockIdx.y;
+    if (k >= n_ray) return;
+    const double *fr = f + rhs * ldf + ray_src[k];
+    const double *cf = ray_coef + (size_t)k * 8;
+    double s = 0.0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) s += cf[q] * fr[q];
+    F[rhs * ldF + (int64_t)ray_c[k] * Kb2 + ray_g[k]] = s;
+}
+
 // One block per (cut leaf, rhs).  c = A_I^+ f_I; the Kbar x Kbar Chebyshev grid
 // on Sbar takes the data at interior nodes and A_{Xbar^E,G} c at exterior
 // nodes; its Chebyshev coefficients truncated to m + n < Kbar (eq.
@@ -60,10 +77,10 @@ __global__ void k_extend(ExtArgs a) {
     const double *f = a.f + rhs * a.ldf + a.stencil_off[c];
     for (int i = threadIdx.x; i < nI; i += blockDim.x) fI[i] = f[i];
     __syncthreads();
-    // c = P_S f_I : one warp per row
+    // c = P_S f_I : one warp per row (universal stencil only)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
-    const double *P = a.pinv + a.pinv_off[c];
-    for (int k = warp; k < NG; k += nwarp) {
+    const double *P = a.ray_F ? nullptr : a.pinv + a.pinv_off[c];
+    for (int k = warp; !a.ray_F && k < NG; k += nwarp) {
         double s = 0.0;
         for (int i = lane; i < nI; i += 32) s += P[(size_t)k * nI + i] * fI[i];
         for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
@@ -75,6 +92,8 @@ __global__ void k_extend(ExtArgs a) {
         int src = gs[g];
         if (src >= 0) {
             F[g] = fI[src];
+        } else if (a.ray_F) {
+            F[g] = a.ray_F[rhs * a.ldR + (int64_t)c * Kb2 + g];
         } else {
             double s = 0.0;
             const double *Ar = a.A_grid + (size_t)g * NG;
@@ -262,7 +281,25 @@ static void run_extension(vpx_plan *p, const double *f, int nrhs, int64_t ldf, d
         a.pinv_df = reinterpret_cast<const float2 *>(p->ext.pinv_df);
         a.cheb_df = reinterpret_cast<const float2 *>(p->ext.cheb_df);
         const size_t smem = extension_smem(p);
-        if (p->opt.precision == VPX_PREC_MIXED) {
+        DevExt &xe = p->ext;
+        const int Kb2e = p->st.Kbar * p->st.Kbar;
+        const int64_t ldFe = (int64_t)xe.ncut * Kb2e;
+        if (xe.mode == 1 && xe.n_ray > 0) {   // exterior grid values along lines
+            launch_pdl(k_ext_rays, dim3((unsigned)((xe.n_ray + 255) / 256), nrhs), dim3(256), 0, s, xe.n_ray, Kb2e,
+                       (const int32_t *)xe.ray_c, (const int32_t *)xe.ray_g, (const int64_t *)xe.ray_src,
+                       (const double *)xe.ray_coef, f, ldf, xe.Fall, ldFe);
+            VPX_LAUNCH("k_ext_rays");
+        }
+        if (xe.mode == 1 && p->opt.precision == VPX_PREC_MIXED) {
+            launch_ext_eval_df(a, xe.ncut, xe.n_tgt, xe.tgt_cut, xe.tgt_leaf,
+                               reinterpret_cast<const ExtTgtGeo *>(xe.tgt_geo), xe.Fall, ldFe,
+                               reinterpret_cast<float2 *>(xe.alpha), nrhs, p->wk.status, s);
+        } else if (xe.mode == 1) {
+            a.ray_F = xe.Fall;
+            a.ldR = ldFe;
+            launch_pdl(k_extend, dim3(p->ext.ncut, nrhs), dim3(256), smem, s, a);
+            VPX_LAUNCH("k_extend");
+        } else if (p->opt.precision == VPX_PREC_MIXED) {
             DevExt &x = p->ext;
             const int Kb2 = p->st.Kbar * p->st.Kbar;
             const int64_t ldc = (int64_t)x.ncut * p->st.NG, ldF = (int64_t)x.ncut * Kb2;

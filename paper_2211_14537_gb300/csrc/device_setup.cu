@@ -436,10 +436,19 @@ void device_setup(vpx_plan *p) {
     x.owned_off = dev_upload(st.owned_off);
     x.owned = dev_upload(st.owned);
     x.pinv = dev_upload(st.pinv);
-    std::vector<double> Ag((size_t)st.Kbar * st.Kbar * st.NG);
-    for (int g = 0; g < st.Kbar * st.Kbar; ++g)
+    const bool lines = st.mode == 1;   // extension along lines: no universal operator, line coefficients instead
+    std::vector<double> Ag(lines ? 0 : (size_t)st.Kbar * st.Kbar * st.NG);
+    for (int g = 0; !lines && g < st.Kbar * st.Kbar; ++g)
         std::copy(&st.A[(size_t)(p->KK + g) * st.NG], &st.A[(size_t)(p->KK + g) * st.NG] + st.NG, &Ag[(size_t)g * st.NG]);
     x.A_grid = dev_upload(Ag);
+    x.mode = st.mode;
+    x.n_ray = (int)st.ray_c.size();
+    x.ray_c = dev_upload(st.ray_c);
+    x.ray_g = dev_upload(st.ray_g);
+    x.ray_src = dev_upload(st.ray_src);
+    x.ray_coef = dev_upload(st.ray_coef);
+    if (lines && p->opt.precision != VPX_PREC_MIXED)
+        x.Fall = dev_alloc<double>((size_t)p->opt.max_rhs * x.ncut * st.Kbar * st.Kbar);
     x.cheb_inv = dev_upload(st.cheb_inv);
     if (p->opt.precision == VPX_PREC_MIXED) {
         // double-float copies for the mixed form's extension
@@ -450,14 +459,14 @@ void device_setup(vpx_plan *p) {
         // A_I^+ rows padded to an even length so that every row block is 16-byte aligned
         std::vector<int64_t> poff(st.cut_leaf.size(), 0);
         size_t tot = 0;
-        for (size_t c = 0; c < st.cut_leaf.size(); ++c) {
+        for (size_t c = 0; !lines && c < st.cut_leaf.size(); ++c) {
             poff[c] = (int64_t)tot;
             tot += (size_t)st.NG * ((st.n_interior[c] + 1) & ~1);
         }
         // the Chebyshev transform padded to an even length (16-byte multiple) likewise
         std::vector<DevExt::DfPair> pd(tot, DevExt::DfPair{0.f, 0.f}), cd((st.cheb_inv.size() + 1) & ~(size_t)1,
                                                                            DevExt::DfPair{0.f, 0.f});
-        for (size_t c = 0; c < st.cut_leaf.size(); ++c) {
+        for (size_t c = 0; !lines && c < st.cut_leaf.size(); ++c) {
             const int nI = st.n_interior[c], nIp = (nI + 1) & ~1;
             for (int k = 0; k < st.NG; ++k)
                 for (int i = 0; i < nI; ++i)
@@ -469,7 +478,7 @@ void device_setup(vpx_plan *p) {
         x.cheb_df = dev_upload(cd);
         // A_{X_Sbar,G} c of every cut leaf as one table pass; targets of the Chebyshev stage
         const int Kb2 = st.Kbar * st.Kbar;
-        if (x.ncut > 0) {
+        if (x.ncut > 0 && !lines) {
             std::vector<std::pair<int, GPair>> tg;
             for (int c = 0; c < x.ncut; ++c) tg.push_back({0, GPair{c, 0, (int64_t)c * Kb2, 1.0}});
             gemm_pass_upload_tables(x.grid_pass, Ag, 1, Kb2, st.NG, true);
@@ -505,7 +514,7 @@ void device_setup(vpx_plan *p) {
         }
         x.tgt_geo = dev_upload(geo);
         for (int c = 0; c < x.ncut; ++c) x.max_interior = std::max(x.max_interior, st.n_interior[c]);
-        x.cbuf = dev_alloc<double>((size_t)p->opt.max_rhs * x.ncut * st.NG);
+        x.cbuf = dev_alloc<double>(lines ? 1 : (size_t)p->opt.max_rhs * x.ncut * st.NG);
         x.Fall = dev_alloc<double>((size_t)p->opt.max_rhs * x.ncut * Kb2);
         x.alpha = dev_alloc<DevExt::DfPair>((size_t)p->opt.max_rhs * x.ncut * ((Kb2 + 1) & ~1));
     }
@@ -545,6 +554,7 @@ void device_free(vpx_plan *p) {
     dev_free(x.pinv_df); dev_free(x.cheb_df); dev_free(x.pinv_df_off); dev_free(x.tgt_geo);
     gemm_pass_free(x.grid_pass);
     dev_free(x.tgt_cut); dev_free(x.tgt_leaf); dev_free(x.cbuf); dev_free(x.Fall); dev_free(x.alpha);
+    dev_free(x.ray_c); dev_free(x.ray_g); dev_free(x.ray_src); dev_free(x.ray_coef);
     dev_free(x.leaf_level); dev_free(x.leaf_ix); dev_free(x.leaf_iy); dev_free(x.owned_flag_dev);
     free_passes(p);
     DevWork &w = p->wk;

@@ -28,6 +28,9 @@ struct ExtArgs {
     int64_t ldf;
     double *fe;
     int64_t ldfe;
+    // extension along lines: the exterior grid values, [rhs][cut][Kbar^2] (null: universal stencil)
+    const double *ray_F = nullptr;
+    int64_t ldR = 0;
 };
 
 // mixed form (extend_df.cu): c = A_I^+ f_I into cbuf[rhs][cut][NG]; then, after

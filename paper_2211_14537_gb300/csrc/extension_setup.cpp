@@ -226,12 +226,40 @@ void pseudo_inverse(int m, int n, const double *AI, double *P, double *cond, dou
 // point (outside), all lines at once, one callback per step.
 constexpr int kRayNodes = 8;
 
+// Floater-Hormann weights of degree d on the nodes x[0..n] (any order):
+// w_k = (-1)^(k-d) sum_{i in J_k} prod_{j=i..i+d, j != k} 1/|x_k - x_j| with the
+// nodes sorted ascending; the coefficients of the interpolant at z follow as
+// (w_k / (z - x_k)) / sum_i w_i / (z - x_i), returned in the order of x.
+static void fh_coefficients(const double *x, int n1, int d, double z, double *coef) {
+    std::vector<int> ord(n1);
+    for (int k = 0; k < n1; ++k) ord[k] = k;
+    std::sort(ord.begin(), ord.end(), [&](int a, int b) { return x[a] < x[b]; });
+    const int n = n1 - 1;
+    std::vector<double> xs(n1), w(n1);
+    for (int k = 0; k < n1; ++k) xs[k] = x[ord[k]];
+    for (int k = 0; k <= n; ++k) {
+        double tot = 0.0;
+        for (int i = std::max(0, k - d); i <= std::min(k, n - d); ++i) {
+            double p = 1.0;
+            for (int j = i; j <= i + d; ++j)
+                if (j != k) p /= std::fabs(xs[k] - xs[j]);
+            tot += p;
+        }
+        w[k] = ((k - d) % 2 == 0 ? 1.0 : -1.0) * tot;
+    }
+    double den = 0.0;
+    for (int k = 0; k <= n; ++k) den += w[k] / (z - xs[k]);
+    for (int k = 0; k <= n; ++k) coef[ord[k]] = w[k] / (z - xs[k]) / den;
+}
+
+constexpr int kRayDegree = 3;   // Floater-Hormann blending degree (the text leaves it open)
+
 void ray_stencil(const vpx_options &opt, const Callbacks &cb, const HostTree &tree, StencilInfo &st,
                  const std::vector<double> &cxy, const std::vector<uint8_t> &ins, int NX, int KK, int KbKb,
                  std::vector<double> &stencil_xy) {
     const int ncut = (int)st.cut_leaf.size();
     std::vector<double> ux, uy, rp, lside;
-    std::vector<int> owner_c;
+    std::vector<int> owner_c, grid_e;
     for (int c = 0; c < ncut; ++c) {
         const double L = std::ldexp(1.0, -tree.leaves[st.cut_leaf[c]].level);
         for (int e = 0; e < KbKb; ++e) {
@@ -244,6 +272,7 @@ void ray_stencil(const vpx_options &opt, const Callbacks &cb, const HostTree &tr
             rp.push_back(r);
             lside.push_back(L);
             owner_c.push_back(c);
+            grid_e.push_back(e);
         }
     }
     const size_t nr = rp.size();
@@ -261,25 +290,40 @@ void ray_stencil(const vpx_options &opt, const Callbacks &cb, const HostTree &tr
             (in[k] ? lo[k] : hi[k]) = m;
         }
     }
+    st.mode = 1;
     st.stencil_off.assign(ncut, 0);
     st.n_interior.assign(ncut, 0);
+    st.grid_src.assign((size_t)ncut * KbKb, -1);
+    st.node_src.assign((size_t)ncut * KK, -1);
+    st.ray_c.clear();
+    st.ray_g.clear();
+    st.ray_src.clear();
+    st.ray_coef.clear();
     size_t k = 0;
+    double rad[kRayNodes], coef[kRayNodes];
     for (int c = 0; c < ncut; ++c) {
         st.stencil_off[c] = (int64_t)(stencil_xy.size() / 2);
         int cnt = 0;
         for (int j = 0; j < KK + KbKb; ++j) {
             if (!ins[(size_t)c * NX + j]) continue;
+            if (j < KK) st.node_src[(size_t)c * KK + j] = cnt;
+            else st.grid_src[(size_t)c * KbKb + (j - KK)] = cnt;
             stencil_xy.push_back(cxy[2 * ((size_t)c * NX + j)]);
             stencil_xy.push_back(cxy[2 * ((size_t)c * NX + j) + 1]);
             ++cnt;
         }
         for (; k < nr && owner_c[k] == c; ++k) {
+            st.ray_c.push_back(c);
+            st.ray_g.push_back(grid_e[k]);
+            st.ray_src.push_back(st.stencil_off[c] + cnt);
             for (int q = 1; q <= kRayNodes; ++q) {
-                const double rad = lo[k] - lside[k] * q / kRayNodes;
-                if (!(rad > 0.0)) fail(VPX_ERR_STENCIL, "ray points reach the origin");
-                stencil_xy.push_back(rad * ux[k]);
-                stencil_xy.push_back(rad * uy[k]);
+                rad[q - 1] = lo[k] - lside[k] * q / kRayNodes;
+                if (!(rad[q - 1] > 0.0)) fail(VPX_ERR_STENCIL, "ray points reach the origin");
+                stencil_xy.push_back(rad[q - 1] * ux[k]);
+                stencil_xy.push_back(rad[q - 1] * uy[k]);
             }
+            fh_coefficients(rad, kRayNodes, kRayDegree, rp[k], coef);
+            for (int q = 0; q < kRayNodes; ++q) st.ray_coef.push_back(coef[q]);
             cnt += kRayNodes;
         }
         st.n_interior[c] = cnt;
@@ -422,15 +466,15 @@ void build_stencil(const vpx_options &opt, const Callbacks &cb, const HostTree &
     std::vector<uint8_t> ins((size_t)ncut * NX, 0);
     if (ncut && cb.inside(cxy.data(), (int64_t)ins.size(), ins.data(), cb.ctx) != 0)
         fail(VPX_ERR_CALLBACK, "inside callback failed");
+    std::vector<std::vector<int>> interior(ncut);
     if (opt.ext_mode == 1) {   // extension along lines (Section 6.4): no support set G in the stencil
         ray_stencil(opt, cb, tree, st, cxy, ins, NX, KK, KbKb, stencil_xy);
-        return;
-    }
+    } else {
+    st.mode = 0;
     st.stencil_off.assign(ncut, 0);
     st.n_interior.assign(ncut, 0);
     st.grid_src.assign((size_t)ncut * KbKb, -1);
     st.node_src.assign((size_t)ncut * KK, -1);
-    std::vector<std::vector<int>> interior(ncut);
     for (int c = 0; c < ncut; ++c) {
         st.stencil_off[c] = (int64_t)(stencil_xy.size() / 2);
         int cnt = 0;
@@ -444,6 +488,7 @@ void build_stencil(const vpx_options &opt, const Callbacks &cb, const HostTree &
             ++cnt;
         }
         st.n_interior[c] = cnt;
+    }
     }
     // owned exterior leaves per cut leaf
     std::vector<int> cut_index(nl, -1);
@@ -466,7 +511,7 @@ void build_stencil(const vpx_options &opt, const Callbacks &cb, const HostTree &
             for (int m = 0; m < Kb; ++m) st.cheb_inv[m * Kb + a] = (m == 0 ? 1.0 : 2.0) / Kb * tv[m];
         }
     }
-    if (!compute_operators) return;
+    if (!compute_operators || st.mode == 1) return;   // mode 1: the line coefficients are the operator
 
     // the universal A (flat limit, plus the Gaussian eps^2 term when rbf_eps > 0)
     {

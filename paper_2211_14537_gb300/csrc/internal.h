@@ -83,6 +83,11 @@ struct StencilInfo {
     std::vector<int32_t> owned_off, owned;     // CSR: owned exterior leaves per cut leaf
     std::vector<int64_t> reg_leaf_off;         // [n_leaves] stencil offset of a regular leaf, -1 otherwise
     double max_pinv_norm = 0.0, max_cond = 0.0;
+    // extension along lines (mode 1): per exterior grid point of every cut leaf
+    int mode = 0;
+    std::vector<int32_t> ray_c, ray_g;         // cut leaf, grid index (by*Kbar + ax)
+    std::vector<int64_t> ray_src;              // position of its first line point in the f column
+    std::vector<double> ray_coef;              // [n][8]: Floater-Hormann coefficients of its line points
 };
 
 // The universal operator of leaf order K on [-1,1]^2 (rows X_S, X_Sbar, G),

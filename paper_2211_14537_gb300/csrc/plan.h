@@ -56,6 +56,11 @@ struct DevExt {
     DfPair *alpha = nullptr;                           // [max_rhs][ncut][Kbar^2 rounded up to even] truncated Chebyshev coefficients
     int32_t *leaf_level = nullptr, *leaf_ix = nullptr, *leaf_iy = nullptr;
     int32_t *owned_flag_dev = nullptr;   // [n_leaves] 1 if the leaf is in an extension list
+    // extension along lines: exterior grid points and their line-point coefficients
+    int mode = 0, n_ray = 0;
+    int32_t *ray_c = nullptr, *ray_g = nullptr;
+    int64_t *ray_src = nullptr;
+    double *ray_coef = nullptr;
 };
 
 struct DevWork {

@@ -58,7 +58,7 @@ CURVE_CB = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_
 EXPORTED = [
     "vpx_default_options", "vpx_plan_create", "vpx_plan_sizes", "vpx_plan_leaves", "vpx_stencil_points",
     "vpx_leaf_nodes", "vpx_boundary_nodes", "vpx_plan_list_counts", "vpx_plan_lists", "vpx_plan_near_tables",
-    "vpx_universal_matrix", "vpx_execute",
+    "vpx_universal_matrix", "vpx_plan_ray_operator", "vpx_execute",
     "vpx_execute_batch", "vpx_autotune", "vpx_autotune_batch",
     "vpx_extend", "vpx_potential", "vpx_potential_static", "vpx_execute_host", "vpx_sync_status", "vpx_set_timing",
     "vpx_get_timings", "vpx_pass_name", "vpx_graph_kernel_count", "vpx_check_bounded_wait", "vpx_error_string", "vpx_last_error_message", "vpx_plan_destroy",
@@ -95,6 +95,7 @@ def load_library(path: str = LIB_PATH):
     L.vpx_potential.argtypes = [vp, vp, ctypes.c_int, i64, vp, i64, vp, i64, vp]
     L.vpx_autotune.argtypes = [vp, vp, ctypes.c_int, i64, vp, P(ctypes.c_int), P(ctypes.c_int)]
     L.vpx_universal_matrix.argtypes = [ctypes.c_int, ctypes.c_double, P(ctypes.c_double), P(i64), P(i64)]
+    L.vpx_plan_ray_operator.argtypes = [vp, P(i64), P(ctypes.c_int32), P(ctypes.c_int32), P(i64), P(ctypes.c_double)]
     L.vpx_autotune_batch.argtypes = [ctypes.c_int, P(vp), P(vp), P(ctypes.c_int), P(i64), vp, P(ctypes.c_int),
                                      P(ctypes.c_int)]
     L.vpx_potential_static.argtypes = [vp, vp, ctypes.c_int, i64, vp, i64, vp, i64, vp]
@@ -191,6 +192,22 @@ class Plan:
         _check(load_library().vpx_plan_lists(self.handle, *[_iptr(x) for x in a]))
         return dict(near=a[0].reshape(nl, N_NEAR), vlist=a[1].reshape(nb, N_V), xlist=a[2].reshape(nb, N_X),
                     wlist=a[3].reshape(nl, N_W), box_level=a[4], box_ix=a[5], box_iy=a[6], box_leaf=a[7])
+
+
+def vpx_plan_ray_operator(plan: "Plan"):
+    """(ray_c, ray_g, ray_src, coef[n, 8]) of a plan extending along lines."""
+    L = load_library()
+    n = ctypes.c_int64()
+    _check(L.vpx_plan_ray_operator(plan.handle, ctypes.byref(n), None, None, None, None))
+    c = np.zeros(n.value, dtype=np.int32)
+    g = np.zeros(n.value, dtype=np.int32)
+    src = np.zeros(n.value, dtype=np.int64)
+    coef = np.zeros((n.value, 8))
+    P = ctypes.POINTER
+    _check(L.vpx_plan_ray_operator(plan.handle, ctypes.byref(n), c.ctypes.data_as(P(ctypes.c_int32)),
+                                   g.ctypes.data_as(P(ctypes.c_int32)), src.ctypes.data_as(P(ctypes.c_int64)),
+                                   coef.ctypes.data_as(P(ctypes.c_double))))
+    return c, g, src, coef
 
 
 def vpx_universal_matrix(K: int, rbf_eps: float = 0.0) -> np.ndarray:

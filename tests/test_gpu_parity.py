@@ -226,6 +226,41 @@ def test_extension_parity_finite_eps(V, precision):
     assert eff > 0.0
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_extension_along_lines_parity(V, precision):
+    """Extension along lines (ext_mode 1, Section 6.4) on a star domain: the
+    library's f^e (line coefficients from the host, gather kernel, then the
+    Chebyshev stage) against the oracle's at every node of every cut and
+    extension-list leaf; and exactness for x^2 + y^2, quadratic along every
+    line through the centre."""
+    dom = W.StarDomain(0.35, [(3, 0.1, 0.3), (5, 0.05, 1.0)])
+    tol = 1e-10 if precision == 0 else 1e-9
+    for name, f in (("smooth", lambda xy: np.sin(3 * xy[:, 0]) * np.cos(2 * xy[:, 1]) + xy[:, 0] ** 3),
+                    ("quadratic", lambda xy: xy[:, 0] ** 2 + xy[:, 1] ** 2)):
+        wl = W.Workload("star_lines", 9, dom, W.TreeOptions(K=8, min_level=4, max_level=4), [f])
+        o = V.vpx_default_options(K=8, min_level=4, max_level=4, p=50, precision=precision, ext_mode=1)
+        plan = V.vpx_plan_create(o, wl.domain, f)
+        tree = O.build_tree(dom, wl.opts, f)
+        pts, meta = O.stencil_points_lines(tree, dom)
+        want = O.leaf_values_lines(tree, dom, f(pts), meta)
+        fs = torch.tensor(f(plan.stencil_points()), dtype=torch.float64, device="cuda")
+        fe = torch.empty(plan.sizes()[1], dtype=torch.float64, device="cuda")
+        V.vpx_extend(plan, fs, fe)
+        assert V.vpx_sync_status(plan) == 0
+        got = fe.cpu().numpy().reshape(tree.n_leaves, -1)
+        fmax = np.max(np.abs(f(pts)))
+        err = exact = 0.0
+        for i, b in enumerate(tree.leaves):
+            if tree.cls[i] == O.CUT or tree.owner[i] >= 0:
+                err = max(err, np.max(np.abs(got[i] - want[i, 0])))
+                exact = max(exact, np.max(np.abs(got[i] - f(O.leaf_nodes(b, tree.t)))))
+        print("lines (precision %d, %s): |f^e - oracle| %.3e, |f^e - f| %.3e, max|f| %.2f"
+              % (precision, name, err, exact, fmax))
+        assert err <= tol * fmax
+        if name == "quadratic":
+            assert exact <= tol * fmax
+
+
 def test_execute_parity_end_to_end_disk(V):
     """Uniform disk, level 4, K = 8: all 16,384 leaf nodes and 256 boundary nodes."""
     wl = W.disk_sincos(level=4, K=8)

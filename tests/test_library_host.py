@@ -10,6 +10,8 @@ from collections import defaultdict
 import numpy as np
 import pytest
 
+EPS = np.finfo(float).eps
+
 import workloads as W
 from oracle import oracle as O
 
@@ -258,12 +260,43 @@ def test_ray_stencil_matches_oracle(V):
     assert lib.shape == orc.shape and np.abs(lib - orc).max() <= 1e-14
 
 
-def test_line_extension_mode_is_host_only_for_now(V):
+def test_line_extension_mode_takes_no_shape_parameter(V):
     wl = W.disk_sincos(level=3)
-    o = V.vpx_default_options(K=8, min_level=3, max_level=3, ext_mode=1)
-    with pytest.raises(V.VpxError) as e:
-        V.vpx_plan_create(o, wl.domain, wl.sources[0])
-    assert e.value.code == V.VPX_ERR_ARG
     o = V.vpx_default_options(K=8, min_level=3, max_level=3, ext_mode=1, rbf_eps=1e-5)
+    with pytest.raises(V.VpxError) as e:
+        V.vpx_plan_create(o, wl.domain, wl.sources[0], host_only=True)
+    assert e.value.code == V.VPX_ERR_ARG
+    o = V.vpx_default_options(K=8, min_level=3, max_level=3, ext_mode=2)
     with pytest.raises(V.VpxError):
         V.vpx_plan_create(o, wl.domain, wl.sources[0], host_only=True)
+
+
+def test_ray_operator_matches_oracle_floater_hormann(V):
+    """The library's line-extension operator (coefficients on the host, from the
+    Floater-Hormann weights' definition) gives the oracle's exterior grid
+    values: sum_q coef[q] f[ray_src + q] against the oracle's barycentric
+    interpolant through the same line points, for a non-polynomial f."""
+    from oracle import oracle as O
+    f = lambda xy: np.sin(3 * xy[:, 0]) * np.cos(2 * xy[:, 1]) + (xy[:, 0] ** 2 + xy[:, 1] ** 2) ** 3
+    dom = W.StarDomain(0.35, [(3, 0.1, 0.3), (5, 0.05, 1.0)])
+    wl = W.Workload("star_lines", 9, dom, W.TreeOptions(K=8, min_level=4, max_level=4), [f])
+    o = V.vpx_default_options(K=8, min_level=4, max_level=4, ext_mode=1)
+    plan = V.vpx_plan_create(o, wl.domain, f, host_only=True)
+    fs = f(plan.stencil_points())
+    rc, rg, src, coef = V.vpx_plan_ray_operator(plan)
+    got = np.array([np.dot(coef[k], fs[src[k]:src[k] + 8]) for k in range(len(rc))])
+    tree = O.build_tree(dom, wl.opts, f)
+    cuts = tree.cut_leaves()
+    want = np.empty(len(rc))
+    for k in range(len(rc)):
+        b = tree.leaves[cuts[rc[k]]]
+        _, XSb, _ = O.cut_leaf_stencil(b, 8, tree.t)
+        pts, radii, rx = O.ray_nodes(dom, XSb[rg[k]], O.box_side(b[0]))
+        order = np.argsort(radii)
+        want[k] = O.fh_eval(radii[order], f(pts)[order], O.fh_weights(radii[order], O.FH_DEGREE), rx)
+    assert len(rc) > 100
+    # rounding of an extrapolation: 64 eps times the coefficients' absolute sum
+    # (a Lebesgue-type constant) times the data's size along the line
+    lam = np.abs(coef).sum(axis=1)
+    fmag = np.array([np.abs(fs[src[k]:src[k] + 8]).max() for k in range(len(rc))])
+    assert np.all(np.abs(got - want) <= 64 * EPS * lam * fmag)
