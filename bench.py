@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--oracle-sample", type=int, default=12000)   # ~10 s of oracle work on 16 cores
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default engine / tile choices")
+    ap.add_argument("--ext-mode", default="stencil", choices=["stencil", "lines"],
+                    help="extension: universal stencil (default) or along lines through the origin (star domains)")
     ap.add_argument("--workload", default="starfish", choices=["starfish", "lshape", "star-batch"],
                     help="lshape: the L-shape refined to level 14 (1.4 M targets); star-batch: the uneven "
                          "batch of 32 star domains in one graph (mixed form), against the same trees run one "
@@ -110,6 +112,16 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
+def plan_options(V, wl, args, precision):
+    """Plan options of the single-tree workloads: the workload's tree, the
+    expansion order, the form, the right-hand sides and the extension mode
+    (universal stencil, or along lines through the origin)."""
+    return V.vpx_default_options(K=wl.opts.K, min_level=wl.opts.min_level, max_level=wl.opts.max_level,
+                                 refine_tol=wl.opts.refine_tol, f_scale=wl.opts.f_scale, p=args.p,
+                                 precision=V.VPX_PREC_MIXED if precision == "mixed" else V.VPX_PREC_FP64,
+                                 max_rhs=args.nrhs, ext_mode=1 if args.ext_mode == "lines" else 0)
+
+
 def run_gpu(args, rank, world, precision):
     import torch
     from paper_2211_14537_gb300 import vpx as V
@@ -118,10 +130,7 @@ def run_gpu(args, rank, world, precision):
     torch.cuda.set_device(dev)
     wl = workload(args.workload)
     t0 = time.perf_counter()
-    o = V.vpx_default_options(K=wl.opts.K, min_level=wl.opts.min_level, max_level=wl.opts.max_level,
-                              refine_tol=wl.opts.refine_tol, f_scale=wl.opts.f_scale, p=args.p,
-                              precision=V.VPX_PREC_MIXED if precision == "mixed" else V.VPX_PREC_FP64,
-                              max_rhs=args.nrhs)
+    o = plan_options(V, wl, args, precision)
     plan = V.vpx_plan_create(o, wl.domain, wl.sources[0])
     setup_s = time.perf_counter() - t0
     n_leaves, nt, ns, nb = plan.sizes()
@@ -467,7 +476,8 @@ def main():
                    "l2": "flushed between timed steps (256 MB write, outside the events)",
                    "graph": "vpx_execute replays a captured CUDA graph",
                    "setup_s": round(r["setup_s"], 3), "parallelism": "replicas" if world > 1 else "single",
-                   "autotune": {"passes_tuned": r["tune"][0], "passes_changed": r["tune"][1]}},
+                   "autotune": {"passes_tuned": r["tune"][0], "passes_changed": r["tune"][1]},
+                   "extension": "along lines" if args.ext_mode == "lines" else "universal stencil"},
         "forms": {f: {"value": res[f]["tg"] * world / (res[f]["ms"] * 1e-3), "ms_per_step": res[f]["ms"],
                       "median_ms_per_step": statistics.median(res[f]["times"]) if res[f].get("times") else None,
                       "rel_err_vs_oracle": errs.get(f), "pass_ms": {k: round(x, 5) for k, x in res[f]["pass_ms"].items()}}

@@ -80,6 +80,7 @@ def test_bench_line_carries_the_contract_keys(monkeypatch, capsys):
               "gpu_launches", "clocks"):
         assert k in d, k
     assert d["n_gpus"] == 1 and d["warmup"] >= 3 and d["config"]["workload"]
+    assert d["config"]["extension"] == "universal stencil"
     assert d["value"] == pytest.approx(184832 / 0.2e-3)                      # the faster form that meets 1e-10
     assert set(d["roofline"]) >= {"bound", "achieved", "peak", "unit", "frac", "traffic"}
     assert d["roofline"]["frac"] == pytest.approx(d["roofline"]["achieved"] / d["roofline"]["peak"])
@@ -88,3 +89,18 @@ def test_bench_line_carries_the_contract_keys(monkeypatch, capsys):
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 16
     assert d["forms"]["mixed"]["median_ms_per_step"] == pytest.approx(0.2)
     assert "latency_floor_us" in d                                             # None without a GPU
+
+
+def test_plan_options_of_the_bench(monkeypatch):
+    """The options bench.py builds its plans from: the default line keeps the
+    universal-stencil extension; --ext-mode lines selects the line extension."""
+    import sys
+    from paper_2211_14537_gb300 import vpx as V
+    for argv, mode in ((["bench.py"], 0), (["bench.py", "--ext-mode", "lines"], 1)):
+        monkeypatch.setattr(sys, "argv", argv)
+        args = bench.parse()
+        wl = bench.workload(args.workload)
+        for prec, code in (("mixed", V.VPX_PREC_MIXED), ("fp64", V.VPX_PREC_FP64)):
+            o = bench.plan_options(V, wl, args, prec)
+            assert (o.K, o.p, o.precision, o.max_rhs, o.ext_mode, o.rbf_eps) == (16, args.p, code, 1, mode, 0.0)
+            assert o.refine_tol == wl.opts.refine_tol and o.max_level == wl.opts.max_level
