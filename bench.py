@@ -390,13 +390,18 @@ def run_batch(args, rank=0, world=1):
     print(json.dumps(out), flush=True)
 
 
-def oracle_sample(wl, n_sample, seed=2213, nthreads=0):
-    """Oracle: own tree + extension, then V at a seeded sample of leaf nodes.
+def oracle_sample(wl, n_sample, seed=2213, nthreads=0, lines=False):
+    """Oracle: own tree + extension (the universal stencil, or along lines),
+    then V at a seeded sample of leaf nodes.
     Returns (indices, V at those, seconds of the potential, threads)."""
     from oracle import oracle as O
     tree = O.build_tree(wl.domain, wl.opts, wl.sources[0])
-    pts, meta = O.stencil_points(tree, wl.domain)
-    vals, _ = O.leaf_values(tree, wl.domain, wl.sources[0](pts)[:, None], meta)
+    if lines:
+        pts, meta = O.stencil_points_lines(tree, wl.domain)
+        vals = O.leaf_values_lines(tree, wl.domain, wl.sources[0](pts)[:, None], meta)
+    else:
+        pts, meta = O.stencil_points(tree, wl.domain)
+        vals, _ = O.leaf_values(tree, wl.domain, wl.sources[0](pts)[:, None], meta)
     nodes = O.all_leaf_nodes(tree)
     rng = np.random.Generator(np.random.PCG64(seed))
     idx = np.sort(rng.choice(len(nodes), min(n_sample, len(nodes)), replace=False))
@@ -426,7 +431,7 @@ def main():
     cpu = None
     if rank == 0 and world == 1:
         try:
-            idx, Vs, dt, thr = oracle_sample(res[forms[0]]["wl"], args.oracle_sample)
+            idx, Vs, dt, thr = oracle_sample(res[forms[0]]["wl"], args.oracle_sample, lines=args.ext_mode == "lines")
             for f in forms:
                 errs[f] = float(np.max(np.abs(res[f]["v"][idx] - Vs)) / np.max(np.abs(Vs)))
             if not args.no_cpu_baseline:
