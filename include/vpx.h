@@ -44,7 +44,8 @@ extern "C" {
 #define VPX_ERR_ARG       -1  /* invalid argument (null pointer, bad size, bad option) */
 #define VPX_ERR_CUDA      -2  /* a CUDA runtime call failed */
 #define VPX_ERR_NOMEM     -3  /* host or device allocation failed */
-#define VPX_ERR_STENCIL   -4  /* a cut leaf has fewer interior stencil points than N_G, or a rank-deficient fit */
+#define VPX_ERR_STENCIL   -4  /* the extension stencil cannot be formed (a cut leaf without interior points;
+                                 ext_mode 1: a ray point outside Omega or at the origin) */
 #define VPX_ERR_DOMAIN    -5  /* the extension square of a cut leaf leaves D */
 #define VPX_ERR_LEVEL     -6  /* refinement would exceed the compiled maximum level */
 #define VPX_ERR_TIMEOUT   -7  /* a bounded device wait gave up */
@@ -75,7 +76,10 @@ typedef struct {
     int    ext_mode;     /* 0 (default): universal-stencil extension (Section 3.2); 1: extension along
                             lines through the origin (Section 6.4: Floater-Hormann, degree 3, eight
                             points per line over one leaf side); Omega must be star-shaped about the
-                            origin */
+                            origin, else plan creation fails with VPX_ERR_STENCIL.  With ext_mode 0 a
+                            cut leaf whose interior points do not determine P_q (fewer than N_G of
+                            them, or a rank-deficient A_I) takes the minimum-norm least-squares fit:
+                            singular values below 1e-13 of the largest are dropped */
 } vpx_options;
 
 /* ---------------------------------------------------------------- callbacks
@@ -264,6 +268,18 @@ int vpx_potential(vpx_plan_t plan, const double *fe_leaf, int nrhs, int64_t ld_f
 #define VPX_STATIC_SCRATCH_DOUBLES (2 * 1024 * 1024)
 int vpx_potential_static(vpx_plan_t plan, const double *fe_leaf, int nrhs, int64_t ld_fe,
                          double *v_leaf, int64_t ld_v, double *v_bdry, int64_t ld_b, void *stream);
+
+/* Net charge of the extended source (Section 6.2): A^e = the integral of f^e
+ * over its support, by each leaf's tensor Gauss-Legendre rule.  Far from D the
+ * potential V[f^e] grows like (A^e / 2 pi) log|x|, which an exterior solver
+ * takes out of its condition at infinity.
+ *   fe_leaf  device, leaf values in the layout vpx_extend writes (column r at
+ *            fe_leaf + r * ld_fe, ld_fe >= n_leaf_nodes); read only
+ *   charge   device, nrhs doubles, written
+ * Two launches on `stream`, no synchronisation; the summation order is fixed,
+ * so equal inputs give bit-equal results.  Errors: VPX_ERR_ARG (null pointer,
+ * nrhs outside [1, max_rhs], ld_fe too small), VPX_ERR_STATE (host-only plan). */
+int vpx_net_charge(vpx_plan_t plan, const double *fe_leaf, int nrhs, int64_t ld_fe, double *charge, void *stream);
 
 /* End to end with HOST buffers (contiguous columns of n_stencil, n_leaf_nodes
  * and n_bdry doubles; v_bdry_host may be NULL): copies f in, runs vpx_execute

@@ -14,7 +14,8 @@ computes, written from the paper (Sections 3.1, 3.2, 4, 4.1):
 * the truncated Chebyshev expansion on the extension square and its
   evaluation on the extension-list leaves (Section 4.1, eq. chebexpbarS);
 * the volume potential by direct quadrature (``vpx_oracle.c``) and its
-  interpolation at boundary nodes (Section 4.1, last paragraph).
+  interpolation at boundary nodes (Section 4.1, last paragraph);
+* the net charge A^e of the extended source (Section 6.2).
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this module.  It shares no code with the CUDA library;
@@ -829,6 +830,20 @@ def volume_potential(tree: OracleTree, values: np.ndarray, targets: np.ndarray, 
     if rc != 0:
         raise RuntimeError("orc_volume_potential failed: %d" % rc)
     return V
+
+
+def net_charge(tree: OracleTree, values: np.ndarray) -> np.ndarray:
+    """A^e = the integral of f^e over its support (Section 6.2, the growth
+    constant of the particular solution at infinity): on every leaf the
+    tensor Gauss-Legendre rule with the leaf's K x K nodes, Jacobian
+    (side / 2)^2.  values: (n_leaves, nrhs, K*K).  Returns (nrhs,)."""
+    _, w = gauss_legendre(tree.K)
+    w2 = np.outer(w, w).ravel()                  # index b*K + a: w_b * w_a
+    out = np.zeros(values.shape[1])
+    for i, b in enumerate(tree.leaves):
+        h = 0.5 * box_side(b[0])
+        out += h * h * (values[i] @ w2)
+    return out
 
 
 def all_leaf_nodes(tree: OracleTree) -> np.ndarray:

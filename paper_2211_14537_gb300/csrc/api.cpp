@@ -462,6 +462,17 @@ int vpx_potential_static(vpx_plan_t p, const double *fe, int nrhs, int64_t ld_fe
     });
 }
 
+int vpx_net_charge(vpx_plan_t p, const double *fe, int nrhs, int64_t ld_fe, double *charge, void *stream) {
+    return guarded([&] {
+        if (!p) fail(VPX_ERR_ARG, "null plan");
+        if (p->host_only) fail(VPX_ERR_STATE, "host-only plan");
+        const int64_t nt = (int64_t)p->leaf_xy.size() / 2;
+        if (nrhs < 1 || nrhs > p->opt.max_rhs) fail(VPX_ERR_ARG, "nrhs out of range");
+        if (!fe || !charge || ld_fe < nt) fail(VPX_ERR_ARG, "bad buffer");
+        device_net_charge(p, fe, ld_fe, nrhs, charge, stream);
+    });
+}
+
 int vpx_execute_host(vpx_plan_t p, const double *f, int nrhs, double *v, double *vb) {
     return guarded([&] {
         if (!p) fail(VPX_ERR_ARG, "null plan");
@@ -514,7 +525,7 @@ const char *vpx_error_string(int code) {
         case VPX_ERR_ARG: return "invalid argument";
         case VPX_ERR_CUDA: return "CUDA error";
         case VPX_ERR_NOMEM: return "out of memory";
-        case VPX_ERR_STENCIL: return "extension stencil under-determined";
+        case VPX_ERR_STENCIL: return "extension stencil cannot be formed";
         case VPX_ERR_DOMAIN: return "geometry outside the root box";
         case VPX_ERR_LEVEL: return "maximum level exceeded";
         case VPX_ERR_TIMEOUT: return "device wait timed out";

@@ -196,6 +196,52 @@ __global__ void k_finish(int64_t n_v, int nan_blocks, int nb, int K, const int32
     if (lane == 0) vb[rhs * ldb + k] = s;
 }
 
+// Net charge A^e = \iint f^e (Section 6.2), by each leaf's tensor
+// Gauss-Legendre rule: sum_leaves (side/2)^2 sum_j w2[j] f^e[leaf][j].  The
+// first kernel gives each block a fixed set of leaves (one warp per leaf,
+// leaves strided by the grid) and writes the block's sum; the second adds the
+// block sums of a right-hand side in a fixed order, so the result does not
+// depend on scheduling.  The grid size depends on n_leaves only.
+__global__ void __launch_bounds__(256) k_charge_partial(int n_leaves, int KK, const int32_t *leaf_level,
+                                                        const double *w2, const double *fe, int64_t ldfe,
+                                                        double *part) {
+    pdl_entry();
+    const int rhs = blockIdx.y, warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const double *F = fe + rhs * ldfe;
+    double s = 0.0;
+    for (int i = blockIdx.x * nw + warp; i < n_leaves; i += gridDim.x * nw) {
+        double t = 0.0;
+        for (int j = lane; j < KK; j += 32) t += w2[j] * F[(int64_t)i * KK + j];
+        const double h = ldexp(0.5, -leaf_level[i]);
+        s += t * h * h;
+    }
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    __shared__ double ws[8];
+    if (lane == 0) ws[warp] = s;
+    __syncthreads();
+    if (warp == 0) {
+        s = lane < nw ? ws[lane] : 0.0;
+        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) part[(int64_t)rhs * gridDim.x + blockIdx.x] = s;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_charge_final(int nparts, const double *part, double *charge) {
+    pdl_entry();
+    const int rhs = blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double s = 0.0;
+    for (int k = threadIdx.x; k < nparts; k += blockDim.x) s += part[(int64_t)rhs * nparts + k];
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    __shared__ double ws[8];
+    if (lane == 0) ws[warp] = s;
+    __syncthreads();
+    if (warp == 0) {
+        s = lane < 8 ? ws[lane] : 0.0;
+        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) charge[rhs] = s;
+    }
+}
+
 // ------------------------------------------------------------ host side
 
 // Dynamic shared memory of the extension kernels (8-byte words: FP64 or a
@@ -355,6 +401,17 @@ void device_potential(vpx_plan *p, const double *fe, int64_t ldfe, int nrhs, dou
     p->last_stream = stream;
     ev_record(p, 0, s);
     run_potential(p, fe, ldfe, nrhs, v, ldv, vb, ldb, s);
+}
+
+void device_net_charge(vpx_plan *p, const double *fe, int64_t ldfe, int nrhs, double *charge, void *stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    p->last_stream = stream;
+    const int nparts = charge_blocks(p->dt.n_leaves);
+    launch_pdl(k_charge_partial, dim3(nparts, nrhs), dim3(256), 0, s, p->dt.n_leaves, p->KK,
+               (const int32_t *)p->ext.leaf_level, (const double *)p->tab.w2, fe, ldfe, p->wk.charge_part);
+    VPX_LAUNCH("k_charge_partial");
+    launch_pdl(k_charge_final, dim3(nrhs), dim3(256), 0, s, nparts, (const double *)p->wk.charge_part, charge);
+    VPX_LAUNCH("k_charge_final");
 }
 
 static void execute_sequence(vpx_plan *p, const double *f, int nrhs, int64_t ldf, double *v, int64_t ldv, double *vb,

@@ -528,6 +528,7 @@ void device_setup(vpx_plan *p) {
     w.mpole = dev_alloc<double>((size_t)w.max_rhs * d.n_boxes * 2 * p->P);
     w.local = dev_alloc<double>((size_t)w.max_rhs * d.n_boxes * 2 * p->P);
     w.status = dev_alloc<int>(1);
+    w.charge_part = dev_alloc<double>((size_t)w.max_rhs * charge_blocks(d.n_leaves));
     x.grid_pass.status = w.status;
     VPX_CUDA(cudaMemset(w.status, 0, sizeof(int)));
     setup_near_pairs(p);
@@ -560,7 +561,7 @@ void device_free(vpx_plan *p) {
     DevWork &w = p->wk;
     dev_free(w.fe); dev_free(w.mpole); dev_free(w.local);
     dev_free(w.nz_leaves); dev_free(w.bdry_leaf); dev_free(w.bdry_w); dev_free(w.status);
-    dev_free(w.f_tmp); dev_free(w.v_tmp); dev_free(w.b_tmp);
+    dev_free(w.f_tmp); dev_free(w.v_tmp); dev_free(w.b_tmp); dev_free(w.charge_part);
     for (auto &ev : p->events)
         if (ev) {
             cudaEventDestroy((cudaEvent_t)ev);

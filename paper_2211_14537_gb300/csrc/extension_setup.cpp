@@ -328,6 +328,24 @@ void ray_stencil(const vpx_options &opt, const Callbacks &cb, const HostTree &tr
         }
         st.n_interior[c] = cnt;
     }
+    // The construction assumes a domain star-shaped about the origin: every
+    // ray point lies between the origin and the ray's one boundary crossing.
+    // Refuse a geometry where that fails (the exterior of inclusions, say)
+    // rather than extend from points outside Omega.
+    std::vector<double> rxy;
+    for (size_t r = 0; r < st.ray_src.size(); ++r)
+        for (int q = 0; q < kRayNodes; ++q) {
+            const size_t p = (size_t)st.ray_src[r] + q;
+            rxy.push_back(stencil_xy[2 * p]);
+            rxy.push_back(stencil_xy[2 * p + 1]);
+        }
+    const size_t nrp = rxy.size() / 2;
+    std::vector<uint8_t> rin(nrp);
+    if (nrp && cb.inside(rxy.data(), (int64_t)nrp, rin.data(), cb.ctx) != 0)
+        fail(VPX_ERR_CALLBACK, "inside callback failed");
+    for (size_t p = 0; p < nrp; ++p)
+        if (!rin[p]) fail(VPX_ERR_STENCIL, "extension along lines: a ray point lies outside Omega "
+                                           "(the domain is not star-shaped about the origin)");
     (void)opt;
 }
 

@@ -74,7 +74,14 @@ struct DevWork {
     double *bdry_w = nullptr;     // [n_bdry][2K] Lagrange weights (x then y)
     int *status = nullptr;        // device status word
     double *f_tmp = nullptr, *v_tmp = nullptr, *b_tmp = nullptr;   // for vpx_execute_host
+    double *charge_part = nullptr;    // [max_rhs][charge_blocks(n_leaves)] block sums of the net charge
 };
+
+// Blocks of the net-charge reduction (8 leaves per block, at most two per SM's worth of 152 SMs).
+inline int charge_blocks(int n_leaves) {
+    const int b = (n_leaves + 7) / 8;
+    return b < 1 ? 1 : (b > 304 ? 304 : b);
+}
 
 struct FmmPasses {                // every contraction of the box FMM as a grouped table GEMM
     GemmPass l2m, m2l, s2l, l2t, m2t, near;
@@ -156,4 +163,5 @@ void device_autotune(int n, vpx_plan *const *plans, const double *const *f, cons
 void device_potential_static(vpx_plan *p, const double *fe_in, int64_t ldfe, int nrhs, double *v, int64_t ldv,
                              double *vb, int64_t ldb, void *stream);
 void device_execute_host(vpx_plan *p, const double *f, int nrhs, double *v, double *vb);
+void device_net_charge(vpx_plan *p, const double *fe, int64_t ldfe, int nrhs, double *charge, void *stream);
 }  // namespace vpx

@@ -60,7 +60,7 @@ EXPORTED = [
     "vpx_leaf_nodes", "vpx_boundary_nodes", "vpx_plan_list_counts", "vpx_plan_lists", "vpx_plan_near_tables",
     "vpx_universal_matrix", "vpx_plan_ray_operator", "vpx_execute",
     "vpx_execute_batch", "vpx_autotune", "vpx_autotune_batch",
-    "vpx_extend", "vpx_potential", "vpx_potential_static", "vpx_execute_host", "vpx_sync_status", "vpx_set_timing",
+    "vpx_extend", "vpx_potential", "vpx_potential_static", "vpx_net_charge", "vpx_execute_host", "vpx_sync_status", "vpx_set_timing",
     "vpx_get_timings", "vpx_pass_name", "vpx_graph_kernel_count", "vpx_check_bounded_wait", "vpx_error_string", "vpx_last_error_message", "vpx_plan_destroy",
 ]
 
@@ -99,6 +99,7 @@ def load_library(path: str = LIB_PATH):
     L.vpx_autotune_batch.argtypes = [ctypes.c_int, P(vp), P(vp), P(ctypes.c_int), P(i64), vp, P(ctypes.c_int),
                                      P(ctypes.c_int)]
     L.vpx_potential_static.argtypes = [vp, vp, ctypes.c_int, i64, vp, i64, vp, i64, vp]
+    L.vpx_net_charge.argtypes = [vp, vp, ctypes.c_int, i64, vp, vp]
     L.vpx_execute_host.argtypes = [vp, P(d), ctypes.c_int, P(d), P(d)]
     L.vpx_sync_status.argtypes = [vp]
     L.vpx_set_timing.argtypes = [vp, ctypes.c_int]
@@ -373,6 +374,15 @@ def vpx_potential_static(plan: Plan, fe_leaf, v_leaf, v_bdry=None, stream=None):
         bp, _, ldb = _cols(v_bdry)
     _check(load_library().vpx_potential_static(plan.handle, ep, nrhs, lde, vp_, ldv, bp, ldb,
                                                _stream_handle(stream)))
+
+
+def vpx_net_charge(plan: Plan, fe_leaf, charge, stream=None):
+    """A^e per right-hand side of the leaf values fe_leaf into the device tensor charge."""
+    ep, nrhs, lde = _cols(fe_leaf)
+    if charge.numel() < nrhs:
+        raise ValueError("charge holds fewer than nrhs values")
+    _check(load_library().vpx_net_charge(plan.handle, ep, nrhs, lde, ctypes.c_void_p(charge.data_ptr()),
+                                         _stream_handle(stream)))
 
 
 def vpx_execute_host(plan: Plan, f_stencil: np.ndarray, nrhs: int = 1):

@@ -1,0 +1,174 @@
+"""GPU parity on a multiply connected domain: the exterior of three starfish
+inclusions (Section 6.2's test, lengths halved to fit D).  Omega surrounds
+every hole, so each cut leaf extends f into an inclusion; the boundary targets
+lie on three closed curves.  The bounds are those of the interior tests: the
+extension within 64 unit roundoffs times its forward-error factor kappa, the
+potential of seeded leaf data within 1e-12 (FP64) and 1e-9 (mixed) relative.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import oracle as O
+from bounds import MIXED_EXT_EPS, extension_bounds, extension_potential_bound
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+EPS = np.finfo(float).eps
+
+
+@pytest.fixture(scope="module")
+def V():
+    import __graft_entry__ as g
+    g.build_library()
+    from paper_2211_14537_gb300 import vpx
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return vpx
+
+
+@pytest.fixture(scope="module")
+def case():
+    """1,150 leaves (224 cut), levels 3 to 7, 328 panels on three curves."""
+    wl = W.exterior_three_stars(K=8, tol=1e-5, max_level=7)
+    tree = O.build_tree(wl.domain, wl.opts, wl.sources[0])
+    pts, meta = O.stencil_points(tree, wl.domain)
+    return wl, tree, pts, meta, extension_bounds(tree, wl.domain, meta)
+
+
+def _plan(V, wl, precision):
+    o = V.vpx_default_options(K=wl.opts.K, min_level=wl.opts.min_level, max_level=wl.opts.max_level,
+                              refine_tol=wl.opts.refine_tol, f_scale=wl.opts.f_scale, p=50,
+                              precision=precision)
+    return V.vpx_plan_create(o, wl.domain, wl.sources[0])
+
+
+def _subset(n, m, seed):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return np.sort(rng.choice(n, size=min(n, m), replace=False))
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_exterior_extension_parity(V, case, precision):
+    wl, tree, pts, meta, kappa = case
+    plan = _plan(V, wl, precision)
+    f = wl.sources[0](pts)
+    want, _ = O.leaf_values(tree, wl.domain, f[:, None], meta)
+    fs = torch.tensor(wl.sources[0](plan.stencil_points()), dtype=torch.float64, device="cuda")
+    fe = torch.empty(plan.sizes()[1], dtype=torch.float64, device="cuda")
+    V.vpx_extend(plan, fs, fe)
+    assert V.vpx_sync_status(plan) == 0
+    got = fe.cpu().numpy().reshape(tree.n_leaves, -1)
+    eps = EPS if precision == 0 else MIXED_EXT_EPS
+    fmax = np.max(np.abs(f))
+    n_holes = 0
+    for i in range(tree.n_leaves):
+        if tree.cls[i] == O.REGULAR:
+            assert np.max(np.abs(got[i] - want[i, 0])) <= 1e-14 * fmax
+        elif tree.cls[i] == O.EXTERIOR and tree.owner[i] < 0:
+            assert np.all(got[i] == 0.0)
+            n_holes += 1
+        else:
+            tol = 64 * eps * max(kappa[i], 1.0) * fmax
+            assert np.max(np.abs(got[i] - want[i, 0])) <= tol, (i, kappa[i])
+    assert n_holes > 0       # leaves deep inside the inclusions carry no source
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_exterior_potential_parity(V, case, precision):
+    wl, tree, _, _, _ = case
+    plan = _plan(V, wl, precision)
+    rng = np.random.Generator(np.random.PCG64(2213))
+    vals = rng.uniform(-1.0, 1.0, size=(tree.n_leaves, 1, tree.K * tree.K))
+    for i in range(tree.n_leaves):
+        if tree.cls[i] == O.EXTERIOR and tree.owner[i] < 0:
+            vals[i] = 0.0
+    nodes = O.all_leaf_nodes(tree)
+    sub = _subset(len(nodes), 2000, 11)
+    want = O.volume_potential(tree, vals, nodes[sub])[:, 0]
+    fe = torch.tensor(vals[:, 0, :].ravel(), dtype=torch.float64, device="cuda")
+    v = torch.empty(len(nodes), dtype=torch.float64, device="cuda")
+    nb = plan.sizes()[3]
+    vb = torch.empty(nb, dtype=torch.float64, device="cuda")
+    V.vpx_potential(plan, fe, v, vb)
+    assert V.vpx_sync_status(plan) == 0
+    err = np.max(np.abs(v.cpu().numpy()[sub] - want)) / np.max(np.abs(want))
+    assert err <= (1e-12 if precision == 0 else 1e-9), err
+    # boundary targets on all three curves: the interpolation of the leaf values
+    assert nb == 16 * wl.domain.n_panels
+    vleaf = v.cpu().numpy().reshape(tree.n_leaves, tree.K * tree.K, 1)
+    wantb = O.interpolate_at(tree, vleaf, O.boundary_nodes(wl.domain))[:, 0]
+    assert np.max(np.abs(vb.cpu().numpy() - wantb)) <= 1e-13 * np.max(np.abs(want))
+
+
+def test_exterior_end_to_end_mixed(V, case):
+    """Stencil data -> V at sampled leaf nodes, mixed form, against the
+    oracle's extension followed by its potential."""
+    wl, tree, pts, meta, kappa = case
+    plan = _plan(V, wl, 1)
+    f = wl.sources[0](pts)
+    vals, _ = O.leaf_values(tree, wl.domain, f[:, None], meta)
+    nodes = O.all_leaf_nodes(tree)
+    sub = _subset(len(nodes), 2000, 12)
+    want = O.volume_potential(tree, vals, nodes[sub])[:, 0]
+    fs = torch.tensor(wl.sources[0](plan.stencil_points()), dtype=torch.float64, device="cuda")
+    _, nt, _, nb = plan.sizes()
+    v = torch.empty(nt, dtype=torch.float64, device="cuda")
+    vb = torch.empty(nb, dtype=torch.float64, device="cuda")
+    V.vpx_execute(plan, fs, v, vb)
+    assert V.vpx_sync_status(plan) == 0
+    scale = np.max(np.abs(want))
+    tol = 1e-9 * scale + extension_potential_bound(tree, kappa, np.max(np.abs(f)), MIXED_EXT_EPS)
+    err = np.max(np.abs(v.cpu().numpy()[sub] - want))
+    print("exterior end to end (mixed): err %.3e tol %.3e (rel %.3e)" % (err, tol, err / scale))
+    assert err <= tol
+
+
+def test_net_charge_parity(V, case):
+    """A^e of the GPU's own f^e against the oracle's quadrature of the same
+    values (the summation orders differ: 1e-13 of the integral of |f^e|, the
+    oracle adding 1,150 leaf sums in sequence), and bit-equal on a repeated
+    call (a fixed summation order)."""
+    wl, tree, pts, meta, kappa = case
+    plan = _plan(V, wl, 0)
+    nt = plan.sizes()[1]
+    fs = torch.tensor(wl.sources[0](plan.stencil_points()), dtype=torch.float64, device="cuda")
+    fe = torch.empty(nt, dtype=torch.float64, device="cuda")
+    V.vpx_extend(plan, fs, fe)
+    q = torch.empty(1, dtype=torch.float64, device="cuda")
+    V.vpx_net_charge(plan, fe, q)
+    assert V.vpx_sync_status(plan) == 0
+    vals = fe.cpu().numpy().reshape(tree.n_leaves, 1, -1)
+    want = O.net_charge(tree, vals)[0]
+    mass = O.net_charge(tree, np.abs(vals))[0]
+    got = q.item()
+    print("net charge %.15e oracle %.15e" % (got, want))
+    assert abs(got - want) <= 1e-13 * mass
+    q2 = torch.empty(1, dtype=torch.float64, device="cuda")
+    V.vpx_net_charge(plan, fe, q2)
+    assert V.vpx_sync_status(plan) == 0 and q2.item() == got
+    # against the oracle's own extension: within the extension's rounding bound
+    f = wl.sources[0](pts)
+    ovals, _ = O.leaf_values(tree, wl.domain, f[:, None], meta)
+    ext = sum(64 * EPS * k * np.max(np.abs(f)) * (2.0 ** -tree.leaves[i][0]) ** 2 for i, k in kappa.items())
+    assert abs(got - O.net_charge(tree, ovals)[0]) <= ext + 1e-13 * mass
+
+
+def test_net_charge_multi_rhs_padded(V):
+    """Three columns of seeded leaf values with a padded leading dimension."""
+    wl = W.exterior_three_stars(K=8, tol=0, min_level=5)
+    o = V.vpx_default_options(K=8, min_level=5, max_level=5, max_rhs=3)
+    plan = V.vpx_plan_create(o, wl.domain, wl.sources[0])
+    tree = O.build_tree(wl.domain, wl.opts, wl.sources[0])
+    rng = np.random.Generator(np.random.PCG64(2214))
+    nt = plan.sizes()[1]
+    vals = rng.uniform(-1.0, 1.0, size=(3, nt))
+    fe = torch.zeros((3, nt + 7), dtype=torch.float64, device="cuda")
+    fe[:, :nt] = torch.tensor(vals)
+    q = torch.full((3,), 9.0, dtype=torch.float64, device="cuda")
+    V.vpx_net_charge(plan, fe[:, :nt], q)
+    assert V.vpx_sync_status(plan) == 0
+    want = O.net_charge(tree, vals.reshape(3, tree.n_leaves, -1).transpose(1, 0, 2))
+    mass = O.net_charge(tree, np.abs(vals).reshape(3, tree.n_leaves, -1).transpose(1, 0, 2))
+    assert np.all(np.abs(q.cpu().numpy() - want) <= 1e-13 * mass)

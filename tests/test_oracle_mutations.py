@@ -67,3 +67,17 @@ def test_dropped_sign_in_the_rational_weights_is_caught(monkeypatch):
         P.test_fh_reproduces_polynomials_of_degree_d()
     with pytest.raises(AssertionError):
         P.test_line_extension_exact_for_quadratic_along_rays()
+
+
+def test_net_charge_without_the_leaf_jacobian_is_caught(monkeypatch):
+    def half_jacobian(tree, values):
+        _, w = O.gauss_legendre(tree.K)
+        w2 = np.outer(w, w).ravel()
+        return sum(0.5 * O.box_side(b[0]) * (values[i] @ w2) for i, b in enumerate(tree.leaves))
+    monkeypatch.setattr(O, "net_charge", half_jacobian)      # planted: (side/2) in place of (side/2)^2
+    with pytest.raises(AssertionError):
+        P.test_net_charge_exact_for_polynomials_on_an_adaptive_tree()
+    with pytest.raises(AssertionError):
+        P.test_net_charge_of_a_gaussian_is_pi_s_squared()
+    with pytest.raises(AssertionError):
+        P.test_net_charge_is_the_growth_of_the_potential_at_infinity()

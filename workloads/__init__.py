@@ -81,6 +81,31 @@ class StarDomain:
         return xy, dxy
 
 
+class ExteriorDomain:
+    """The exterior of several star-shaped inclusions (within the root box D):
+    Omega = D minus the closures of the inclusions (Section 6.2).  The boundary
+    is the union of the inclusions' panels, numbered inclusion by inclusion
+    (orientation plays no part in the particular solution)."""
+
+    def __init__(self, inclusions: Sequence[StarDomain]):
+        self.inclusions = list(inclusions)
+        self.n_panels = sum(d.n_panels for d in self.inclusions)
+
+    def inside(self, xy: np.ndarray) -> np.ndarray:
+        xy = np.asarray(xy, dtype=np.float64).reshape(-1, 2)
+        out = np.ones(len(xy), dtype=bool)
+        for d in self.inclusions:
+            out &= ~d.inside(xy)
+        return out
+
+    def curve(self, i: int, t) -> Tuple[np.ndarray, np.ndarray]:
+        for d in self.inclusions:
+            if i < d.n_panels:
+                return d.curve(i, t)
+            i -= d.n_panels
+        raise IndexError("panel index out of range")
+
+
 class PolygonDomain:
     """Polygon given by its vertices (counter-clockwise).
 
@@ -320,6 +345,39 @@ def lshape_expsin(K: int = 16, base_level: int = 6, max_level: int = 14, corner_
     return Workload("lshape_expsin_k%d" % K, 4, dom,
                     TreeOptions(K=K, min_level=base_level, max_level=max_level, refine_tol=1e-10, f_scale=3.0),
                     [f_exp_sin], "L-shape side 0.8, f=-3e^x sin2y, base level %d, corners to level %d" % (base_level, max_level))
+
+
+def exterior_three_stars(K: int = 8, tol: float = 1e-8, min_level: int = 3, max_level: int = 10) -> Workload:
+    """The exterior test of Section 6.2, halved in size so that the extension
+    squares of its cut leaves stay in D = [-0.5, 0.5]^2: three starfish
+    inclusions z = R (1 + a cos(N t)) e^{-it} + c with (R, a, N, c) = (0.12, 0.3,
+    5, (0.186, -0.15)), (0.17, 0.3, 4, (-0.21, -0.03)), (0.2, 0.2, 3, (0.2, 0.15))
+    at full size, and f = Laplacian of sum_j exp(-|x - y_j|^2 / beta_j) with
+    y = (0.1, 0.07), (0.09, -0.25), (-0.21, -0.25) and beta = 1e-3, 1e-3/2.1,
+    1e-3/4.5 (the exact solution's log term is harmonic in Omega).  Scaling
+    lengths by 1/2 scales the centres, radii and y_j by 1/2 and beta_j by 1/4.
+    The Gaussian centres lie inside the inclusions, so the extension runs into
+    the steep side of each bump."""
+    s = 0.5
+    incl = [StarDomain(s * 0.12, [(5, 0.3, 0.0)], center=(s * 0.186, s * -0.15)),
+            StarDomain(s * 0.17, [(4, 0.3, 0.0)], center=(s * -0.21, s * -0.03)),
+            StarDomain(s * 0.2, [(3, 0.2, 0.0)], center=(s * 0.2, s * 0.15))]
+    dom = ExteriorDomain(incl)
+    ys = s * np.array([[0.1, 0.07], [0.09, -0.25], [-0.21, -0.25]])
+    betas = s * s * np.array([1e-3, 1e-3 / 2.1, 1e-3 / 4.5])
+
+    def f(xy):
+        xy = np.asarray(xy, dtype=np.float64).reshape(-1, 2)
+        out = np.zeros(len(xy))
+        for y, b in zip(ys, betas):
+            r2 = np.sum((xy - y) ** 2, axis=1)
+            out += (4.0 * r2 / (b * b) - 4.0 / b) * np.exp(-r2 / b)
+        return out
+    return Workload("exterior_three_stars_k%d" % K, 6, dom,
+                    TreeOptions(K=K, min_level=min_level, max_level=max(min_level, max_level) if tol else min_level,
+                                refine_tol=tol, f_scale=1e4),
+                    [f], "exterior of three starfish inclusions (Section 6.2, lengths x 1/2), "
+                    "f = Laplacian of 3 Gaussians, adaptive tol %g, K=%d" % (tol, K))
 
 
 def star_batch(n_domains: int = 32, K: int = 8, tol: Optional[float] = None, max_level: int = 11):
