@@ -106,6 +106,72 @@ class ExteriorDomain:
         raise IndexError("panel index out of range")
 
 
+class SawDomain:
+    """The simply connected domain of Section 6.1's second interior test:
+    z(theta) = a (2 + b sin(m theta)) exp(i (theta + b sin(m theta))),
+    a = 0.17, b = 0.5, m = 7, theta in [0, 2 pi).  The polar angle
+    phi(theta) = theta + b sin(m theta) turns back (phi' = 1 + b m cos(m theta)
+    changes sign), so the domain is not star-shaped: the inside test counts
+    the crossings of the outward ray from the point, solving phi(theta) =
+    psi (mod 2 pi) by bisection on each interval where phi is monotone.
+    Panels are equal arcs in theta."""
+
+    def __init__(self, a: float = 0.17, b: float = 0.5, m: int = 7, n_panels: Optional[int] = None):
+        self.a, self.b, self.m = float(a), float(b), int(m)
+        c = np.arccos(-1.0 / (self.b * self.m)) if self.b * self.m > 1.0 else None
+        cuts = [0.0, TWO_PI]
+        if c is not None:
+            for j in range(self.m + 1):
+                for th in ((c + TWO_PI * j) / self.m, (TWO_PI * (j + 1) - c) / self.m):
+                    if 0.0 < th < TWO_PI:
+                        cuts.append(th)
+        self._cuts = np.array(sorted(cuts))
+        self.n_panels = int(n_panels) if n_panels else choose_panel_count(self, [64, 96, 128, 160, 192, 256, 320,
+                                                                                  384, 512, 640, 768, 1024])
+
+    def rad(self, th):
+        return self.a * (2.0 + self.b * np.sin(self.m * th))
+
+    def phi(self, th):
+        return th + self.b * np.sin(self.m * th)
+
+    def inside(self, xy: np.ndarray) -> np.ndarray:
+        xy = np.asarray(xy, dtype=np.float64).reshape(-1, 2)
+        rho = np.hypot(xy[:, 0], xy[:, 1])
+        psi = np.mod(np.arctan2(xy[:, 1], xy[:, 0]), TWO_PI)
+        count = np.zeros(len(xy), dtype=np.int64)
+        for lo, hi in zip(self._cuts[:-1], self._cuts[1:]):
+            plo, phi_hi = self.phi(lo), self.phi(hi)
+            up = phi_hi > plo
+            for k in (-1, 0, 1):
+                tgt = psi + TWO_PI * k
+                # half-open in theta: a root at the interval's upper end belongs to the next one
+                sel = np.nonzero((tgt >= min(plo, phi_hi)) & (tgt < max(plo, phi_hi)) if up else
+                                 (tgt > min(plo, phi_hi)) & (tgt <= max(plo, phi_hi)))[0]
+                if len(sel) == 0:
+                    continue
+                a = np.full(len(sel), lo)
+                c = np.full(len(sel), hi)
+                for _ in range(64):
+                    mid = 0.5 * (a + c)
+                    below = (self.phi(mid) < tgt[sel]) if up else (self.phi(mid) > tgt[sel])
+                    a = np.where(below, mid, a)
+                    c = np.where(below, c, mid)
+                count[sel] += self.rad(0.5 * (a + c)) > rho[sel]
+        return (count % 2) == 1
+
+    def curve(self, i: int, t) -> Tuple[np.ndarray, np.ndarray]:
+        dth = TWO_PI / self.n_panels
+        th = i * dth + (np.asarray(t, dtype=np.float64) + 1.0) * 0.5 * dth
+        r, p = self.rad(th), self.phi(th)
+        dr = self.a * self.b * self.m * np.cos(self.m * th)
+        dp = 1.0 + self.b * self.m * np.cos(self.m * th)
+        c, s = np.cos(p), np.sin(p)
+        xy = np.stack([r * c, r * s], axis=1)
+        dxy = np.stack([(dr * c - r * dp * s) * 0.5 * dth, (dr * s + r * dp * c) * 0.5 * dth], axis=1)
+        return xy, dxy
+
+
 class PolygonDomain:
     """Polygon given by its vertices (counter-clockwise).
 
@@ -378,6 +444,42 @@ def exterior_three_stars(K: int = 8, tol: float = 1e-8, min_level: int = 3, max_
                                 refine_tol=tol, f_scale=1e4),
                     [f], "exterior of three starfish inclusions (Section 6.2, lengths x 1/2), "
                     "f = Laplacian of 3 Gaussians, adaptive tol %g, K=%d" % (tol, K))
+
+
+def u_harmext(xy):
+    """The exact solution of Section 6.1's interior tests:
+    u = sin(10 (x + y)) + x^2 - 3 y + 8 + exp(-500 x^2)."""
+    xy = np.asarray(xy, dtype=np.float64).reshape(-1, 2)
+    x, y = xy[:, 0], xy[:, 1]
+    return np.sin(10.0 * (x + y)) + x * x - 3.0 * y + 8.0 + np.exp(-500.0 * x * x)
+
+
+def f_harmext(xy):
+    """f = Laplacian of u_harmext = -200 sin(10 (x + y)) + 2 + (1e6 x^2 - 1000) exp(-500 x^2)."""
+    xy = np.asarray(xy, dtype=np.float64).reshape(-1, 2)
+    x, y = xy[:, 0], xy[:, 1]
+    return -200.0 * np.sin(10.0 * (x + y)) + 2.0 + (1e6 * x * x - 1000.0) * np.exp(-500.0 * x * x)
+
+
+def saw_harmext(level: int = 5, K: int = 8, n_panels: Optional[int] = None) -> Workload:
+    """Section 6.1's second interior test on a uniform tree: the saw domain,
+    f = Laplacian of u_harmext, Dirichlet data g = u_harmext on the boundary.
+    Without n_panels: 256 panels up to level 5 (|gamma'| resolved to 5e-8 on
+    every panel, below the level-5 error of 6e-5), else the panel rule."""
+    if n_panels is None and level <= 5:
+        n_panels = 256
+    return Workload("saw_harmext_l%d_k%d" % (level, K), 7, SawDomain(n_panels=n_panels),
+                    TreeOptions(K=K, min_level=level, max_level=level), [f_harmext],
+                    "saw domain (Section 6.1), u = sin(10(x+y)) + x^2 - 3y + 8 + exp(-500x^2), uniform level %d" % level)
+
+
+def grid_100(dom, n: int = 100) -> np.ndarray:
+    """The points of a uniform n x n grid on D (endpoints included) inside Omega,
+    where Section 6 measures the solution's error."""
+    g = np.linspace(-0.5, 0.5, n)
+    X, Y = np.meshgrid(g, g, indexing="xy")
+    pts = np.stack([X.ravel(), Y.ravel()], axis=1)
+    return pts[dom.inside(pts)]
 
 
 def star_batch(n_domains: int = 32, K: int = 8, tol: Optional[float] = None, max_level: int = 11):
