@@ -269,6 +269,36 @@ int vpx_potential(vpx_plan_t plan, const double *fe_leaf, int nrhs, int64_t ld_f
 int vpx_potential_static(vpx_plan_t plan, const double *fe_leaf, int nrhs, int64_t ld_fe,
                          double *v_leaf, int64_t ld_v, double *v_bdry, int64_t ld_b, void *stream);
 
+/* ------------------------------------------------ boundary correction (host part)
+ * Interior Dirichlet problem on a simply connected Omega (Section 5):
+ * u = V[f^e] + D[sigma] with (-1/2 + D)[sigma] = g - V[f^e] on the boundary,
+ * D the double layer with the outward normal (eqs. dlpot, dblker, inteq),
+ * discretised on the panels' Gauss-Legendre nodes (eq. discdblpotpanel).
+ *
+ * vpx_bie_setup computes, once per plan, the Nystrom geometry and the
+ * product-integration corrections (Helsing-Ojala, Section 5) for every leaf
+ * node within reach of a panel (|zeta| < 2 in the panel's coordinates).  Host
+ * work only; threads on all cores.  Errors: VPX_ERR_ARG (null plan),
+ * VPX_ERR_STATE (no panels; panel ends that do not meet, i.e. not one closed
+ * curve; a clockwise curve).  A leaf node exactly on the boundary has no
+ * defined correction. */
+int vpx_bie_setup(vpx_plan_t plan);
+
+/* Per boundary node (n_bdry of them, panel-major): the outward unit normal
+ * (nu, 2 doubles), s*w = |gamma_i'(t_j)| times the Gauss-Legendre weight, and
+ * the signed curvature (gamma'' from differentiating the degree-(nq-1)
+ * interpolant of gamma' on the panel).  Host arrays; any may be NULL.
+ * Errors: VPX_ERR_ARG, VPX_ERR_STATE (vpx_bie_setup has not run). */
+int vpx_bie_geometry(vpx_plan_t plan, double *nu, double *sw, double *kappa);
+
+/* The corrections in CSR form over the leaf nodes: *n_corr entries; off
+ * (n_leaf_nodes + 1), panel (n_corr) and w (n_corr x nq, row-major) may each
+ * be NULL (call once with all NULL for the count).  For leaf node q,
+ * D[sigma](x_q) = sum_b K(x_q, y_b) s_b w_b sigma_b
+ *               + sum_{e in [off[q], off[q+1])} sum_j w[e][j] sigma[panel[e] * nq + j],
+ * K the kernel of eq. dblker.  Errors: VPX_ERR_ARG, VPX_ERR_STATE. */
+int vpx_bie_corrections(vpx_plan_t plan, int64_t *n_corr, int64_t *off, int32_t *panel, double *w);
+
 /* Net charge of the extended source (Section 6.2): A^e = the integral of f^e
  * over its support, by each leaf's tensor Gauss-Legendre rule.  Far from D the
  * potential V[f^e] grows like (A^e / 2 pi) log|x|, which an exterior solver

@@ -153,10 +153,15 @@ static void build_leaf_and_boundary_nodes(vpx_plan *p, const Callbacks &cb) {
     std::vector<double> g, gw;
     gauss_legendre(nq, g, gw);
     p->bdry_xy.resize(2 * (size_t)cb.n_panels * nq);
-    std::vector<double> dxy(2 * nq);
-    for (int i = 0; i < cb.n_panels; ++i)
-        if (cb.curve(i, g.data(), nq, &p->bdry_xy[2 * (size_t)i * nq], dxy.data(), cb.ctx) != 0)
+    p->bdry_dxy.resize(2 * (size_t)cb.n_panels * nq);
+    p->bdry_ends.resize(4 * (size_t)cb.n_panels);
+    const double ends_t[2] = {-1.0, 1.0};
+    double ends_d[4];
+    for (int i = 0; i < cb.n_panels; ++i) {
+        if (cb.curve(i, g.data(), nq, &p->bdry_xy[2 * (size_t)i * nq], &p->bdry_dxy[2 * (size_t)i * nq], cb.ctx) != 0 ||
+            cb.curve(i, ends_t, 2, &p->bdry_ends[4 * (size_t)i], ends_d, cb.ctx) != 0)
             fail(VPX_ERR_CALLBACK, "curve callback failed");
+    }
     // containing leaf (a point on an edge belongs to the box with the larger
     // index, except on the top/right edge of D) and its Lagrange weights
     std::unordered_map<uint64_t, int32_t> idx;
@@ -459,6 +464,34 @@ int vpx_potential_static(vpx_plan_t p, const double *fe, int nrhs, int64_t ld_fe
         if (nrhs < 1) fail(VPX_ERR_ARG, "nrhs out of range");
         if (!fe || !v || ld_fe < nt || ld_v < nt || (vb && ld_b < nbd)) fail(VPX_ERR_ARG, "bad buffer");
         device_potential_static(p, fe, ld_fe, nrhs, v, ld_v, vb, ld_b, stream);
+    });
+}
+
+int vpx_bie_setup(vpx_plan_t p) {
+    return guarded([&] {
+        if (!p) fail(VPX_ERR_ARG, "null plan");
+        bie_setup(p);
+    });
+}
+
+int vpx_bie_geometry(vpx_plan_t p, double *nu, double *sw, double *kappa) {
+    return guarded([&] {
+        if (!p) fail(VPX_ERR_ARG, "null plan");
+        if (!p->bie.ready) fail(VPX_ERR_STATE, "vpx_bie_setup has not run");
+        if (nu) std::copy(p->bie.nu.begin(), p->bie.nu.end(), nu);
+        if (sw) std::copy(p->bie.sw.begin(), p->bie.sw.end(), sw);
+        if (kappa) std::copy(p->bie.kappa.begin(), p->bie.kappa.end(), kappa);
+    });
+}
+
+int vpx_bie_corrections(vpx_plan_t p, int64_t *n_corr, int64_t *off, int32_t *panel, double *w) {
+    return guarded([&] {
+        if (!p || !n_corr) fail(VPX_ERR_ARG, "null argument");
+        if (!p->bie.ready) fail(VPX_ERR_STATE, "vpx_bie_setup has not run");
+        *n_corr = (int64_t)p->bie.corr_panel.size();
+        if (off) std::copy(p->bie.corr_off.begin(), p->bie.corr_off.end(), off);
+        if (panel) std::copy(p->bie.corr_panel.begin(), p->bie.corr_panel.end(), panel);
+        if (w) std::copy(p->bie.corr_w.begin(), p->bie.corr_w.end(), w);
     });
 }
 

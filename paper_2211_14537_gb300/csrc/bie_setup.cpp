@@ -1,0 +1,235 @@
+// bie_setup.cpp -- host part of the boundary correction (Section 5) for the
+// interior Dirichlet problem on a simply connected domain:
+//
+//   u = V[f^e] + D[sigma],  (-1/2 + D)[sigma] = g - V[f^e] on Gamma,
+//   D[sigma](x) = int (1/2pi) (x - y).nu(y) / |x - y|^2 sigma(y) ds_y,
+//
+// nu the outward normal (eqs. dlpot, dblker, inteq).  The Nystrom
+// discretisation uses the panels' Gauss-Legendre nodes with s = |gamma'| and
+// the weights w (eq. discdblpotpanel); on the diagonal the kernel takes its
+// limit on the boundary, -kappa / (4 pi).  Near a panel the Gauss-Legendre sum
+// loses accuracy; there the panel's contribution is integrated exactly
+// against the polynomial through its nodes (Helsing-Ojala product
+// integration, named in Section 5): in complex form a panel contributes
+// -(1/2pi) Im int sigma(tau) dtau / (tau - z).  This file computes the
+// geometry and, for every leaf node within reach of a panel, the weights that
+// replace that panel's plain terms.
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <thread>
+
+#include "internal.h"
+#include "plan.h"
+
+namespace vpx {
+
+using cplx = std::complex<double>;
+
+namespace {
+
+constexpr double kNearRadius = 2.0;   // product integration when |zeta| < 2 (panel coordinates)
+
+// Differentiation matrix at the nodes t (barycentric form): Dm[j][k] =
+// (bw_k / bw_j) / (t_j - t_k), diagonal minus the row sum.
+std::vector<double> diff_matrix(const std::vector<double> &t, const std::vector<double> &bw) {
+    const int n = (int)t.size();
+    std::vector<double> Dm((size_t)n * n, 0.0);
+    for (int j = 0; j < n; ++j) {
+        double diag = 0.0;
+        for (int k = 0; k < n; ++k)
+            if (k != j) {
+                Dm[(size_t)j * n + k] = (bw[k] / bw[j]) / (t[j] - t[k]);
+                diag -= Dm[(size_t)j * n + k];
+            }
+        Dm[(size_t)j * n + j] = diag;
+    }
+    return Dm;
+}
+
+// Value of the interpolant through (t_j, v_j) at s (barycentric, second form).
+cplx interp(const std::vector<double> &t, const std::vector<double> &bw, const cplx *v, double s) {
+    cplx num = 0.0;
+    double den = 0.0;
+    for (size_t j = 0; j < t.size(); ++j) {
+        const double d = s - t[j];
+        if (d == 0.0) return v[j];
+        num += v[j] * (bw[j] / d);
+        den += bw[j] / d;
+    }
+    return num / den;
+}
+
+// Solve the complex n x n system M x = r in place (partial pivoting); M row-major.
+void csolve(int n, std::vector<cplx> &M, std::vector<cplx> &r) {
+    for (int c = 0; c < n; ++c) {
+        int piv = c;
+        for (int i = c + 1; i < n; ++i)
+            if (std::abs(M[(size_t)i * n + c]) > std::abs(M[(size_t)piv * n + c])) piv = i;
+        if (piv != c) {
+            for (int k = 0; k < n; ++k) std::swap(M[(size_t)c * n + k], M[(size_t)piv * n + k]);
+            std::swap(r[c], r[piv]);
+        }
+        const cplx d = M[(size_t)c * n + c];
+        for (int i = c + 1; i < n; ++i) {
+            const cplx f = M[(size_t)i * n + c] / d;
+            if (f == cplx(0.0)) continue;
+            for (int k = c; k < n; ++k) M[(size_t)i * n + k] -= f * M[(size_t)c * n + k];
+            r[i] -= f * r[c];
+        }
+    }
+    for (int i = n - 1; i >= 0; --i) {
+        cplx s = r[i];
+        for (int k = i + 1; k < n; ++k) s -= M[(size_t)i * n + k] * r[k];
+        r[i] = s / M[(size_t)i * n + i];
+    }
+}
+
+struct PanelData {
+    std::vector<double> t, bw, Dm;
+};
+
+// lam with sum_j lam_j sigma_j = int_panel sigma dtau / (tau - z), sigma the
+// polynomial of degree nq - 1 in xi = (2 tau - a - b) / (b - a) through the
+// nodes: lam solves V^T lam = p with V[j][k] = xi_j^k and p_k = int xi^k /
+// (xi - zeta) dxi along the panel (p_k = zeta p_{k-1} + (1 - (-1)^k) / k).
+void product_weights(const PanelData &P, const cplx *tau, cplx a, cplx b, cplx z, cplx *lam) {
+    const int n = (int)P.t.size();
+    std::vector<cplx> xi(n), dxi(n, 0.0);
+    for (int j = 0; j < n; ++j) xi[j] = (2.0 * tau[j] - (a + b)) / (b - a);
+    const cplx zeta = (2.0 * z - (a + b)) / (b - a);
+    std::vector<cplx> p(n);
+    p[0] = std::log((1.0 - zeta) / (-1.0 - zeta));     // along the chord [-1, 1]
+    if (std::fabs(zeta.real()) < 1.0) {
+        // height of the curved panel where its real part is Re(zeta): Newton on
+        // the interpolant xi(t), derivative from the differentiation matrix
+        for (int j = 0; j < n; ++j)
+            for (int k = 0; k < n; ++k) dxi[j] += P.Dm[(size_t)j * n + k] * xi[k];
+        double s = zeta.real();
+        for (int it = 0; it < 60; ++it) {
+            const double f = interp(P.t, P.bw, xi.data(), s).real() - zeta.real();
+            const double step = f / interp(P.t, P.bw, dxi.data(), s).real();
+            s -= step;
+            if (std::fabs(step) < 1e-16) break;
+        }
+        const double h = interp(P.t, P.bw, xi.data(), s).imag();
+        // between the panel and its chord the two integrals differ by the residue
+        if (h != 0.0 && zeta.imag() / h > 0.0 && zeta.imag() / h < 1.0)
+            p[0] += cplx(0.0, h > 0.0 ? -2.0 * M_PI : 2.0 * M_PI);
+    }
+    for (int k = 1; k < n; ++k) p[k] = zeta * p[k - 1] + ((k % 2) ? 2.0 / k : 0.0);
+    std::vector<cplx> VT((size_t)n * n);
+    for (int j = 0; j < n; ++j) {
+        cplx pw = 1.0;
+        for (int k = 0; k < n; ++k) {
+            VT[(size_t)k * n + j] = pw;
+            pw *= xi[j];
+        }
+    }
+    csolve(n, VT, p);
+    for (int j = 0; j < n; ++j) lam[j] = p[j];
+}
+
+}  // namespace
+
+void bie_setup(vpx_plan *pl) {
+    BieHost &B = pl->bie;
+    if (B.ready) return;
+    const int nq = pl->opt.n_quad_bdry;
+    const int np = (int)(pl->bdry_ends.size() / 4);
+    const size_t N = pl->bdry_xy.size() / 2;
+    if (np == 0) fail(VPX_ERR_STATE, "the boundary correction needs boundary panels");
+    // one closed curve, counter-clockwise: panel i ends where panel i+1 starts
+    const double *E = pl->bdry_ends.data();
+    double len = 0.0;
+    for (int i = 0; i < np; ++i) len += std::hypot(E[4 * i + 2] - E[4 * i], E[4 * i + 3] - E[4 * i + 1]);
+    for (int i = 0; i < np; ++i) {
+        const int k = (i + 1) % np;
+        if (std::hypot(E[4 * i + 2] - E[4 * k], E[4 * i + 3] - E[4 * k + 1]) > 1e-10 * len)
+            fail(VPX_ERR_STATE, "the boundary correction needs one closed curve (panel ends must meet)");
+    }
+    std::vector<double> t, w;
+    gauss_legendre(nq, t, w);
+    PanelData P{t, barycentric_weights(t), {}};
+    P.Dm = diff_matrix(P.t, P.bw);
+    B.nq = nq;
+    B.n_panels = np;
+    B.nu.assign(2 * N, 0.0);
+    B.sw.assign(N, 0.0);
+    B.kappa.assign(N, 0.0);
+    double area2 = 0.0;   // twice the signed area, int (x y' - y x') dt
+    for (int i = 0; i < np; ++i)
+        for (int j = 0; j < nq; ++j) {
+            const size_t q = (size_t)i * nq + j;
+            const double dx = pl->bdry_dxy[2 * q], dy = pl->bdry_dxy[2 * q + 1];
+            double ddx = 0.0, ddy = 0.0;
+            for (int k = 0; k < nq; ++k) {
+                ddx += P.Dm[(size_t)j * nq + k] * pl->bdry_dxy[2 * ((size_t)i * nq + k)];
+                ddy += P.Dm[(size_t)j * nq + k] * pl->bdry_dxy[2 * ((size_t)i * nq + k) + 1];
+            }
+            const double s = std::hypot(dx, dy);
+            B.nu[2 * q] = dy / s;
+            B.nu[2 * q + 1] = -dx / s;
+            B.sw[q] = s * w[j];
+            B.kappa[q] = (dx * ddy - dy * ddx) / (s * s * s);
+            area2 += w[j] * (pl->bdry_xy[2 * q] * dy - pl->bdry_xy[2 * q + 1] * dx);
+        }
+    if (!(area2 > 0.0)) fail(VPX_ERR_STATE, "the boundary correction needs a counter-clockwise boundary");
+
+    // (leaf node, panel) pairs with |zeta| < kNearRadius, i.e. the node within
+    // |b - a| of the panel's chord midpoint; candidate leaves by box overlap
+    const auto &L = pl->tree.leaves;
+    const int KK = pl->KK;
+    const size_t nt = pl->leaf_xy.size() / 2;
+    std::vector<std::vector<int32_t>> near_of(nt);
+    for (int i = 0; i < np; ++i) {
+        const double mx = 0.5 * (E[4 * i] + E[4 * i + 2]), my = 0.5 * (E[4 * i + 1] + E[4 * i + 3]);
+        const double R = kNearRadius * 0.5 * std::hypot(E[4 * i + 2] - E[4 * i], E[4 * i + 3] - E[4 * i + 1]);
+        for (size_t l = 0; l < L.size(); ++l) {
+            const double s = std::ldexp(1.0, -L[l].level);
+            const double x0 = -0.5 + L[l].ix * s, y0 = -0.5 + L[l].iy * s;
+            if (mx + R < x0 || mx - R > x0 + s || my + R < y0 || my - R > y0 + s) continue;
+            for (int k = 0; k < KK; ++k) {
+                const size_t q = l * KK + k;
+                if (std::hypot(pl->leaf_xy[2 * q] - mx, pl->leaf_xy[2 * q + 1] - my) < R) near_of[q].push_back(i);
+            }
+        }
+    }
+    B.corr_off.assign(nt + 1, 0);
+    for (size_t q = 0; q < nt; ++q) B.corr_off[q + 1] = B.corr_off[q] + (int64_t)near_of[q].size();
+    const int64_t nc = B.corr_off[nt];
+    B.corr_panel.assign(nc, 0);
+    B.corr_w.assign((size_t)nc * nq, 0.0);
+    for (size_t q = 0; q < nt; ++q)
+        std::copy(near_of[q].begin(), near_of[q].end(), B.corr_panel.begin() + B.corr_off[q]);
+    std::vector<cplx> tau(N);
+    for (size_t q = 0; q < N; ++q) tau[q] = cplx(pl->bdry_xy[2 * q], pl->bdry_xy[2 * q + 1]);
+    auto work = [&](size_t q0, size_t q1) {
+        std::vector<cplx> lam(nq);
+        for (size_t q = q0; q < q1; ++q) {
+            const double x = pl->leaf_xy[2 * q], y = pl->leaf_xy[2 * q + 1];
+            for (int64_t e = B.corr_off[q]; e < B.corr_off[q + 1]; ++e) {
+                const int i = B.corr_panel[e];
+                const cplx a(E[4 * i], E[4 * i + 1]), b(E[4 * i + 2], E[4 * i + 3]);
+                product_weights(P, &tau[(size_t)i * nq], a, b, cplx(x, y), lam.data());
+                for (int j = 0; j < nq; ++j) {
+                    const size_t n = (size_t)i * nq + j;
+                    const double dx = x - pl->bdry_xy[2 * n], dy = y - pl->bdry_xy[2 * n + 1];
+                    const double plain = (dx * B.nu[2 * n] + dy * B.nu[2 * n + 1]) / (dx * dx + dy * dy) * B.sw[n];
+                    B.corr_w[(size_t)e * nq + j] = (-lam[j].imag() - plain) / (2.0 * M_PI);
+                }
+            }
+        }
+    };
+    const unsigned nth = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+    std::vector<std::thread> th;
+    const size_t chunk = (nt + nth - 1) / nth;
+    for (unsigned k = 0; k < nth; ++k) {
+        const size_t q0 = k * chunk, q1 = std::min(nt, q0 + chunk);
+        if (q0 < q1) th.emplace_back(work, q0, q1);
+    }
+    for (auto &x : th) x.join();
+    B.ready = true;
+}
+
+}  // namespace vpx

@@ -66,6 +66,19 @@ struct Callbacks {
 
 void build_tree(const vpx_options &opt, const Callbacks &cb, HostTree &tree);
 
+// ------------------------------------------------------- boundary correction
+// Host part of the interior Dirichlet correction (Section 5): Nystrom
+// geometry and, per leaf node within reach of a panel, the product-integration
+// weights that replace that panel's Gauss-Legendre terms.
+struct BieHost {
+    bool ready = false;
+    int nq = 0, n_panels = 0;
+    std::vector<double> nu, sw, kappa;     // outward normal (2 per node), s*w, signed curvature
+    std::vector<int64_t> corr_off;         // [n_leaf_nodes + 1]
+    std::vector<int32_t> corr_panel;       // panel of each correction
+    std::vector<double> corr_w;            // [n_corr][nq]: product weight minus the plain term
+};
+
 // ------------------------------------------------------- stencil / extension
 struct StencilInfo {
     int q = 0, Kbar = 0, NG = 0, NX = 0;       // NX = K*K + Kbar*Kbar + NG universal points

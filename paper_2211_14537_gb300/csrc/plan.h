@@ -110,6 +110,9 @@ struct vpx_plan {
     std::vector<double> bdry_xy;
     std::vector<int32_t> bdry_leaf;
     std::vector<double> bdry_w;
+    std::vector<double> bdry_dxy;     // gamma_i'(t_j) at the boundary nodes
+    std::vector<double> bdry_ends;    // per panel gamma_i(-1), gamma_i(1): 4 doubles
+    vpx::BieHost bie;                 // boundary correction (host part), filled by vpx_bie_setup
     // host copies of the boxes (level, Morton order) and lists
     std::vector<int32_t> box_level, box_ix, box_iy, box_parent, box_child0, box_leaf;
     std::vector<uint32_t> box_morton;
@@ -164,4 +167,5 @@ void device_potential_static(vpx_plan *p, const double *fe_in, int64_t ldfe, int
                              double *vb, int64_t ldb, void *stream);
 void device_execute_host(vpx_plan *p, const double *f, int nrhs, double *v, double *vb);
 void device_net_charge(vpx_plan *p, const double *fe, int64_t ldfe, int nrhs, double *charge, void *stream);
+void bie_setup(vpx_plan *p);
 }  // namespace vpx

@@ -60,7 +60,7 @@ EXPORTED = [
     "vpx_leaf_nodes", "vpx_boundary_nodes", "vpx_plan_list_counts", "vpx_plan_lists", "vpx_plan_near_tables",
     "vpx_universal_matrix", "vpx_plan_ray_operator", "vpx_execute",
     "vpx_execute_batch", "vpx_autotune", "vpx_autotune_batch",
-    "vpx_extend", "vpx_potential", "vpx_potential_static", "vpx_net_charge", "vpx_execute_host", "vpx_sync_status", "vpx_set_timing",
+    "vpx_extend", "vpx_potential", "vpx_potential_static", "vpx_net_charge", "vpx_bie_setup", "vpx_bie_geometry", "vpx_bie_corrections", "vpx_execute_host", "vpx_sync_status", "vpx_set_timing",
     "vpx_get_timings", "vpx_pass_name", "vpx_graph_kernel_count", "vpx_check_bounded_wait", "vpx_error_string", "vpx_last_error_message", "vpx_plan_destroy",
 ]
 
@@ -100,6 +100,9 @@ def load_library(path: str = LIB_PATH):
                                      P(ctypes.c_int)]
     L.vpx_potential_static.argtypes = [vp, vp, ctypes.c_int, i64, vp, i64, vp, i64, vp]
     L.vpx_net_charge.argtypes = [vp, vp, ctypes.c_int, i64, vp, vp]
+    L.vpx_bie_setup.argtypes = [vp]
+    L.vpx_bie_geometry.argtypes = [vp, P(d), P(d), P(d)]
+    L.vpx_bie_corrections.argtypes = [vp, P(i64), P(i64), P(i32), P(d)]
     L.vpx_execute_host.argtypes = [vp, P(d), ctypes.c_int, P(d), P(d)]
     L.vpx_sync_status.argtypes = [vp]
     L.vpx_set_timing.argtypes = [vp, ctypes.c_int]
@@ -383,6 +386,32 @@ def vpx_net_charge(plan: Plan, fe_leaf, charge, stream=None):
         raise ValueError("charge holds fewer than nrhs values")
     _check(load_library().vpx_net_charge(plan.handle, ep, nrhs, lde, ctypes.c_void_p(charge.data_ptr()),
                                          _stream_handle(stream)))
+
+
+def vpx_bie_setup(plan: Plan):
+    _check(load_library().vpx_bie_setup(plan.handle))
+
+
+def vpx_bie_geometry(plan: Plan):
+    """(nu (n_bdry, 2), s*w (n_bdry,), kappa (n_bdry,)) after vpx_bie_setup."""
+    nb = plan.sizes()[3]
+    nu, sw, ka = np.zeros((nb, 2)), np.zeros(nb), np.zeros(nb)
+    _check(load_library().vpx_bie_geometry(plan.handle, _dptr(nu), _dptr(sw), _dptr(ka)))
+    return nu, sw, ka
+
+
+def vpx_bie_corrections(plan: Plan, nq: int = 16):
+    """(off (n_leaf_nodes + 1,), panel (n_corr,), w (n_corr, nq)) after vpx_bie_setup."""
+    L = load_library()
+    n = ctypes.c_int64(0)
+    _check(L.vpx_bie_corrections(plan.handle, ctypes.byref(n), None, None, None))
+    nt = plan.sizes()[1]
+    off = np.zeros(nt + 1, dtype=np.int64)
+    pan = np.zeros(n.value, dtype=np.int32)
+    w = np.zeros((n.value, nq))
+    _check(L.vpx_bie_corrections(plan.handle, ctypes.byref(n), off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                 pan.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _dptr(w)))
+    return off, pan, w
 
 
 def vpx_execute_host(plan: Plan, f_stencil: np.ndarray, nrhs: int = 1):

@@ -13,6 +13,7 @@ import pytest
 EPS = np.finfo(float).eps
 
 import workloads as W
+from oracle import bie as B
 from oracle import oracle as O
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -322,3 +323,64 @@ def test_ray_operator_matches_oracle_floater_hormann(V):
     lam = np.abs(coef).sum(axis=1)
     fmag = np.array([np.abs(fs[src[k]:src[k] + 8]).max() for k in range(len(rc))])
     assert np.all(np.abs(got - want) <= 64 * EPS * lam * fmag)
+
+
+@pytest.mark.parametrize("name", ["starfish_k8", "saw_l5"])
+def test_bie_host_part_matches_oracle(V, name):
+    """Boundary correction, host part (Section 5): normals, s*w and curvature
+    equal the oracle's; the plain sum plus the library's product-integration
+    corrections reproduces the oracle's D[sigma] at leaf nodes near and far
+    from the boundary, for the density of harmonic Dirichlet data."""
+    wl = W.starfish_gaussian(K=8, tol=1e-8, max_level=8) if name == "starfish_k8" else W.saw_harmext(5)
+    plan = _plan(V, wl)
+    with pytest.raises(V.VpxError) as e:
+        V.vpx_bie_geometry(plan)
+    assert e.value.code == V.VPX_ERR_STATE
+    V.vpx_bie_setup(plan)
+    nu, sw, ka = V.vpx_bie_geometry(plan)
+    g = B.BoundaryGeometry(wl.domain)
+    assert np.abs(nu - g.nu).max() < 1e-15 and np.abs(sw - g.s * g.w).max() < 1e-16
+    assert np.abs(ka - g.kappa).max() < 1e-12 * np.abs(g.kappa).max()
+    off, pan, w = V.vpx_bie_corrections(plan)
+    uh = lambda p: np.exp(3 * p[:, 0]) * np.cos(3 * p[:, 1]) + p[:, 0] * p[:, 1]
+    sigma = B.solve_density(g, uh(g.y))
+    X = plan.leaf_nodes()
+    rng = np.random.default_rng(9)
+    near = np.nonzero(np.diff(off) > 0)[0]
+    sel = np.concatenate([rng.choice(near, 200, replace=False), rng.choice(len(X), 60, replace=False)])
+    got = np.empty(len(sel))
+    for k, q in enumerate(sel):
+        d = X[q] - g.y
+        got[k] = np.sum((d * nu).sum(1) / (d * d).sum(1) * sw * sigma) / (2 * np.pi)
+        for e in range(off[q], off[q + 1]):
+            got[k] += w[e] @ sigma[pan[e] * 16:(pan[e] + 1) * 16]
+    want = B.dlp_eval(g, sigma, X[sel])
+    assert np.abs(got - want).max() < 1e-13 * np.abs(want).max()
+    ins = wl.domain.inside(X[sel])
+    assert np.abs(got[ins] - uh(X[sel][ins])).max() < (1e-11 if name == "starfish_k8" else 1e-8)
+
+
+def test_bie_setup_refuses_what_it_cannot_solve(V):
+    """Several closed curves (the exterior of inclusions), a clockwise curve,
+    and no boundary at all are refused with VPX_ERR_STATE."""
+    ext = W.exterior_three_stars(K=8, tol=0, min_level=4)
+    plan = _plan(V, ext)
+    with pytest.raises(V.VpxError) as e:
+        V.vpx_bie_setup(plan)
+    assert e.value.code == V.VPX_ERR_STATE and "closed curve" in str(e.value)
+
+    class Clockwise(W.StarDomain):
+        def curve(self, i, t):
+            xy, d = W.StarDomain.curve(self, self.n_panels - 1 - i, -np.asarray(t))
+            return xy, -d
+    cw = Clockwise(0.35, (), n_panels=16)
+    o = V.vpx_default_options(K=8, min_level=3, max_level=3)
+    plan = V.vpx_plan_create(o, cw, W.f_sincos, host_only=True)
+    with pytest.raises(V.VpxError) as e:
+        V.vpx_bie_setup(plan)
+    assert e.value.code == V.VPX_ERR_STATE and "counter-clockwise" in str(e.value)
+    o = V.vpx_default_options(K=8, min_level=2, max_level=2)
+    plan = V.vpx_plan_create(o, W.WholeBoxDomain(), W.f_sincos, host_only=True)
+    with pytest.raises(V.VpxError) as e:
+        V.vpx_bie_setup(plan)
+    assert e.value.code == V.VPX_ERR_STATE
