@@ -45,18 +45,27 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default engine / tile choices")
     ap.add_argument("--ext-mode", default="stencil", choices=["stencil", "lines"],
                     help="extension: universal stencil (default) or along lines through the origin (star domains)")
-    ap.add_argument("--workload", default="starfish", choices=["starfish", "lshape", "star-batch"],
-                    help="lshape: the L-shape refined to level 14 (1.4 M targets); star-batch: the uneven "
+    ap.add_argument("--workload", default="starfish", choices=["starfish", "lshape", "exterior", "star-batch"],
+                    help="lshape: the L-shape refined to level 14 (1.4 M targets); exterior: D minus three "
+                         "starfish inclusions (Section 6.2, 265 k targets); star-batch: the uneven "
                          "batch of 32 star domains in one graph (mixed form), against the same trees run one "
                          "after another in both forms")
     return ap.parse_args()
 
 
+DOMAIN_LABEL = {"starfish": "starfish", "lshape": "L-shape", "exterior": "exterior of three inclusions"}
+
+
 def workload(name="starfish"):
-    """The single-tree workloads: the adaptive starfish (the default line) and
-    the L-shape refined to level 14 toward its corners (1.4 M targets)."""
+    """The single-tree workloads: the adaptive starfish (the default line),
+    the L-shape refined to level 14 toward its corners (1.4 M targets) and the
+    exterior of three starfish inclusions (Section 6.2, 265 k targets)."""
     import workloads as W
-    return W.lshape_expsin() if name == "lshape" else W.starfish_gaussian(K=16)
+    if name == "lshape":
+        return W.lshape_expsin()
+    if name == "exterior":
+        return W.exterior_three_stars()
+    return W.starfish_gaussian(K=16)
 
 
 class ClockSampler:
@@ -472,7 +481,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if head == "fp64" else "bf16 (exact 7-bit slices) + f64",
-        "data": "synthetic (seeded analytic source on the %s domain)" % ("L-shape" if args.workload == "lshape" else "starfish"),
+        "data": "synthetic (seeded analytic source on the %s domain)" % DOMAIN_LABEL[args.workload],
         "config": {"workload": r["wl"].name, "description": r["wl"].description, "K": r["K"], "p": args.p,
                    "refine_tol": r["wl"].opts.refine_tol, "n_leaves": r["n_leaves"], "leaf_targets": r["nt"],
                    "boundary_targets": r["nb"], "stencil_points": r["ns"], "nrhs": args.nrhs,

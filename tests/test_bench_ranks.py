@@ -56,7 +56,8 @@ def test_reduce_on_one_rank_is_identity():
     assert bench.reduce_over_ranks(3.0, 7, "cpu", 1) == (3.0, 7.0)
 
 
-def test_bench_line_carries_the_contract_keys(monkeypatch, capsys):
+@pytest.mark.parametrize("wl_name", ["starfish", "exterior"])
+def test_bench_line_carries_the_contract_keys(monkeypatch, capsys, wl_name):
     """bench.main() on one rank, the GPU run and the oracle sample replaced by
     fixed results: one JSON line with the keys of the benchmark contract."""
     import json
@@ -72,7 +73,7 @@ def test_bench_line_carries_the_contract_keys(monkeypatch, capsys):
 
     monkeypatch.setattr(bench, "run_gpu", fake_run_gpu)
     monkeypatch.setattr(bench, "oracle_sample", lambda wl, n, **k: (np.arange(10), np.ones(10), 1.0, 16))
-    monkeypatch.setattr(sys, "argv", ["bench.py"])
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--workload", wl_name])
     bench.main()
     d = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
     for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
@@ -89,6 +90,8 @@ def test_bench_line_carries_the_contract_keys(monkeypatch, capsys):
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 16
     assert d["forms"]["mixed"]["median_ms_per_step"] == pytest.approx(0.2)
     assert "latency_floor_us" in d                                             # None without a GPU
+    assert d["config"]["workload"] == bench.workload(wl_name).name
+    assert bench.DOMAIN_LABEL[wl_name] in d["data"]
 
 
 def test_plan_options_of_the_bench(monkeypatch):
