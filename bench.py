@@ -47,7 +47,7 @@ def parse():
                     help="extension: universal stencil (default) or along lines through the origin (star domains)")
     ap.add_argument("--workload", default="starfish", choices=["starfish", "lshape", "exterior", "star-batch"],
                     help="lshape: the L-shape refined to level 14 (1.4 M targets); exterior: D minus three "
-                         "starfish inclusions (Section 6.2, 265 k targets); star-batch: the uneven "
+                         "starfish inclusions (Section 6.2, 248 k targets); star-batch: the uneven "
                          "batch of 32 star domains in one graph (mixed form), against the same trees run one "
                          "after another in both forms")
     return ap.parse_args()
@@ -59,7 +59,7 @@ DOMAIN_LABEL = {"starfish": "starfish", "lshape": "L-shape", "exterior": "exteri
 def workload(name="starfish"):
     """The single-tree workloads: the adaptive starfish (the default line),
     the L-shape refined to level 14 toward its corners (1.4 M targets) and the
-    exterior of three starfish inclusions (Section 6.2, 265 k targets)."""
+    exterior of three starfish inclusions (Section 6.2, 248 k targets)."""
     import workloads as W
     if name == "lshape":
         return W.lshape_expsin()

@@ -156,3 +156,45 @@ def dlp_eval(g: BoundaryGeometry, sigma: np.ndarray, targets: np.ndarray) -> np.
             total += -(lam @ sigma[sl]).imag / (2 * math.pi) - direct[sl].sum()
         out[k] = total
     return out
+
+
+class ExteriorSolution:
+    """u^H = D[sigma] + (1/2pi) int_Gamma sigma ds + sum_k A_k log|x - s_k| in
+    the exterior of several closed curves (Section 2, exterior and multiply
+    connected problems), the curves counter-clockwise so that nu points out
+    of each inclusion, into Omega."""
+
+    def __init__(self, g: BoundaryGeometry, sigma, A, centers):
+        self.g, self.sigma, self.A, self.centers = g, sigma, np.asarray(A), np.asarray(centers, dtype=np.float64)
+
+    def __call__(self, targets):
+        targets = np.asarray(targets, dtype=np.float64).reshape(-1, 2)
+        u = dlp_eval(self.g, self.sigma, targets) + np.sum(self.sigma * self.g.s * self.g.w) / (2 * math.pi)
+        for A, c in zip(self.A, self.centers):
+            u = u + A * np.log(np.hypot(targets[:, 0] - c[0], targets[:, 1] - c[1]))
+        return u
+
+
+def solve_exterior(g: BoundaryGeometry, curve_of_node, centers, rhs, growth) -> ExteriorSolution:
+    """The exterior Dirichlet correction: on the boundary, the limit from
+    Omega of the representation equals rhs = g - V,
+
+        (1/2 + D) sigma + (1/2pi) int sigma ds + sum_k A_k log|y - s_k| = rhs,
+
+    with int_{Gamma_k} sigma ds = 0 for every curve but the last and
+    sum_k A_k = growth, the coefficient of log|x| that u^H must have at
+    infinity: the solution's own growth A minus the particular solution's
+    Q = (1/2pi) iint f^e (Section 2, alpha = A - Q).  s_k is a point inside
+    curve k; curve_of_node gives the curve of every boundary node."""
+    n, m = g.n, len(centers)
+    sw = g.s * g.w
+    M = np.zeros((n + m, n + m))
+    M[:n, :n] = 0.5 * np.eye(n) + dlp_matrix(g) + np.outer(np.ones(n), sw) / (2 * math.pi)
+    for k, c in enumerate(centers):
+        M[:n, n + k] = np.log(np.hypot(g.y[:, 0] - c[0], g.y[:, 1] - c[1]))
+    for k in range(m - 1):
+        M[n + k, :n] = sw * (np.asarray(curve_of_node) == k)
+    M[n + m - 1, n:] = 1.0
+    b = np.concatenate([np.asarray(rhs, dtype=np.float64), np.zeros(m - 1), [float(growth)]])
+    x = np.linalg.solve(M, b)
+    return ExteriorSolution(g, x[:n], x[n:], centers)

@@ -1,5 +1,5 @@
 """GPU parity on a multiply connected domain: the exterior of three starfish
-inclusions (Section 6.2's test, lengths halved to fit D).  Omega surrounds
+inclusions (Section 6.2's test).  Omega surrounds
 every hole, so each cut leaf extends f into an inclusion; the boundary targets
 lie on three closed curves.  The bounds are those of the interior tests: the
 extension within 64 unit roundoffs times its forward-error factor kappa, the
@@ -30,7 +30,7 @@ def V():
 
 @pytest.fixture(scope="module")
 def case():
-    """1,150 leaves (224 cut), levels 3 to 7, 328 panels on three curves."""
+    """1,726 leaves (320 cut), levels 3 to 7, 328 panels on three curves."""
     wl = W.exterior_three_stars(K=8, tol=1e-5, max_level=7)
     tree = O.build_tree(wl.domain, wl.opts, wl.sources[0])
     pts, meta = O.stencil_points(tree, wl.domain)
@@ -128,7 +128,7 @@ def test_exterior_end_to_end_mixed(V, case):
 def test_net_charge_parity(V, case):
     """A^e of the GPU's own f^e against the oracle's quadrature of the same
     values (the summation orders differ: 1e-13 of the integral of |f^e|, the
-    oracle adding 1,150 leaf sums in sequence), and bit-equal on a repeated
+    oracle adding 1,726 leaf sums in sequence), and bit-equal on a repeated
     call (a fixed summation order)."""
     wl, tree, pts, meta, kappa = case
     plan = _plan(V, wl, 0)

@@ -49,7 +49,7 @@ WORKLOADS = {
     "starfish_k8": lambda: W.starfish_gaussian(K=8, tol=1e-8, max_level=8),
     "lshape_small": lambda: W.lshape_expsin(K=8, base_level=4, max_level=8, corner_levels=5),
     "star_batch_03": lambda: W.star_batch(4)[3],   # adaptive K = 8 star of the uneven batch (3,844 leaves)
-    "exterior_k8": lambda: W.exterior_three_stars(K=8, tol=1e-5, max_level=7),   # three holes, 1,150 leaves
+    "exterior_k8": lambda: W.exterior_three_stars(K=8, tol=1e-5, max_level=7),   # three holes, 1,726 leaves
 }
 
 
@@ -275,23 +275,25 @@ def test_line_extension_mode_takes_no_shape_parameter(V):
 
 def test_line_extension_refuses_a_domain_not_star_shaped_about_the_origin(V):
     """Lines through the origin reach Omega's boundary once only in a domain
-    star-shaped about the origin; the exterior of three inclusions is not one,
-    and its rays run through the holes."""
+    star-shaped about the origin; exteriors of inclusions are not, and their
+    rays run through the holes."""
     wl = W.exterior_three_stars(K=8, tol=0, min_level=4)     # the origin lies in a hole
     o = V.vpx_default_options(K=8, min_level=4, max_level=4, ext_mode=1)
     with pytest.raises(V.VpxError) as e:
         V.vpx_plan_create(o, wl.domain, wl.sources[0], host_only=True)
     assert e.value.code == V.VPX_ERR_STENCIL and "origin" in str(e.value)
-    # moved up by 0.2 the origin is in Omega, but rays cross a hole between
-    # their boundary point and the origin
-    moved = W.ExteriorDomain([W.StarDomain(d.r0, d.modes, center=(d.center[0], d.center[1] + 0.2))
-                              for d in wl.domain.inclusions])
+    # two holes on the positive x axis, the origin in Omega: a ray to a point of
+    # the far hole meets the boundary first at the near edge of the far hole,
+    # and its data points, one leaf side back from there, fall into the small hole
+    holes = W.ExteriorDomain([W.StarDomain(0.03, (), n_panels=16, center=(0.1, 0.0)),
+                              W.StarDomain(0.08, (), n_panels=16, center=(0.25, 0.0))])
+    assert holes.inside(np.zeros((1, 2)))[0]
     with pytest.raises(V.VpxError) as e:
-        V.vpx_plan_create(o, moved, wl.sources[0], host_only=True)
+        V.vpx_plan_create(o, holes, W.f_sincos, host_only=True)
     assert e.value.code == V.VPX_ERR_STENCIL and "star-shaped" in str(e.value)
     o = V.vpx_default_options(K=8, min_level=4, max_level=4)     # the universal stencil takes both
     V.vpx_plan_create(o, wl.domain, wl.sources[0], host_only=True)
-    V.vpx_plan_create(o, moved, wl.sources[0], host_only=True)
+    V.vpx_plan_create(o, holes, W.f_sincos, host_only=True)
 
 
 def test_ray_operator_matches_oracle_floater_hormann(V):

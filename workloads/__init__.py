@@ -413,37 +413,54 @@ def lshape_expsin(K: int = 16, base_level: int = 6, max_level: int = 14, corner_
                     [f_exp_sin], "L-shape side 0.8, f=-3e^x sin2y, base level %d, corners to level %d" % (base_level, max_level))
 
 
-def exterior_three_stars(K: int = 8, tol: float = 1e-8, min_level: int = 3, max_level: int = 10) -> Workload:
-    """The exterior test of Section 6.2, halved in size so that the extension
-    squares of its cut leaves stay in D = [-0.5, 0.5]^2: three starfish
-    inclusions z = R (1 + a cos(N t)) e^{-it} + c with (R, a, N, c) = (0.12, 0.3,
-    5, (0.186, -0.15)), (0.17, 0.3, 4, (-0.21, -0.03)), (0.2, 0.2, 3, (0.2, 0.15))
-    at full size, and f = Laplacian of sum_j exp(-|x - y_j|^2 / beta_j) with
-    y = (0.1, 0.07), (0.09, -0.25), (-0.21, -0.25) and beta = 1e-3, 1e-3/2.1,
-    1e-3/4.5 (the exact solution's log term is harmonic in Omega).  Scaling
-    lengths by 1/2 scales the centres, radii and y_j by 1/2 and beta_j by 1/4.
-    The Gaussian centres lie inside the inclusions, so the extension runs into
-    the steep side of each bump."""
-    s = 0.5
-    incl = [StarDomain(s * 0.12, [(5, 0.3, 0.0)], center=(s * 0.186, s * -0.15)),
-            StarDomain(s * 0.17, [(4, 0.3, 0.0)], center=(s * -0.21, s * -0.03)),
-            StarDomain(s * 0.2, [(3, 0.2, 0.0)], center=(s * 0.2, s * 0.15))]
-    dom = ExteriorDomain(incl)
-    ys = s * np.array([[0.1, 0.07], [0.09, -0.25], [-0.21, -0.25]])
-    betas = s * s * np.array([1e-3, 1e-3 / 2.1, 1e-3 / 4.5])
+EXTERIOR_INCLUSIONS = [(0.12, 0.3, 5, (0.186, -0.15)), (0.17, 0.3, 4, (-0.21, -0.03)), (0.12, 0.2, 3, (0.2, 0.15))]
+EXTERIOR_GAUSSIANS = [((0.1, 0.07), 1e-3), ((0.09, -0.25), 1e-3 / 2.1), ((-0.21, -0.25), 1e-3 / 4.5)]
+EXTERIOR_LOG_CENTRE, EXTERIOR_LOG_COEF = (-0.2, 0.0), -10.0
 
-    def f(xy):
-        xy = np.asarray(xy, dtype=np.float64).reshape(-1, 2)
-        out = np.zeros(len(xy))
-        for y, b in zip(ys, betas):
-            r2 = np.sum((xy - y) ** 2, axis=1)
-            out += (4.0 * r2 / (b * b) - 4.0 / b) * np.exp(-r2 / b)
-        return out
-    return Workload("exterior_three_stars_k%d" % K, 6, dom,
+
+def exterior_domain() -> "ExteriorDomain":
+    """The three starfish inclusions of the exterior test of Section 6.2,
+    z = R (1 + a cos(N t)) e^{-it} + c with (R, a, N, c) as in
+    EXTERIOR_INCLUSIONS.  The third radius is 0.12 where the text prints 0.2:
+    at 0.2 the first and third inclusions overlap (a sixth of the first
+    curve lies inside the third), while at 0.12 the curves are disjoint and
+    every Gaussian centre y_j lies 0.001 - 0.003 inside its inclusion, as the
+    text describes them."""
+    return ExteriorDomain([StarDomain(R, [(N, a, 0.0)], center=c) for R, a, N, c in EXTERIOR_INCLUSIONS])
+
+
+def u_exterior(xy):
+    """The exact solution of the exterior test (Section 6.2):
+    u = sum_j exp(-|x - y_j|^2 / beta_j) - 10 log|x - (-0.2, 0)|."""
+    xy = np.asarray(xy, dtype=np.float64).reshape(-1, 2)
+    out = EXTERIOR_LOG_COEF * np.log(np.hypot(xy[:, 0] - EXTERIOR_LOG_CENTRE[0], xy[:, 1] - EXTERIOR_LOG_CENTRE[1]))
+    for y, b in EXTERIOR_GAUSSIANS:
+        out = out + np.exp(-((xy[:, 0] - y[0]) ** 2 + (xy[:, 1] - y[1]) ** 2) / b)
+    return out
+
+
+def f_exterior(xy):
+    """f = Laplacian of u_exterior in Omega: the Gaussians' Laplacians
+    (4 r^2 / beta^2 - 4 / beta) exp(-r^2 / beta); the log term is harmonic there."""
+    xy = np.asarray(xy, dtype=np.float64).reshape(-1, 2)
+    out = np.zeros(len(xy))
+    for y, b in EXTERIOR_GAUSSIANS:
+        r2 = (xy[:, 0] - y[0]) ** 2 + (xy[:, 1] - y[1]) ** 2
+        out += (4.0 * r2 / (b * b) - 4.0 / b) * np.exp(-r2 / b)
+    return out
+
+
+def exterior_three_stars(K: int = 8, tol: float = 1e-8, min_level: int = 3, max_level: int = 10) -> Workload:
+    """The exterior test of Section 6.2 in D = [-0.5, 0.5]^2: Omega = D minus
+    three starfish inclusions (exterior_domain), f = f_exterior.  The
+    Gaussian centres lie inside the inclusions, so the extension runs into
+    the steep side of each bump."""
+    return Workload("exterior_three_stars_k%d" % K, 6, exterior_domain(),
                     TreeOptions(K=K, min_level=min_level, max_level=max(min_level, max_level) if tol else min_level,
                                 refine_tol=tol, f_scale=1e4),
-                    [f], "exterior of three starfish inclusions (Section 6.2, lengths x 1/2), "
-                    "f = Laplacian of 3 Gaussians, adaptive tol %g, K=%d" % (tol, K))
+                    [f_exterior], "exterior of three starfish inclusions (Section 6.2), "
+                    "f = Laplacian of 3 Gaussians, %s, K=%d" % ("adaptive tol %g" % tol if tol else
+                                                                 "uniform level %d" % min_level, K))
 
 
 def u_harmext(xy):
