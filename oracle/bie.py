@@ -198,3 +198,44 @@ def solve_exterior(g: BoundaryGeometry, curve_of_node, centers, rhs, growth) -> 
     b = np.concatenate([np.asarray(rhs, dtype=np.float64), np.zeros(m - 1), [float(growth)]])
     x = np.linalg.solve(M, b)
     return ExteriorSolution(g, x[:n], x[n:], centers)
+
+
+class HoledSolution:
+    """u^H = D[sigma] + sum_k A_k log|x - s_k| inside an outer curve with holes
+    (Section 2, multiply connected interior problem), every curve
+    counter-clockwise: D uses each curve's own outward normal, which points
+    into Omega on the holes, so there the density is the paper's with its
+    sign changed."""
+
+    def __init__(self, g: BoundaryGeometry, sigma, A, centers):
+        self.g, self.sigma, self.A, self.centers = g, sigma, np.asarray(A), np.asarray(centers, dtype=np.float64)
+
+    def __call__(self, targets):
+        targets = np.asarray(targets, dtype=np.float64).reshape(-1, 2)
+        u = dlp_eval(self.g, self.sigma, targets)
+        for A, c in zip(self.A, self.centers):
+            u = u + A * np.log(np.hypot(targets[:, 0] - c[0], targets[:, 1] - c[1]))
+        return u
+
+
+def solve_holed(g: BoundaryGeometry, curve_of_node, hole_centers, rhs) -> HoledSolution:
+    """The multiply connected interior correction: curve 0 is the outer
+    boundary, curves 1..m the holes, s_k a point inside hole k.  On the
+    boundary the limit from Omega equals rhs = g - V:
+
+        (-1/2 on curve 0, +1/2 on the holes) sigma + D sigma + sum_k A_k log|y - s_k| = rhs,
+
+    (the interior jump for the outer curve, the exterior jump of each hole's
+    own double layer), with int_{Gamma_k} sigma ds = 0 on every hole
+    (eq. densconst), which removes the m homogeneous solutions."""
+    n, m = g.n, len(hole_centers)
+    curve_of_node = np.asarray(curve_of_node)
+    sw = g.s * g.w
+    M = np.zeros((n + m, n + m))
+    M[:n, :n] = dlp_matrix(g) + np.diag(np.where(curve_of_node == 0, -0.5, 0.5))
+    for k, c in enumerate(hole_centers):
+        M[:n, n + k] = np.log(np.hypot(g.y[:, 0] - c[0], g.y[:, 1] - c[1]))
+        M[n + k, :n] = sw * (curve_of_node == k + 1)
+    b = np.concatenate([np.asarray(rhs, dtype=np.float64), np.zeros(m)])
+    x = np.linalg.solve(M, b)
+    return HoledSolution(g, x[:n], x[n:], hole_centers)

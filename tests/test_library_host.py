@@ -50,6 +50,7 @@ WORKLOADS = {
     "lshape_small": lambda: W.lshape_expsin(K=8, base_level=4, max_level=8, corner_levels=5),
     "star_batch_03": lambda: W.star_batch(4)[3],   # adaptive K = 8 star of the uneven batch (3,844 leaves)
     "exterior_k8": lambda: W.exterior_three_stars(K=8, tol=1e-5, max_level=7),   # three holes, 1,726 leaves
+    "doubly_connected_l5": lambda: W.doubly_connected_harmext(5),                  # a hole in a star
 }
 
 

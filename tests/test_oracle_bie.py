@@ -1,9 +1,10 @@
 """Pins of the boundary-correction oracle (Section 5): each checks the oracle
 against a fact that does not come from it -- eigenvalues of the circle's
 Nystrom matrix, Gauss's law for the double layer, curvature in closed form,
-recovery of harmonic functions (inside one curve, and outside three with their
-fluxes), and the paper's printed errors for its saw domain (Section 6.1) and
-exterior (Section 6.2) tests -- and the planted mistakes at the end must each
+recovery of harmonic functions (inside one curve, inside a curve with a hole,
+and outside three curves, with their fluxes), and the paper's printed errors
+for its saw domain and doubly connected (Section 6.1) and exterior
+(Section 6.2) tests -- and the planted mistakes at the end must each
 fail one of them."""
 import math
 
@@ -174,6 +175,53 @@ def test_exterior_poisson_meets_the_papers_printed_errors():
         assert linf <= printed[lev][0] and l2 <= printed[lev][1], (lev, linf, l2)
 
 
+def _holed_setup():
+    dom = W.doubly_connected_domain()
+    g = B.BoundaryGeometry(dom)
+    curve = np.concatenate([np.full(d.n_panels * B.NQ, k) for k, d in enumerate(dom.curves)])
+    return dom, g, curve, [h.center for h in dom.holes]
+
+
+def test_holed_harmonic_data_are_reproduced():
+    """Inside the doubly connected domain of Section 6.1: boundary data of
+    u = e^{3x} cos 3y + 0.7 log|x - a| (a inside the hole, harmonic in Omega,
+    flux 0.7 through the hole) give A_1 = 0.7 and u, near both curves."""
+    dom, g, curve, centers = _holed_setup()
+    uh = lambda p: np.exp(3 * p[:, 0]) * np.cos(3 * p[:, 1]) + 0.7 * np.log(np.hypot(p[:, 0] - 0.01, p[:, 1] + 0.005))
+    sol = B.solve_holed(g, curve, centers, uh(g.y))
+    assert abs(sol.A[0] - 0.7) < 1e-12
+    p = np.concatenate([_near_points(dom.outer, 8, 6), _near_points(dom.holes[0], 8, 7)])
+    p = np.concatenate([p[dom.inside(p)], [[0.15, 0.0], [-0.1, 0.12]]])
+    assert np.max(np.abs(sol(p) - uh(p))) < 1e-12
+
+
+@pytest.fixture(scope="module")
+def holed_errors():
+    out = {}
+    dom, g, curve, centers = _holed_setup()
+    for lev in (4, 5):
+        wl = W.doubly_connected_harmext(lev)
+        tree = O.build_tree(wl.domain, wl.opts, wl.sources[0])
+        pts, meta = O.stencil_points(tree, wl.domain)
+        vals, _ = O.leaf_values(tree, wl.domain, wl.sources[0](pts)[:, None], meta)
+        sol = B.solve_holed(g, curve, centers, W.u_harmext(g.y) - O.volume_potential(tree, vals, g.y)[:, 0])
+        grid = W.grid_100(wl.domain)
+        e, ue = O.volume_potential(tree, vals, grid)[:, 0] + sol(grid) - W.u_harmext(grid), W.u_harmext(grid)
+        out[lev] = (np.max(np.abs(e)) / np.max(np.abs(ue)), np.linalg.norm(e) / np.linalg.norm(ue))
+    return out
+
+
+def test_doubly_connected_poisson_meets_the_papers_printed_errors(holed_errors):
+    """Section 6.1, first test, uniform trees: the paper prints relative
+    errors (l_inf, l_2) of (1.32e-4, 6.78e-6) at N = 128 (level 4) and
+    (9.88e-7, 5.18e-8) at N = 256 (level 5); measured 1.8e-5, 1.3e-6 and
+    1.8e-8, 1.3e-9."""
+    printed = {4: (0.0001317230021190127, 6.776708317503218e-06), 5: (9.882552819353315e-07, 5.17741104087048e-08)}
+    for lev, (linf, l2) in holed_errors.items():
+        assert linf <= printed[lev][0] and l2 <= printed[lev][1], (lev, linf, l2)
+    assert holed_errors[4][0] / holed_errors[5][0] > 100
+
+
 # ---------------------------------------------------------------- planted mistakes
 
 def test_wrong_jump_sign_is_caught(monkeypatch):
@@ -209,3 +257,10 @@ def test_exterior_jump_of_the_wrong_side_is_caught(monkeypatch):
     monkeypatch.setattr(B, "dlp_matrix", lambda g: real(g) - np.eye(g.n))     # planted: -1/2 + D outside
     with pytest.raises(AssertionError):
         test_exterior_harmonic_data_are_reproduced()
+
+
+def test_holes_with_the_interior_jump_are_caught(monkeypatch):
+    real = B.dlp_matrix
+    monkeypatch.setattr(B, "dlp_matrix", lambda g: real(g) - np.diag(np.where(np.arange(g.n) >= 160 * B.NQ, 1.0, 0.0)))
+    with pytest.raises(AssertionError):        # planted: -1/2 on the hole's curve too
+        test_holed_harmonic_data_are_reproduced()

@@ -172,6 +172,32 @@ class SawDomain:
         return xy, dxy
 
 
+class HoledDomain:
+    """Omega = the inside of an outer star-shaped curve minus the closures of
+    inner star-shaped holes (the multiply connected interior problem of
+    Section 2).  Panels: the outer curve's, then each hole's, every curve
+    counter-clockwise."""
+
+    def __init__(self, outer: StarDomain, holes: Sequence[StarDomain]):
+        self.outer, self.holes = outer, list(holes)
+        self.curves = [outer] + self.holes
+        self.n_panels = sum(d.n_panels for d in self.curves)
+
+    def inside(self, xy: np.ndarray) -> np.ndarray:
+        xy = np.asarray(xy, dtype=np.float64).reshape(-1, 2)
+        out = self.outer.inside(xy)
+        for h in self.holes:
+            out &= ~h.inside(xy)
+        return out
+
+    def curve(self, i: int, t) -> Tuple[np.ndarray, np.ndarray]:
+        for d in self.curves:
+            if i < d.n_panels:
+                return d.curve(i, t)
+            i -= d.n_panels
+        raise IndexError("panel index out of range")
+
+
 class PolygonDomain:
     """Polygon given by its vertices (counter-clockwise).
 
@@ -488,6 +514,25 @@ def saw_harmext(level: int = 5, K: int = 8, n_panels: Optional[int] = None) -> W
     return Workload("saw_harmext_l%d_k%d" % (level, K), 7, SawDomain(n_panels=n_panels),
                     TreeOptions(K=K, min_level=level, max_level=level), [f_harmext],
                     "saw domain (Section 6.1), u = sin(10(x+y)) + x^2 - 3y + 8 + exp(-500x^2), uniform level %d" % level)
+
+
+def doubly_connected_domain() -> "HoledDomain":
+    """Section 6.1's first test: r(theta) = sum_j c_j cos(j theta) + d_j sin(j theta)
+    with, outside, c_0 = 0.25, d_3 = c_6 = c_8 = c_10 = 0.01, c_5 = 0.02 and, for
+    the hole, c_0 = 0.05, c_2 = d_3 = c_5 = c_7 = 0.005 (sin = cos shifted by -pi/2)."""
+    h = -0.5 * np.pi
+    outer = StarDomain(0.25, [(3, 0.04, h), (6, 0.04, 0.0), (8, 0.04, 0.0), (10, 0.04, 0.0), (5, 0.08, 0.0)])
+    hole = StarDomain(0.05, [(2, 0.1, 0.0), (3, 0.1, h), (5, 0.1, 0.0), (7, 0.1, 0.0)])
+    return HoledDomain(outer, [hole])
+
+
+def doubly_connected_harmext(level: int = 5, K: int = 8) -> Workload:
+    """Section 6.1's first interior test on a uniform tree: the doubly connected
+    domain, f = Laplacian of u_harmext, Dirichlet data u_harmext on both curves."""
+    return Workload("doubly_connected_harmext_l%d_k%d" % (level, K), 8, doubly_connected_domain(),
+                    TreeOptions(K=K, min_level=level, max_level=level), [f_harmext],
+                    "doubly connected domain (Section 6.1), u = sin(10(x+y)) + x^2 - 3y + 8 + exp(-500x^2), "
+                    "uniform level %d" % level)
 
 
 def grid_100(dom, n: int = 100) -> np.ndarray:
