@@ -270,19 +270,29 @@ int vpx_potential_static(vpx_plan_t plan, const double *fe_leaf, int nrhs, int64
                          double *v_leaf, int64_t ld_v, double *v_bdry, int64_t ld_b, void *stream);
 
 /* ------------------------------------------------ boundary correction (host part)
- * Interior Dirichlet problem on a simply connected Omega (Section 5):
- * u = V[f^e] + D[sigma] with (-1/2 + D)[sigma] = g - V[f^e] on the boundary,
- * D the double layer with the outward normal (eqs. dlpot, dblker, inteq),
- * discretised on the panels' Gauss-Legendre nodes (eq. discdblpotpanel).
+ * Dirichlet problem (Section 5): u = V[f^e] + D[sigma] (+ the log terms of
+ * multiply connected and exterior domains, Section 2), with D the double
+ * layer of eqs. dlpot / dblker discretised on the panels' Gauss-Legendre
+ * nodes (eq. discdblpotpanel).  The panels form closed curves, each
+ * counter-clockwise, numbered curve by curve; D uses each curve's outward
+ * normal, so the limit from Omega is -1/2 sigma + D sigma on Omega's outer
+ * boundary and +1/2 sigma + D sigma on a curve that Omega surrounds (a hole,
+ * or an inclusion of an exterior problem).
  *
- * vpx_bie_setup computes, once per plan, the Nystrom geometry and the
- * product-integration corrections (Helsing-Ojala, Section 5) for every leaf
- * node within reach of a panel (|zeta| < 2 in the panel's coordinates).  Host
- * work only; threads on all cores.  Errors: VPX_ERR_ARG (null plan),
- * VPX_ERR_STATE (no panels; panel ends that do not meet, i.e. not one closed
- * curve; a clockwise curve).  A leaf node exactly on the boundary has no
- * defined correction. */
-int vpx_bie_setup(vpx_plan_t plan);
+ * vpx_bie_setup computes, once per plan, the Nystrom geometry, the curves and
+ * the side of Omega at each (one call of `inside` at a point just off every
+ * curve), and the product-integration corrections (Helsing-Ojala, Section 5)
+ * for every leaf node within reach of a panel (|zeta| < 2 in the panel's
+ * coordinates).  Host work only; threads on all cores.  Errors: VPX_ERR_ARG
+ * (null argument), VPX_ERR_CALLBACK, VPX_ERR_STATE (no panels; panel ends
+ * that do not close into curves; a clockwise curve; two outer curves).  A
+ * leaf node exactly on the boundary has no defined correction. */
+int vpx_bie_setup(vpx_plan_t plan, vpx_inside_cb inside, void *ctx);
+
+/* The curves found by vpx_bie_setup: their number, the outer one (-1 for an
+ * exterior problem), and per boundary node its curve and jump (+-1/2).
+ * curve_of_node and jump may be NULL.  Errors: VPX_ERR_ARG, VPX_ERR_STATE. */
+int vpx_bie_topology(vpx_plan_t plan, int *n_curves, int *outer_curve, int32_t *curve_of_node, double *jump);
 
 /* Per boundary node (n_bdry of them, panel-major): the outward unit normal
  * (nu, 2 doubles), s*w = |gamma_i'(t_j)| times the Gauss-Legendre weight, and

@@ -467,10 +467,21 @@ int vpx_potential_static(vpx_plan_t p, const double *fe, int nrhs, int64_t ld_fe
     });
 }
 
-int vpx_bie_setup(vpx_plan_t p) {
+int vpx_bie_setup(vpx_plan_t p, vpx_inside_cb inside, void *ctx) {
     return guarded([&] {
-        if (!p) fail(VPX_ERR_ARG, "null plan");
-        bie_setup(p);
+        if (!p || !inside) fail(VPX_ERR_ARG, "null argument");
+        bie_setup(p, inside, ctx);
+    });
+}
+
+int vpx_bie_topology(vpx_plan_t p, int *n_curves, int *outer_curve, int32_t *curve_of_node, double *jump) {
+    return guarded([&] {
+        if (!p || !n_curves || !outer_curve) fail(VPX_ERR_ARG, "null argument");
+        if (!p->bie.ready) fail(VPX_ERR_STATE, "vpx_bie_setup has not run");
+        *n_curves = p->bie.n_curves;
+        *outer_curve = p->bie.outer_curve;
+        if (curve_of_node) std::copy(p->bie.curve_of_node.begin(), p->bie.curve_of_node.end(), curve_of_node);
+        if (jump) std::copy(p->bie.jump.begin(), p->bie.jump.end(), jump);
     });
 }
 

@@ -1,5 +1,5 @@
-// bie_setup.cpp -- host part of the boundary correction (Section 5) for the
-// interior Dirichlet problem on a simply connected domain:
+// bie_setup.cpp -- host part of the boundary correction (Section 5); for the
+// interior Dirichlet problem on a simply connected domain
 //
 //   u = V[f^e] + D[sigma],  (-1/2 + D)[sigma] = g - V[f^e] on Gamma,
 //   D[sigma](x) = int (1/2pi) (x - y).nu(y) / |x - y|^2 sigma(y) ds_y,
@@ -13,7 +13,11 @@
 // integration, named in Section 5): in complex form a panel contributes
 // -(1/2pi) Im int sigma(tau) dtau / (tau - z).  This file computes the
 // geometry and, for every leaf node within reach of a panel, the weights that
-// replace that panel's plain terms.
+// replace that panel's plain terms.  With several closed curves (holes, or the
+// inclusions of an exterior problem, Section 2) each curve is classified by
+// the side Omega lies on, which sets the jump of its double layer: -1/2 on
+// Omega's outer boundary, +1/2 on a curve Omega surrounds (every curve
+// counter-clockwise, nu pointing out of the region it encloses).
 #include <algorithm>
 #include <cmath>
 #include <complex>
@@ -132,49 +136,89 @@ void product_weights(const PanelData &P, const cplx *tau, cplx a, cplx b, cplx z
 
 }  // namespace
 
-void bie_setup(vpx_plan *pl) {
+void bie_setup(vpx_plan *pl, vpx_inside_cb inside, void *ctx) {
     BieHost &B = pl->bie;
     if (B.ready) return;
     const int nq = pl->opt.n_quad_bdry;
     const int np = (int)(pl->bdry_ends.size() / 4);
     const size_t N = pl->bdry_xy.size() / 2;
     if (np == 0) fail(VPX_ERR_STATE, "the boundary correction needs boundary panels");
-    // one closed curve, counter-clockwise: panel i ends where panel i+1 starts
+    // closed curves: a curve runs over consecutive panels, each starting where
+    // the previous one ends, until one ends where the curve's first panel starts
     const double *E = pl->bdry_ends.data();
     double len = 0.0;
     for (int i = 0; i < np; ++i) len += std::hypot(E[4 * i + 2] - E[4 * i], E[4 * i + 3] - E[4 * i + 1]);
-    for (int i = 0; i < np; ++i) {
-        const int k = (i + 1) % np;
-        if (std::hypot(E[4 * i + 2] - E[4 * k], E[4 * i + 3] - E[4 * k + 1]) > 1e-10 * len)
-            fail(VPX_ERR_STATE, "the boundary correction needs one closed curve (panel ends must meet)");
+    const double tol = 1e-10 * len;
+    auto meets = [&](int i, int k) { return std::hypot(E[4 * i + 2] - E[4 * k], E[4 * i + 3] - E[4 * k + 1]) <= tol; };
+    std::vector<int> first_panel;
+    for (int i = 0; i < np;) {
+        const int f = i;
+        while (i < np && !meets(i, f)) {
+            if (i + 1 >= np || !meets(i, i + 1))
+                fail(VPX_ERR_STATE, "the boundary correction needs closed curves (panel ends must meet)");
+            ++i;
+        }
+        first_panel.push_back(f);
+        ++i;
     }
+    first_panel.push_back(np);
+    const int nc = (int)first_panel.size() - 1;
     std::vector<double> t, w;
     gauss_legendre(nq, t, w);
     PanelData P{t, barycentric_weights(t), {}};
     P.Dm = diff_matrix(P.t, P.bw);
     B.nq = nq;
     B.n_panels = np;
+    B.n_curves = nc;
     B.nu.assign(2 * N, 0.0);
     B.sw.assign(N, 0.0);
     B.kappa.assign(N, 0.0);
-    double area2 = 0.0;   // twice the signed area, int (x y' - y x') dt
-    for (int i = 0; i < np; ++i)
-        for (int j = 0; j < nq; ++j) {
-            const size_t q = (size_t)i * nq + j;
-            const double dx = pl->bdry_dxy[2 * q], dy = pl->bdry_dxy[2 * q + 1];
-            double ddx = 0.0, ddy = 0.0;
-            for (int k = 0; k < nq; ++k) {
-                ddx += P.Dm[(size_t)j * nq + k] * pl->bdry_dxy[2 * ((size_t)i * nq + k)];
-                ddy += P.Dm[(size_t)j * nq + k] * pl->bdry_dxy[2 * ((size_t)i * nq + k) + 1];
+    B.curve_of_node.assign(N, 0);
+    B.jump.assign(N, 0.0);
+    std::vector<double> area2(nc, 0.0);   // twice each curve's signed area, int (x y' - y x') dt
+    for (int c = 0; c < nc; ++c)
+        for (int i = first_panel[c]; i < first_panel[c + 1]; ++i)
+            for (int j = 0; j < nq; ++j) {
+                const size_t q = (size_t)i * nq + j;
+                const double dx = pl->bdry_dxy[2 * q], dy = pl->bdry_dxy[2 * q + 1];
+                double ddx = 0.0, ddy = 0.0;
+                for (int k = 0; k < nq; ++k) {
+                    ddx += P.Dm[(size_t)j * nq + k] * pl->bdry_dxy[2 * ((size_t)i * nq + k)];
+                    ddy += P.Dm[(size_t)j * nq + k] * pl->bdry_dxy[2 * ((size_t)i * nq + k) + 1];
+                }
+                const double s = std::hypot(dx, dy);
+                B.nu[2 * q] = dy / s;
+                B.nu[2 * q + 1] = -dx / s;
+                B.sw[q] = s * w[j];
+                B.kappa[q] = (dx * ddy - dy * ddx) / (s * s * s);
+                B.curve_of_node[q] = c;
+                area2[c] += w[j] * (pl->bdry_xy[2 * q] * dy - pl->bdry_xy[2 * q + 1] * dx);
             }
-            const double s = std::hypot(dx, dy);
-            B.nu[2 * q] = dy / s;
-            B.nu[2 * q + 1] = -dx / s;
-            B.sw[q] = s * w[j];
-            B.kappa[q] = (dx * ddy - dy * ddx) / (s * s * s);
-            area2 += w[j] * (pl->bdry_xy[2 * q] * dy - pl->bdry_xy[2 * q + 1] * dx);
+    for (int c = 0; c < nc; ++c)
+        if (!(area2[c] > 0.0)) fail(VPX_ERR_STATE, "the boundary correction needs counter-clockwise curves");
+    // the side of Omega: a point just off the middle node of each curve's
+    // first panel, along the curve's outward normal, is in Omega exactly when
+    // Omega lies outside the curve (a hole, or an inclusion of an exterior
+    // problem: jump +1/2); otherwise the curve is Omega's outer boundary (-1/2)
+    std::vector<double> probe(2 * nc);
+    for (int c = 0; c < nc; ++c) {
+        const size_t q = (size_t)first_panel[c] * nq + nq / 2;
+        const double L = std::hypot(E[4 * first_panel[c] + 2] - E[4 * first_panel[c]],
+                                    E[4 * first_panel[c] + 3] - E[4 * first_panel[c] + 1]);
+        probe[2 * c] = pl->bdry_xy[2 * q] + 1e-3 * L * B.nu[2 * q];
+        probe[2 * c + 1] = pl->bdry_xy[2 * q + 1] + 1e-3 * L * B.nu[2 * q + 1];
+    }
+    std::vector<uint8_t> in(nc);
+    if (inside(probe.data(), nc, in.data(), ctx) != 0) fail(VPX_ERR_CALLBACK, "inside callback failed");
+    B.outer_curve = -1;
+    for (int c = 0; c < nc; ++c) {
+        if (!in[c]) {
+            if (B.outer_curve >= 0) fail(VPX_ERR_STATE, "the boundary correction found two outer curves");
+            B.outer_curve = c;
         }
-    if (!(area2 > 0.0)) fail(VPX_ERR_STATE, "the boundary correction needs a counter-clockwise boundary");
+        for (int i = first_panel[c]; i < first_panel[c + 1]; ++i)
+            for (int j = 0; j < nq; ++j) B.jump[(size_t)i * nq + j] = in[c] ? 0.5 : -0.5;
+    }
 
     // (leaf node, panel) pairs with |zeta| < kNearRadius, i.e. the node within
     // |b - a| of the panel's chord midpoint; candidate leaves by box overlap
@@ -197,9 +241,9 @@ void bie_setup(vpx_plan *pl) {
     }
     B.corr_off.assign(nt + 1, 0);
     for (size_t q = 0; q < nt; ++q) B.corr_off[q + 1] = B.corr_off[q] + (int64_t)near_of[q].size();
-    const int64_t nc = B.corr_off[nt];
-    B.corr_panel.assign(nc, 0);
-    B.corr_w.assign((size_t)nc * nq, 0.0);
+    const int64_t n_corr = B.corr_off[nt];
+    B.corr_panel.assign(n_corr, 0);
+    B.corr_w.assign((size_t)n_corr * nq, 0.0);
     for (size_t q = 0; q < nt; ++q)
         std::copy(near_of[q].begin(), near_of[q].end(), B.corr_panel.begin() + B.corr_off[q]);
     std::vector<cplx> tau(N);

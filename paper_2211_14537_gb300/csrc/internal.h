@@ -72,8 +72,10 @@ void build_tree(const vpx_options &opt, const Callbacks &cb, HostTree &tree);
 // weights that replace that panel's Gauss-Legendre terms.
 struct BieHost {
     bool ready = false;
-    int nq = 0, n_panels = 0;
+    int nq = 0, n_panels = 0, n_curves = 0, outer_curve = -1;   // outer_curve -1: an exterior problem
     std::vector<double> nu, sw, kappa;     // outward normal (2 per node), s*w, signed curvature
+    std::vector<int32_t> curve_of_node;    // closed curve of every boundary node
+    std::vector<double> jump;              // -1/2 on the outer curve, +1/2 on curves Omega surrounds
     std::vector<int64_t> corr_off;         // [n_leaf_nodes + 1]
     std::vector<int32_t> corr_panel;       // panel of each correction
     std::vector<double> corr_w;            // [n_corr][nq]: product weight minus the plain term

@@ -167,5 +167,5 @@ void device_potential_static(vpx_plan *p, const double *fe_in, int64_t ldfe, int
                              double *vb, int64_t ldb, void *stream);
 void device_execute_host(vpx_plan *p, const double *f, int nrhs, double *v, double *vb);
 void device_net_charge(vpx_plan *p, const double *fe, int64_t ldfe, int nrhs, double *charge, void *stream);
-void bie_setup(vpx_plan *p);
+void bie_setup(vpx_plan *p, vpx_inside_cb inside, void *ctx);
 }  // namespace vpx

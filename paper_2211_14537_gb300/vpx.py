@@ -60,7 +60,7 @@ EXPORTED = [
     "vpx_leaf_nodes", "vpx_boundary_nodes", "vpx_plan_list_counts", "vpx_plan_lists", "vpx_plan_near_tables",
     "vpx_universal_matrix", "vpx_plan_ray_operator", "vpx_execute",
     "vpx_execute_batch", "vpx_autotune", "vpx_autotune_batch",
-    "vpx_extend", "vpx_potential", "vpx_potential_static", "vpx_net_charge", "vpx_bie_setup", "vpx_bie_geometry", "vpx_bie_corrections", "vpx_execute_host", "vpx_sync_status", "vpx_set_timing",
+    "vpx_extend", "vpx_potential", "vpx_potential_static", "vpx_net_charge", "vpx_bie_setup", "vpx_bie_topology", "vpx_bie_geometry", "vpx_bie_corrections", "vpx_execute_host", "vpx_sync_status", "vpx_set_timing",
     "vpx_get_timings", "vpx_pass_name", "vpx_graph_kernel_count", "vpx_check_bounded_wait", "vpx_error_string", "vpx_last_error_message", "vpx_plan_destroy",
 ]
 
@@ -100,7 +100,8 @@ def load_library(path: str = LIB_PATH):
                                      P(ctypes.c_int)]
     L.vpx_potential_static.argtypes = [vp, vp, ctypes.c_int, i64, vp, i64, vp, i64, vp]
     L.vpx_net_charge.argtypes = [vp, vp, ctypes.c_int, i64, vp, vp]
-    L.vpx_bie_setup.argtypes = [vp]
+    L.vpx_bie_setup.argtypes = [vp, INSIDE_CB, vp]
+    L.vpx_bie_topology.argtypes = [vp, P(ctypes.c_int), P(ctypes.c_int), P(i32), P(d)]
     L.vpx_bie_geometry.argtypes = [vp, P(d), P(d), P(d)]
     L.vpx_bie_corrections.argtypes = [vp, P(i64), P(i64), P(i32), P(d)]
     L.vpx_execute_host.argtypes = [vp, P(d), ctypes.c_int, P(d), P(d)]
@@ -389,7 +390,17 @@ def vpx_net_charge(plan: Plan, fe_leaf, charge, stream=None):
 
 
 def vpx_bie_setup(plan: Plan):
-    _check(load_library().vpx_bie_setup(plan.handle))
+    """Host part of the boundary correction, with the domain's own inside test."""
+    _check(load_library().vpx_bie_setup(plan.handle, plan._keep[1], None))
+
+
+def vpx_bie_topology(plan: Plan):
+    """(n_curves, outer_curve, curve_of_node (n_bdry,), jump (n_bdry,)) after vpx_bie_setup."""
+    nb = plan.sizes()[3]
+    nc, oc = ctypes.c_int(0), ctypes.c_int(0)
+    cn, jp = np.zeros(nb, dtype=np.int32), np.zeros(nb)
+    _check(load_library().vpx_bie_topology(plan.handle, ctypes.byref(nc), ctypes.byref(oc), _iptr(cn), _dptr(jp)))
+    return nc.value, oc.value, cn, jp
 
 
 def vpx_bie_geometry(plan: Plan):

@@ -363,15 +363,50 @@ def test_bie_host_part_matches_oracle(V, name):
     assert np.abs(got[ins] - uh(X[sel][ins])).max() < (1e-11 if name == "starfish_k8" else 1e-8)
 
 
-def test_bie_setup_refuses_what_it_cannot_solve(V):
-    """Several closed curves (the exterior of inclusions), a clockwise curve,
-    and no boundary at all are refused with VPX_ERR_STATE."""
-    ext = W.exterior_three_stars(K=8, tol=0, min_level=4)
-    plan = _plan(V, ext)
-    with pytest.raises(V.VpxError) as e:
-        V.vpx_bie_setup(plan)
-    assert e.value.code == V.VPX_ERR_STATE and "closed curve" in str(e.value)
+@pytest.mark.parametrize("name", ["exterior", "doubly_connected"])
+def test_bie_host_part_on_several_curves(V, name):
+    """Closed curves and the side of Omega: the exterior of three inclusions
+    (no outer curve, +1/2 on all three) and the domain with a hole (outer
+    curve 0 at -1/2, the hole at +1/2); the corrected D[sigma] equals the
+    oracle's for the densities that reproduce harmonic data there."""
+    if name == "exterior":
+        wl = W.exterior_three_stars(K=8, tol=1e-5, max_level=7)
+        curves, outer = wl.domain.inclusions, -1
+    else:
+        wl = W.doubly_connected_harmext(5)
+        curves, outer = wl.domain.curves, 0
+    plan = _plan(V, wl)
+    V.vpx_bie_setup(plan)
+    nc, oc, cn, jp = V.vpx_bie_topology(plan)
+    want_cn = np.concatenate([np.full(d.n_panels * 16, k) for k, d in enumerate(curves)])
+    assert nc == len(curves) and oc == outer and np.array_equal(cn, want_cn)
+    assert np.array_equal(jp, np.where(cn == outer, -0.5, 0.5))
+    g = B.BoundaryGeometry(wl.domain)
+    if name == "exterior":
+        cs = [d.center for d in curves]
+        uh = lambda p: sum(c * np.log(np.hypot(p[:, 0] - s[0], p[:, 1] - s[1])) for c, s in zip([1.5, -0.7, 2.0], cs))
+        sol = B.solve_exterior(g, cn, cs, uh(g.y), 0.8)
+    else:
+        uh = lambda p: np.exp(3 * p[:, 0]) * np.cos(3 * p[:, 1]) + 0.7 * np.log(np.hypot(p[:, 0], p[:, 1]))
+        sol = B.solve_holed(g, cn, [curves[1].center], uh(g.y))
+    nu, sw, _ = V.vpx_bie_geometry(plan)
+    off, pan, w = V.vpx_bie_corrections(plan)
+    X = plan.leaf_nodes()
+    rng = np.random.default_rng(10)
+    sel = rng.choice(np.nonzero(np.diff(off) > 0)[0], 150, replace=False)
+    got = np.empty(len(sel))
+    for k, q in enumerate(sel):
+        d = X[q] - g.y
+        got[k] = np.sum((d * nu).sum(1) / (d * d).sum(1) * sw * sol.sigma) / (2 * np.pi)
+        for e in range(off[q], off[q + 1]):
+            got[k] += w[e] @ sol.sigma[pan[e] * 16:(pan[e] + 1) * 16]
+    want = B.dlp_eval(g, sol.sigma, X[sel])
+    assert np.abs(got - want).max() < 1e-13 * max(1.0, np.abs(want).max())
 
+
+def test_bie_setup_refuses_what_it_cannot_solve(V):
+    """A clockwise curve, panels that do not close into curves, and no
+    boundary at all are refused with VPX_ERR_STATE."""
     class Clockwise(W.StarDomain):
         def curve(self, i, t):
             xy, d = W.StarDomain.curve(self, self.n_panels - 1 - i, -np.asarray(t))
@@ -382,6 +417,16 @@ def test_bie_setup_refuses_what_it_cannot_solve(V):
     with pytest.raises(V.VpxError) as e:
         V.vpx_bie_setup(plan)
     assert e.value.code == V.VPX_ERR_STATE and "counter-clockwise" in str(e.value)
+
+    class Open(W.StarDomain):            # the last panel stops half way
+        def curve(self, i, t):
+            if i == self.n_panels - 1:
+                t = (np.asarray(t) - 1.0) * 0.5
+            return W.StarDomain.curve(self, i, t)
+    plan = V.vpx_plan_create(o, Open(0.35, (), n_panels=16), W.f_sincos, host_only=True)
+    with pytest.raises(V.VpxError) as e:
+        V.vpx_bie_setup(plan)
+    assert e.value.code == V.VPX_ERR_STATE and "closed curves" in str(e.value)
     o = V.vpx_default_options(K=8, min_level=2, max_level=2)
     plan = V.vpx_plan_create(o, W.WholeBoxDomain(), W.f_sincos, host_only=True)
     with pytest.raises(V.VpxError) as e:
