@@ -294,6 +294,35 @@ int vpx_bie_setup(vpx_plan_t plan, vpx_inside_cb inside, void *ctx);
  * curve_of_node and jump may be NULL.  Errors: VPX_ERR_ARG, VPX_ERR_STATE. */
 int vpx_bie_topology(vpx_plan_t plan, int *n_curves, int *outer_curve, int32_t *curve_of_node, double *jump);
 
+/* The log terms: one per curve that Omega surrounds, centred at the curve's
+ * area centroid (which must lie outside Omega); n_unknowns = n_bdry + n_log,
+ * the length of the solution vector of vpx_bie_solve.  curve (n_log) and
+ * centre (2 n_log) may be NULL.  Errors: VPX_ERR_ARG, VPX_ERR_STATE. */
+int vpx_bie_log_terms(vpx_plan_t plan, int *n_log, int32_t *curve, double *centre, int64_t *n_unknowns);
+
+/* Solve for the density and the log coefficients (device plans; the system
+ * was assembled and inverted on the device by vpx_bie_setup, Gauss-Jordan
+ * with partial pivoting):  boundary rows  jump sigma + D sigma
+ * [+ (1/2pi) int sigma, exterior] + sum_k A_k log|y - s_k| = g - vb;  one
+ * zero-circulation row per hole (for an exterior problem per inclusion but
+ * the last) and, for an exterior problem, sum_k A_k = growth, the coefficient
+ * of log|x| that u - V must have at infinity (A - Q, Section 2).
+ *   g, vb  device, n_bdry doubles: Dirichlet data and V at the boundary nodes
+ *   sol    device, n_unknowns doubles, written: sigma (panel-major), then A_k
+ * One right-hand side; two launches on `stream`.  Errors: VPX_ERR_ARG,
+ * VPX_ERR_STATE (host-only plan, no setup). */
+int vpx_bie_solve(vpx_plan_t plan, const double *g, const double *vb, double growth, double *sol, void *stream);
+
+/* u = V + D[sigma] + sum_k A_k log|x - s_k| [+ (1/2pi) int sigma, exterior]
+ * at every leaf node: the kernel summed over all boundary nodes in FP64, plus
+ * the product-integration corrections of the panels near each node.  At leaf
+ * nodes outside Omega the value is that of the same formula there, not u.
+ *   sol    device, n_unknowns doubles (vpx_bie_solve's output)
+ *   v_leaf device, n_leaf_nodes doubles (V, e.g. vpx_potential's output)
+ *   u_leaf device, n_leaf_nodes doubles, written (may equal v_leaf)
+ * Errors: VPX_ERR_ARG, VPX_ERR_STATE. */
+int vpx_bie_eval(vpx_plan_t plan, const double *sol, const double *v_leaf, double *u_leaf, void *stream);
+
 /* Per boundary node (n_bdry of them, panel-major): the outward unit normal
  * (nu, 2 doubles), s*w = |gamma_i'(t_j)| times the Gauss-Legendre weight, and
  * the signed curvature (gamma'' from differentiating the degree-(nq-1)

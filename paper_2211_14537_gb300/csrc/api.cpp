@@ -485,6 +485,35 @@ int vpx_bie_topology(vpx_plan_t p, int *n_curves, int *outer_curve, int32_t *cur
     });
 }
 
+int vpx_bie_log_terms(vpx_plan_t p, int *n_log, int32_t *curve, double *centre, int64_t *n_unknowns) {
+    return guarded([&] {
+        if (!p || !n_log || !n_unknowns) fail(VPX_ERR_ARG, "null argument");
+        if (!p->bie.ready) fail(VPX_ERR_STATE, "vpx_bie_setup has not run");
+        *n_log = p->bie.n_log;
+        *n_unknowns = p->bie.n_unknowns;
+        if (curve) std::copy(p->bie.log_curve.begin(), p->bie.log_curve.end(), curve);
+        if (centre) std::copy(p->bie.log_centre.begin(), p->bie.log_centre.end(), centre);
+    });
+}
+
+int vpx_bie_solve(vpx_plan_t p, const double *g, const double *vb, double growth, double *sol, void *stream) {
+    return guarded([&] {
+        if (!p || !g || !vb || !sol) fail(VPX_ERR_ARG, "null argument");
+        if (p->host_only) fail(VPX_ERR_STATE, "host-only plan");
+        if (!p->bie.ready) fail(VPX_ERR_STATE, "vpx_bie_setup has not run");
+        device_bie_solve(p, g, vb, growth, sol, stream);
+    });
+}
+
+int vpx_bie_eval(vpx_plan_t p, const double *sol, const double *v_leaf, double *u_leaf, void *stream) {
+    return guarded([&] {
+        if (!p || !sol || !v_leaf || !u_leaf) fail(VPX_ERR_ARG, "null argument");
+        if (p->host_only) fail(VPX_ERR_STATE, "host-only plan");
+        if (!p->bie.ready) fail(VPX_ERR_STATE, "vpx_bie_setup has not run");
+        device_bie_eval(p, sol, v_leaf, u_leaf, stream);
+    });
+}
+
 int vpx_bie_geometry(vpx_plan_t p, double *nu, double *sw, double *kappa) {
     return guarded([&] {
         if (!p) fail(VPX_ERR_ARG, "null plan");

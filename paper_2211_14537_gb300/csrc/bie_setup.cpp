@@ -220,6 +220,36 @@ void bie_setup(vpx_plan *pl, vpx_inside_cb inside, void *ctx) {
             for (int j = 0; j < nq; ++j) B.jump[(size_t)i * nq + j] = in[c] ? 0.5 : -0.5;
     }
 
+    // one log term per curve that Omega surrounds, centred at the curve's
+    // area centroid (Green: A = 1/2 int (x y' - y x'), A cx = 1/2 int x^2 y',
+    // A cy = -1/2 int y^2 x'), which must lie outside Omega
+    B.log_curve.clear();
+    B.log_centre.clear();
+    for (int c = 0; c < nc; ++c) {
+        if (c == B.outer_curve) continue;
+        double a2 = 0.0, mx = 0.0, my = 0.0;
+        for (int i = first_panel[c]; i < first_panel[c + 1]; ++i)
+            for (int j = 0; j < nq; ++j) {
+                const size_t q = (size_t)i * nq + j;
+                const double x = pl->bdry_xy[2 * q], yq = pl->bdry_xy[2 * q + 1];
+                const double dx = pl->bdry_dxy[2 * q], dy = pl->bdry_dxy[2 * q + 1];
+                a2 += w[j] * (x * dy - yq * dx);
+                mx += w[j] * x * x * dy;
+                my -= w[j] * yq * yq * dx;
+            }
+        B.log_curve.push_back(c);
+        B.log_centre.push_back(mx / a2);
+        B.log_centre.push_back(my / a2);
+    }
+    B.n_log = (int)B.log_curve.size();
+    if (B.n_log) {
+        std::vector<uint8_t> cin(B.n_log);
+        if (inside(B.log_centre.data(), B.n_log, cin.data(), ctx) != 0) fail(VPX_ERR_CALLBACK, "inside callback failed");
+        for (int k = 0; k < B.n_log; ++k)
+            if (cin[k]) fail(VPX_ERR_STATE, "the centroid of a hole or inclusion lies in Omega (no log centre)");
+    }
+    B.n_unknowns = (int)N + B.n_log;
+
     // (leaf node, panel) pairs with |zeta| < kNearRadius, i.e. the node within
     // |b - a| of the panel's chord midpoint; candidate leaves by box overlap
     const auto &L = pl->tree.leaves;
@@ -273,6 +303,7 @@ void bie_setup(vpx_plan *pl, vpx_inside_cb inside, void *ctx) {
         if (q0 < q1) th.emplace_back(work, q0, q1);
     }
     for (auto &x : th) x.join();
+    if (!pl->host_only) device_bie_setup(pl);
     B.ready = true;
 }
 

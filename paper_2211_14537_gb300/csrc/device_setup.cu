@@ -541,6 +541,7 @@ void device_copy_near_tables(vpx_plan *p, double *out) {
 }
 
 void device_free(vpx_plan *p) {
+    device_bie_free(p);
     DevTree &d = p->dt;
     dev_free(d.box_level); dev_free(d.box_ix); dev_free(d.box_iy); dev_free(d.box_parent);
     dev_free(d.box_child0); dev_free(d.box_leaf); dev_free(d.box_morton); dev_free(d.box_nz);

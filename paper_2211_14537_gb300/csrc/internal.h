@@ -70,8 +70,20 @@ void build_tree(const vpx_options &opt, const Callbacks &cb, HostTree &tree);
 // Host part of the interior Dirichlet correction (Section 5): Nystrom
 // geometry and, per leaf node within reach of a panel, the product-integration
 // weights that replace that panel's Gauss-Legendre terms.
+struct BieDev {                          // device copies (device plans only)
+    double *y = nullptr, *nu = nullptr, *sw = nullptr, *leaf_xy = nullptr, *corr_w = nullptr, *log_c = nullptr;
+    int64_t *corr_off = nullptr;
+    int32_t *corr_panel = nullptr;
+    double *rhs = nullptr, *cst = nullptr;
+    double *minv = nullptr;              // [n_unknowns][n_unknowns] inverse of the Nystrom system
+};
+
 struct BieHost {
     bool ready = false;
+    int n_log = 0, n_unknowns = 0;         // log terms; N + n_log
+    std::vector<int32_t> log_curve;        // curve of each log term (the holes, or every inclusion)
+    std::vector<double> log_centre;        // a point inside that curve, 2 per term
+    BieDev dev;
     int nq = 0, n_panels = 0, n_curves = 0, outer_curve = -1;   // outer_curve -1: an exterior problem
     std::vector<double> nu, sw, kappa;     // outward normal (2 per node), s*w, signed curvature
     std::vector<int32_t> curve_of_node;    // closed curve of every boundary node

@@ -168,4 +168,8 @@ void device_potential_static(vpx_plan *p, const double *fe_in, int64_t ldfe, int
 void device_execute_host(vpx_plan *p, const double *f, int nrhs, double *v, double *vb);
 void device_net_charge(vpx_plan *p, const double *fe, int64_t ldfe, int nrhs, double *charge, void *stream);
 void bie_setup(vpx_plan *p, vpx_inside_cb inside, void *ctx);
+void device_bie_setup(vpx_plan *p);
+void device_bie_solve(vpx_plan *p, const double *g, const double *vb, double growth, double *sol, void *stream);
+void device_bie_eval(vpx_plan *p, const double *sol, const double *v, double *u, void *stream);
+void device_bie_free(vpx_plan *p);
 }  // namespace vpx

@@ -60,7 +60,7 @@ EXPORTED = [
     "vpx_leaf_nodes", "vpx_boundary_nodes", "vpx_plan_list_counts", "vpx_plan_lists", "vpx_plan_near_tables",
     "vpx_universal_matrix", "vpx_plan_ray_operator", "vpx_execute",
     "vpx_execute_batch", "vpx_autotune", "vpx_autotune_batch",
-    "vpx_extend", "vpx_potential", "vpx_potential_static", "vpx_net_charge", "vpx_bie_setup", "vpx_bie_topology", "vpx_bie_geometry", "vpx_bie_corrections", "vpx_execute_host", "vpx_sync_status", "vpx_set_timing",
+    "vpx_extend", "vpx_potential", "vpx_potential_static", "vpx_net_charge", "vpx_bie_setup", "vpx_bie_topology", "vpx_bie_log_terms", "vpx_bie_solve", "vpx_bie_eval", "vpx_bie_geometry", "vpx_bie_corrections", "vpx_execute_host", "vpx_sync_status", "vpx_set_timing",
     "vpx_get_timings", "vpx_pass_name", "vpx_graph_kernel_count", "vpx_check_bounded_wait", "vpx_error_string", "vpx_last_error_message", "vpx_plan_destroy",
 ]
 
@@ -102,6 +102,9 @@ def load_library(path: str = LIB_PATH):
     L.vpx_net_charge.argtypes = [vp, vp, ctypes.c_int, i64, vp, vp]
     L.vpx_bie_setup.argtypes = [vp, INSIDE_CB, vp]
     L.vpx_bie_topology.argtypes = [vp, P(ctypes.c_int), P(ctypes.c_int), P(i32), P(d)]
+    L.vpx_bie_log_terms.argtypes = [vp, P(ctypes.c_int), P(i32), P(d), P(i64)]
+    L.vpx_bie_solve.argtypes = [vp, vp, vp, d, vp, vp]
+    L.vpx_bie_eval.argtypes = [vp, vp, vp, vp, vp]
     L.vpx_bie_geometry.argtypes = [vp, P(d), P(d), P(d)]
     L.vpx_bie_corrections.argtypes = [vp, P(i64), P(i64), P(i32), P(d)]
     L.vpx_execute_host.argtypes = [vp, P(d), ctypes.c_int, P(d), P(d)]
@@ -401,6 +404,27 @@ def vpx_bie_topology(plan: Plan):
     cn, jp = np.zeros(nb, dtype=np.int32), np.zeros(nb)
     _check(load_library().vpx_bie_topology(plan.handle, ctypes.byref(nc), ctypes.byref(oc), _iptr(cn), _dptr(jp)))
     return nc.value, oc.value, cn, jp
+
+
+def vpx_bie_log_terms(plan: Plan):
+    """(curve (n_log,), centre (n_log, 2), n_unknowns) after vpx_bie_setup."""
+    L = load_library()
+    n, nu = ctypes.c_int(0), ctypes.c_int64(0)
+    _check(L.vpx_bie_log_terms(plan.handle, ctypes.byref(n), None, None, ctypes.byref(nu)))
+    cv, ce = np.zeros(n.value, dtype=np.int32), np.zeros((n.value, 2))
+    _check(L.vpx_bie_log_terms(plan.handle, ctypes.byref(n), _iptr(cv), _dptr(ce), ctypes.byref(nu)))
+    return cv, ce, nu.value
+
+
+def vpx_bie_solve(plan: Plan, g, vb, sol, growth: float = 0.0, stream=None):
+    """Device tensors: g, vb (n_bdry), sol (n_unknowns) written."""
+    _check(load_library().vpx_bie_solve(plan.handle, _tptr(g), _tptr(vb), float(growth), _tptr(sol),
+                                        _stream_handle(stream)))
+
+
+def vpx_bie_eval(plan: Plan, sol, v_leaf, u_leaf, stream=None):
+    """Device tensors: u_leaf = V + the correction at every leaf node."""
+    _check(load_library().vpx_bie_eval(plan.handle, _tptr(sol), _tptr(v_leaf), _tptr(u_leaf), _stream_handle(stream)))
 
 
 def vpx_bie_geometry(plan: Plan):

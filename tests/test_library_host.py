@@ -340,6 +340,8 @@ def test_bie_host_part_matches_oracle(V, name):
         V.vpx_bie_geometry(plan)
     assert e.value.code == V.VPX_ERR_STATE
     V.vpx_bie_setup(plan)
+    nc, oc, _, jp = V.vpx_bie_topology(plan)
+    assert nc == 1 and oc == 0 and np.all(jp == -0.5) and V.vpx_bie_log_terms(plan)[2] == len(jp)
     nu, sw, ka = V.vpx_bie_geometry(plan)
     g = B.BoundaryGeometry(wl.domain)
     assert np.abs(nu - g.nu).max() < 1e-15 and np.abs(sw - g.s * g.w).max() < 1e-16
@@ -381,6 +383,11 @@ def test_bie_host_part_on_several_curves(V, name):
     want_cn = np.concatenate([np.full(d.n_panels * 16, k) for k, d in enumerate(curves)])
     assert nc == len(curves) and oc == outer and np.array_equal(cn, want_cn)
     assert np.array_equal(jp, np.where(cn == outer, -0.5, 0.5))
+    # one log term per curve that Omega surrounds, centred inside that curve
+    lc, centre, n_unknowns = V.vpx_bie_log_terms(plan)
+    assert list(lc) == [c for c in range(nc) if c != outer] and n_unknowns == len(cn) + len(lc)
+    for c, p in zip(lc, centre):
+        assert curves[c].inside(p[None, :])[0] and not wl.domain.inside(p[None, :])[0]
     g = B.BoundaryGeometry(wl.domain)
     if name == "exterior":
         cs = [d.center for d in curves]
