@@ -439,3 +439,68 @@ def test_bie_setup_refuses_what_it_cannot_solve(V):
     with pytest.raises(V.VpxError) as e:
         V.vpx_bie_setup(plan)
     assert e.value.code == V.VPX_ERR_STATE
+
+
+@pytest.mark.parametrize("name", ["starfish", "doubly_connected", "exterior"])
+def test_bie_system_from_the_library_data_reproduces_harmonic_data(V, name):
+    """The Nystrom system that vpx_bie_solve inverts, written out as the header
+    defines it from the library's own geometry, jumps, log centres and
+    corrections (numpy here; the device assembles the same rows): solved for
+    the boundary values of a harmonic u, it returns the fluxes through holes
+    and inclusions and reproduces u at leaf nodes in Omega, near the boundary
+    and far from it."""
+    if name == "starfish":
+        wl, growth = W.starfish_gaussian(K=8, tol=1e-8, max_level=8), 0.0
+        uh = lambda p: np.exp(3 * p[:, 0]) * np.cos(3 * p[:, 1]) + p[:, 0] * p[:, 1]
+        flux = []
+    elif name == "doubly_connected":
+        wl, growth, flux = W.doubly_connected_harmext(5), 0.0, [0.7]
+        uh = lambda p: np.exp(3 * p[:, 0]) * np.cos(3 * p[:, 1]) + 0.7 * np.log(np.hypot(p[:, 0] - 0.01, p[:, 1]))
+    else:
+        wl = W.exterior_three_stars(K=8, tol=1e-5, max_level=7)
+        cs, flux = [d.center for d in wl.domain.inclusions], [1.5, -0.7, 2.0]
+        growth = sum(flux)
+        uh = lambda p: (sum(c * np.log(np.hypot(p[:, 0] - s[0], p[:, 1] - s[1])) for c, s in zip(flux, cs)) +
+                        (1 / ((p[:, 0] + 1j * p[:, 1]) - complex(*cs[0]))).real)
+    plan = _plan(V, wl)
+    V.vpx_bie_setup(plan)
+    _, oc, cn, jp = V.vpx_bie_topology(plan)
+    lc, centre, nunk = V.vpx_bie_log_terms(plan)
+    nu, sw, ka = V.vpx_bie_geometry(plan)
+    off, pan, w = V.vpx_bie_corrections(plan)
+    y = plan.boundary_nodes()
+    N, nl, ext = len(y), len(lc), oc < 0
+    d = y[:, None, :] - y[None, :, :]
+    r2 = (d * d).sum(2)
+    np.fill_diagonal(r2, 1.0)
+    M = np.zeros((nunk, nunk))
+    M[:N, :N] = (d * nu[None, :, :]).sum(2) / r2 / (2 * np.pi) * sw[None, :]
+    np.fill_diagonal(M[:N, :N], -ka / (4 * np.pi) * sw)
+    M[:N, :N] += np.diag(jp) + (np.outer(np.ones(N), sw) / (2 * np.pi) if ext else 0.0)
+    for k in range(nl):
+        M[:N, N + k] = np.log(np.hypot(y[:, 0] - centre[k, 0], y[:, 1] - centre[k, 1]))
+        if ext and k == nl - 1:
+            M[N + k, N:] = 1.0
+        else:
+            M[N + k, :N] = sw * (cn == lc[k])
+    rhs = np.concatenate([uh(y), np.zeros(nl)])
+    if ext:
+        rhs[-1] = growth
+    sol = np.linalg.solve(M, rhs)
+    sig, A = sol[:N], sol[N:]
+    assert np.allclose(A, flux, atol=1e-10, rtol=0)
+    X = plan.leaf_nodes()
+    ins = wl.domain.inside(X)
+    rng = np.random.default_rng(11)
+    sel = np.concatenate([rng.choice(np.nonzero((np.diff(off) > 0) & ins)[0], 120, replace=False),
+                          rng.choice(np.nonzero(ins)[0], 40, replace=False)])
+    u = np.empty(len(sel))
+    for k, q in enumerate(sel):
+        dq = X[q] - y
+        u[k] = np.sum((dq * nu).sum(1) / (dq * dq).sum(1) * sw * sig) / (2 * np.pi)
+        for e in range(off[q], off[q + 1]):
+            u[k] += w[e] @ sig[pan[e] * 16:(pan[e] + 1) * 16]
+        u[k] += sum(A[j] * np.log(np.hypot(*(X[q] - centre[j]))) for j in range(nl))
+        if ext:
+            u[k] += np.sum(sw * sig) / (2 * np.pi)
+    assert np.abs(u - uh(X[sel])).max() < 1e-11
