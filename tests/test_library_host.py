@@ -412,8 +412,8 @@ def test_bie_host_part_on_several_curves(V, name):
 
 
 def test_bie_setup_refuses_what_it_cannot_solve(V):
-    """A clockwise curve, panels that do not close into curves, and no
-    boundary at all are refused with VPX_ERR_STATE."""
+    """A clockwise curve, panels that do not close into curves, no boundary
+    at all, and a hole without a log centre are refused with VPX_ERR_STATE."""
     class Clockwise(W.StarDomain):
         def curve(self, i, t):
             xy, d = W.StarDomain.curve(self, self.n_panels - 1 - i, -np.asarray(t))
@@ -439,6 +439,16 @@ def test_bie_setup_refuses_what_it_cannot_solve(V):
     with pytest.raises(V.VpxError) as e:
         V.vpx_bie_setup(plan)
     assert e.value.code == V.VPX_ERR_STATE
+    # a C-shaped hole: its centroid lies in the opening, i.e. in Omega, so the
+    # hole has no log centre there
+    c_hole = W.PolygonDomain([(0.1, 0.1), (-0.1, 0.1), (-0.1, -0.1), (0.1, -0.1), (0.1, -0.06), (-0.06, -0.06),
+                              (-0.06, 0.06), (0.1, 0.06)], panels_per_side=2)
+    holed = W.HoledDomain(W.StarDomain(0.4, (), n_panels=32), [c_hole])
+    o = V.vpx_default_options(K=8, min_level=4, max_level=4)
+    plan = V.vpx_plan_create(o, holed, W.f_sincos, host_only=True)
+    with pytest.raises(V.VpxError) as e:
+        V.vpx_bie_setup(plan)
+    assert e.value.code == V.VPX_ERR_STATE and "centroid" in str(e.value)
 
 
 @pytest.mark.parametrize("name", ["starfish", "doubly_connected", "exterior"])
