@@ -399,10 +399,26 @@ def run_batch(args, rank=0, world=1):
     print(json.dumps(out), flush=True)
 
 
-def oracle_sample(wl, n_sample, seed=2213, nthreads=0, lines=False):
+def algorithmic_flops(K, p, n_leaves, lc):
+    """Real flops per right-hand side of each pass from the list sizes
+    (complex multiply-add = 8): near 2K^4 + 2K^2 per pair, L2M and L2T
+    4(p+1)K^2 per leaf, lists i+ and i- 4(p+1)K^2 per pair, M2M and L2L
+    4(p+1)^2 per child box, M2L 8(p+1)^2 per pair."""
+    P = p + 1
+    children = max(int(lc.get("n_boxes", 0)) - 1, 0)
+    out = {"near": lc["near"] * (2 * K ** 4 + 2 * K * K), "l2m": 4 * P * K * K * n_leaves,
+           "m2m": 4 * P * P * children, "m2l": 8 * P * P * lc["m2l"], "s2l": 4 * P * K * K * lc["s2l"],
+           "m2t": 4 * P * K * K * lc["m2t"], "l2l": 4 * P * P * children, "l2t": 4 * P * K * K * n_leaves}
+    out["total"] = sum(out.values())
+    return out
+
+
+def oracle_sample(wl, n_sample, seed=2213, nthreads=0, lines=False, n_one_core=0):
     """Oracle: own tree + extension (the universal stencil, or along lines),
-    then V at a seeded sample of leaf nodes.
-    Returns (indices, V at those, seconds of the potential, threads)."""
+    then V at a seeded sample of leaf nodes on all host cores and, if
+    n_one_core, at the first n_one_core of them again on one core.
+    Returns (indices, V at those, seconds of the potential, threads,
+    (targets, seconds) on one core or None)."""
     from oracle import oracle as O
     tree = O.build_tree(wl.domain, wl.opts, wl.sources[0])
     if lines:
@@ -417,7 +433,13 @@ def oracle_sample(wl, n_sample, seed=2213, nthreads=0, lines=False):
     t0 = time.perf_counter()
     Vs = O.volume_potential(tree, vals, nodes[idx], nthreads)[:, 0]
     dt = time.perf_counter() - t0
-    return idx, Vs, dt, O.lib().orc_max_threads() if nthreads == 0 else nthreads
+    one = None
+    if n_one_core:
+        sub1 = nodes[idx[:n_one_core]]
+        t1 = time.perf_counter()
+        O.volume_potential(tree, vals, sub1, 1)
+        one = (len(sub1), time.perf_counter() - t1)
+    return idx, Vs, dt, O.lib().orc_max_threads() if nthreads == 0 else nthreads, one
 
 
 def main():
@@ -440,13 +462,18 @@ def main():
     cpu = None
     if rank == 0 and world == 1:
         try:
-            idx, Vs, dt, thr = oracle_sample(res[forms[0]]["wl"], args.oracle_sample, lines=args.ext_mode == "lines")
+            idx, Vs, dt, thr, one = oracle_sample(res[forms[0]]["wl"], args.oracle_sample, lines=args.ext_mode == "lines",
+                                                  n_one_core=0 if args.no_cpu_baseline else 96)
             for f in forms:
                 errs[f] = float(np.max(np.abs(res[f]["v"][idx] - Vs)) / np.max(np.abs(Vs)))
             if not args.no_cpu_baseline:
                 cpu = {"value": len(idx) / dt, "unit": UNIT, "cores": thr, "kind": "oracle",
                        "sample": "direct-quadrature V at %d of %d leaf nodes (seeded), oracle tree+extension "
-                                 "excluded, %.1f s" % (len(idx), res[forms[0]]["nt"], dt)}
+                                 "excluded, %.1f s" % (len(idx), res[forms[0]]["nt"], dt),
+                       "extrapolated_full_s": res[forms[0]]["tg"] * dt / len(idx)}
+                if one:
+                    cpu["one_core"] = {"value": one[0] / one[1], "unit": UNIT, "cores": 1,
+                                       "sample": "the first %d of those targets, %.1f s" % one}
         except Exception as e:   # noqa: BLE001 - report, do not hide the GPU number
             cpu = {"value": None, "error": repr(e)}
     # headline: the fastest form whose error against the oracle meets 1e-10
@@ -487,6 +514,7 @@ def main():
                    "boundary_targets": r["nb"], "stencil_points": r["ns"], "nrhs": args.nrhs,
                    "precision": head, "near_pairs": r["lc"]["near"], "m2l_pairs": r["lc"]["m2l"],
                    "s2l_pairs": r["lc"]["s2l"], "m2t_pairs": r["lc"]["m2t"], "levels": r["lc"]["n_levels"],
+                   "algorithmic_flops_per_rhs": algorithmic_flops(r["K"], args.p, r["n_leaves"], r["lc"]),
                    "l2": "flushed between timed steps (256 MB write, outside the events)",
                    "graph": "vpx_execute replays a captured CUDA graph",
                    "setup_s": round(r["setup_s"], 3), "parallelism": "replicas" if world > 1 else "single",

@@ -72,7 +72,7 @@ def test_bench_line_carries_the_contract_keys(monkeypatch, capsys, wl_name):
                     e2e_s=3e-4, v=np.ones(182272), K=16, graph_kernels=24, tune=(7, 0), times=[0.2, 0.21, 0.19])
 
     monkeypatch.setattr(bench, "run_gpu", fake_run_gpu)
-    monkeypatch.setattr(bench, "oracle_sample", lambda wl, n, **k: (np.arange(10), np.ones(10), 1.0, 16))
+    monkeypatch.setattr(bench, "oracle_sample", lambda wl, n, **k: (np.arange(10), np.ones(10), 1.0, 16, (4, 2.0)))
     monkeypatch.setattr(sys, "argv", ["bench.py", "--workload", wl_name])
     bench.main()
     d = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
@@ -88,6 +88,12 @@ def test_bench_line_carries_the_contract_keys(monkeypatch, capsys, wl_name):
     assert set(d["e2e"]) >= {"value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step"}
     assert d["e2e"]["h2d_bytes_per_step"] == 8 * 129619 and d["gpu_launches"] == 24 * d["steps"]
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 16
+    assert d["cpu_baseline"]["one_core"] == {"value": 2.0, "unit": d["unit"], "cores": 1,
+                                             "sample": "the first 4 of those targets, 2.0 s"}
+    assert d["cpu_baseline"]["extrapolated_full_s"] == pytest.approx(184832 / 10.0)
+    fl = d["config"]["algorithmic_flops_per_rhs"]
+    assert fl["near"] == 4900 * (2 * 16 ** 4 + 2 * 256) and fl["m2l"] == 8 * 41 ** 2 * 14104
+    assert fl["total"] == sum(v for k, v in fl.items() if k != "total")
     assert d["forms"]["mixed"]["median_ms_per_step"] == pytest.approx(0.2)
     assert "latency_floor_us" in d                                             # None without a GPU
     assert d["config"]["workload"] == bench.workload(wl_name).name
