@@ -56,7 +56,7 @@ def test_reduce_on_one_rank_is_identity():
     assert bench.reduce_over_ranks(3.0, 7, "cpu", 1) == (3.0, 7.0)
 
 
-@pytest.mark.parametrize("wl_name", ["starfish", "exterior"])
+@pytest.mark.parametrize("wl_name", ["starfish", "exterior", "disk-multi-rhs"])
 def test_bench_line_carries_the_contract_keys(monkeypatch, capsys, wl_name):
     """bench.main() on one rank, the GPU run and the oracle sample replaced by
     fixed results: one JSON line with the keys of the benchmark contract."""
@@ -98,6 +98,7 @@ def test_bench_line_carries_the_contract_keys(monkeypatch, capsys, wl_name):
     assert "latency_floor_us" in d                                             # None without a GPU
     assert d["config"]["workload"] == bench.workload(wl_name).name
     assert bench.DOMAIN_LABEL[wl_name] in d["data"]
+    assert d["scaling"] == ("strong" if wl_name == "disk-multi-rhs" else "weak")
 
 
 def test_plan_options_of_the_bench(monkeypatch):
@@ -113,3 +114,13 @@ def test_plan_options_of_the_bench(monkeypatch):
             o = bench.plan_options(V, wl, args, prec)
             assert (o.K, o.p, o.precision, o.max_rhs, o.ext_mode, o.rbf_eps) == (16, args.p, code, 1, mode, 0.0)
             assert o.refine_tol == wl.opts.refine_tol and o.max_level == wl.opts.max_level
+
+
+@pytest.mark.parametrize("world", [1, 2, 3, 5, 8])
+def test_rhs_blocks_cover_every_column_once(world):
+    """The 64 right-hand sides of the multi-RHS workload split into
+    contiguous blocks whose sizes differ by at most one."""
+    blocks = [bench.rhs_block(64, r, world) for r in range(world)]
+    assert sum(blocks, []) == list(range(64))
+    sizes = [len(b) for b in blocks]
+    assert max(sizes) - min(sizes) <= 1
