@@ -1,8 +1,10 @@
 """CPU-side checks of the library: the shared object loads and exports every
-function declared in include/vpx.h; the host tree (Section 4 rules) equals the
-oracle's tree; the interaction lists (the routine the device kernel runs,
-here executed on the host) count every (target leaf, source leaf) pair
-exactly once across near, list i, list i+ and list i- (Fig. tree_levels)."""
+function declared in include/vpx.h, and a C99 program links against it; the
+host tree (Section 4 rules) equals the oracle's tree; the interaction lists
+(built on the host and uploaded) count every (target leaf, source leaf) pair
+exactly once across near, list i, list i+ and list i- (Fig. tree_levels); the
+stencil, the operators and the boundary-correction host part equal the
+oracle's."""
 import os
 import re
 from collections import defaultdict
@@ -35,6 +37,31 @@ def test_library_exports_every_declared_symbol(V):
     for n in names:
         assert hasattr(L, n), n
     assert set(V.EXPORTED) == names
+
+
+def test_c99_program_links_against_the_library(V, tmp_path):
+    """The header is plain C (C99, pedantic, warnings as errors) and a C caller
+    gets the defaults and the error strings without a GPU."""
+    import subprocess
+    src = tmp_path / "caller.c"
+    src.write_text(
+        '#include <stdio.h>\n#include "vpx.h"\n'
+        "int main(void) {\n"
+        "    vpx_options o;\n"
+        "    if (vpx_default_options(&o) != VPX_OK) return 1;\n"
+        '    printf("%d %d %d %s\\n", o.K, o.p, o.n_quad_bdry, vpx_error_string(VPX_ERR_DOMAIN));\n'
+        "    return vpx_default_options(NULL) == VPX_ERR_ARG ? 0 : 2;\n"
+        "}\n")
+    lib = os.path.dirname(V.LIB_PATH)
+    exe = tmp_path / "caller"
+    subprocess.run(["gcc", "-std=c99", "-pedantic", "-Wall", "-Wextra", "-Werror", str(src), "-I",
+                    os.path.join(ROOT, "include"), "-L", lib, "-lvpx", "-Wl,-rpath," + lib, "-o", str(exe)],
+                   check=True, capture_output=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    K, p, nq, msg = r.stdout.split(maxsplit=3)
+    o = V.vpx_default_options()
+    assert (int(K), int(p), int(nq)) == (o.K, o.p, o.n_quad_bdry) and "root box" in msg
 
 
 def _plan(V, wl, host_only=True):
