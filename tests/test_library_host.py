@@ -78,6 +78,7 @@ WORKLOADS = {
     "star_batch_03": lambda: W.star_batch(4)[3],   # adaptive K = 8 star of the uneven batch (3,844 leaves)
     "exterior_k8": lambda: W.exterior_three_stars(K=8, tol=1e-5, max_level=7),   # three holes, 1,726 leaves
     "doubly_connected_l5": lambda: W.doubly_connected_harmext(5),                  # a hole in a star
+    "square_l5": lambda: W.square_pwsmooth(5),                                      # rotated square, graded corners
 }
 
 
@@ -355,13 +356,14 @@ def test_ray_operator_matches_oracle_floater_hormann(V):
     assert np.all(np.abs(got - want) <= 64 * EPS * lam * fmag)
 
 
-@pytest.mark.parametrize("name", ["starfish_k8", "saw_l5"])
+@pytest.mark.parametrize("name", ["starfish_k8", "saw_l5", "square_l5"])
 def test_bie_host_part_matches_oracle(V, name):
     """Boundary correction, host part (Section 5): normals, s*w and curvature
     equal the oracle's; the plain sum plus the library's product-integration
     corrections reproduces the oracle's D[sigma] at leaf nodes near and far
     from the boundary, for the density of harmonic Dirichlet data."""
-    wl = W.starfish_gaussian(K=8, tol=1e-8, max_level=8) if name == "starfish_k8" else W.saw_harmext(5)
+    wl = {"starfish_k8": lambda: W.starfish_gaussian(K=8, tol=1e-8, max_level=8), "saw_l5": lambda: W.saw_harmext(5),
+          "square_l5": lambda: W.square_pwsmooth(5)}[name]()
     plan = _plan(V, wl)
     with pytest.raises(V.VpxError) as e:
         V.vpx_bie_geometry(plan)
@@ -372,7 +374,9 @@ def test_bie_host_part_matches_oracle(V, name):
     nu, sw, ka = V.vpx_bie_geometry(plan)
     g = B.BoundaryGeometry(wl.domain)
     assert np.abs(nu - g.nu).max() < 1e-15 and np.abs(sw - g.s * g.w).max() < 1e-16
-    assert np.abs(ka - g.kappa).max() < 1e-12 * np.abs(g.kappa).max()
+    # the square's flat panels have kappa = 0; both sides then return the rounding
+    # of differentiating a constant gamma' on panels down to 2^-10 of a side
+    assert np.abs(ka - g.kappa).max() < 1e-12 * np.abs(g.kappa).max() + 1e-9
     off, pan, w = V.vpx_bie_corrections(plan)
     uh = lambda p: np.exp(3 * p[:, 0]) * np.cos(3 * p[:, 1]) + p[:, 0] * p[:, 1]
     sigma = B.solve_density(g, uh(g.y))
@@ -389,7 +393,7 @@ def test_bie_host_part_matches_oracle(V, name):
     want = B.dlp_eval(g, sigma, X[sel])
     assert np.abs(got - want).max() < 1e-13 * np.abs(want).max()
     ins = wl.domain.inside(X[sel])
-    assert np.abs(got[ins] - uh(X[sel][ins])).max() < (1e-11 if name == "starfish_k8" else 1e-8)
+    assert np.abs(got[ins] - uh(X[sel][ins])).max() < {"starfish_k8": 1e-11, "saw_l5": 1e-8, "square_l5": 1e-8}[name]
 
 
 @pytest.mark.parametrize("name", ["exterior", "doubly_connected"])

@@ -535,6 +535,49 @@ def doubly_connected_harmext(level: int = 5, K: int = 8) -> Workload:
                     "uniform level %d" % level)
 
 
+SQUARE_CENTRE, SQUARE_SIDE, SQUARE_ANGLE = (0.01, -0.02), 0.5, np.pi / 3
+SQUARE_POINTS = np.array([[-0.35, -0.135], [-0.09, 0.42], [0.445, 0.09], [0.135, -0.405]])
+SQUARE_BETA = 800.0
+
+
+def u_square(xy):
+    """Section 6.3's solution, read as u = -2 sum_j (Ei(-beta r_j^2) - log r_j^2),
+    r_j = |x - x_j|, beta = 800: smooth everywhere (the two logarithmic
+    singularities at x_j cancel), with Laplacian 8 beta sum_j exp(-beta r_j^2)."""
+    from scipy.special import expi
+    xy = np.asarray(xy, dtype=np.float64).reshape(-1, 2)
+    out = np.zeros(len(xy))
+    for x in SQUARE_POINTS:
+        r2 = (xy[:, 0] - x[0]) ** 2 + (xy[:, 1] - x[1]) ** 2
+        out += -2.0 * (expi(-SQUARE_BETA * r2) - np.log(r2))
+    return out
+
+
+def f_square(xy):
+    """f = Laplacian of u_square = 8 beta sum_j exp(-beta |x - x_j|^2)."""
+    xy = np.asarray(xy, dtype=np.float64).reshape(-1, 2)
+    out = np.zeros(len(xy))
+    for x in SQUARE_POINTS:
+        out += 8.0 * SQUARE_BETA * np.exp(-SQUARE_BETA * ((xy[:, 0] - x[0]) ** 2 + (xy[:, 1] - x[1]) ** 2))
+    return out
+
+
+def square_domain(panels_per_side: int = 16, corner_levels: int = 10) -> PolygonDomain:
+    """Section 6.3: the square of side 0.5 centred at (0.01, -0.02), rotated by
+    pi/3, counter-clockwise; panels graded dyadically toward the corners."""
+    c, h, a = np.array(SQUARE_CENTRE), 0.5 * SQUARE_SIDE, SQUARE_ANGLE
+    rot = np.array([[np.cos(a), -np.sin(a)], [np.sin(a), np.cos(a)]])
+    verts = [tuple(c + rot @ np.array(v)) for v in [(-h, -h), (h, -h), (h, h), (-h, h)]]
+    return PolygonDomain(verts, panels_per_side, corner_levels)
+
+
+def square_pwsmooth(level: int = 5, K: int = 8) -> Workload:
+    """Section 6.3's piecewise smooth test on a uniform tree."""
+    return Workload("square_pwsmooth_l%d_k%d" % (level, K), 9, square_domain(),
+                    TreeOptions(K=K, min_level=level, max_level=level), [f_square],
+                    "rotated square (Section 6.3), f = 8 beta sum exp(-beta |x - x_j|^2), uniform level %d" % level)
+
+
 def grid_100(dom, n: int = 100) -> np.ndarray:
     """The points of a uniform n x n grid on D (endpoints included) inside Omega,
     where Section 6 measures the solution's error."""
