@@ -56,7 +56,7 @@ def test_reduce_on_one_rank_is_identity():
     assert bench.reduce_over_ranks(3.0, 7, "cpu", 1) == (3.0, 7.0)
 
 
-@pytest.mark.parametrize("wl_name", ["starfish", "exterior", "disk-multi-rhs"])
+@pytest.mark.parametrize("wl_name", ["starfish", "exterior", "disk-multi-rhs", "doubly-connected"])
 def test_bench_line_carries_the_contract_keys(monkeypatch, capsys, wl_name):
     """bench.main() on one rank, the GPU run and the oracle sample replaced by
     fixed results: one JSON line with the keys of the benchmark contract."""
