@@ -79,6 +79,7 @@ WORKLOADS = {
     "exterior_k8": lambda: W.exterior_three_stars(K=8, tol=1e-5, max_level=7),   # three holes, 1,726 leaves
     "doubly_connected_l5": lambda: W.doubly_connected_harmext(5),                  # a hole in a star
     "square_l5": lambda: W.square_pwsmooth(5),                                      # rotated square, graded corners
+    "doubly_connected_adaptive": W.doubly_connected_adaptive,                       # the paper's timing run: 3,778 leaves
 }
 
 
