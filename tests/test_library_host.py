@@ -546,3 +546,23 @@ def test_bie_system_from_the_library_data_reproduces_harmonic_data(V, name):
         if ext:
             u[k] += np.sum(sw * sig) / (2 * np.pi)
     assert np.abs(u - uh(X[sel])).max() < 1e-11
+
+
+def test_bie_device_calls_refuse_host_only_plans_and_missing_setup(V):
+    """vpx_bie_solve and vpx_bie_eval check their plan before touching any
+    pointer: a host-only plan, or a plan without vpx_bie_setup, is refused."""
+    torch = pytest.importorskip("torch")
+    wl = W.disk_sincos(level=3)
+    plan = _plan(V, wl)
+    x = torch.zeros(8, dtype=torch.float64)
+    calls = (lambda: V.vpx_bie_solve(plan, x, x, x, stream=0), lambda: V.vpx_bie_eval(plan, x, x, x, stream=0))
+    for call in calls:
+        with pytest.raises(V.VpxError) as e:
+            call()
+        assert e.value.code == V.VPX_ERR_STATE
+    V.vpx_bie_setup(plan)
+    for call in calls:
+        with pytest.raises(V.VpxError) as e:
+            call()
+        assert e.value.code == V.VPX_ERR_STATE and "host-only" in str(e.value)
+    assert V.load_library().vpx_bie_solve(plan.handle, None, None, 0.0, None, None) == V.VPX_ERR_ARG
