@@ -568,9 +568,12 @@ def main():
 
 def run_reference(args, world):
     """The oracle as the reference arm: each step = direct-quadrature V at a
-    bounded seeded sample of the same workload's leaf nodes."""
+    bounded seeded sample of the leaf nodes of the workload named by
+    --workload (the first tree of the batch)."""
     from oracle import oracle as O
-    wl = workload()
+    import workloads as W
+    # the same workload as the GPU arm's line (for the batch, its first tree)
+    wl = W.star_batch(1)[0] if args.workload == "star-batch" else workload(args.workload)
     tree = O.build_tree(wl.domain, wl.opts, wl.sources[0])
     pts, meta = O.stencil_points(tree, wl.domain)
     vals, _ = O.leaf_values(tree, wl.domain, wl.sources[0](pts)[:, None], meta)

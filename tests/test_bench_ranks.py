@@ -124,3 +124,21 @@ def test_rhs_blocks_cover_every_column_once(world):
     assert sum(blocks, []) == list(range(64))
     sizes = [len(b) for b in blocks]
     assert max(sizes) - min(sizes) <= 1
+
+
+def test_reference_arm_follows_the_workload(monkeypatch, capsys):
+    """bench.py --impl reference times the oracle on the workload the GPU arm
+    names (here the multi-RHS disk, with the oracle's potential replaced by a
+    fast stand-in), and prints the reference line's keys."""
+    import json
+    import sys
+    import numpy as np
+    from oracle import oracle as O
+    monkeypatch.setattr(O, "volume_potential", lambda tree, vals, pts, *a: np.zeros((len(pts), 1)))
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--workload", "disk-multi-rhs",
+                                      "--steps", "2", "--warmup", "1"])
+    bench.main()
+    d = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert d["impl"] == "reference" and d["config"]["workload"] == bench.workload("disk-multi-rhs").name
+    assert d["steps"] == 2 and d["cpu_baseline"]["kind"] == "oracle"
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
