@@ -134,17 +134,11 @@ void product_weights(const PanelData &P, const cplx *tau, cplx a, cplx b, cplx z
     for (int j = 0; j < n; ++j) lam[j] = p[j];
 }
 
-}  // namespace
-
-void bie_setup(vpx_plan *pl, vpx_inside_cb inside, void *ctx) {
-    BieHost &B = pl->bie;
-    if (B.ready) return;
-    const int nq = pl->opt.n_quad_bdry;
+// Closed curves: a curve runs over consecutive panels, each starting where the
+// previous one ends, until one ends where the curve's first panel starts.
+// Returns the first panel of every curve, then the panel count.
+std::vector<int> split_curves(const vpx_plan *pl) {
     const int np = (int)(pl->bdry_ends.size() / 4);
-    const size_t N = pl->bdry_xy.size() / 2;
-    if (np == 0) fail(VPX_ERR_STATE, "the boundary correction needs boundary panels");
-    // closed curves: a curve runs over consecutive panels, each starting where
-    // the previous one ends, until one ends where the curve's first panel starts
     const double *E = pl->bdry_ends.data();
     double len = 0.0;
     for (int i = 0; i < np; ++i) len += std::hypot(E[4 * i + 2] - E[4 * i], E[4 * i + 3] - E[4 * i + 1]);
@@ -162,22 +156,22 @@ void bie_setup(vpx_plan *pl, vpx_inside_cb inside, void *ctx) {
         ++i;
     }
     first_panel.push_back(np);
-    const int nc = (int)first_panel.size() - 1;
-    std::vector<double> t, w;
-    gauss_legendre(nq, t, w);
-    PanelData P{t, barycentric_weights(t), {}};
-    P.Dm = diff_matrix(P.t, P.bw);
-    B.nq = nq;
-    B.n_panels = np;
-    B.n_curves = nc;
+    return first_panel;
+}
+
+// Normals, s*w, curvature and the curve of every node; every curve must be
+// counter-clockwise (positive signed area, twice it = int (x y' - y x') dt).
+void node_geometry(const vpx_plan *pl, const std::vector<int> &first, const PanelData &P, const std::vector<double> &w,
+                   BieHost &B) {
+    const int nq = B.nq, nc = B.n_curves;
+    const size_t N = pl->bdry_xy.size() / 2;
     B.nu.assign(2 * N, 0.0);
     B.sw.assign(N, 0.0);
     B.kappa.assign(N, 0.0);
     B.curve_of_node.assign(N, 0);
-    B.jump.assign(N, 0.0);
-    std::vector<double> area2(nc, 0.0);   // twice each curve's signed area, int (x y' - y x') dt
+    std::vector<double> area2(nc, 0.0);
     for (int c = 0; c < nc; ++c)
-        for (int i = first_panel[c]; i < first_panel[c + 1]; ++i)
+        for (int i = first[c]; i < first[c + 1]; ++i)
             for (int j = 0; j < nq; ++j) {
                 const size_t q = (size_t)i * nq + j;
                 const double dx = pl->bdry_dxy[2 * q], dy = pl->bdry_dxy[2 * q + 1];
@@ -196,39 +190,49 @@ void bie_setup(vpx_plan *pl, vpx_inside_cb inside, void *ctx) {
             }
     for (int c = 0; c < nc; ++c)
         if (!(area2[c] > 0.0)) fail(VPX_ERR_STATE, "the boundary correction needs counter-clockwise curves");
-    // the side of Omega: a point just off the middle node of each curve's
-    // first panel, along the curve's outward normal, is in Omega exactly when
-    // Omega lies outside the curve (a hole, or an inclusion of an exterior
-    // problem: jump +1/2); otherwise the curve is Omega's outer boundary (-1/2)
+}
+
+// The side of Omega: a point just off the middle node of each curve's first
+// panel, along the curve's outward normal, is in Omega exactly when Omega lies
+// outside the curve (a hole, or an inclusion of an exterior problem: jump
+// +1/2); otherwise the curve is Omega's outer boundary (-1/2).
+void curve_sides(const vpx_plan *pl, const std::vector<int> &first, BieHost &B, vpx_inside_cb inside, void *ctx) {
+    const int nq = B.nq, nc = B.n_curves;
+    const double *E = pl->bdry_ends.data();
     std::vector<double> probe(2 * nc);
     for (int c = 0; c < nc; ++c) {
-        const size_t q = (size_t)first_panel[c] * nq + nq / 2;
-        const double L = std::hypot(E[4 * first_panel[c] + 2] - E[4 * first_panel[c]],
-                                    E[4 * first_panel[c] + 3] - E[4 * first_panel[c] + 1]);
+        const size_t q = (size_t)first[c] * nq + nq / 2;
+        const int f = first[c];
+        const double L = std::hypot(E[4 * f + 2] - E[4 * f], E[4 * f + 3] - E[4 * f + 1]);
         probe[2 * c] = pl->bdry_xy[2 * q] + 1e-3 * L * B.nu[2 * q];
         probe[2 * c + 1] = pl->bdry_xy[2 * q + 1] + 1e-3 * L * B.nu[2 * q + 1];
     }
     std::vector<uint8_t> in(nc);
     if (inside(probe.data(), nc, in.data(), ctx) != 0) fail(VPX_ERR_CALLBACK, "inside callback failed");
     B.outer_curve = -1;
+    B.jump.assign(pl->bdry_xy.size() / 2, 0.0);
     for (int c = 0; c < nc; ++c) {
         if (!in[c]) {
             if (B.outer_curve >= 0) fail(VPX_ERR_STATE, "the boundary correction found two outer curves");
             B.outer_curve = c;
         }
-        for (int i = first_panel[c]; i < first_panel[c + 1]; ++i)
+        for (int i = first[c]; i < first[c + 1]; ++i)
             for (int j = 0; j < nq; ++j) B.jump[(size_t)i * nq + j] = in[c] ? 0.5 : -0.5;
     }
+}
 
-    // one log term per curve that Omega surrounds, centred at the curve's
-    // area centroid (Green: A = 1/2 int (x y' - y x'), A cx = 1/2 int x^2 y',
-    // A cy = -1/2 int y^2 x'), which must lie outside Omega
+// One log term per curve that Omega surrounds, centred at the curve's area
+// centroid (Green: A = 1/2 int (x y' - y x'), A cx = 1/2 int x^2 y',
+// A cy = -1/2 int y^2 x'), which must lie outside Omega.
+void log_terms(const vpx_plan *pl, const std::vector<int> &first, const std::vector<double> &w, BieHost &B,
+               vpx_inside_cb inside, void *ctx) {
+    const int nq = B.nq;
     B.log_curve.clear();
     B.log_centre.clear();
-    for (int c = 0; c < nc; ++c) {
+    for (int c = 0; c < B.n_curves; ++c) {
         if (c == B.outer_curve) continue;
         double a2 = 0.0, mx = 0.0, my = 0.0;
-        for (int i = first_panel[c]; i < first_panel[c + 1]; ++i)
+        for (int i = first[c]; i < first[c + 1]; ++i)
             for (int j = 0; j < nq; ++j) {
                 const size_t q = (size_t)i * nq + j;
                 const double x = pl->bdry_xy[2 * q], yq = pl->bdry_xy[2 * q + 1];
@@ -248,13 +252,19 @@ void bie_setup(vpx_plan *pl, vpx_inside_cb inside, void *ctx) {
         for (int k = 0; k < B.n_log; ++k)
             if (cin[k]) fail(VPX_ERR_STATE, "the centroid of a hole or inclusion lies in Omega (no log centre)");
     }
-    B.n_unknowns = (int)N + B.n_log;
+    B.n_unknowns = (int)(pl->bdry_xy.size() / 2) + B.n_log;
+}
 
-    // (leaf node, panel) pairs with |zeta| < kNearRadius, i.e. the node within
-    // |b - a| of the panel's chord midpoint; candidate leaves by box overlap
+// Product-integration corrections: for every (leaf node, panel) pair with
+// |zeta| < kNearRadius, i.e. the node within |b - a| of the panel's chord
+// midpoint (candidate leaves by box overlap), the Helsing-Ojala weights minus
+// the panel's plain terms, CSR over the leaf nodes; computed on all cores.
+void near_corrections(const vpx_plan *pl, const PanelData &P, BieHost &B) {
+    const int nq = B.nq, np = B.n_panels;
+    const double *E = pl->bdry_ends.data();
     const auto &L = pl->tree.leaves;
     const int KK = pl->KK;
-    const size_t nt = pl->leaf_xy.size() / 2;
+    const size_t nt = pl->leaf_xy.size() / 2, N = pl->bdry_xy.size() / 2;
     std::vector<std::vector<int32_t>> near_of(nt);
     for (int i = 0; i < np; ++i) {
         const double mx = 0.5 * (E[4 * i] + E[4 * i + 2]), my = 0.5 * (E[4 * i + 1] + E[4 * i + 3]);
@@ -303,6 +313,26 @@ void bie_setup(vpx_plan *pl, vpx_inside_cb inside, void *ctx) {
         if (q0 < q1) th.emplace_back(work, q0, q1);
     }
     for (auto &x : th) x.join();
+}
+
+}  // namespace
+
+void bie_setup(vpx_plan *pl, vpx_inside_cb inside, void *ctx) {
+    BieHost &B = pl->bie;
+    if (B.ready) return;
+    if (pl->bdry_ends.empty()) fail(VPX_ERR_STATE, "the boundary correction needs boundary panels");
+    const std::vector<int> first = split_curves(pl);
+    B.nq = pl->opt.n_quad_bdry;
+    B.n_panels = (int)(pl->bdry_ends.size() / 4);
+    B.n_curves = (int)first.size() - 1;
+    std::vector<double> t, w;
+    gauss_legendre(B.nq, t, w);
+    PanelData P{t, barycentric_weights(t), {}};
+    P.Dm = diff_matrix(P.t, P.bw);
+    node_geometry(pl, first, P, w, B);
+    curve_sides(pl, first, B, inside, ctx);
+    log_terms(pl, first, w, B, inside, ctx);
+    near_corrections(pl, P, B);
     if (!pl->host_only) device_bie_setup(pl);
     B.ready = true;
 }
