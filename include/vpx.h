@@ -309,8 +309,9 @@ int vpx_bie_log_terms(vpx_plan_t plan, int *n_log, int32_t *curve, double *centr
  * of log|x| that u - V must have at infinity (A - Q, Section 2).
  *   g, vb  device, n_bdry doubles: Dirichlet data and V at the boundary nodes
  *   sol    device, n_unknowns doubles, written: sigma (panel-major), then A_k
- * One right-hand side; two launches on `stream`.  Errors: VPX_ERR_ARG,
- * VPX_ERR_STATE (host-only plan, no setup). */
+ * One right-hand side; two launches on `stream`.  The plan holds one
+ * right-hand-side buffer: calls on one plan must be serialised (one stream).
+ * Errors: VPX_ERR_ARG, VPX_ERR_STATE (host-only plan, no setup). */
 int vpx_bie_solve(vpx_plan_t plan, const double *g, const double *vb, double growth, double *sol, void *stream);
 
 /* u = V + D[sigma] + sum_k A_k log|x - s_k| [+ (1/2pi) int sigma, exterior]
