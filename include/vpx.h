@@ -324,6 +324,16 @@ int vpx_bie_solve(vpx_plan_t plan, const double *g, const double *vb, double gro
  * Errors: VPX_ERR_ARG, VPX_ERR_STATE. */
 int vpx_bie_eval(vpx_plan_t plan, const double *sol, const double *v_leaf, double *u_leaf, void *stream);
 
+/* Each boundary node's double-layer term (density 1) as a multipole of the
+ * leaf that holds it, in the box FMM's scaled form: for a leaf of side L and
+ * centre c, Phi(z) = a_0 log(z - c) + sum_{k>=1} at_k (L / (z - c))^k with
+ * (1/2pi) Re Phi the potential; here a_0 = 0 and at_k = -i gamma'(t_j) w_j
+ * (1/L) ((y - c) / L)^(k-1) (complex, stored Re, Im).  *n_coef = 2(p + 1)
+ * doubles per node; out (n_bdry x n_coef, row-major) may be NULL.  These are
+ * the source terms through which the density enters the FMM passes.
+ * Errors: VPX_ERR_ARG, VPX_ERR_STATE (vpx_bie_setup has not run). */
+int vpx_bie_dipole_multipoles(vpx_plan_t plan, int *n_coef, double *out);
+
 /* Per boundary node (n_bdry of them, panel-major): the outward unit normal
  * (nu, 2 doubles), s*w = |gamma_i'(t_j)| times the Gauss-Legendre weight, and
  * the signed curvature (gamma'' from differentiating the degree-(nq-1)

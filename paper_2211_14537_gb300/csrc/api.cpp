@@ -514,6 +514,15 @@ int vpx_bie_eval(vpx_plan_t p, const double *sol, const double *v_leaf, double *
     });
 }
 
+int vpx_bie_dipole_multipoles(vpx_plan_t p, int *n_coef, double *out) {
+    return guarded([&] {
+        if (!p || !n_coef) fail(VPX_ERR_ARG, "null argument");
+        if (!p->bie.ready) fail(VPX_ERR_STATE, "vpx_bie_setup has not run");
+        *n_coef = 2 * p->P;
+        if (out) std::copy(p->bie.p2m.begin(), p->bie.p2m.end(), out);
+    });
+}
+
 int vpx_bie_geometry(vpx_plan_t p, double *nu, double *sw, double *kappa) {
     return guarded([&] {
         if (!p) fail(VPX_ERR_ARG, "null plan");

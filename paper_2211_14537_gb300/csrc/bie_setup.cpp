@@ -315,6 +315,32 @@ void near_corrections(const vpx_plan *pl, const PanelData &P, BieHost &B) {
     for (auto &x : th) x.join();
 }
 
+// Each boundary node's double-layer term as a multipole of the leaf that holds
+// it, in the box FMM's scaled form Phi(z) = a_0 log(z - c) + sum_k at_k
+// (L / (z - c))^k, with (1/2pi) Re Phi the potential.  In complex form the node
+// contributes Re(q / (z - tau)) with q = -i gamma'(t_j) w_j sigma / (2pi), and
+// 1/(z - tau) = sum_{k>=1} (tau - c)^(k-1) / (z - c)^k, so for sigma = 1
+//   a_0 = 0,  at_k = -i gamma' w (1/L) ((tau - c) / L)^(k-1).
+void dipole_multipoles(const vpx_plan *pl, const std::vector<double> &w, BieHost &B) {
+    const int nq = B.nq, P = pl->P;
+    const size_t N = pl->bdry_xy.size() / 2;
+    B.p2m.assign(N * 2 * P, 0.0);
+    for (size_t q = 0; q < N; ++q) {
+        const Leaf &lf = pl->tree.leaves[pl->bdry_leaf[q]];
+        const double L = std::ldexp(1.0, -lf.level);
+        const cplx c(-0.5 + (lf.ix + 0.5) * L, -0.5 + (lf.iy + 0.5) * L);
+        const cplx tau(pl->bdry_xy[2 * q], pl->bdry_xy[2 * q + 1]);
+        const cplx dtau(pl->bdry_dxy[2 * q], pl->bdry_dxy[2 * q + 1]);
+        cplx a = cplx(0.0, -1.0) * dtau * (w[q % nq] / L);
+        const cplx r = (tau - c) / L;
+        for (int k = 1; k < P; ++k) {
+            B.p2m[q * 2 * P + 2 * k] = a.real();
+            B.p2m[q * 2 * P + 2 * k + 1] = a.imag();
+            a *= r;
+        }
+    }
+}
+
 }  // namespace
 
 void bie_setup(vpx_plan *pl, vpx_inside_cb inside, void *ctx) {
@@ -333,6 +359,7 @@ void bie_setup(vpx_plan *pl, vpx_inside_cb inside, void *ctx) {
     curve_sides(pl, first, B, inside, ctx);
     log_terms(pl, first, w, B, inside, ctx);
     near_corrections(pl, P, B);
+    dipole_multipoles(pl, w, B);
     if (!pl->host_only) device_bie_setup(pl);
     B.ready = true;
 }

@@ -91,6 +91,7 @@ struct BieHost {
     std::vector<int64_t> corr_off;         // [n_leaf_nodes + 1]
     std::vector<int32_t> corr_panel;       // panel of each correction
     std::vector<double> corr_w;            // [n_corr][nq]: product weight minus the plain term
+    std::vector<double> p2m;               // [N][2P]: each node's dipole (sigma = 1) as a multipole of its leaf
 };
 
 // ------------------------------------------------------- stencil / extension

@@ -60,7 +60,7 @@ EXPORTED = [
     "vpx_leaf_nodes", "vpx_boundary_nodes", "vpx_plan_list_counts", "vpx_plan_lists", "vpx_plan_near_tables",
     "vpx_universal_matrix", "vpx_plan_ray_operator", "vpx_execute",
     "vpx_execute_batch", "vpx_autotune", "vpx_autotune_batch",
-    "vpx_extend", "vpx_potential", "vpx_potential_static", "vpx_net_charge", "vpx_bie_setup", "vpx_bie_topology", "vpx_bie_log_terms", "vpx_bie_solve", "vpx_bie_eval", "vpx_bie_geometry", "vpx_bie_corrections", "vpx_execute_host", "vpx_sync_status", "vpx_set_timing",
+    "vpx_extend", "vpx_potential", "vpx_potential_static", "vpx_net_charge", "vpx_bie_setup", "vpx_bie_topology", "vpx_bie_log_terms", "vpx_bie_solve", "vpx_bie_eval", "vpx_bie_dipole_multipoles", "vpx_bie_geometry", "vpx_bie_corrections", "vpx_execute_host", "vpx_sync_status", "vpx_set_timing",
     "vpx_get_timings", "vpx_pass_name", "vpx_graph_kernel_count", "vpx_check_bounded_wait", "vpx_error_string", "vpx_last_error_message", "vpx_plan_destroy",
 ]
 
@@ -105,6 +105,7 @@ def load_library(path: str = LIB_PATH):
     L.vpx_bie_log_terms.argtypes = [vp, P(ctypes.c_int), P(i32), P(d), P(i64)]
     L.vpx_bie_solve.argtypes = [vp, vp, vp, d, vp, vp]
     L.vpx_bie_eval.argtypes = [vp, vp, vp, vp, vp]
+    L.vpx_bie_dipole_multipoles.argtypes = [vp, P(ctypes.c_int), P(d)]
     L.vpx_bie_geometry.argtypes = [vp, P(d), P(d), P(d)]
     L.vpx_bie_corrections.argtypes = [vp, P(i64), P(i64), P(i32), P(d)]
     L.vpx_execute_host.argtypes = [vp, P(d), ctypes.c_int, P(d), P(d)]
@@ -425,6 +426,16 @@ def vpx_bie_solve(plan: Plan, g, vb, sol, growth: float = 0.0, stream=None):
 def vpx_bie_eval(plan: Plan, sol, v_leaf, u_leaf, stream=None):
     """Device tensors: u_leaf = V + the correction at every leaf node."""
     _check(load_library().vpx_bie_eval(plan.handle, _tptr(sol), _tptr(v_leaf), _tptr(u_leaf), _stream_handle(stream)))
+
+
+def vpx_bie_dipole_multipoles(plan: Plan):
+    """(n_bdry, p + 1) complex: each node's unit double-layer term as a scaled multipole of its leaf."""
+    L = load_library()
+    n = ctypes.c_int(0)
+    _check(L.vpx_bie_dipole_multipoles(plan.handle, ctypes.byref(n), None))
+    out = np.zeros((plan.sizes()[3], n.value))
+    _check(L.vpx_bie_dipole_multipoles(plan.handle, ctypes.byref(n), _dptr(out)))
+    return out[:, 0::2] + 1j * out[:, 1::2]
 
 
 def vpx_bie_geometry(plan: Plan):

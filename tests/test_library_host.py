@@ -566,3 +566,37 @@ def test_bie_device_calls_refuse_host_only_plans_and_missing_setup(V):
             call()
         assert e.value.code == V.VPX_ERR_STATE and "host-only" in str(e.value)
     assert V.load_library().vpx_bie_solve(plan.handle, None, None, 0.0, None, None) == V.VPX_ERR_ARG
+
+
+def test_dipole_multipoles_reproduce_the_double_layer_far_away(V):
+    """The density enters the box FMM through each boundary node's multipole
+    about its leaf: summed over a leaf's nodes and evaluated 2 to 5 leaf sides
+    away, (1/2pi) Re sum_k at_k (L / (z - c))^k equals the direct sum of the
+    double-layer kernel over those nodes (p = 40: to rounding)."""
+    wl = W.starfish_gaussian(K=8, tol=1e-8, max_level=8)
+    o = V.vpx_default_options(K=8, min_level=wl.opts.min_level, max_level=wl.opts.max_level,
+                              refine_tol=wl.opts.refine_tol, f_scale=wl.opts.f_scale, p=40)
+    plan = V.vpx_plan_create(o, wl.domain, wl.sources[0], host_only=True)
+    V.vpx_bie_setup(plan)
+    M = V.vpx_bie_dipole_multipoles(plan)
+    assert M.shape[1] == 41 and np.all(M[:, 0] == 0)
+    nu, sw, _ = V.vpx_bie_geometry(plan)
+    y = plan.boundary_nodes()
+    tree = O.build_tree(wl.domain, wl.opts, wl.sources[0])
+    leaf_of = np.array([O.locate_leaf(tree, p) for p in y])
+    sigma = np.cos(3 * np.arange(len(y)) * 2 * np.pi / len(y)) + 0.3
+    rng = np.random.default_rng(12)
+    for li in rng.choice(np.unique(leaf_of), 6, replace=False):
+        nodes = np.nonzero(leaf_of == li)[0]
+        lev, ix, iy = tree.leaves[li]
+        L = 2.0 ** -lev
+        c = complex(-0.5 + (ix + 0.5) * L, -0.5 + (iy + 0.5) * L)
+        a = M[nodes].T @ sigma[nodes]
+        for dist in (2.0, 3.5, 5.0):
+            ang = rng.uniform(0, 2 * np.pi)
+            z = c + dist * L * np.exp(1j * ang)
+            k = np.arange(41)
+            phi = np.sum(a[1:] * (L / (z - c)) ** k[1:])
+            d = np.array([z.real, z.imag]) - y[nodes]
+            direct = np.sum((d * nu[nodes]).sum(1) / (d * d).sum(1) * sw[nodes] * sigma[nodes]) / (2 * np.pi)
+            assert abs(phi.real / (2 * np.pi) - direct) <= 1e-13 * np.sum(np.abs(sw[nodes] * sigma[nodes])) / L
