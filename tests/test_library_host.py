@@ -572,7 +572,8 @@ def test_dipole_multipoles_reproduce_the_double_layer_far_away(V):
     """The density enters the box FMM through each boundary node's multipole
     about its leaf: summed over a leaf's nodes and evaluated 2 to 5 leaf sides
     away, (1/2pi) Re sum_k at_k (L / (z - c))^k equals the direct sum of the
-    double-layer kernel over those nodes (p = 40: to rounding)."""
+    double-layer kernel over those nodes (p = 40: to rounding); so does the
+    local expansion of the same nodes about a box three sides away (list i+)."""
     wl = W.starfish_gaussian(K=8, tol=1e-8, max_level=8)
     o = V.vpx_default_options(K=8, min_level=wl.opts.min_level, max_level=wl.opts.max_level,
                               refine_tol=wl.opts.refine_tol, f_scale=wl.opts.f_scale, p=40)
@@ -600,3 +601,16 @@ def test_dipole_multipoles_reproduce_the_double_layer_far_away(V):
             d = np.array([z.real, z.imag]) - y[nodes]
             direct = np.sum((d * nu[nodes]).sum(1) / (d * d).sum(1) * sw[nodes] * sigma[nodes]) / (2 * np.pi)
             assert abs(phi.real / (2 * np.pi) - direct) <= 1e-13 * np.sum(np.abs(sw[nodes] * sigma[nodes])) / L
+        # the same nodes as a local expansion about a box of side L two to four
+        # sides away (list i+): bt_l = i gamma' w L^l / (tau - c)^(l+1), with
+        # gamma' w = s w (-nu_y + i nu_x) on a counter-clockwise curve
+        gw = sw[nodes] * (-nu[nodes, 1] + 1j * nu[nodes, 0])
+        tau = y[nodes, 0] + 1j * y[nodes, 1]
+        cT = c + 3.0 * L * np.exp(1j * rng.uniform(0, 2 * np.pi))
+        b = np.array([np.sum(1j * gw * sigma[nodes] * L ** l / (tau - cT) ** (l + 1)) for l in range(41)])
+        for _ in range(3):
+            z = cT + 0.5 * L * rng.uniform(-1, 1) + 0.5j * L * rng.uniform(-1, 1)
+            psi = np.sum(b * ((z - cT) / L) ** np.arange(41))
+            d = np.array([z.real, z.imag]) - y[nodes]
+            direct = np.sum((d * nu[nodes]).sum(1) / (d * d).sum(1) * sw[nodes] * sigma[nodes]) / (2 * np.pi)
+            assert abs(psi.real / (2 * np.pi) - direct) <= 1e-12 * np.sum(np.abs(sw[nodes] * sigma[nodes])) / L
