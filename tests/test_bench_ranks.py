@@ -48,7 +48,8 @@ def test_reduce_over_two_gloo_ranks():
     with tempfile.TemporaryDirectory() as d:
         mp.spawn(_rank_main, args=(2, _free_port(), d), nprocs=2, join=True)
         for r in range(2):
-            ms, units = open(os.path.join(d, "r%d" % r)).read().split()
+            with open(os.path.join(d, "r%d" % r)) as fh:
+                ms, units = fh.read().split()
             assert float(ms) == 2.5 and float(units) == 300.0
 
 

@@ -30,7 +30,8 @@ def V():
 
 
 def test_library_exports_every_declared_symbol(V):
-    hdr = open(os.path.join(ROOT, "include", "vpx.h")).read()
+    with open(os.path.join(ROOT, "include", "vpx.h")) as fh:
+        hdr = fh.read()
     names = set(re.findall(r"^(?:int|void|const char \*)\s*\*?\s*(vpx_\w+)\s*\(", hdr, flags=re.M))
     assert len(names) >= 20
     L = V.load_library()
