@@ -262,7 +262,10 @@ int vpx_potential(vpx_plan_t plan, const double *fe_leaf, int nrhs, int64_t ld_f
  * allocator owns the device, or an allocation or its failure is unacceptable
  * mid-run).  The first call on a device looks up the array's device address
  * (once per device); make that first call before any stream capture.
- * Returns VPX_ERR_ARG when nrhs * n_boxes * 4 * (p + 1) exceeds the array.
+ * Returns VPX_ERR_ARG, before any device work, when nrhs is outside
+ * [1, max_rhs] (the mixed form's slice buffers are plan workspace sized by
+ * max_rhs) or when nrhs * n_boxes * 4 * (p + 1) exceeds the array.  The
+ * passes zero both expansion arrays at the start of every call.
  * All calls share the array: calls that overlap on the GPU (any stream, any
  * plan) race and must be serialised by the caller. */
 #define VPX_STATIC_SCRATCH_DOUBLES (2 * 1024 * 1024)

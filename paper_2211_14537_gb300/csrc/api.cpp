@@ -459,9 +459,12 @@ int vpx_potential_static(vpx_plan_t p, const double *fe, int nrhs, int64_t ld_fe
                          double *vb, int64_t ld_b, void *stream) {
     return guarded([&] {
         if (!p) fail(VPX_ERR_ARG, "null plan");
+        // the slice buffers of the mixed form are plan workspace sized by max_rhs,
+        // so the column count is bounded here as in vpx_potential (checked first,
+        // before any device state is touched)
+        if (nrhs < 1 || nrhs > p->opt.max_rhs) fail(VPX_ERR_ARG, "nrhs out of range");
         if (p->host_only) fail(VPX_ERR_STATE, "host-only plan");
         int64_t nt = (int64_t)p->leaf_xy.size() / 2, nbd = (int64_t)p->bdry_xy.size() / 2;
-        if (nrhs < 1) fail(VPX_ERR_ARG, "nrhs out of range");
         if (!fe || !v || ld_fe < nt || ld_v < nt || (vb && ld_b < nbd)) fail(VPX_ERR_ARG, "bad buffer");
         device_potential_static(p, fe, ld_fe, nrhs, v, ld_v, vb, ld_b, stream);
     });

@@ -43,6 +43,24 @@ static double *static_scratch_address() {
     return g_addr[dev];
 }
 
+namespace {
+// Makes the plan's device current for the lifetime of the guard and puts the
+// caller's device back on every exit, the error paths included.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        VPX_CUDA(cudaGetDevice(&prev));
+        if (prev != dev) VPX_CUDA(cudaSetDevice(dev));
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+}  // namespace
+
+void ev_record(vpx_plan *p, int i, cudaStream_t s);
+
 void device_potential_static(vpx_plan *p, const double *fe, int64_t ldfe, int nrhs, double *v, int64_t ldv,
                              double *vb, int64_t ldb, void *stream) {
     const int64_t per = (int64_t)nrhs * p->dt.n_boxes * 2 * p->P;   // one expansion array
@@ -50,16 +68,14 @@ void device_potential_static(vpx_plan *p, const double *fe, int64_t ldfe, int nr
         fail(VPX_ERR_ARG, "vpx_potential_static: nrhs * n_boxes * 4(p+1) = " + std::to_string(2 * per) +
                               " doubles exceeds the static scratch of " +
                               std::to_string((long long)VPX_STATIC_SCRATCH_DOUBLES));
-    int cur = -1;
-    VPX_CUDA(cudaGetDevice(&cur));
-    if (cur != p->device) VPX_CUDA(cudaSetDevice(p->device));
+    DeviceGuard guard(p->device);
     double *base = static_scratch_address();
     cudaStream_t s = (cudaStream_t)stream;
     p->last_stream = stream;
-    // every expansion coefficient the passes read is written earlier in the
-    // same call, so the scratch needs no clearing between calls
+    ev_record(p, 0, s);
+    // the passes zero both expansion arrays at the start of every call (the
+    // scratch keeps the previous call's values until then)
     run_potential_scratch(p, fe, ldfe, nrhs, v, ldv, vb, ldb, base, base + per, s);
-    if (cur != p->device && cur >= 0) VPX_CUDA(cudaSetDevice(cur));
 }
 
 }  // namespace vpx

@@ -202,6 +202,25 @@ def test_batch_refuses_host_only_plans_and_bad_arrays(V):
     assert L.vpx_execute_batch(0, None, None, None, None, None, None, None, None, None) == V.VPX_ERR_ARG
 
 
+def test_potential_static_refuses_too_many_columns_before_any_launch(V):
+    """vpx_potential_static bounds nrhs by the plan's max_rhs before it looks at
+    the device state: the mixed form's slice buffers are plan workspace sized by
+    max_rhs, so more columns than that would write past them."""
+    torch = pytest.importorskip("torch")
+    wl = W.disk_sincos(level=3)
+    plan = _plan(V, wl)   # host-only, max_rhs = 1
+    nt = plan.sizes()[1]
+    fe = torch.zeros((2, nt), dtype=torch.float64)
+    v = torch.zeros((2, nt), dtype=torch.float64)
+    with pytest.raises(V.VpxError) as e:
+        V.vpx_potential_static(plan, fe, v, stream=0)
+    assert e.value.code == V.VPX_ERR_ARG
+    # within range, the host-only plan is a state error as for vpx_potential
+    with pytest.raises(V.VpxError) as e:
+        V.vpx_potential_static(plan, fe[:1], v[:1], stream=0)
+    assert e.value.code == V.VPX_ERR_STATE
+
+
 def test_autotune_refuses_host_only_plan(V):
     torch = pytest.importorskip("torch")
     wl = W.disk_sincos(level=3)
