@@ -1,10 +1,13 @@
 """Benchmark: volume-potential targets/s of the particular-solution stage.
 
-Workload: the adaptive starfish problem -- r(t) = 0.35 (1 + 0.3 cos 5t),
-f = exp(-|x - (0.1, 0.05)|^2 / 0.02^2), K = 16 Gauss-Legendre nodes per leaf,
-refined until the Legendre tail coefficients fall below 1e-10.  One step = one
-call of vpx_execute: extension of f on the cut leaves plus the box-FMM volume
-potential at every leaf node and boundary node, on device-resident inputs.
+Default workload: the largest single-GPU configuration, the L-shaped polygon
+[-0.4,0.4]^2 minus [0,0.4]^2 with f = Laplacian of exp(x) sin(2y), a uniform
+level-6 tree refined toward the six corners to level 14, K = 16
+Gauss-Legendre nodes per leaf (5,407 leaves, 1.38 M leaf targets).  One step =
+one call of vpx_execute: extension of f on the cut leaves plus the box-FMM
+volume potential at every leaf node and boundary node, on device-resident
+inputs.  The line also carries the uneven 32-tree batch (one graph) as the
+key "batch" (skip with --no-batch).
 
 Prints one JSON line (rank 0).  `--impl reference` times the CPU FP64 oracle
 (direct quadrature) on a bounded sample of the same targets instead.
@@ -40,12 +43,14 @@ def parse():
     ap.add_argument("--p", type=int, default=40)
     ap.add_argument("--precision", default="both", choices=["fp64", "mixed", "both"])
     ap.add_argument("--nrhs", type=int, default=1)
-    ap.add_argument("--oracle-sample", type=int, default=12000)   # ~10 s of oracle work on 16 cores
+    ap.add_argument("--oracle-sample", type=int, default=0,
+                    help="targets of the oracle's sample (0: sized for about 15 s of oracle work on all cores)")
+    ap.add_argument("--no-batch", action="store_true", help="leave the uneven 32-tree batch out of the line")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default engine / tile choices")
     ap.add_argument("--ext-mode", default="stencil", choices=["stencil", "lines"],
                     help="extension: universal stencil (default) or along lines through the origin (star domains)")
-    ap.add_argument("--workload", default="starfish",
+    ap.add_argument("--workload", default="lshape",
                     choices=["starfish", "lshape", "exterior", "doubly-connected", "disk-multi-rhs", "star-batch"],
                     help="lshape: the L-shape refined to level 14 (1.4 M targets); disk-multi-rhs: the disk tree "
                          "with 64 distinct right-hand sides, split into column blocks over the ranks; "
@@ -302,12 +307,13 @@ def reduce_over_ranks(ms, units, device, world):
     return float(t.item()), float(u.item())
 
 
-def run_batch(args, rank=0, world=1):
+def run_batch(args, rank=0, world=1, as_key=False):
     """Uneven batch: 32 random star domains, each with its own mixture and tree,
     in one vpx_execute_batch graph (mixed form), against the same trees run one
     after another (mixed, and FP64 as in a plain sequential solver).  On N
     ranks each takes a size-balanced share of the trees (no collective on the
-    data path); value = all ranks' targets / the slowest rank's time."""
+    data path); value = all ranks' targets / the slowest rank's time.  With
+    as_key, returns the batch's figures (rank 0) instead of printing a line."""
     import torch
     import workloads as W
     from paper_2211_14537_gb300 import vpx as V
@@ -399,7 +405,15 @@ def run_batch(args, rank=0, world=1):
     bdry_all = reduce_over_ranks(0.0, sum(sz[3] for sz in sizes), dev, world)[1]
     kernels = reduce_over_ranks(0.0, kernels, dev, world)[1]
     if rank != 0:
-        return
+        return None
+    if as_key:
+        return {"workload": "star_batch_32", "trees": len(wls_all), "leaf_targets": int(leaf_all),
+                "boundary_targets": int(bdry_all), "value": rate(ms_batch), "unit": UNIT, "ms_per_step": ms_batch,
+                "mixed_sequential": {"value": rate(ms_seq_mixed), "ms_per_step": ms_seq_mixed},
+                "fp64_sequential": {"value": rate(ms_seq_fp64), "ms_per_step": ms_seq_fp64},
+                "kernels_per_step": int(kernels),
+                "autotune": {"passes_tuned": tuned[0], "passes_changed": tuned[1]},
+                "setup_s": {"mixed": round(setup_mixed, 2), "fp64": round(setup_fp64, 2)}, "clocks": cl}
     out = {
         "metric": METRIC, "value": rate(ms_batch), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": ms_batch, "higher_is_better": True, "scaling": "weak",
@@ -438,12 +452,15 @@ def algorithmic_flops(K, p, n_leaves, lc):
     return out
 
 
-def oracle_sample(wl, n_sample, seed=2213, nthreads=0, lines=False, n_one_core=0):
+def oracle_sample(wl, n_sample=0, seconds=15.0, seed=2213, lines=False, one_core_s=0.0):
     """Oracle: own tree + extension (the universal stencil, or along lines),
     then V at a seeded sample of leaf nodes on all host cores and, if
-    n_one_core, at the first n_one_core of them again on one core.
-    Returns (indices, V at those, seconds of the potential, threads,
-    (targets, seconds) on one core or None)."""
+    one_core_s > 0, on one core at an evenly spread subset of the same sample
+    (about one_core_s seconds).  n_sample = 0 sizes the sample for about
+    `seconds` of oracle work, calibrated on 64 targets.  Returns a dict: the
+    oracle's leaf values (leaf-major, the library's layout), the sample
+    indices, V there, the seconds and threads of the all-core run and the
+    one-core (targets, seconds) or None."""
     from oracle import oracle as O
     tree = O.build_tree(wl.domain, wl.opts, wl.sources[0])
     if lines:
@@ -453,18 +470,69 @@ def oracle_sample(wl, n_sample, seed=2213, nthreads=0, lines=False, n_one_core=0
         pts, meta = O.stencil_points(tree, wl.domain)
         vals, _ = O.leaf_values(tree, wl.domain, wl.sources[0](pts)[:, None], meta)
     nodes = O.all_leaf_nodes(tree)
+    threads = O.lib().orc_max_threads()     # all host cores, read before any one-core run
     rng = np.random.Generator(np.random.PCG64(seed))
-    idx = np.sort(rng.choice(len(nodes), min(n_sample, len(nodes)), replace=False))
+    perm = rng.permutation(len(nodes))
+    if n_sample <= 0:
+        t0 = time.perf_counter()
+        O.volume_potential(tree, vals, nodes[np.sort(perm[:64])], threads)
+        per = (time.perf_counter() - t0) / 64
+        n_sample = int(min(max(seconds / per, 128), len(nodes)))
+    idx = np.sort(perm[:min(n_sample, len(nodes))])
     t0 = time.perf_counter()
-    Vs = O.volume_potential(tree, vals, nodes[idx], nthreads)[:, 0]
+    Vs = O.volume_potential(tree, vals, nodes[idx], threads)[:, 0]
     dt = time.perf_counter() - t0
     one = None
-    if n_one_core:
-        sub1 = nodes[idx[:n_one_core]]
+    if one_core_s > 0:
+        n1 = int(max(16, min(len(idx), one_core_s / (dt / len(idx) * threads))))
+        sub1 = idx[::max(1, len(idx) // n1)]
         t1 = time.perf_counter()
-        O.volume_potential(tree, vals, sub1, 1)
+        O.volume_potential(tree, vals, nodes[sub1], 1)
         one = (len(sub1), time.perf_counter() - t1)
-    return idx, Vs, dt, O.lib().orc_max_threads() if nthreads == 0 else nthreads, one
+    return {"vals": vals, "idx": idx, "V": Vs, "seconds": dt, "threads": threads, "one_core": one,
+            "n_leaves": tree.n_leaves}
+
+
+def measured_peaks():
+    """The measured peaks of this GPU pool (MEASURED_PEAKS.json beside
+    this file), else the profiling recipe's fallback figures."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return {"bf16_tflops": float(d["bf16_tflops"]), "bf16_tflops_sustained": float(d["bf16_tflops_sustained"]),
+                "hbm_gbs": float(d["hbm_gbs"]), "source": "measured (MEASURED_PEAKS.json)"}
+    except (OSError, KeyError, ValueError):
+        return {"bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "hbm_gbs": 6800.0,
+                "source": "fallback (recipe: one earlier GB300 measurement)"}
+
+
+# DRAM bytes (read + written) of one launch of the near-field kernel, from an
+# ncu capture, keyed by (workload, right-hand sides, SHA-256 prefix of the
+# kernel's source file).  A changed kernel source matches no key, so the line
+# then reports traffic as null until the kernel is captured again.
+NEAR_TRAFFIC = {}
+
+
+def kernel_source_key(fname="gemm_ws.cu"):
+    import hashlib
+    with open(os.path.join(ROOT, "paper_2211_14537_gb300", "csrc", fname), "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+def potential_error(V, plan, vals, idx, Vs):
+    """Relative max-norm error at the sampled targets of the library's volume
+    potential of the oracle's own leaf values (the potential alone, without the
+    extension's conditioning)."""
+    import torch
+    nt = vals.shape[0] * vals.shape[2]
+    fe = torch.tensor(np.ascontiguousarray(vals[:, 0, :].ravel()), dtype=torch.float64, device="cuda")
+    v = torch.empty(nt, dtype=torch.float64, device="cuda")
+    V.vpx_potential(plan, fe, v, None, stream=0)
+    torch.cuda.synchronize()
+    if V.vpx_sync_status(plan) != 0:
+        raise RuntimeError("device status error in the potential check")
+    return float(np.max(np.abs(v.cpu().numpy()[idx] - Vs)) / np.max(np.abs(Vs)))
 
 
 def main():
@@ -483,52 +551,67 @@ def main():
         return
     forms = ["fp64", "mixed"] if args.precision == "both" else [args.precision]
     res = {f: run_gpu(args, rank, world, f) for f in forms}
-    errs = {}
+    errs, errs_e2e = {}, {}
     cpu = None
     if rank == 0 and world == 1:
         try:
-            idx, Vs, dt, thr, one = oracle_sample(res[forms[0]]["wl"], args.oracle_sample, lines=args.ext_mode == "lines",
-                                                  n_one_core=0 if args.no_cpu_baseline else 96)
+            o = oracle_sample(res[forms[0]]["wl"], args.oracle_sample, lines=args.ext_mode == "lines",
+                              one_core_s=0.0 if args.no_cpu_baseline else 5.0)
+            idx, Vs = o["idx"], o["V"]
             for f in forms:
-                errs[f] = float(np.max(np.abs(res[f]["v"][idx] - Vs)) / np.max(np.abs(Vs)))
+                # the potential of the oracle's own f^e (the metric's error), and
+                # end to end from the stencil data, where the two sides' extension
+                # fits (two backward-stable least-squares solutions) also differ
+                errs[f] = potential_error(V_module(), res[f]["plan"], o["vals"], idx, Vs)
+                errs_e2e[f] = float(np.max(np.abs(res[f]["v"][idx] - Vs)) / np.max(np.abs(Vs)))
             if not args.no_cpu_baseline:
-                cpu = {"value": len(idx) / dt, "unit": UNIT, "cores": thr, "kind": "oracle",
-                       "sample": "direct-quadrature V at %d of %d leaf nodes (seeded), oracle tree+extension "
-                                 "excluded, %.1f s" % (len(idx), res[forms[0]]["nt"], dt),
+                dt = o["seconds"]
+                cpu = {"value": len(idx) / dt, "unit": UNIT, "cores": o["threads"], "kind": "oracle",
+                       "sample": "direct-quadrature V at %d of %d leaf nodes (seeded) on %d threads, oracle "
+                                 "tree+extension excluded, %.1f s" % (len(idx), res[forms[0]]["nt"], o["threads"], dt),
                        "extrapolated_full_s": res[forms[0]]["tg"] * dt / len(idx)}
-                if one:
-                    cpu["one_core"] = {"value": one[0] / one[1], "unit": UNIT, "cores": 1,
-                                       "sample": "the first %d of those targets, %.1f s" % one}
+                if o["one_core"]:
+                    n1, t1 = o["one_core"]
+                    cpu["one_core"] = {"value": n1 / t1, "unit": UNIT, "cores": 1,
+                                       "sample": "%d targets spread evenly over the same sample, one thread, %.1f s"
+                                                 % (n1, t1)}
         except Exception as e:   # noqa: BLE001 - report, do not hide the GPU number
             cpu = {"value": None, "error": repr(e)}
-    # headline: the fastest form whose error against the oracle meets 1e-10
+    # headline: the fastest form whose potential error against the oracle meets 1e-10
     ok = [f for f in forms if errs.get(f, 0.0) <= 1e-10]
     head = min(ok or forms, key=lambda f: res[f]["ms"])
     r = res[head]
     ms_max, tg_all = reduce_over_ranks(r["ms"], r["tg"], "cuda", world)   # replicas: every rank one tree
     value = tg_all / (ms_max * 1e-3)
+    peaks = measured_peaks()
+    method_flops = r["near_flops"] + 2.0 * r["K"] ** 2 * r["lc"]["near"] * args.nrhs   # 2K^4 + 2K^2 per pair
+    near_s = r["near_ms"] * 1e-3
     if head == "mixed":
-        # exact bf16 slice products: 15 slice pairs per near-field product
-        bf16_flops = 15 * r["near_flops"]
-        achieved = bf16_flops / (r["near_ms"] * 1e-3) / 1e12
-        peak = 1918.1
-        kname = ("k_gemm_frag (near-field pass, exact bf16 slices on mma.sync)" if os.environ.get("VPX_NO_TC")
-                 else "k_gemm_ws (near-field pass, exact bf16 slices on tcgen05: TMA tables, TMEM accumulators)")
-        # DRAM bytes read + written by one launch of the near-field kernel on this
-        # workload, from an ncu capture of the kernel as it stands (profiles/);
-        # reset to None whenever the kernel changes
-        traffic = (24641280 if not os.environ.get("VPX_NO_TC") and args.nrhs == 1 and args.workload == "starfish"
-                   else None)
-        roof = {"kernel": kname, "bound": "tensor",
-                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
-                "traffic_unit": "bytes per launch",
-                "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst)",
-                "fp64_equivalent_tflops": r["near_flops"] / (r["near_ms"] * 1e-3) / 1e12}
+        tc = not os.environ.get("VPX_NO_TC")
+        achieved = method_flops / near_s / 1e12
+        peak = peaks["bf16_tflops"]
+        key = (r["wl"].name, args.nrhs, kernel_source_key("gemm_ws.cu" if tc else "gemm_frag.cu"))
+        roof = {"kernel": ("k_gemm_ws (near-field pass: exact bf16 slices on tcgen05, TMA tables, TMEM accumulators)"
+                           if tc else "k_gemm_frag (near-field pass: exact bf16 slices on mma.sync)"),
+                "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": NEAR_TRAFFIC.get(key), "traffic_unit": "bytes per launch (ncu dram__bytes read+write)",
+                "work": "method flops 2K^4 + 2K^2 per near pair (%d pairs), per launch" % r["lc"]["near"],
+                "peak_source": "bf16 dense burst, %s" % peaks["source"],
+                "slice_products_tflops": 15 * r["near_flops"] / near_s / 1e12,
+                "slice_products_note": "the 15 exact bf16 slice products per FP64-equivalent product the "
+                                       "tensor pipe executes, per second"}
     else:
-        achieved = r["near_flops"] / (r["near_ms"] * 1e-3) / 1e12
+        achieved = method_flops / near_s / 1e12
         roof = {"kernel": "k_gemm_fp64 (near-field pass)", "bound": "alu", "achieved": achieved,
                 "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                "peak_source": "nominal GB300 FP64 (recipe); probe measured 1.20"}
+                "work": "method flops 2K^4 + 2K^2 per near pair, per launch",
+                "peak_source": "nominal GB300 FP64 (recipe); an FMA probe measured 1.20"}
+    batch = None
+    if not args.no_batch and args.nrhs == 1:
+        try:
+            batch = run_batch(args, rank, world, as_key=True)
+        except Exception as e:   # noqa: BLE001 - the single-tree line stands on its own
+            batch = {"error": repr(e)}
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": ms_max, "higher_is_better": True,
@@ -549,9 +632,13 @@ def main():
                    "extension": "along lines" if args.ext_mode == "lines" else "universal stencil"},
         "forms": {f: {"value": res[f]["tg"] * world / (res[f]["ms"] * 1e-3), "ms_per_step": res[f]["ms"],
                       "median_ms_per_step": statistics.median(res[f]["times"]) if res[f].get("times") else None,
-                      "rel_err_vs_oracle": errs.get(f), "pass_ms": {k: round(x, 5) for k, x in res[f]["pass_ms"].items()}}
+                      "rel_err_vs_oracle": errs.get(f), "rel_err_end_to_end": errs_e2e.get(f),
+                      "pass_ms": {k: round(x, 5) for k, x in res[f]["pass_ms"].items()}}
                   for f in forms},
         "rel_err_vs_oracle": errs.get(head),
+        "rel_err_note": "rel_err_vs_oracle: the library's potential of the oracle's own extended source at the "
+                        "sampled targets; rel_err_end_to_end: from the stencil data, including the difference of "
+                        "the two sides' extension fits",
         "roofline": roof,
         "gpu_launches": r["graph_kernels"] * args.steps,
         "e2e": {"value": r["tg"] * world / r["e2e_s"], "unit": UNIT,
@@ -560,10 +647,17 @@ def main():
         "clocks": r["clocks"],
         "latency_floor_us": latency_floor_us() if rank == 0 else None,
     }
+    if batch is not None:
+        out["batch"] = batch
     if cpu is not None:
         out["cpu_baseline"] = cpu
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+def V_module():
+    from paper_2211_14537_gb300 import vpx as V
+    return V
 
 
 def run_reference(args, world):

@@ -305,6 +305,16 @@ class _Geometry:
         return m
 
 
+def legendre_tail_max(F: np.ndarray, Vinv: np.ndarray, K: int) -> float:
+    """Refinement measure of one leaf (Section 4, R8 reading): the largest
+    |c_mn| over total degree m + n >= K-1 of the tensor Legendre coefficients
+    of the leaf's K x K node values F[b][a] (b the y index), with
+    Vinv = inverse Legendre Vandermonde matrix of the leaf nodes."""
+    C = Vinv @ F @ Vinv.T          # C[n][m]: degree n in y, m in x
+    mm, nn = np.meshgrid(np.arange(K), np.arange(K), indexing="xy")
+    return float(np.max(np.abs(C[(mm + nn) >= K - 1])))
+
+
 def build_tree(dom, opts, f_refine, verbose=False) -> OracleTree:
     """Quad-tree by the rules of Section 4 (our reading, applied literally).
 
@@ -323,8 +333,6 @@ def build_tree(dom, opts, f_refine, verbose=False) -> OracleTree:
     t, _ = gauss_legendre(K)
     geo = _Geometry(dom)
     Vinv = np.linalg.inv(npleg.legvander(t, K - 1))
-    mm, nn = np.meshgrid(np.arange(K), np.arange(K), indexing="xy")
-    tail_mask = (mm + nn) >= K - 1
     cls_cache: Dict = {}
 
     def classify(b):
@@ -342,8 +350,7 @@ def build_tree(dom, opts, f_refine, verbose=False) -> OracleTree:
 
     def unresolved(b):
         F = np.asarray(f_refine(leaf_nodes(b, t)), dtype=np.float64).reshape(K, K)  # [b][a]
-        C = Vinv @ F @ Vinv.T          # C[n][m]: degree n in y, m in x
-        return np.max(np.abs(C[tail_mask])) > opts.refine_tol * opts.f_scale
+        return legendre_tail_max(F, Vinv, K) > opts.refine_tol * opts.f_scale
 
     def split_phase_a(b):
         l = b[0]

@@ -57,7 +57,7 @@ def test_reduce_on_one_rank_is_identity():
     assert bench.reduce_over_ranks(3.0, 7, "cpu", 1) == (3.0, 7.0)
 
 
-@pytest.mark.parametrize("wl_name", ["starfish", "exterior", "disk-multi-rhs", "doubly-connected"])
+@pytest.mark.parametrize("wl_name", ["lshape", "starfish", "exterior", "disk-multi-rhs", "doubly-connected"])
 def test_bench_line_carries_the_contract_keys(monkeypatch, capsys, wl_name):
     """bench.main() on one rank, the GPU run and the oracle sample replaced by
     fixed results: one JSON line with the keys of the benchmark contract."""
@@ -66,15 +66,20 @@ def test_bench_line_carries_the_contract_keys(monkeypatch, capsys, wl_name):
     import numpy as np
 
     def fake_run_gpu(args, rank, world, prec):
-        return dict(wl=bench.workload(args.workload), ms=0.2 if prec == "mixed" else 1.5, setup_s=0.6,
+        return dict(plan=prec, wl=bench.workload(args.workload), ms=0.2 if prec == "mixed" else 1.5, setup_s=0.6,
                     tg=184832, nt=182272, nb=2560, ns=129619, n_leaves=712,
                     lc={"near": 4900, "m2l": 14104, "s2l": 822, "m2t": 1112, "n_levels": 7},
-                    pass_ms={"near": 0.05}, near_flops=6.4e8, near_ms=0.05, clocks={"sm_mhz": 2070.0},
+                    pass_ms={"near": 0.05}, near_flops=2.0 * 16 ** 4 * 4900, near_ms=0.05, clocks={"sm_mhz": 2070.0},
                     e2e_s=3e-4, v=np.ones(182272), K=16, graph_kernels=24, tune=(7, 0), times=[0.2, 0.21, 0.19])
 
     monkeypatch.setattr(bench, "run_gpu", fake_run_gpu)
-    monkeypatch.setattr(bench, "oracle_sample", lambda wl, n, **k: (np.arange(10), np.ones(10), 1.0, 16, (4, 2.0)))
-    monkeypatch.setattr(sys, "argv", ["bench.py", "--workload", wl_name])
+    monkeypatch.setattr(bench, "oracle_sample",
+                        lambda wl, n, **k: {"vals": None, "idx": np.arange(10), "V": np.ones(10), "seconds": 1.0,
+                                            "threads": 16, "one_core": (4, 2.0), "n_leaves": 712})
+    # the potential check of the oracle's own f^e: the FP64 form exact, the mixed form within 1e-10
+    monkeypatch.setattr(bench, "potential_error", lambda V, plan, vals, idx, Vs: 3e-11 if plan == "mixed" else 1e-15)
+    monkeypatch.setattr(bench, "V_module", lambda: None)
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--workload", wl_name, "--no-batch"])
     bench.main()
     d = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
     for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
@@ -86,11 +91,16 @@ def test_bench_line_carries_the_contract_keys(monkeypatch, capsys, wl_name):
     assert d["value"] == pytest.approx(184832 / 0.2e-3)                      # the faster form that meets 1e-10
     assert set(d["roofline"]) >= {"bound", "achieved", "peak", "unit", "frac", "traffic"}
     assert d["roofline"]["frac"] == pytest.approx(d["roofline"]["achieved"] / d["roofline"]["peak"])
+    # the method's own work, 2K^4 + 2K^2 per near pair, over the near pass time; the peak is the measured one
+    assert d["roofline"]["achieved"] == pytest.approx(4900 * (2 * 16 ** 4 + 2 * 256) / 0.05e-3 / 1e12)
+    assert d["roofline"]["peak"] == pytest.approx(bench.measured_peaks()["bf16_tflops"])
+    assert d["roofline"]["traffic"] is None                                   # no capture of this kernel source
+    assert d["rel_err_vs_oracle"] == pytest.approx(3e-11)
+    assert d["forms"]["mixed"]["rel_err_end_to_end"] == 0.0
     assert set(d["e2e"]) >= {"value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step"}
     assert d["e2e"]["h2d_bytes_per_step"] == 8 * 129619 and d["gpu_launches"] == 24 * d["steps"]
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 16
-    assert d["cpu_baseline"]["one_core"] == {"value": 2.0, "unit": d["unit"], "cores": 1,
-                                             "sample": "the first 4 of those targets, 2.0 s"}
+    assert d["cpu_baseline"]["one_core"]["value"] == 2.0 and d["cpu_baseline"]["one_core"]["cores"] == 1
     assert d["cpu_baseline"]["extrapolated_full_s"] == pytest.approx(184832 / 10.0)
     fl = d["config"]["algorithmic_flops_per_rhs"]
     assert fl["near"] == 4900 * (2 * 16 ** 4 + 2 * 256) and fl["m2l"] == 8 * 41 ** 2 * 14104

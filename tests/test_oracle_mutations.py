@@ -81,3 +81,76 @@ def test_net_charge_without_the_leaf_jacobian_is_caught(monkeypatch):
         P.test_net_charge_of_a_gaussian_is_pi_s_squared()
     with pytest.raises(AssertionError):
         P.test_net_charge_is_the_growth_of_the_potential_at_infinity()
+
+
+def _first_overlapping_owner(tree):
+    """Planted: the first cut leaf (Z-order) whose extension square overlaps the
+    exterior leaf, in place of the nearest one."""
+    cut = tree.cut_leaves()
+    owner = [-1] * tree.n_leaves
+    for j, b in enumerate(tree.leaves):
+        if tree.cls[j] != O.EXTERIOR:
+            continue
+        x0, x1, y0, y1 = O.box_bounds(b)
+        for i in cut:
+            a0, a1, b0, b1 = O.box_bounds(tree.leaves[i])
+            s = a1 - a0
+            if min(x1, a1 + s) > max(x0, a0 - s) and min(y1, b1 + s) > max(y0, b0 - s):
+                owner[j] = i
+                break
+    return owner
+
+
+_REAL_OWNERS = O.extension_owners
+
+
+def _earlier_wins_ties(tree):
+    """Planted: the nearest cut leaf, but the earlier one in Z-order on a tie."""
+    real = _REAL_OWNERS(tree)
+    cut = tree.cut_leaves()
+    owner = list(real)
+    for j, o in enumerate(real):
+        if o < 0:
+            continue
+        cj = np.array(O.box_center(tree.leaves[j]))
+        d2o = np.sum((np.array(O.box_center(tree.leaves[o])) - cj) ** 2)
+        for i in cut:
+            if i >= o:
+                break
+            a0, a1, b0, b1 = O.box_bounds(tree.leaves[i])
+            s = a1 - a0
+            x0, x1, y0, y1 = O.box_bounds(tree.leaves[j])
+            ov = min(x1, a1 + s) > max(x0, a0 - s) and min(y1, b1 + s) > max(y0, b0 - s)
+            if ov and np.sum((np.array(O.box_center(tree.leaves[i])) - cj) ** 2) == d2o:
+                owner[j] = i
+                break
+    return owner
+
+
+@pytest.mark.parametrize("planted", [_first_overlapping_owner, _earlier_wins_ties])
+def test_wrong_extension_owner_rule_is_caught(monkeypatch, planted):
+    import test_oracle_tree_rules as T
+    monkeypatch.setattr(O, "extension_owners", planted)
+    caught = 0
+    for name in T.OWNER_TREES:
+        try:
+            T.test_extension_owners_brute_force(name)
+        except AssertionError:
+            caught += 1
+    assert caught > 0
+
+
+@pytest.mark.parametrize("mask", ["degree_K", "tensor"])
+def test_wrong_refinement_tail_is_caught(monkeypatch, mask):
+    """Planted: the tail taken from total degree >= K (the K-1 diagonal dropped),
+    or as a tensor tail (max(m, n) >= K-1) in place of the total degree."""
+    import test_oracle_tree_rules as T
+
+    def planted(F, Vinv, K):
+        C = Vinv @ F @ Vinv.T
+        mm, nn = np.meshgrid(np.arange(K), np.arange(K), indexing="xy")
+        sel = (mm + nn) >= K if mask == "degree_K" else np.maximum(mm, nn) >= K - 1
+        return float(np.max(np.abs(C[sel])))
+    monkeypatch.setattr(O, "legendre_tail_max", planted)
+    with pytest.raises(AssertionError):
+        T.test_refinement_matches_closed_form_legendre_tails(*T.R8_CASES[0])
