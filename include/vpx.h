@@ -400,6 +400,16 @@ int vpx_graph_kernel_count(vpx_plan_t plan, int64_t *kernels);
  * VPX_ERR_ARG for a null argument, VPX_ERR_CUDA / VPX_ERR_NODEV. */
 int vpx_check_bounded_wait(int *status);
 
+/* Invert the n x n row-major host matrix a into inv (host, n x n) with the
+ * device Gauss-Jordan elimination that vpx_bie_setup runs on the Nystrom
+ * system (partial pivoting, one pivot column per step), on the current
+ * device.  *status receives 0, or VPX_ERR_STATE when a pivot column is zero
+ * or not a number (a singular matrix): the elimination then stops, and inv
+ * holds no inverse.  The paper has no counterpart; it is the library's
+ * self-check of its inversion and of that stop.  Errors: VPX_ERR_ARG (a null
+ * argument, n < 1), VPX_ERR_CUDA, VPX_ERR_NODEV, VPX_ERR_NOMEM. */
+int vpx_check_gauss_jordan(int n, const double *a, double *inv, int *status);
+
 const char *vpx_error_string(int code);
 const char *vpx_last_error_message(void);
 

@@ -277,9 +277,11 @@ int vpx_plan_create(const vpx_options *opt, int n_panels, vpx_curve_cb curve, vp
         build_stencil(p->opt, cb, p->tree, p->stencil_xy, p->st, !p->host_only);
         build_leaf_and_boundary_nodes(p, cb);
         build_boxes(p);
-        build_lists_host(p);
+        if (p->host_only)
+            build_lists_host(p);
+        else
+            device_setup(p);   // builds the interaction lists on the device
         count_lists(p);
-        if (!p->host_only) device_setup(p);
     });
     if (rc != VPX_OK) {
         if (p) {
@@ -590,6 +592,11 @@ int vpx_get_timings(vpx_plan_t p, double *ms, int n) {
 int vpx_check_bounded_wait(int *status) {
     if (!status) return VPX_ERR_ARG;
     return guarded([&] { return vpx::device_check_bounded_wait(status); });
+}
+
+int vpx_check_gauss_jordan(int n, const double *a, double *inv, int *status) {
+    if (n < 1 || !a || !inv || !status) return VPX_ERR_ARG;
+    return guarded([&] { *status = vpx::device_check_gauss_jordan(n, a, inv); });
 }
 
 int vpx_graph_kernel_count(vpx_plan_t p, int64_t *kernels) {

@@ -66,9 +66,11 @@ __global__ void k_bie_assemble(int N, int n_log, int ntot, int exterior, const d
 }
 
 // pivot of column k: the row of largest magnitude among k..ntot-1 (the first
-// of equal ones), its value; a zero column latches VPX_ERR_STATE
+// of equal ones), its value; a zero column latches VPX_ERR_STATE, after which
+// every kernel of the elimination returns at once (the setup then fails)
 __global__ void __launch_bounds__(1024) k_gj_pivot(int ntot, int k, const double *aug, int *piv_row, double *piv_val,
                                                    int *status) {
+    if (*(volatile int *)status != 0) return;
     const int64_t ld = 2 * (int64_t)ntot;
     __shared__ double sv[1024];
     __shared__ int si[1024];
@@ -108,7 +110,8 @@ __global__ void __launch_bounds__(1024) k_gj_pivot(int ntot, int k, const double
 }
 
 // rows k and p exchanged, the new row k divided by the pivot
-__global__ void k_gj_swap(int ntot, int k, double *aug, const int *piv_row, const double *piv_val) {
+__global__ void k_gj_swap(int ntot, int k, double *aug, const int *piv_row, const double *piv_val, const int *status) {
+    if (*(const volatile int *)status != 0) return;
     const int64_t ld = 2 * (int64_t)ntot;
     const int p = *piv_row;
     const double pv = *piv_val;
@@ -119,7 +122,8 @@ __global__ void k_gj_swap(int ntot, int k, double *aug, const int *piv_row, cons
     }
 }
 
-__global__ void k_gj_factors(int ntot, int k, const double *aug, double *fac) {
+__global__ void k_gj_factors(int ntot, int k, const double *aug, double *fac, const int *status) {
+    if (*(const volatile int *)status != 0) return;
     const int64_t ld = 2 * (int64_t)ntot;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ntot; i += gridDim.x * blockDim.x)
         fac[i] = (i == k) ? 0.0 : aug[(int64_t)i * ld + k];
@@ -127,7 +131,8 @@ __global__ void k_gj_factors(int ntot, int k, const double *aug, double *fac) {
 
 // every other row minus its multiple of row k; columns left of k are already
 // unit vectors, and row k vanishes there
-__global__ void k_gj_eliminate(int ntot, int k, double *aug, const double *fac) {
+__global__ void k_gj_eliminate(int ntot, int k, double *aug, const double *fac, const int *status) {
+    if (*(const volatile int *)status != 0) return;
     const int64_t ld = 2 * (int64_t)ntot;
     const int64_t width = ld - k;
     const int64_t total = (int64_t)ntot * width;
@@ -223,6 +228,40 @@ __global__ void __launch_bounds__(kTile) k_bie_eval(EvalArgs a) {
 
 }  // namespace
 
+// Inverse of the n x n matrix held in the left half of aug (n x 2n, row-major,
+// the right half the identity) by Gauss-Jordan with partial pivoting, one
+// pivot column per step, into inv (n x n).  Returns 0, or VPX_ERR_STATE when a
+// pivot column is zero (or not a number): the pivot kernel latches the status,
+// every later kernel of the elimination returns at once, and the host loop
+// stops at its next check (every 256 columns).  Synchronous.
+int gauss_jordan_inverse(int ntot, double *aug, double *inv) {
+    double *fac = dev_alloc<double>(ntot), *pv = dev_alloc<double>(1);
+    int *pr = dev_alloc<int>(1), *status = dev_alloc<int>(1);
+    VPX_CUDA(cudaMemset(status, 0, sizeof(int)));
+    const int grid = 152 * 8;
+    int st = 0;
+    for (int k = 0; k < ntot; ++k) {
+        k_gj_pivot<<<1, 1024>>>(ntot, k, aug, pr, pv, status);
+        k_gj_swap<<<(2 * ntot + 255) / 256, 256>>>(ntot, k, aug, pr, pv, status);
+        k_gj_factors<<<(ntot + 255) / 256, 256>>>(ntot, k, aug, fac, status);
+        k_gj_eliminate<<<grid, 256>>>(ntot, k, aug, fac, status);
+        if ((k & 255) == 255) {
+            VPX_LAUNCH("Gauss-Jordan inversion");
+            VPX_CUDA(cudaMemcpy(&st, status, sizeof(int), cudaMemcpyDeviceToHost));
+            if (st != 0) break;
+        }
+    }
+    VPX_LAUNCH("Gauss-Jordan inversion");
+    VPX_CUDA(cudaMemcpy2D(inv, sizeof(double) * ntot, aug + ntot, sizeof(double) * 2 * ntot, sizeof(double) * ntot,
+                          ntot, cudaMemcpyDeviceToDevice));
+    VPX_CUDA(cudaMemcpy(&st, status, sizeof(int), cudaMemcpyDeviceToHost));
+    dev_free(fac);
+    dev_free(pv);
+    dev_free(pr);
+    dev_free(status);
+    return st;
+}
+
 void device_bie_setup(vpx_plan *pl) {
     if (pl->device >= 0) VPX_CUDA(cudaSetDevice(pl->device));
     BieHost &B = pl->bie;
@@ -243,35 +282,33 @@ void device_bie_setup(vpx_plan *pl) {
     d.minv = dev_alloc<double>((size_t)ntot * ntot);
     double *kappa = dev_upload(B.kappa), *jump = dev_upload(B.jump);
     int32_t *curve = dev_upload(B.curve_of_node), *log_curve = dev_upload(B.log_curve);
-    double *aug = dev_alloc<double>((size_t)ntot * 2 * ntot), *fac = dev_alloc<double>(ntot), *pv = dev_alloc<double>(1);
-    int *pr = dev_alloc<int>(1), *status = dev_alloc<int>(1);
-    VPX_CUDA(cudaMemset(status, 0, sizeof(int)));
+    double *aug = dev_alloc<double>((size_t)ntot * 2 * ntot);
     const int exterior = B.outer_curve < 0 ? 1 : 0;
-    const int grid = 152 * 8;
-    k_bie_assemble<<<grid, 256>>>(N, B.n_log, ntot, exterior, d.y, d.nu, d.sw, kappa, jump, curve, d.log_c, log_curve,
-                                  aug);
+    k_bie_assemble<<<152 * 8, 256>>>(N, B.n_log, ntot, exterior, d.y, d.nu, d.sw, kappa, jump, curve, d.log_c,
+                                     log_curve, aug);
     VPX_LAUNCH("k_bie_assemble");
-    for (int k = 0; k < ntot; ++k) {
-        k_gj_pivot<<<1, 1024>>>(ntot, k, aug, pr, pv, status);
-        k_gj_swap<<<(2 * ntot + 255) / 256, 256>>>(ntot, k, aug, pr, pv);
-        k_gj_factors<<<(ntot + 255) / 256, 256>>>(ntot, k, aug, fac);
-        k_gj_eliminate<<<grid, 256>>>(ntot, k, aug, fac);
-    }
-    VPX_LAUNCH("Gauss-Jordan inversion");
-    VPX_CUDA(cudaMemcpy2D(d.minv, sizeof(double) * ntot, aug + ntot, sizeof(double) * 2 * ntot, sizeof(double) * ntot,
-                          ntot, cudaMemcpyDeviceToDevice));
-    int st = 0;
-    VPX_CUDA(cudaMemcpy(&st, status, sizeof(int), cudaMemcpyDeviceToHost));
+    const int st = gauss_jordan_inverse(ntot, aug, d.minv);
     dev_free(aug);
-    dev_free(fac);
-    dev_free(pv);
-    dev_free(pr);
-    dev_free(status);
     dev_free(kappa);
     dev_free(jump);
     dev_free(curve);
     dev_free(log_curve);
     if (st != 0) fail(VPX_ERR_STATE, "the boundary-correction system is singular");
+}
+
+int device_check_gauss_jordan(int n, const double *a, double *inv) {
+    double *aug = dev_alloc<double>((size_t)n * 2 * n), *out = dev_alloc<double>((size_t)n * n);
+    std::vector<double> h((size_t)n * 2 * n, 0.0);
+    for (int i = 0; i < n; ++i) {
+        for (int j = 0; j < n; ++j) h[(size_t)i * 2 * n + j] = a[(size_t)i * n + j];
+        h[(size_t)i * 2 * n + n + i] = 1.0;
+    }
+    VPX_CUDA(cudaMemcpy(aug, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice));
+    const int st = gauss_jordan_inverse(n, aug, out);
+    VPX_CUDA(cudaMemcpy(inv, out, sizeof(double) * n * n, cudaMemcpyDeviceToHost));
+    dev_free(aug);
+    dev_free(out);
+    return st;
 }
 
 void device_bie_solve(vpx_plan *pl, const double *g, const double *vb, double growth, double *sol, void *stream) {

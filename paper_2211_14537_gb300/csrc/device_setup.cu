@@ -1,6 +1,7 @@
-// device_setup.cu -- per-geometry setup on the GPU: near-field tables (polar
-// quadrature), S2L tables, the small expansion/translation tables computed on
-// the host, and the upload of the tree and its interaction lists.
+// device_setup.cu -- per-geometry setup on the GPU: the upload of the tree,
+// its interaction lists (built on the device), near-field tables (polar
+// quadrature), S2L tables and the small expansion/translation tables computed
+// on the host.
 #include <algorithm>
 #include <cmath>
 #include <complex>
@@ -370,6 +371,7 @@ void setup_tables(vpx_plan *p) {
 // --------------------------------------------------------------- uploads
 
 void setup_near_pairs(vpx_plan *p);   // device_exec.cu
+void build_lists_device(vpx_plan *p, cudaStream_t s);   // lists_device.cu
 void setup_passes(vpx_plan *p);       // fmm_passes.cu
 void free_passes(vpx_plan *p);
 
@@ -416,11 +418,8 @@ void device_setup(vpx_plan *p) {
     p->ext.leaf_level = dev_upload(llev);
     p->ext.leaf_ix = dev_upload(lix);
     p->ext.leaf_iy = dev_upload(liy);
-    // interaction lists (built on the host, once per geometry)
-    d.near = dev_upload(p->near);
-    d.vlist = dev_upload(p->vlist);
-    d.xlist = dev_upload(p->xlist);
-    d.wlist = dev_upload(p->wlist);
+    // interaction lists, built on the device once per geometry (per level)
+    build_lists_device(p, s);
     setup_tables(p);
     // extension data
     const StencilInfo &st = p->st;

@@ -188,6 +188,17 @@ void fmm_tables_host(vpx_plan *p, std::vector<double> &l2m, std::vector<double> 
 
 // ------------------------------------------------------------- setup
 
+void setup_chains(vpx_plan *p, const std::vector<double> &m2m, const std::vector<double> &l2l);   // chain.cu
+void free_chains(vpx_plan *p);
+void chain_reset(vpx_plan *p, cudaStream_t s);
+void chain_run(vpx_plan *p, bool up, double *x, int64_t ldm, int nrhs, cudaStream_t s);
+
+// The level chains as one persistent launch each, unless the tables do not fit
+// shared memory or VPX_PER_LEVEL_CHAINS is set (the per-level passes then run them).
+static bool use_chains(const vpx_plan *p) {
+    return p->fmm.chain.ok && getenv("VPX_PER_LEVEL_CHAINS") == nullptr;
+}
+
 void setup_passes(vpx_plan *p) {
     const bool mixed = p->opt.precision == VPX_PREC_MIXED;
     const int KK = p->KK, P = p->P, P2 = 2 * P, nl = (int)p->tree.leaves.size(), nb = (int)p->box_level.size();
@@ -364,11 +375,13 @@ void setup_passes(vpx_plan *p) {
     }
     for (GemmPass *g : {&F.l2m, &F.m2l, &F.s2l, &F.l2t, &F.m2t, &F.near}) g->status = p->wk.status;
     for (int l = 0; l <= kMaxLevel; ++l) F.m2m[l].status = F.l2l[l].status = p->wk.status;
+    setup_chains(p, m2m, l2l);
     VPX_CUDA(cudaDeviceSynchronize());
 }
 
 void free_passes(vpx_plan *p) {
     FmmPasses &F = p->fmm;
+    free_chains(p);
     gemm_pass_free(F.l2m);
     gemm_pass_free(F.m2l);
     gemm_pass_free(F.s2l);
@@ -421,6 +434,8 @@ void run_potential_passes(vpx_plan *p, const double *fe, int64_t ldfe, int nrhs,
     ev_record_pass(p, 1, s);
     VPX_CUDA(cudaMemsetAsync(mp, 0, sizeof(double) * ldm * nrhs, s));
     VPX_CUDA(cudaMemsetAsync(lo, 0, sizeof(double) * ldm * nrhs, s));
+    const bool chains = use_chains(p);
+    if (chains) chain_reset(p, s);
     VPX_CUDA(cudaMemset2DAsync(v, sizeof(double) * ldv, 0, sizeof(double) * (size_t)nl * KK, nrhs, s));
     // the leaf-value slices serve L2M, the near field and list i+ (slicing L2M's
     // 256-long vectors on the fly took longer than slicing once before it)
@@ -438,7 +453,9 @@ void run_potential_passes(vpx_plan *p, const double *fe, int64_t ldfe, int nrhs,
     // main stream: upward pass
     gemm_run(F.l2m, vf, mp, ldm, nrhs, mixed, s);
     ev_record_pass(p, 2, s);
-    for (int l = d.n_levels - 1; l >= 3; --l) gemm_run(F.m2m[l - 1], vm, mp, ldm, nrhs, mixed, s);
+    if (chains) chain_run(p, true, mp, ldm, nrhs, s);
+    else
+        for (int l = d.n_levels - 1; l >= 3; --l) gemm_run(F.m2m[l - 1], vm, mp, ldm, nrhs, mixed, s);
     if (mixed) slice_vectors(vmf, 0, nb, P2, kp_m, nrhs, s);
     // the final multipoles feed the constant terms and list i- on the third
     // stream, beside M2L on this one (all accumulate into distinct sums)
@@ -461,7 +478,9 @@ void run_potential_passes(vpx_plan *p, const double *fe, int64_t ldfe, int nrhs,
     gemm_run(F.m2l, vmf, lo, ldm, nrhs, mixed, s);
     VPX_CUDA(cudaStreamWaitEvent(s, (cudaEvent_t)p->ev_lc, 0));
     ev_record_pass(p, 4, s);
-    for (int l = 2; l + 1 < d.n_levels; ++l) gemm_run(F.l2l[l], vl, lo, ldm, nrhs, mixed, s);
+    if (chains) chain_run(p, false, lo, ldm, nrhs, s);
+    else
+        for (int l = 2; l + 1 < d.n_levels; ++l) gemm_run(F.l2l[l], vl, lo, ldm, nrhs, mixed, s);
     ev_record_pass(p, 5, s);
     gemm_run(F.l2t, vl, v, ldv, nrhs, mixed, s);
     ev_record_pass(p, 6, s);

@@ -6,9 +6,9 @@
 // fp32 accumulators in tensor memory (one per order d = k + l; exact, see
 // gemm.cu), then recombines them.  Two orientations:
 //
-//   TM = true  (near field): M = 128 table rows, N = 64 pairs, S = 5;
-//   TM = false (lists i, i+, i-, L2M): M = 128 pairs, N = 48 or 64 table
-//              rows, S = 6.
+//   TM = true  (the default): M = 128 table rows, N = 64 pairs, S = 5 (near
+//              field) or 6 (far field: L2M, lists i, i+ and i-);
+//   TM = false (VPX_TC_PAIRS): M = 128 pairs, N = 48 or 64 table rows, S = 6.
 //
 // Roles (256 threads):
 //   warp 0, one lane   table tiles by TMA bulk copies (cp.async.bulk): the
@@ -345,8 +345,12 @@ static int ws_rows_n(const GemmPass &g) { return g.M <= 96 ? 48 : 64; }
 // environment variable VPX_TC_PAIRS selects it).
 static int ws_kind(const GemmPass &g) {
     if (!g.tslices || g.Kpad % TW_K != 0) return 0;
-    if (g.slices == 5 && g.Mpad % TW_M == 0) return 1;
     if (g.slices == 6 && getenv("VPX_TC_PAIRS") != nullptr) return 2;
+    // table rows on M for 5 or 6 slices: the far-field tables (82 rows at
+    // p = 40) take one 128-row block, whose copies read up to 127 rows past
+    // the last chunk into the interleaved table's padding; rows >= M are
+    // computed and dropped
+    if (g.slices == 5 || g.slices == 6) return 1;
     return 0;
 }
 
@@ -383,6 +387,7 @@ static void ws_attr() {
 
 void gemm_ws_prepare_device() {
     ws_attr<true, 5, 64>();
+    ws_attr<true, 6, 64>();
     ws_attr<false, 6, 48>();
     ws_attr<false, 6, 64>();
 }
@@ -410,8 +415,9 @@ void gemm_ws_run(const GemmPass &g, const VecSet &vs, double *out, int64_t ldo, 
     if (g.ws_kind == 1) {
         if (g.n_tiles == 0) return;
         a.tiles = g.tiles;
-        dim3 grid(g.n_tiles, g.Mpad / TW_M, nrhs);
-        launch_pdl(k_gemm_ws<true, 5, 64>, grid, dim3(TW_THREADS), WsShape<true, 5, 64>::SMEM, st, a);
+        dim3 grid(g.n_tiles, (g.M + TW_M - 1) / TW_M, nrhs);
+        if (g.slices == 5) launch_pdl(k_gemm_ws<true, 5, 64>, grid, dim3(TW_THREADS), WsShape<true, 5, 64>::SMEM, st, a);
+        else launch_pdl(k_gemm_ws<true, 6, 64>, grid, dim3(TW_THREADS), WsShape<true, 6, 64>::SMEM, st, a);
     } else {
         if (g.n_tiles_p == 0) return;
         a.tiles = g.tiles_p;

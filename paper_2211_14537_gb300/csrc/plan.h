@@ -83,6 +83,17 @@ inline int charge_blocks(int n_leaves) {
     return b < 1 ? 1 : (b > 304 ? 304 : b);
 }
 
+// The level chains (M2M up, L2L down) as one persistent launch each (chain.cu).
+struct ChainPlan {
+    bool ok = false;              // false: the per-level passes run the chains
+    int n_up = 0, n0_up = 0, n_down = 0, n0_down = 0, max_ctas = 0;
+    void *tab_up = nullptr, *tab_down = nullptr;     // [4][P][P] complex tables (FP64 or hi/lo float pairs)
+    int16_t *kr_up = nullptr, *kr_down = nullptr;     // [4][P][2] non-zero column ranges
+    int32_t *items_up = nullptr, *items_down = nullptr, *need = nullptr;
+    int *ws = nullptr;            // both queue blocks, zeroed before every step
+    size_t ws_ints = 0;
+};
+
 struct FmmPasses {                // every contraction of the box FMM as a grouped table GEMM
     GemmPass l2m, m2l, s2l, l2t, m2t, near;
     GemmPass m2m[kMaxLevel + 1];  // parents at level l
@@ -93,6 +104,7 @@ struct FmmPasses {                // every contraction of the box FMM as a group
     int32_t *lc_off = nullptr, *lc_idx = nullptr, *tc_off = nullptr, *tc_idx = nullptr;
     double *lc_coef = nullptr, *tc_coef = nullptr;
     int32_t *fe_ex = nullptr, *mp_ex = nullptr;
+    ChainPlan chain;
 };
 
 }  // namespace vpx
@@ -172,4 +184,6 @@ void device_bie_setup(vpx_plan *p);
 void device_bie_solve(vpx_plan *p, const double *g, const double *vb, double growth, double *sol, void *stream);
 void device_bie_eval(vpx_plan *p, const double *sol, const double *v, double *u, void *stream);
 void device_bie_free(vpx_plan *p);
+int gauss_jordan_inverse(int n, double *aug_dev, double *inv_dev);   // bie_device.cu
+int device_check_gauss_jordan(int n, const double *a_host, double *inv_host);
 }  // namespace vpx

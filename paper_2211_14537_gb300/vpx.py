@@ -61,7 +61,7 @@ EXPORTED = [
     "vpx_universal_matrix", "vpx_plan_ray_operator", "vpx_execute",
     "vpx_execute_batch", "vpx_autotune", "vpx_autotune_batch",
     "vpx_extend", "vpx_potential", "vpx_potential_static", "vpx_net_charge", "vpx_bie_setup", "vpx_bie_topology", "vpx_bie_log_terms", "vpx_bie_solve", "vpx_bie_eval", "vpx_bie_dipole_multipoles", "vpx_bie_geometry", "vpx_bie_corrections", "vpx_execute_host", "vpx_sync_status", "vpx_set_timing",
-    "vpx_get_timings", "vpx_pass_name", "vpx_graph_kernel_count", "vpx_check_bounded_wait", "vpx_error_string", "vpx_last_error_message", "vpx_plan_destroy",
+    "vpx_get_timings", "vpx_pass_name", "vpx_graph_kernel_count", "vpx_check_bounded_wait", "vpx_check_gauss_jordan", "vpx_error_string", "vpx_last_error_message", "vpx_plan_destroy",
 ]
 
 _lib = None
@@ -114,6 +114,7 @@ def load_library(path: str = LIB_PATH):
     L.vpx_get_timings.argtypes = [vp, P(d), ctypes.c_int]
     L.vpx_graph_kernel_count.argtypes = [vp, P(ctypes.c_int64)]
     L.vpx_check_bounded_wait.argtypes = [P(ctypes.c_int)]
+    L.vpx_check_gauss_jordan.argtypes = [ctypes.c_int, P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_int)]
     L.vpx_pass_name.argtypes = [ctypes.c_int]
     L.vpx_pass_name.restype = ctypes.c_char_p
     L.vpx_error_string.argtypes = [ctypes.c_int]
@@ -497,3 +498,14 @@ def vpx_get_timings(plan: Plan):
     _check(load_library().vpx_get_timings(plan.handle, _dptr(a), VPX_N_PASSES))
     L = load_library()
     return {L.vpx_pass_name(i).decode(): float(a[i]) for i in range(VPX_N_PASSES)}
+
+
+def vpx_check_gauss_jordan(a: np.ndarray):
+    """(inverse, status) of the square host matrix a by the device Gauss-Jordan
+    elimination of the boundary correction; status VPX_ERR_STATE for a
+    singular matrix."""
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    inv = np.zeros_like(a)
+    st = ctypes.c_int(0)
+    _check(load_library().vpx_check_gauss_jordan(a.shape[0], _dptr(a), _dptr(inv), ctypes.byref(st)))
+    return inv, st.value

@@ -31,12 +31,13 @@ def chebyshev_stage_norm(b, K, targets):
     return max(np.abs(W).reshape(len(targets), -1).sum(axis=1).max(), 1.0)
 
 
-def extension_bounds(tree, dom, meta):
+def extension_bounds(tree, dom, meta, only=None):
     """Per extended leaf: the forward-error factor of the two-stage
     extrapolation, kappa = Lambda * ||A_E|| * ||A_I^+|| (infinity norms), with
     Lambda the norm of the Chebyshev stage (grid values -> target values);
     both implementations are backward stable, so they differ by
-    O(eps * kappa * max|f_I|).  Computed from the oracle's own operators."""
+    O(eps * kappa * max|f_I|).  Computed from the oracle's own operators;
+    `only` restricts it to the given cut leaves (and the leaves they own)."""
     owned = {}
     for j, o in enumerate(tree.owner):
         if o >= 0:
@@ -46,6 +47,8 @@ def extension_bounds(tree, dom, meta):
     A = O.universal_matrix(K)
     kappa = {}
     for i in tree.cut_leaves():
+        if only is not None and i not in only:
+            continue
         off, n, masks = meta[i]
         AI = A[np.concatenate(masks)]
         AE = A[K * K:K * K + Kbar * Kbar][~masks[1]]
