@@ -40,7 +40,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--p", type=int, default=40)
+    ap.add_argument("--p", type=int, default=27,
+                    help="expansion order: 27 keeps the potential error at the arithmetic's floor (below 1e-12) on the L-shape and the starfish")
     ap.add_argument("--precision", default="both", choices=["fp64", "mixed", "both"])
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--oracle-sample", type=int, default=0,
@@ -606,6 +607,12 @@ def main():
                 "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
                 "work": "method flops 2K^4 + 2K^2 per near pair, per launch",
                 "peak_source": "nominal GB300 FP64 (recipe); an FMA probe measured 1.20"}
+    ext_modes = None
+    if not args.no_batch and args.nrhs == 1 and rank == 0:
+        try:
+            ext_modes = extension_modes(args)
+        except Exception as e:   # noqa: BLE001 - the single-tree line stands on its own
+            ext_modes = {"error": repr(e)}
     batch = None
     if not args.no_batch and args.nrhs == 1:
         try:
@@ -649,10 +656,62 @@ def main():
     }
     if batch is not None:
         out["batch"] = batch
+    if ext_modes is not None:
+        out["extension_modes"] = ext_modes
     if cpu is not None:
         out["cpu_baseline"] = cpu
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+def extension_modes(args):
+    """Cost of the extension along lines (Section 6.4) beside the universal
+    stencil's and a potential (VFMM) call, on the starfish (K = 16, the star
+    of the lines through its centre): CUDA events around vpx_extend and
+    vpx_potential on device-resident data, L2 flushed before each call, median
+    of 20 calls, both forms of the mixed plan."""
+    import torch
+    import workloads as W
+    from paper_2211_14537_gb300 import vpx as V
+    wl = W.starfish_gaussian(K=16)
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    out = {"workload": wl.name, "precision": "mixed"}
+
+    def timed(call):
+        ts = []
+        for i in range(23):
+            with torch.cuda.stream(stream):
+                flush.fill_(float(i))
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+            call()
+            with torch.cuda.stream(stream):
+                e1.record(stream)
+            torch.cuda.synchronize(dev)
+            if i >= 3:
+                ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    for mode, code in (("stencil", 0), ("lines", 1)):
+        o = V.vpx_default_options(K=wl.opts.K, min_level=wl.opts.min_level, max_level=wl.opts.max_level,
+                                  refine_tol=wl.opts.refine_tol, f_scale=wl.opts.f_scale, p=args.p,
+                                  precision=V.VPX_PREC_MIXED, ext_mode=code)
+        plan = V.vpx_plan_create(o, wl.domain, wl.sources[0])
+        _, nt, ns, nb = plan.sizes()
+        f = torch.tensor(wl.sources[0](plan.stencil_points()), dtype=torch.float64, device=dev)
+        fe = torch.empty(nt, dtype=torch.float64, device=dev)
+        v = torch.empty(nt, dtype=torch.float64, device=dev)
+        out[mode + "_extension_ms"] = timed(lambda: V.vpx_extend(plan, f, fe, stream=stream))
+        if mode == "stencil":
+            out["potential_ms"] = timed(lambda: V.vpx_potential(plan, fe, v, None, stream=stream))
+        if V.vpx_sync_status(plan) != 0:
+            raise RuntimeError("device status error in the extension timing")
+        out[mode + "_stencil_points"] = ns
+    out["lines_over_stencil"] = out["lines_extension_ms"] / out["stencil_extension_ms"]
+    out["lines_over_potential"] = out["lines_extension_ms"] / out["potential_ms"]
+    return out
 
 
 def V_module():

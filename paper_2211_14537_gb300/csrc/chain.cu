@@ -37,6 +37,7 @@
 // per launch.
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 #include "bulk.cuh"
@@ -51,7 +52,8 @@ struct ChainArgs {
     int P, nrhs, n_slots, n0, G;  // slots: ready boxes at the start + boxes queued (downward); G: column groups per row
     int64_t ldm;                  // doubles per right-hand side of the expansion arrays
     const int32_t *items0;        // [n0] initially ready boxes
-    const int32_t *parent, *child0, *need;   // per box; need: non-zero children to wait for (upward, 0: never queued)
+    const int2 *up_of;            // per box: (parent, position 0..3 among its siblings)
+    const int32_t *child0, *need; // per box; need: non-zero children to wait for (upward, 0: not translated on)
     const void *tab;              // [4][P][P] complex: double2 (FP64 form) or float4 hi/lo pairs (mixed form)
     const int16_t *krange;        // [4][P][2] non-zero column range of every row
     int *ws;                      // [2 + n_boxes + n_slots]: claim, push, per-box counts, queued slots (box + 1)
@@ -91,54 +93,76 @@ __device__ inline void chain_push(const ChainArgs &a, int box) {
     if (s < a.n_slots - a.n0) atomicExch(a.ws + 2 + a.n_boxes + s, box + 1);
 }
 
+// table entries per thread and box, ceil(P / G): at most 8 for P <= 45, 16 for P <= 64
+
 // One CTA processes one box at a time; the tables stay in global memory (a
-// few hundred KB, L2-resident), so the CTA needs almost no shared memory and
+// few hundred KB, L2-resident), so the CTA needs little shared memory and
 // several fit on an SM beside the near-field kernel of the other stream.
-// Thread t < P G takes row t / G and the columns klo + (t % G) + G j.
-template <bool DF, bool UP>
+// Thread t < P G takes row t / G and the columns klo + (t % G) + G j; it loads
+// all its table entries of the box at once, then computes.  Upward, CTA b
+// starts from leaves b, b + grid, ... (a claim never waits, so no counter).
+template <bool DF, bool UP, int CH_NK>
 __global__ void __launch_bounds__(CH_THREADS) k_chain(ChainArgs a) {
     pdl_entry();
-    __shared__ __align__(16) float4 s_vec[kMaxP];           // the source expansion (hi/lo pairs, or FP64 bits)
-    __shared__ __align__(16) double s_part[2 * CH_THREADS];  // partial sums (re, im) per thread
+    typedef typename std::conditional<DF, float4, double2>::type E;
+    __shared__ __align__(16) E s_vec[kMaxP];                 // the source expansion
+    __shared__ __align__(16) E s_part[CH_THREADS];           // partial sums (re, im) per thread
+    __shared__ int16_t s_kr[4 * kMaxP * 2];                  // non-zero column ranges of the four tables
     __shared__ int s_item;
     const int P = a.P, G = a.G, tid = threadIdx.x;
     const int row = tid / G, g = tid % G;
     const bool act = row < P;
-    int c = -1;   // the box in hand; -1: claim the next slot
+    for (int i = tid; i < 4 * P * 2; i += CH_THREADS) s_kr[i] = a.krange[i];
+    int c = -1;          // the box in hand; -1: claim the next slot
+    int next_leaf = blockIdx.x;
     for (;;) {
         __syncthreads();   // the previous box's reads of s_vec, s_part and s_item are done
         if (c < 0) {
-            if (tid == 0) s_item = chain_claim(a);
-            __syncthreads();
-            c = s_item;
+            if (UP) {
+                c = next_leaf < a.n0 ? a.items0[next_leaf] : -1;
+                next_leaf += gridDim.x;
+            } else {
+                if (tid == 0) s_item = chain_claim(a);
+                __syncthreads();
+                c = s_item;
+            }
             if (c < 0) break;
         }
-        const int par = a.parent[c];
-        const int pos = c - a.child0[par];
+        const int2 up = a.up_of[c];
+        const int par = up.x, pos = up.y;
         const int src = UP ? c : par, dst = UP ? par : c;
         int klo = 0, khi = -1;
         if (act) {
-            klo = a.krange[((size_t)pos * P + row) * 2];
-            khi = a.krange[((size_t)pos * P + row) * 2 + 1];
+            klo = s_kr[(pos * P + row) * 2];
+            khi = s_kr[(pos * P + row) * 2 + 1];
+        }
+        const E *T = reinterpret_cast<const E *>(a.tab) + ((size_t)pos * P + (act ? row : 0)) * P;
+        E tv[CH_NK];
+#pragma unroll
+        for (int j = 0; j < CH_NK; ++j) {
+            const int k = klo + g + j * G;
+            if (k <= khi) tv[j] = __ldg(T + k);
         }
         for (int r = 0; r < a.nrhs; ++r) {
             const double *xs = a.x + r * a.ldm + (int64_t)src * 2 * P;
-            for (int k = tid; k < P; k += CH_THREADS) {
-                const double re = __ldcg(xs + 2 * k), im = __ldcg(xs + 2 * k + 1);
+            if (tid < P) {
+                const double re = __ldcg(xs + 2 * tid), im = __ldcg(xs + 2 * tid + 1);
                 if (DF) {
                     const df32 hr = df_split_bits(re), hi = df_split_bits(im);
-                    s_vec[k] = make_float4(hr.hi, hr.lo, hi.hi, hi.lo);
+                    reinterpret_cast<float4 *>(s_vec)[tid] = make_float4(hr.hi, hr.lo, hi.hi, hi.lo);
                 } else {
-                    reinterpret_cast<double2 *>(s_vec)[k] = make_double2(re, im);
+                    reinterpret_cast<double2 *>(s_vec)[tid] = make_double2(re, im);
                 }
             }
             __syncthreads();
             if (DF) {
-                const float4 *T = reinterpret_cast<const float4 *>(a.tab) + ((size_t)pos * P + (act ? row : 0)) * P;
                 df32 sr{0.f, 0.f}, si{0.f, 0.f};
-                for (int k = klo + g; k <= khi; k += G) {
-                    const float4 t = __ldg(T + k);
-                    const float4 v = s_vec[k];
+#pragma unroll
+                for (int j = 0; j < CH_NK; ++j) {
+                    const int k = klo + g + j * G;
+                    if (k > khi) break;
+                    const float4 t = reinterpret_cast<const float4 &>(tv[j]);
+                    const float4 v = reinterpret_cast<const float4 *>(s_vec)[k];
                     df_mac(sr, df32{t.x, t.y}, df32{v.x, v.y});
                     df_mac(sr, df32{-t.z, -t.w}, df32{v.z, v.w});
                     df_mac(si, df32{t.x, t.y}, df32{v.z, v.w});
@@ -148,19 +172,21 @@ __global__ void __launch_bounds__(CH_THREADS) k_chain(ChainArgs a) {
                 si = df_norm(si);
                 reinterpret_cast<float4 *>(s_part)[tid] = make_float4(sr.hi, sr.lo, si.hi, si.lo);
             } else {
-                const double2 *T = reinterpret_cast<const double2 *>(a.tab) + ((size_t)pos * P + (act ? row : 0)) * P;
                 double sr = 0.0, si = 0.0;
-                for (int k = klo + g; k <= khi; k += G) {
-                    const double2 t = __ldg(T + k);
+#pragma unroll
+                for (int j = 0; j < CH_NK; ++j) {
+                    const int k = klo + g + j * G;
+                    if (k > khi) break;
+                    const double2 t = reinterpret_cast<const double2 &>(tv[j]);
                     const double2 v = reinterpret_cast<const double2 *>(s_vec)[k];
                     sr = fma(t.x, v.x, fma(-t.y, v.y, sr));
                     si = fma(t.x, v.y, fma(t.y, v.x, si));
                 }
-                s_part[2 * tid] = sr;
-                s_part[2 * tid + 1] = si;
+                reinterpret_cast<double2 *>(s_part)[tid] = make_double2(sr, si);
             }
             __syncthreads();
-            for (int l = tid; l < P; l += CH_THREADS) {
+            if (tid < P) {
+                const int l = tid;
                 double out_re, out_im;
                 if (DF) {
                     df32 sr{0.f, 0.f}, si{0.f, 0.f};
@@ -174,8 +200,9 @@ __global__ void __launch_bounds__(CH_THREADS) k_chain(ChainArgs a) {
                 } else {
                     out_re = out_im = 0.0;
                     for (int q = 0; q < G; ++q) {
-                        out_re += s_part[2 * (l * G + q)];
-                        out_im += s_part[2 * (l * G + q) + 1];
+                        const double2 v = reinterpret_cast<const double2 *>(s_part)[l * G + q];
+                        out_re += v.x;
+                        out_im += v.y;
                     }
                 }
                 double *xd = a.x + r * a.ldm + (int64_t)dst * 2 * P + 2 * l;
@@ -213,6 +240,111 @@ __global__ void __launch_bounds__(CH_THREADS) k_chain(ChainArgs a) {
     }
 }
 
+// ---------------------------------------------------------------- subtrees
+//
+// Below the cut level Lc (the deepest level holding at least kDenseLevel
+// boxes; level 2 if none does) an adaptive tree is sparse: a few hundred
+// boxes per level, grouped around the features it resolves.  There one CTA
+// takes the whole subtree of each non-leaf box at level Lc and runs its level
+// chain with barriers between levels, one warp per translation, instead of one
+// launch per level: upward the children's multipoles into their parents from
+// the deepest level to Lc, downward the parents' locals into their children
+// from Lc + 1 to the deepest.  Levels up to Lc keep their per-level passes.
+// The four translation tables sit in shared memory (complex, P x P, stored
+// transposed); a lane takes one row (two for P > 32) and sums it over its
+// non-zero range.
+constexpr int ST_THREADS = 512;
+constexpr int kDenseLevel = 1024;
+
+struct SubtreeArgs {
+    int P, nrhs;
+    int64_t ldm;
+    const int32_t *root_seg;      // [n_roots + 1] segments (levels) of each subtree
+    const int32_t *seg_item;      // [n_segs + 1] items of each segment
+    const int32_t *item;          // [n_items][3]: source box, destination box, child position
+    const void *tab;              // [4][P][P] complex: double2 or float4 hi/lo pairs
+    const int16_t *krange;        // [4][P][2]
+    double *x;                    // expansions, [rhs][box][2P]
+    int add;                      // 1: atomic add (upward, several children), 0: read-modify-write (downward)
+};
+
+template <bool DF>
+__global__ void __launch_bounds__(ST_THREADS, 1) k_subtree(SubtreeArgs a) {
+    pdl_entry();
+    typedef typename std::conditional<DF, float4, double2>::type E;
+    extern __shared__ __align__(16) unsigned char stsm[];
+    E *tab = reinterpret_cast<E *>(stsm);
+    __shared__ int16_t s_kr[4 * kMaxP * 2];
+    __shared__ __align__(16) E s_vec[ST_THREADS / 32][kMaxP];   // each warp's source expansion
+    const int P = a.P, warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = ST_THREADS >> 5;
+    E *wv = s_vec[warp];
+    {   // transposed, [pos][k][l]: the lanes (rows l) of a warp read consecutive words at a fixed k
+        const E *src = reinterpret_cast<const E *>(a.tab);
+        for (int i = threadIdx.x; i < 4 * P * P; i += ST_THREADS) {
+            const int pos = i / (P * P), l = (i / P) % P, k = i % P;
+            tab[((size_t)pos * P + k) * P + l] = src[i];
+        }
+        for (int i = threadIdx.x; i < 4 * P * 2; i += ST_THREADS) s_kr[i] = a.krange[i];
+    }
+    __syncthreads();
+    for (int sg = a.root_seg[blockIdx.x]; sg < a.root_seg[blockIdx.x + 1]; ++sg) {
+        for (int it = a.seg_item[sg] + warp; it < a.seg_item[sg + 1]; it += nw) {
+            const int src = a.item[3 * it], dst = a.item[3 * it + 1], pos = a.item[3 * it + 2];
+            const E *T = tab + (size_t)pos * P * P;
+            for (int r = 0; r < a.nrhs; ++r) {
+                const double *xs = a.x + r * a.ldm + (int64_t)src * 2 * P;
+                double *xd = a.x + r * a.ldm + (int64_t)dst * 2 * P;
+                for (int k = lane; k < P; k += 32) {
+                    const double re = __ldcg(xs + 2 * k), im = __ldcg(xs + 2 * k + 1);
+                    if (DF) {
+                        const df32 hr = df_split_bits(re), hi = df_split_bits(im);
+                        reinterpret_cast<float4 *>(wv)[k] = make_float4(hr.hi, hr.lo, hi.hi, hi.lo);
+                    } else {
+                        reinterpret_cast<double2 *>(wv)[k] = make_double2(re, im);
+                    }
+                }
+                __syncwarp();
+                for (int l = lane; l < P; l += 32) {
+                    const int klo = s_kr[(pos * P + l) * 2], khi = s_kr[(pos * P + l) * 2 + 1];
+                    double out_re, out_im;
+                    if (DF) {
+                        df32 sr{0.f, 0.f}, si{0.f, 0.f};
+                        for (int k = klo; k <= khi; ++k) {
+                            const float4 t = reinterpret_cast<const float4 *>(T)[(size_t)k * P + l];
+                            const float4 v = reinterpret_cast<const float4 *>(wv)[k];
+                            df_mac(sr, df32{t.x, t.y}, df32{v.x, v.y});
+                            df_mac(sr, df32{-t.z, -t.w}, df32{v.z, v.w});
+                            df_mac(si, df32{t.x, t.y}, df32{v.z, v.w});
+                            df_mac(si, df32{t.z, t.w}, df32{v.x, v.y});
+                        }
+                        out_re = df_to_f64_scaled(df_norm(sr), 0);
+                        out_im = df_to_f64_scaled(df_norm(si), 0);
+                    } else {
+                        double sr = 0.0, si = 0.0;
+                        for (int k = klo; k <= khi; ++k) {
+                            const double2 t = reinterpret_cast<const double2 *>(T)[(size_t)k * P + l];
+                            const double2 v = reinterpret_cast<const double2 *>(wv)[k];
+                            sr = fma(t.x, v.x, fma(-t.y, v.y, sr));
+                            si = fma(t.x, v.y, fma(t.y, v.x, si));
+                        }
+                        out_re = sr;
+                        out_im = si;
+                    }
+                    if (a.add) {
+                        atomicAdd(xd + 2 * l, out_re);
+                        atomicAdd(xd + 2 * l + 1, out_im);
+                    } else {
+                        xd[2 * l] = __ldcg(xd + 2 * l) + out_re;
+                        xd[2 * l + 1] = __ldcg(xd + 2 * l + 1) + out_im;
+                    }
+                }
+                __syncwarp();   // wv is rewritten for the next column or item
+            }
+        }
+        __syncthreads();   // this level's results are visible to the next level's warps
+    }
+}
+
 // ------------------------------------------------------------------ host
 
 // The complex form of four real 2P x 2P translation tables (rows 2l, 2l+1 and
@@ -244,6 +376,13 @@ static bool complex_tables(const std::vector<double> &real4, int P, std::vector<
     return true;
 }
 
+
+static void setup_subtrees(vpx_plan *p, ChainPlan &C);
+
+static int chain_nk(int P) {
+    const int G = std::max(1, CH_THREADS / P);
+    return (P + G - 1) / G <= 8 ? 8 : 16;
+}
 
 // Builds both chains of a plan:
 // tables in the form's arithmetic, initially ready boxes, counts to wait for,
@@ -289,25 +428,108 @@ void setup_chains(vpx_plan *p, const std::vector<double> &m2m, const std::vector
     C.n_up = C.n0_up;            // upward: the leaves are the only claims
     C.n0_down = (int)down0.size();
     C.n_down = C.n0_down + n_queued;
+    std::vector<int32_t> up_of(2 * (size_t)nb, 0);
+    for (int b = 0; b < nb; ++b) {
+        const int pa = p->box_parent[b];
+        up_of[2 * b] = pa;
+        up_of[2 * b + 1] = pa >= 0 ? b - p->box_child0[pa] : 0;
+    }
+    C.up_of = dev_upload(up_of);
     C.items_up = dev_upload(up0);
     C.items_down = dev_upload(down0);
     C.need = dev_upload(need);
     C.ws_ints = (size_t)(2 + nb + C.n_up) + (size_t)(2 + nb + C.n_down);
     C.ws = dev_alloc<int>(C.ws_ints);
     int occ = 0;
-    if (mixed)
-        VPX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_chain<true, true>, CH_THREADS, 0));
+    const int nk = chain_nk(P);
+    if (mixed && nk == 8)
+        VPX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_chain<true, true, 8>, CH_THREADS, 0));
+    else if (mixed)
+        VPX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_chain<true, true, 16>, CH_THREADS, 0));
+    else if (nk == 8)
+        VPX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_chain<false, true, 8>, CH_THREADS, 0));
     else
-        VPX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_chain<false, true>, CH_THREADS, 0));
+        VPX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_chain<false, true, 16>, CH_THREADS, 0));
     int dev = 0, nsm = 0;
     VPX_CUDA(cudaGetDevice(&dev));
     VPX_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     C.max_ctas = std::max(1, std::min(occ, 8)) * nsm;
+    if (mixed) setup_subtrees(p, C);
     C.ok = occ > 0;
+}
+
+static size_t subtree_smem(int P) { return (size_t)4 * P * P * 16; }
+
+// The subtree work of the mixed form: the cut level, and per root the
+// segments (levels) and items of both directions.
+static void setup_subtrees(vpx_plan *p, ChainPlan &C) {
+    const int nb = (int)p->box_level.size(), nlev = p->n_levels, P = p->P;
+    if (subtree_smem(P) + sizeof(float4) * (ST_THREADS / 32) * kMaxP + 1024 > 227 * 1024) return;
+    int lc = 2;
+    for (int l = nlev - 1; l >= 2; --l)
+        if (p->level_start[l + 1] - p->level_start[l] >= kDenseLevel) {
+            lc = l;
+            break;
+        }
+    if (lc >= nlev - 1) return;
+    std::vector<int32_t> root_seg[2], seg_item[2], item[2];
+    for (int d = 0; d < 2; ++d) {
+        root_seg[d].push_back(0);
+        seg_item[d].push_back(0);
+    }
+    int n_roots = 0;
+    for (int r = p->level_start[lc]; r < p->level_start[lc + 1]; ++r) {
+        if (p->box_child0[r] < 0) continue;
+        ++n_roots;
+        std::vector<std::vector<int32_t>> lev(1, std::vector<int32_t>{r});
+        while (true) {
+            std::vector<int32_t> next;
+            for (int b : lev.back())
+                if (p->box_child0[b] >= 0)
+                    for (int k = 0; k < 4; ++k) next.push_back(p->box_child0[b] + k);
+            if (next.empty()) break;
+            lev.push_back(next);
+        }
+        // upward: deepest level first, non-zero boxes into their parents (atomic)
+        for (int li = (int)lev.size() - 1; li >= 1; --li) {
+            bool any = false;
+            for (int c : lev[li]) {
+                if (!p->box_nz[c]) continue;
+                const int pa = p->box_parent[c];
+                item[0].insert(item[0].end(), {c, pa, c - p->box_child0[pa]});
+                any = true;
+            }
+            if (any) seg_item[0].push_back((int32_t)(item[0].size() / 3));
+        }
+        // downward: shallowest level first, every box from its parent
+        for (int li = 1; li < (int)lev.size(); ++li) {
+            for (int c : lev[li]) {
+                const int pa = p->box_parent[c];
+                item[1].insert(item[1].end(), {pa, c, c - p->box_child0[pa]});
+            }
+            seg_item[1].push_back((int32_t)(item[1].size() / 3));
+        }
+        for (int d = 0; d < 2; ++d) root_seg[d].push_back((int32_t)seg_item[d].size() - 1);
+    }
+    if (n_roots == 0) return;
+    for (int d = 0; d < 2; ++d) {
+        C.st_root_seg[d] = dev_upload(root_seg[d]);
+        C.st_seg_item[d] = dev_upload(seg_item[d]);
+        C.st_item[d] = dev_upload(item[d]);
+    }
+    const size_t smem = subtree_smem(P);
+    VPX_CUDA(cudaFuncSetAttribute(k_subtree<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    C.lc = lc;
+    C.n_roots = n_roots;
 }
 
 void free_chains(vpx_plan *p) {
     ChainPlan &C = p->fmm.chain;
+    for (int d = 0; d < 2; ++d) {
+        dev_free(C.st_root_seg[d]);
+        dev_free(C.st_seg_item[d]);
+        dev_free(C.st_item[d]);
+    }
     dev_free(C.tab_up);
     dev_free(C.tab_down);
     dev_free(C.kr_up);
@@ -315,8 +537,30 @@ void free_chains(vpx_plan *p) {
     dev_free(C.items_up);
     dev_free(C.items_down);
     dev_free(C.need);
+    dev_free(C.up_of);
     dev_free(C.ws);
     C = ChainPlan();
+}
+
+// One launch of the subtree chains below the cut level (mixed form): upward
+// into the cut level's boxes, or downward from them.
+void subtree_run(vpx_plan *p, bool up, double *x, int64_t ldm, int nrhs, cudaStream_t s) {
+    const ChainPlan &C = p->fmm.chain;
+    if (C.n_roots == 0) return;
+    SubtreeArgs a;
+    a.P = p->P;
+    a.nrhs = nrhs;
+    a.ldm = ldm;
+    const int d = up ? 0 : 1;
+    a.root_seg = C.st_root_seg[d];
+    a.seg_item = C.st_seg_item[d];
+    a.item = C.st_item[d];
+    a.tab = up ? C.tab_up : C.tab_down;
+    a.krange = up ? C.kr_up : C.kr_down;
+    a.x = x;
+    a.add = up ? 1 : 0;
+    launch_pdl(k_subtree<true>, dim3(C.n_roots), dim3(ST_THREADS), subtree_smem(p->P), s, a);
+    VPX_LAUNCH("k_subtree");
 }
 
 // Zeroes both queue blocks (one memset, ahead of the upward chain).
@@ -337,7 +581,7 @@ void chain_run(vpx_plan *p, bool up, double *x, int64_t ldm, int nrhs, cudaStrea
     if (a.n_slots == 0) return;
     a.ldm = ldm;
     a.items0 = up ? C.items_up : C.items_down;
-    a.parent = p->dt.box_parent;
+    a.up_of = reinterpret_cast<const int2 *>(C.up_of);
     a.child0 = p->dt.box_child0;
     a.need = C.need;
     a.tab = up ? C.tab_up : C.tab_down;
@@ -349,10 +593,18 @@ void chain_run(vpx_plan *p, bool up, double *x, int64_t ldm, int nrhs, cudaStrea
     const dim3 grid((unsigned)std::min(a.n_slots, C.max_ctas));
     const size_t smem = 0;
     const bool mixed = p->opt.precision == VPX_PREC_MIXED;
-    if (mixed && up) launch_pdl(k_chain<true, true>, grid, dim3(CH_THREADS), smem, s, a);
-    else if (mixed) launch_pdl(k_chain<true, false>, grid, dim3(CH_THREADS), smem, s, a);
-    else if (up) launch_pdl(k_chain<false, true>, grid, dim3(CH_THREADS), smem, s, a);
-    else launch_pdl(k_chain<false, false>, grid, dim3(CH_THREADS), smem, s, a);
+    const int nk = chain_nk(p->P);
+    if (nk == 8) {
+        if (mixed && up) launch_pdl(k_chain<true, true, 8>, grid, dim3(CH_THREADS), smem, s, a);
+        else if (mixed) launch_pdl(k_chain<true, false, 8>, grid, dim3(CH_THREADS), smem, s, a);
+        else if (up) launch_pdl(k_chain<false, true, 8>, grid, dim3(CH_THREADS), smem, s, a);
+        else launch_pdl(k_chain<false, false, 8>, grid, dim3(CH_THREADS), smem, s, a);
+    } else {
+        if (mixed && up) launch_pdl(k_chain<true, true, 16>, grid, dim3(CH_THREADS), smem, s, a);
+        else if (mixed) launch_pdl(k_chain<true, false, 16>, grid, dim3(CH_THREADS), smem, s, a);
+        else if (up) launch_pdl(k_chain<false, true, 16>, grid, dim3(CH_THREADS), smem, s, a);
+        else launch_pdl(k_chain<false, false, 16>, grid, dim3(CH_THREADS), smem, s, a);
+    }
     VPX_LAUNCH("k_chain");
 }
 

@@ -62,21 +62,42 @@ __device__ __forceinline__ void pdl_entry() {
 
 bool pdl_enabled();   // false when VPX_NO_PDL is set (read once)
 
+// Scheduling priority of the launches made on this thread (a hint to the
+// block scheduler, recorded in captured graphs): kNoPriority leaves the
+// stream's own.  The execute path runs its critical chain at the device's
+// greatest priority and the near field, which only has to finish by the end,
+// at the least, so that it yields SMs to the chain.
+constexpr int kNoPriority = -1000000;
+int &launch_priority();
+int priority_greatest();
+int priority_least();
+struct LaunchPriority {
+    int prev;
+    explicit LaunchPriority(int p) : prev(launch_priority()) { launch_priority() = p; }
+    ~LaunchPriority() { launch_priority() = prev; }
+};
+
 // kernel<<<grid, block, smem, s>>>(args...) with the programmatic
 // stream-serialization attribute: the kernel may begin while the previous
 // kernel of the stream finishes (it waits in pdl_entry for that kernel's data)
 template <typename... KArgs, typename... Args>
 void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args &&...args) {
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = pdl_enabled() ? 1 : 0;
+    unsigned n_attr = 1;
+    if (launch_priority() != kNoPriority) {
+        attr[1].id = cudaLaunchAttributePriority;
+        attr[1].val.priority = launch_priority();
+        n_attr = 2;
+    }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = grid;
     cfg.blockDim = block;
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = n_attr;
     VPX_CUDA(cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...));
 }
 

@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "dev_common.cuh"
+#include "slice_math.cuh"
 #include "ext.cuh"
 
 namespace vpx {
@@ -25,17 +26,46 @@ __device__ inline double box_side_d(int level) { return ldexp(1.0, -level); }
 // ---------------------------------------------------------------- extension
 
 // regular leaves: copy data; exterior leaves outside every extension list: 0
-__global__ void k_leafvals(int n_leaves, int KK, const int32_t *leaf_cls, const int32_t *owner_flag,
-                           const int64_t *reg_off, const double *f, int64_t ldf, double *fe, int64_t ldfe) {
+// The leaf values that need no extension, one warp per leaf: a regular leaf
+// takes the data at its nodes, an exterior leaf in no extension list is zero
+// (cut leaves and extension-list leaves are the extension's).  In the mixed
+// form (sl non-null) the warp also writes the leaf's exact bf16 slices and
+// exponent, as the potential's passes read them (slice_math.cuh).
+__global__ void __launch_bounds__(256) k_leafvals(int n_leaves, int KK, int kpad, const int32_t *leaf_cls,
+                                                  const int32_t *owner_flag, const int64_t *reg_off, const double *f,
+                                                  int64_t ldf, double *fe, int64_t ldfe, uint16_t *sl, int32_t *ex) {
     pdl_entry();
-    const int rhs = blockIdx.y;
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (int64_t)n_leaves * KK) return;
-    const int leaf = (int)(idx / KK), j = (int)(idx % KK);
+    const int rhs = blockIdx.y, lane = threadIdx.x & 31;
+    const int leaf = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (leaf >= n_leaves) return;
     const int cls = leaf_cls[leaf];
-    double *o = fe + rhs * ldfe + idx;
-    if (cls == kRegular) *o = f[rhs * ldf + reg_off[leaf] + j];
-    else if (cls == kExterior && owner_flag[leaf] == 0) *o = 0.0;
+    const bool reg = cls == kRegular;
+    if (!reg && !(cls == kExterior && owner_flag[leaf] == 0)) return;
+    double xv[kSliceMaxPerLane];
+    uint64_t mb = 0;
+    const double *src = reg ? f + rhs * ldf + reg_off[leaf] : nullptr;
+    double *o = fe + rhs * ldfe + (int64_t)leaf * KK;
+#pragma unroll
+    for (int q = 0; q < kSliceMaxPerLane; ++q) {
+        const int j = lane + 32 * q;
+        xv[q] = (reg && j < KK) ? src[j] : 0.0;
+        if (j < KK) o[j] = xv[q];
+        const uint64_t t = slice_abs_bits(xv[q]);
+        mb = t > mb ? t : mb;
+    }
+    if (!sl) return;
+    const int e = slice_warp_expo(mb);
+    uint16_t *out = sl + ((size_t)rhs * n_leaves + leaf) * kSlicesS * kpad;
+#pragma unroll
+    for (int q = 0; q < kSliceMaxPerLane; ++q) {
+        const int j = lane + 32 * q;
+        if (j >= kpad) break;
+        uint16_t d[kSlicesS];
+        slice_digits(slice_fixed_point(xv[q], e), d);
+#pragma unroll
+        for (int k = 0; k < kSlicesS; ++k) out[(size_t)k * kpad + j] = d[k];
+    }
+    if (lane == 0) ex[(size_t)rhs * n_leaves + leaf] = e;
 }
 
 // Extension along lines (Section 6.4): the value at each exterior grid point
@@ -257,7 +287,11 @@ static size_t extension_smem(const vpx_plan *p) {
 static void prepare_extension(vpx_plan *p) {
     const size_t smem = extension_smem(p);
     if (smem > 48 * 1024) VPX_CUDA(cudaFuncSetAttribute(k_extend, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    if (p->opt.precision == VPX_PREC_MIXED) extend_df_prepare(p->ext.max_interior, p->K, p->st.Kbar);
+    // the coefficient kernel runs for the universal stencil only (its shared
+    // memory holds a cut leaf's interior stencil values, which along lines
+    // would be the line points as well)
+    if (p->opt.precision == VPX_PREC_MIXED)
+        extend_df_prepare(p->ext.mode == 1 ? 0 : p->ext.max_interior, p->K, p->st.Kbar, p->st.NG);
 }
 
 // Per-plan index arrays of the execute path: non-zero leaves and the
@@ -283,19 +317,25 @@ void ev_record(vpx_plan *p, int i, cudaStream_t s) {
 
 void ev_record_pass(vpx_plan *p, int i, cudaStream_t s) { ev_record(p, i, s); }
 
+// Leaf values f^e of every leaf into fe; with slice = true (mixed form) also
+// their exact slices into the plan's slice buffer, written by the kernels that
+// produce the values, so that the potential need not slice them again.
 static void run_extension(vpx_plan *p, const double *f, int nrhs, int64_t ldf, double *fe, int64_t ldfe,
-                          cudaStream_t s) {
+                          cudaStream_t s, bool slice = false) {
     const int nl = p->dt.n_leaves, KK = p->KK;
     const int64_t n = (int64_t)nl * KK;
+    const int kpad_f = (KK + 31) / 32 * 32;
+    uint16_t *sl = slice ? p->fmm.fe_sl : nullptr;
+    int32_t *ex = slice ? p->fmm.fe_ex : nullptr;
     // regular and unowned exterior leaves on the second stream, beside the
     // extension (which writes only the cut leaves and their extension lists)
     cudaStream_t aux = (cudaStream_t)p->aux_stream;
     if (n > 0) {
         VPX_CUDA(cudaEventRecord((cudaEvent_t)p->ev_lvf, s));
         VPX_CUDA(cudaStreamWaitEvent(aux, (cudaEvent_t)p->ev_lvf, 0));
-        dim3 g((unsigned)((n + 255) / 256), nrhs);
-        launch_pdl(k_leafvals, g, dim3(256), 0, aux, nl, KK, p->dt.leaf_cls, p->ext.owned_flag_dev, p->ext.reg_leaf_off, f,
-                   ldf, fe, ldfe);
+        dim3 g((unsigned)((nl + 7) / 8), nrhs);
+        launch_pdl(k_leafvals, g, dim3(256), 0, aux, nl, KK, kpad_f, p->dt.leaf_cls, p->ext.owned_flag_dev,
+                   p->ext.reg_leaf_off, f, ldf, fe, ldfe, sl, ex);
         VPX_LAUNCH("k_leafvals");
         VPX_CUDA(cudaEventRecord((cudaEvent_t)p->ev_lv, aux));
     }
@@ -326,6 +366,11 @@ static void run_extension(vpx_plan *p, const double *f, int nrhs, int64_t ldf, d
         a.ldfe = ldfe;
         a.pinv_df = reinterpret_cast<const float2 *>(p->ext.pinv_df);
         a.cheb_df = reinterpret_cast<const float2 *>(p->ext.cheb_df);
+        a.agT_df = reinterpret_cast<const float2 *>(p->ext.agT_df);
+        a.fe_sl = sl;
+        a.fe_ex = ex;
+        a.n_leaves = nl;
+        a.kpad = kpad_f;
         const size_t smem = extension_smem(p);
         DevExt &xe = p->ext;
         const int Kb2e = p->st.Kbar * p->st.Kbar;
@@ -347,15 +392,23 @@ static void run_extension(vpx_plan *p, const double *f, int nrhs, int64_t ldf, d
             VPX_LAUNCH("k_extend");
         } else if (p->opt.precision == VPX_PREC_MIXED) {
             DevExt &x = p->ext;
-            const int Kb2 = p->st.Kbar * p->st.Kbar;
-            const int64_t ldc = (int64_t)x.ncut * p->st.NG, ldF = (int64_t)x.ncut * Kb2;
             a.pinv_df_off = x.pinv_df_off;
-            launch_ext_coeff_df(a, x.ncut, x.max_interior, nrhs, x.cbuf, ldc, p->wk.status, s);
-            VecSet vc{x.cbuf, ldc, p->st.NG, nullptr, nullptr, x.ncut, 0};
-            gemm_run(x.grid_pass, vc, x.Fall, ldF, nrhs, true, s);
-            launch_ext_eval_df(a, x.ncut, x.n_tgt, x.tgt_cut, x.tgt_leaf,
-                               reinterpret_cast<const ExtTgtGeo *>(x.tgt_geo), x.Fall, ldF,
-                               reinterpret_cast<float2 *>(x.alpha), nrhs, p->wk.status, s);
+            if (getenv("VPX_EXT_THREE_STEPS")) {   // the earlier form: fit, table pass for the grid, coefficients
+                const int Kb2 = p->st.Kbar * p->st.Kbar;
+                const int64_t ldc = (int64_t)x.ncut * p->st.NG, ldF = (int64_t)x.ncut * Kb2;
+                launch_ext_coeff_df(a, x.ncut, x.max_interior, nrhs, x.cbuf, ldc, p->wk.status, s);
+                VecSet vc{x.cbuf, ldc, p->st.NG, nullptr, nullptr, x.ncut, 0};
+                gemm_run(x.grid_pass, vc, x.Fall, ldF, nrhs, true, s);
+                launch_ext_eval_df(a, x.ncut, x.n_tgt, x.tgt_cut, x.tgt_leaf,
+                                   reinterpret_cast<const ExtTgtGeo *>(x.tgt_geo), x.Fall, ldF,
+                                   reinterpret_cast<float2 *>(x.alpha), nrhs, p->wk.status, s);
+            } else {   // one kernel per cut leaf up to the coefficients, then the evaluation
+                launch_ext_fit_df(a, x.ncut, x.max_interior, nrhs, reinterpret_cast<float2 *>(x.alpha), p->wk.status,
+                                  s);
+                launch_ext_eval_df(a, x.ncut, x.n_tgt, x.tgt_cut, x.tgt_leaf,
+                                   reinterpret_cast<const ExtTgtGeo *>(x.tgt_geo), nullptr, 0,
+                                   reinterpret_cast<float2 *>(x.alpha), nrhs, p->wk.status, s);
+            }
         } else {
             launch_pdl(k_extend, dim3(p->ext.ncut, nrhs), dim3(256), smem, s, a);
             VPX_LAUNCH("k_extend");
@@ -365,13 +418,14 @@ static void run_extension(vpx_plan *p, const double *f, int nrhs, int64_t ldf, d
 }
 
 void run_potential_passes(vpx_plan *p, const double *fe, int64_t ldfe, int nrhs, double *v, int64_t ldv, double *vb,
-                          int64_t ldb, double *mp, double *lo, cudaStream_t s);
+                          int64_t ldb, double *mp, double *lo, cudaStream_t s, bool fe_sliced);
 
 // The box FMM and the boundary interpolation, with the multipole and local
-// expansions in the scratch arrays mp and lo (each nrhs x n_boxes x 2P doubles).
+// expansions in the scratch arrays mp and lo (each nrhs x n_boxes x 2P doubles);
+// fe_sliced: the leaf values' slices are already in the plan's slice buffer.
 void run_potential_scratch(vpx_plan *p, const double *fe, int64_t ldfe, int nrhs, double *v, int64_t ldv, double *vb,
-                           int64_t ldb, double *mp, double *lo, cudaStream_t s) {
-    run_potential_passes(p, fe, ldfe, nrhs, v, ldv, vb, ldb, mp, lo, s);
+                           int64_t ldb, double *mp, double *lo, cudaStream_t s, bool fe_sliced) {
+    run_potential_passes(p, fe, ldfe, nrhs, v, ldv, vb, ldb, mp, lo, s, fe_sliced);
     const int nbd = (vb != nullptr) ? (int)p->bdry_leaf.size() : 0;
     const int64_t n_v = (int64_t)p->dt.n_leaves * p->KK;
     const int nan_blocks = (int)((n_v + 255) / 256);
@@ -386,7 +440,7 @@ void run_potential_scratch(vpx_plan *p, const double *fe, int64_t ldfe, int nrhs
 
 static void run_potential(vpx_plan *p, const double *fe, int64_t ldfe, int nrhs, double *v, int64_t ldv, double *vb,
                           int64_t ldb, cudaStream_t s) {
-    run_potential_scratch(p, fe, ldfe, nrhs, v, ldv, vb, ldb, p->wk.mpole, p->wk.local, s);
+    run_potential_scratch(p, fe, ldfe, nrhs, v, ldv, vb, ldb, p->wk.mpole, p->wk.local, s, false);
 }
 
 void device_extend(vpx_plan *p, const double *f, int nrhs, int64_t ldf, double *fe, int64_t ldfe, void *stream) {
@@ -417,9 +471,10 @@ void device_net_charge(vpx_plan *p, const double *fe, int64_t ldfe, int nrhs, do
 static void execute_sequence(vpx_plan *p, const double *f, int nrhs, int64_t ldf, double *v, int64_t ldv, double *vb,
                              int64_t ldb, cudaStream_t s) {
     const int64_t ldfe = (int64_t)p->dt.n_leaves * p->KK;
+    const bool mixed = p->opt.precision == VPX_PREC_MIXED;
     ev_record(p, 0, s);
-    run_extension(p, f, nrhs, ldf, p->wk.fe, ldfe, s);
-    run_potential(p, p->wk.fe, ldfe, nrhs, v, ldv, vb, ldb, s);
+    run_extension(p, f, nrhs, ldf, p->wk.fe, ldfe, s, mixed);
+    run_potential_scratch(p, p->wk.fe, ldfe, nrhs, v, ldv, vb, ldb, p->wk.mpole, p->wk.local, s, mixed);
 }
 
 // The whole sequence (about 25 kernels) is captured into a CUDA graph on the
@@ -635,9 +690,11 @@ void device_autotune(int n, vpx_plan *const *plans, const double *const *f, cons
                 if (role >= sizeof(vpx_plan)) continue;
                 TunePass t{c, role, gemm_choice(*c.g), {}};
                 // engine 0 routes to tcgen05 where eligible, else to the fragment engine;
-                // engine 1 forces the fragment engine (a distinct choice only where tcgen05 is eligible)
-                const int frag_engine = gemm_ws_eligible(*c.g, c.vs) ? 1 : 0;
-                if (frag_engine == 1) t.cand.push_back(GemmChoice{0, 0});
+                // engine 1 forces the fragment engine (a distinct choice only where tcgen05 is
+                // eligible; elsewhere both values mean the fragment engine, so the pass keeps its own)
+                const bool tc = gemm_ws_eligible(*c.g, c.vs);
+                const int frag_engine = tc ? 1 : c.g->engine;
+                if (tc) t.cand.push_back(GemmChoice{0, 0});
                 t.cand.push_back(GemmChoice{frag_engine, 8});
                 t.cand.push_back(GemmChoice{frag_engine, 32});
                 bool has_default = false;

@@ -18,7 +18,7 @@
 namespace vpx {
 
 void run_potential_scratch(vpx_plan *p, const double *fe, int64_t ldfe, int nrhs, double *v, int64_t ldv, double *vb,
-                           int64_t ldb, double *mp, double *lo, cudaStream_t s);
+                           int64_t ldb, double *mp, double *lo, cudaStream_t s, bool fe_sliced);
 
 static __device__ __align__(256) double g_static_scratch[VPX_STATIC_SCRATCH_DOUBLES];
 
@@ -75,7 +75,7 @@ void device_potential_static(vpx_plan *p, const double *fe, int64_t ldfe, int nr
     ev_record(p, 0, s);
     // the passes zero both expansion arrays at the start of every call (the
     // scratch keeps the previous call's values until then)
-    run_potential_scratch(p, fe, ldfe, nrhs, v, ldv, vb, ldb, base, base + per, s);
+    run_potential_scratch(p, fe, ldfe, nrhs, v, ldv, vb, ldb, base, base + per, s, false);
 }
 
 }  // namespace vpx

@@ -192,11 +192,27 @@ void setup_chains(vpx_plan *p, const std::vector<double> &m2m, const std::vector
 void free_chains(vpx_plan *p);
 void chain_reset(vpx_plan *p, cudaStream_t s);
 void chain_run(vpx_plan *p, bool up, double *x, int64_t ldm, int nrhs, cudaStream_t s);
+void subtree_run(vpx_plan *p, bool up, double *x, int64_t ldm, int nrhs, cudaStream_t s);
 
-// The level chains as one persistent launch each, unless the tables do not fit
-// shared memory or VPX_PER_LEVEL_CHAINS is set (the per-level passes then run them).
+// The mixed form's level chains below the cut level as one subtree launch per
+// direction (VPX_NO_SUBTREES keeps every level on its own pass): the cut
+// level, or -1.
+static int subtree_cut(const vpx_plan *p) {
+    if (p->opt.precision != VPX_PREC_MIXED || p->fmm.chain.n_roots == 0 || getenv("VPX_NO_SUBTREES")) return -1;
+    return p->fmm.chain.lc;
+}
+
+// The level chains as one persistent launch each in the FP64 form, one launch
+// per level in the mixed form: measured on the L-shape step, the persistent
+// chains cut the FP64 form's L2L from 0.38 to 0.14 ms, while the mixed form's
+// double-float row engine per level ran as fast as they did beside the
+// near-field kernel (0.684 against 0.692 ms per step).  VPX_PERSISTENT_CHAINS
+// (1 or 0) overrides the choice for either form.
 static bool use_chains(const vpx_plan *p) {
-    return p->fmm.chain.ok && getenv("VPX_PER_LEVEL_CHAINS") == nullptr;
+    if (!p->fmm.chain.ok) return false;
+    const char *e = getenv("VPX_PERSISTENT_CHAINS");
+    if (e) return e[0] == '1';
+    return p->opt.precision != VPX_PREC_MIXED;
 }
 
 void setup_passes(vpx_plan *p) {
@@ -415,7 +431,7 @@ void ev_record_pass(vpx_plan *p, int i, cudaStream_t s);
 // locals with atomics, and are joined where their results are read (the
 // locals before L2L, V before the last launch).
 void run_potential_passes(vpx_plan *p, const double *fe, int64_t ldfe, int nrhs, double *v, int64_t ldv, double *vb,
-                          int64_t ldb, double *mp, double *lo, cudaStream_t s) {
+                          int64_t ldb, double *mp, double *lo, cudaStream_t s, bool fe_sliced) {
     const bool mixed = p->opt.precision == VPX_PREC_MIXED;
     const int P = p->P, P2 = 2 * P, KK = p->KK;
     const DevTree &d = p->dt;
@@ -431,6 +447,7 @@ void run_potential_passes(vpx_plan *p, const double *fe, int64_t ldfe, int nrhs,
     VecSet vmf{mp, ldm, P2, F.mp_sl, F.mp_ex, nb, kp_m};
     if (!mixed) vmf = vm;
     cudaStream_t aux = (cudaStream_t)p->aux_stream, aux2 = (cudaStream_t)p->aux2_stream;
+    LaunchPriority critical(priority_greatest());
     ev_record_pass(p, 1, s);
     VPX_CUDA(cudaMemsetAsync(mp, 0, sizeof(double) * ldm * nrhs, s));
     VPX_CUDA(cudaMemsetAsync(lo, 0, sizeof(double) * ldm * nrhs, s));
@@ -439,23 +456,32 @@ void run_potential_passes(vpx_plan *p, const double *fe, int64_t ldfe, int nrhs,
     VPX_CUDA(cudaMemset2DAsync(v, sizeof(double) * ldv, 0, sizeof(double) * (size_t)nl * KK, nrhs, s));
     // the leaf-value slices serve L2M, the near field and list i+ (slicing L2M's
     // 256-long vectors on the fly took longer than slicing once before it)
-    if (mixed) slice_vectors(vf, 0, nl, KK, kp_f, nrhs, s);
+    if (mixed && !fe_sliced) slice_vectors(vf, 0, nl, KK, kp_f, nrhs, s);
     // fork: the near field on the second stream; list i+ (leaf values ->
     // local), then the constant terms and list i- on the third
     VPX_CUDA(cudaEventRecord((cudaEvent_t)p->ev_fork, s));
     VPX_CUDA(cudaStreamWaitEvent(aux, (cudaEvent_t)p->ev_fork, 0));
     VPX_CUDA(cudaStreamWaitEvent(aux2, (cudaEvent_t)p->ev_fork, 0));
     ev_record_pass(p, VPX_N_PASSES + 1, aux);
-    gemm_run(F.near, vf, v, ldv, nrhs, mixed, aux);
+    {
+        LaunchPriority background(priority_least());
+        gemm_run(F.near, vf, v, ldv, nrhs, mixed, aux);
+    }
     ev_record_pass(p, VPX_N_PASSES + 2, aux);
     VPX_CUDA(cudaEventRecord((cudaEvent_t)p->ev_join, aux));
     gemm_run(F.s2l, vf, lo, ldm, nrhs, mixed, aux2);
     // main stream: upward pass
     gemm_run(F.l2m, vf, mp, ldm, nrhs, mixed, s);
     ev_record_pass(p, 2, s);
-    if (chains) chain_run(p, true, mp, ldm, nrhs, s);
-    else
+    const int lc = chains ? -1 : subtree_cut(p);
+    if (chains) {
+        chain_run(p, true, mp, ldm, nrhs, s);
+    } else if (lc >= 0) {   // the sparse levels into the cut level, then parents above it level by level
+        subtree_run(p, true, mp, ldm, nrhs, s);
+        for (int l = lc - 1; l >= 2; --l) gemm_run(F.m2m[l], vm, mp, ldm, nrhs, mixed, s);
+    } else {
         for (int l = d.n_levels - 1; l >= 3; --l) gemm_run(F.m2m[l - 1], vm, mp, ldm, nrhs, mixed, s);
+    }
     if (mixed) slice_vectors(vmf, 0, nb, P2, kp_m, nrhs, s);
     // the final multipoles feed the constant terms and list i- on the third
     // stream, beside M2L on this one (all accumulate into distinct sums)
@@ -478,9 +504,14 @@ void run_potential_passes(vpx_plan *p, const double *fe, int64_t ldfe, int nrhs,
     gemm_run(F.m2l, vmf, lo, ldm, nrhs, mixed, s);
     VPX_CUDA(cudaStreamWaitEvent(s, (cudaEvent_t)p->ev_lc, 0));
     ev_record_pass(p, 4, s);
-    if (chains) chain_run(p, false, lo, ldm, nrhs, s);
-    else
+    if (chains) {
+        chain_run(p, false, lo, ldm, nrhs, s);
+    } else if (lc >= 0) {   // parents above the cut level level by level, then the sparse levels below it
+        for (int l = 2; l < lc; ++l) gemm_run(F.l2l[l], vl, lo, ldm, nrhs, mixed, s);
+        subtree_run(p, false, lo, ldm, nrhs, s);
+    } else {
         for (int l = 2; l + 1 < d.n_levels; ++l) gemm_run(F.l2l[l], vl, lo, ldm, nrhs, mixed, s);
+    }
     ev_record_pass(p, 5, s);
     gemm_run(F.l2t, vl, v, ldv, nrhs, mixed, s);
     ev_record_pass(p, 6, s);

@@ -103,7 +103,6 @@ __device__ __host__ inline int slice_expo(double amax) {
 }
 
 // One warp per (vector, rhs): exponent and slices (slice_math.cuh), zero padded to Kpad.
-constexpr int kSliceMaxPerLane = 8;   // Kpad <= 256
 
 __global__ void k_slice_vec(const double *vbase, int64_t vld, int vstride, int first, int count, int Kd, int Kpad,
                             int nvec, uint16_t *slices, int32_t *expo) {
@@ -303,6 +302,35 @@ bool pdl_enabled() {
 
 void gemm_set_recorder(std::vector<GemmCall> *rec) { t_recorder = rec; }
 
+int &launch_priority() {
+    static thread_local int prio = kNoPriority;
+    return prio;
+}
+
+static void priority_range(int &least, int &greatest) {
+    static int l = 0, g = 0, done = 0;
+    if (!done) {
+        VPX_CUDA(cudaDeviceGetStreamPriorityRange(&l, &g));
+        done = 1;
+    }
+    least = l;
+    greatest = g;
+}
+
+int priority_greatest() {
+    if (getenv("VPX_NO_PRIORITY")) return kNoPriority;
+    int l, g;
+    priority_range(l, g);
+    return g;
+}
+
+int priority_least() {
+    if (getenv("VPX_NO_PRIORITY")) return kNoPriority;
+    int l, g;
+    priority_range(l, g);
+    return l;
+}
+
 bool gemm_frag_eligible(const GemmPass &g, const VecSet &vs);
 void gemm_rows_run(const GemmPass &g, const VecSet &vs, double *out, int64_t ldo, int nrhs, void *s);
 bool gemm_ws_eligible(const GemmPass &g, const VecSet &vs);
@@ -338,8 +366,10 @@ void gemm_run(const GemmPass &g, const VecSet &vs, double *out, int64_t ldo, int
         return;
     }
     if (t_recorder) t_recorder->push_back(GemmCall{const_cast<GemmPass *>(&g), vs, out, ldo, nrhs});
-    const bool no_tc = getenv("VPX_NO_TC") != nullptr;   // read per call: lets a test compare the engines
-    if (!no_tc && g.engine == 0 && gemm_ws_eligible(g, vs)) {
+    // read per call, so that a test can compare the engines: VPX_NO_TC keeps
+    // every pass off tcgen05, VPX_TC_ALL puts every eligible pass on it
+    const bool no_tc = getenv("VPX_NO_TC") != nullptr, all_tc = getenv("VPX_TC_ALL") != nullptr;
+    if (!no_tc && (g.engine == 0 || all_tc) && gemm_ws_eligible(g, vs)) {
         gemm_ws_run(g, vs, out, ldo, nrhs, sv);
         return;
     }

@@ -377,6 +377,11 @@ void gemm_ws_prepare(GemmPass &g) {
     VPX_CUDA(cudaDeviceSynchronize());
     g.tint = ti;
     g.ws_kind = kind;
+    // the far-field (six-slice) passes start on the fragment engine: their
+    // tables (2(p+1) <= 64 rows at the operating p) fill less than half of the
+    // 128-row MMA block here (measured: M2L 156 us here, about 90 us there on
+    // the L-shape at p = 27); the autotuner keeps tcgen05 as a candidate
+    if (kind == 1 && g.slices == 6) g.engine = 1;
 }
 
 template <bool TM, int S, int NB>

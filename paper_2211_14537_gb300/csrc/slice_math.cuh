@@ -24,8 +24,21 @@
 
 namespace vpx {
 
+constexpr int kSliceMaxPerLane = 8;   // elements per lane when a warp slices one vector: Kpad <= 256
+
+// exponent e with max|x| in [2^{e-1}, 2^e), from the largest |bit pattern|
+// (|x| compares as its bit pattern); 0 for an all-zero vector
+__device__ inline int slice_expo_of_bits(uint64_t mb) {
+    if (mb == 0) return 0;
+    const int bex = (int)(mb >> 52);
+    if (bex != 0) return bex - 1022;
+    int e = 0;
+    frexp(__longlong_as_double((long long)mb), &e);   // subnormal maximum
+    return e;
+}
+
 // exponent e of the largest |x| over a warp's elements, given each lane's
-// max |bit pattern| (|x| compares as its bit pattern): max|x| in [2^{e-1}, 2^e)
+// max |bit pattern|: max|x| in [2^{e-1}, 2^e)
 __device__ inline int slice_warp_expo(uint64_t mb) {
     for (int o = 16; o; o >>= 1) {
         const uint64_t t = (uint64_t)__shfl_xor_sync(0xffffffffu, (long long)mb, o);

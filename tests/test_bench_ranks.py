@@ -103,7 +103,8 @@ def test_bench_line_carries_the_contract_keys(monkeypatch, capsys, wl_name):
     assert d["cpu_baseline"]["one_core"]["value"] == 2.0 and d["cpu_baseline"]["one_core"]["cores"] == 1
     assert d["cpu_baseline"]["extrapolated_full_s"] == pytest.approx(184832 / 10.0)
     fl = d["config"]["algorithmic_flops_per_rhs"]
-    assert fl["near"] == 4900 * (2 * 16 ** 4 + 2 * 256) and fl["m2l"] == 8 * 41 ** 2 * 14104
+    P = d["config"]["p"] + 1
+    assert fl["near"] == 4900 * (2 * 16 ** 4 + 2 * 256) and fl["m2l"] == 8 * P ** 2 * 14104
     assert fl["total"] == sum(v for k, v in fl.items() if k != "total")
     assert d["forms"]["mixed"]["median_ms_per_step"] == pytest.approx(0.2)
     assert "latency_floor_us" in d                                             # None without a GPU

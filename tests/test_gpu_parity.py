@@ -443,11 +443,13 @@ def test_mixed_full_size_sampled(V):
 
 
 def test_tcgen05_engine_matches_mma_engine(V):
-    """The tcgen05 (tensor-memory) engines and the mma.sync engine compute the
+    """The tcgen05 (tensor-memory) engine and the mma.sync engine compute the
     same exact slice-order sums; they differ only where a pass's inner
     dimension is split (the mma.sync engine rounds each 64-deep chunk's pair
     value, about 2^-46 relative, then adds the chunks).  Their potentials agree
-    a thousand times closer than the mixed form's error bound of 1e-9."""
+    a thousand times closer than the mixed form's error bound of 1e-9: the
+    default routing (near field on tcgen05), every pass on mma.sync, and every
+    eligible pass (near field and the six-slice far field) on tcgen05."""
     import os
     wl = CASES["disk_l3_k16"]()
     plan = make_plan(V, wl, precision=1)
@@ -457,19 +459,27 @@ def test_tcgen05_engine_matches_mma_engine(V):
     n = fe.numel()
     v_tc = torch.empty(n, dtype=torch.float64, device="cuda")
     v_mma = torch.empty(n, dtype=torch.float64, device="cuda")
+    v_all = torch.empty(n, dtype=torch.float64, device="cuda")
     os.environ.pop("VPX_NO_TC", None)
     V.vpx_potential(plan, fe, v_tc)
     assert V.vpx_sync_status(plan) == 0
-    os.environ["VPX_NO_TC"] = "1"
     try:
+        os.environ["VPX_NO_TC"] = "1"
         V.vpx_potential(plan, fe, v_mma)
+        assert V.vpx_sync_status(plan) == 0
+        os.environ.pop("VPX_NO_TC")
+        os.environ["VPX_TC_ALL"] = "1"        # the far-field passes on tcgen05 too
+        V.vpx_potential(plan, fe, v_all)
         assert V.vpx_sync_status(plan) == 0
     finally:
         os.environ.pop("VPX_NO_TC", None)
+        os.environ.pop("VPX_TC_ALL", None)
     scale = float(v_mma.abs().max())
     diff = float((v_tc - v_mma).abs().max())
-    print("tcgen05 vs mma.sync max diff %.3e (scale %.3e)" % (diff, scale))
-    assert diff <= 1e-12 * scale
+    diff_all = float((v_all - v_mma).abs().max())
+    print("tcgen05 vs mma.sync max diff %.3e, every eligible pass on tcgen05 %.3e (scale %.3e)"
+          % (diff, diff_all, scale))
+    assert diff <= 1e-12 * scale and diff_all <= 1e-12 * scale
 
 
 def _oracle_leaf_values(wl, tree, srcs):
@@ -589,11 +599,14 @@ def test_c4_lshape_full_size_sampled(V, precision):
 @pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("name", ["starfish_k8_adaptive", "lshape_k8_adaptive"])
 def test_level_chains_persistent_equal_per_level(V, name, precision):
-    """M2M and L2L as one persistent launch each (the default) against one
-    launch per level (VPX_PER_LEVEL_CHAINS): the same translations summed in
-    another order, so the potentials agree to rounding (1e-13 of max |V| in
-    FP64, 1e-12 in the double-float mixed form); both on three right-hand
-    sides with a padded leading dimension."""
+    """The level chains three ways: one persistent launch each
+    (VPX_PERSISTENT_CHAINS = 1, the FP64 form's default), one launch per level
+    (VPX_PERSISTENT_CHAINS = 0 and VPX_NO_SUBTREES), and the default (in the
+    mixed form: one subtree launch per direction below the cut level, per-level
+    passes above it).  The same translations summed in another order, so the
+    potentials agree to rounding (1e-13 of max |V| in FP64, 1e-12 in the
+    double-float mixed form); three right-hand sides with a padded leading
+    dimension."""
     import os
     wl = CASES[name]()
     plan = make_plan(V, wl, max_rhs=3, precision=precision)
@@ -604,17 +617,22 @@ def test_level_chains_persistent_equal_per_level(V, name, precision):
     for r in range(3):
         fe[r, :nt] = torch.tensor(vals[:, r, :].ravel())
     out = {}
-    for mode in ("chain", "levels"):
+    for mode in ("chain", "levels", "default"):
+        if mode != "default":
+            os.environ["VPX_PERSISTENT_CHAINS"] = "1" if mode == "chain" else "0"
         if mode == "levels":
-            os.environ["VPX_PER_LEVEL_CHAINS"] = "1"
+            os.environ["VPX_NO_SUBTREES"] = "1"
         try:
             v = torch.empty((3, nt), dtype=torch.float64, device="cuda")
             V.vpx_potential(plan, fe[:, :nt], v)
             assert V.vpx_sync_status(plan) == 0
             out[mode] = v.cpu().numpy()
         finally:
-            os.environ.pop("VPX_PER_LEVEL_CHAINS", None)
+            os.environ.pop("VPX_PERSISTENT_CHAINS", None)
+            os.environ.pop("VPX_NO_SUBTREES", None)
     scale = np.max(np.abs(out["levels"]))
-    diff = np.max(np.abs(out["chain"] - out["levels"]))
-    print("%s precision %d: persistent chains vs per-level %.2e (scale %.2e)" % (name, precision, diff, scale))
-    assert diff <= (1e-13 if precision == 0 else 1e-12) * scale
+    tol = (1e-13 if precision == 0 else 1e-12) * scale
+    for mode in ("chain", "default"):
+        diff = np.max(np.abs(out[mode] - out["levels"]))
+        print("%s precision %d: %s vs per-level %.2e (scale %.2e)" % (name, precision, mode, diff, scale))
+        assert diff <= tol, mode
