@@ -418,7 +418,7 @@ def run_batch(args, rank=0, world=1, as_key=False):
     out = {
         "metric": METRIC, "value": rate(ms_batch), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": ms_batch, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "bf16 (exact 7-bit slices) + f64",
+        "vs_baseline": None, "dtype": "bf16 (exact 8-bit slices) + f64",
         "data": "synthetic (32 seeded random star domains, each with its own Gaussian mixture)",
         "config": {"workload": "star_batch_32", "K": 8, "p": args.p, "trees": len(wls_all),
                    "trees_per_rank": "size-balanced shares" if world > 1 else "all",
@@ -623,7 +623,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": ms_max, "higher_is_better": True,
         "scaling": "strong" if args.workload == "disk-multi-rhs" else "weak",
-        "vs_baseline": None, "dtype": "f64" if head == "fp64" else "bf16 (exact 7-bit slices) + f64",
+        "vs_baseline": None, "dtype": "f64" if head == "fp64" else "bf16 (exact 8-bit slices) + f64",
         "data": "synthetic (seeded analytic source on the %s domain)" % DOMAIN_LABEL[args.workload],
         "config": {"workload": r["wl"].name, "description": r["wl"].description, "K": r["K"], "p": args.p,
                    "refine_tol": r["wl"].opts.refine_tol, "n_leaves": r["n_leaves"], "leaf_targets": r["nt"],

@@ -240,111 +240,6 @@ __global__ void __launch_bounds__(CH_THREADS) k_chain(ChainArgs a) {
     }
 }
 
-// ---------------------------------------------------------------- subtrees
-//
-// Below the cut level Lc (the deepest level holding at least kDenseLevel
-// boxes; level 2 if none does) an adaptive tree is sparse: a few hundred
-// boxes per level, grouped around the features it resolves.  There one CTA
-// takes the whole subtree of each non-leaf box at level Lc and runs its level
-// chain with barriers between levels, one warp per translation, instead of one
-// launch per level: upward the children's multipoles into their parents from
-// the deepest level to Lc, downward the parents' locals into their children
-// from Lc + 1 to the deepest.  Levels up to Lc keep their per-level passes.
-// The four translation tables sit in shared memory (complex, P x P, stored
-// transposed); a lane takes one row (two for P > 32) and sums it over its
-// non-zero range.
-constexpr int ST_THREADS = 512;
-constexpr int kDenseLevel = 1024;
-
-struct SubtreeArgs {
-    int P, nrhs;
-    int64_t ldm;
-    const int32_t *root_seg;      // [n_roots + 1] segments (levels) of each subtree
-    const int32_t *seg_item;      // [n_segs + 1] items of each segment
-    const int32_t *item;          // [n_items][3]: source box, destination box, child position
-    const void *tab;              // [4][P][P] complex: double2 or float4 hi/lo pairs
-    const int16_t *krange;        // [4][P][2]
-    double *x;                    // expansions, [rhs][box][2P]
-    int add;                      // 1: atomic add (upward, several children), 0: read-modify-write (downward)
-};
-
-template <bool DF>
-__global__ void __launch_bounds__(ST_THREADS, 1) k_subtree(SubtreeArgs a) {
-    pdl_entry();
-    typedef typename std::conditional<DF, float4, double2>::type E;
-    extern __shared__ __align__(16) unsigned char stsm[];
-    E *tab = reinterpret_cast<E *>(stsm);
-    __shared__ int16_t s_kr[4 * kMaxP * 2];
-    __shared__ __align__(16) E s_vec[ST_THREADS / 32][kMaxP];   // each warp's source expansion
-    const int P = a.P, warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = ST_THREADS >> 5;
-    E *wv = s_vec[warp];
-    {   // transposed, [pos][k][l]: the lanes (rows l) of a warp read consecutive words at a fixed k
-        const E *src = reinterpret_cast<const E *>(a.tab);
-        for (int i = threadIdx.x; i < 4 * P * P; i += ST_THREADS) {
-            const int pos = i / (P * P), l = (i / P) % P, k = i % P;
-            tab[((size_t)pos * P + k) * P + l] = src[i];
-        }
-        for (int i = threadIdx.x; i < 4 * P * 2; i += ST_THREADS) s_kr[i] = a.krange[i];
-    }
-    __syncthreads();
-    for (int sg = a.root_seg[blockIdx.x]; sg < a.root_seg[blockIdx.x + 1]; ++sg) {
-        for (int it = a.seg_item[sg] + warp; it < a.seg_item[sg + 1]; it += nw) {
-            const int src = a.item[3 * it], dst = a.item[3 * it + 1], pos = a.item[3 * it + 2];
-            const E *T = tab + (size_t)pos * P * P;
-            for (int r = 0; r < a.nrhs; ++r) {
-                const double *xs = a.x + r * a.ldm + (int64_t)src * 2 * P;
-                double *xd = a.x + r * a.ldm + (int64_t)dst * 2 * P;
-                for (int k = lane; k < P; k += 32) {
-                    const double re = __ldcg(xs + 2 * k), im = __ldcg(xs + 2 * k + 1);
-                    if (DF) {
-                        const df32 hr = df_split_bits(re), hi = df_split_bits(im);
-                        reinterpret_cast<float4 *>(wv)[k] = make_float4(hr.hi, hr.lo, hi.hi, hi.lo);
-                    } else {
-                        reinterpret_cast<double2 *>(wv)[k] = make_double2(re, im);
-                    }
-                }
-                __syncwarp();
-                for (int l = lane; l < P; l += 32) {
-                    const int klo = s_kr[(pos * P + l) * 2], khi = s_kr[(pos * P + l) * 2 + 1];
-                    double out_re, out_im;
-                    if (DF) {
-                        df32 sr{0.f, 0.f}, si{0.f, 0.f};
-                        for (int k = klo; k <= khi; ++k) {
-                            const float4 t = reinterpret_cast<const float4 *>(T)[(size_t)k * P + l];
-                            const float4 v = reinterpret_cast<const float4 *>(wv)[k];
-                            df_mac(sr, df32{t.x, t.y}, df32{v.x, v.y});
-                            df_mac(sr, df32{-t.z, -t.w}, df32{v.z, v.w});
-                            df_mac(si, df32{t.x, t.y}, df32{v.z, v.w});
-                            df_mac(si, df32{t.z, t.w}, df32{v.x, v.y});
-                        }
-                        out_re = df_to_f64_scaled(df_norm(sr), 0);
-                        out_im = df_to_f64_scaled(df_norm(si), 0);
-                    } else {
-                        double sr = 0.0, si = 0.0;
-                        for (int k = klo; k <= khi; ++k) {
-                            const double2 t = reinterpret_cast<const double2 *>(T)[(size_t)k * P + l];
-                            const double2 v = reinterpret_cast<const double2 *>(wv)[k];
-                            sr = fma(t.x, v.x, fma(-t.y, v.y, sr));
-                            si = fma(t.x, v.y, fma(t.y, v.x, si));
-                        }
-                        out_re = sr;
-                        out_im = si;
-                    }
-                    if (a.add) {
-                        atomicAdd(xd + 2 * l, out_re);
-                        atomicAdd(xd + 2 * l + 1, out_im);
-                    } else {
-                        xd[2 * l] = __ldcg(xd + 2 * l) + out_re;
-                        xd[2 * l + 1] = __ldcg(xd + 2 * l + 1) + out_im;
-                    }
-                }
-                __syncwarp();   // wv is rewritten for the next column or item
-            }
-        }
-        __syncthreads();   // this level's results are visible to the next level's warps
-    }
-}
-
 // ------------------------------------------------------------------ host
 
 // The complex form of four real 2P x 2P translation tables (rows 2l, 2l+1 and
@@ -376,8 +271,6 @@ static bool complex_tables(const std::vector<double> &real4, int P, std::vector<
     return true;
 }
 
-
-static void setup_subtrees(vpx_plan *p, ChainPlan &C);
 
 static int chain_nk(int P) {
     const int G = std::max(1, CH_THREADS / P);
@@ -454,82 +347,11 @@ void setup_chains(vpx_plan *p, const std::vector<double> &m2m, const std::vector
     VPX_CUDA(cudaGetDevice(&dev));
     VPX_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     C.max_ctas = std::max(1, std::min(occ, 8)) * nsm;
-    if (mixed) setup_subtrees(p, C);
     C.ok = occ > 0;
-}
-
-static size_t subtree_smem(int P) { return (size_t)4 * P * P * 16; }
-
-// The subtree work of the mixed form: the cut level, and per root the
-// segments (levels) and items of both directions.
-static void setup_subtrees(vpx_plan *p, ChainPlan &C) {
-    const int nb = (int)p->box_level.size(), nlev = p->n_levels, P = p->P;
-    if (subtree_smem(P) + sizeof(float4) * (ST_THREADS / 32) * kMaxP + 1024 > 227 * 1024) return;
-    int lc = 2;
-    for (int l = nlev - 1; l >= 2; --l)
-        if (p->level_start[l + 1] - p->level_start[l] >= kDenseLevel) {
-            lc = l;
-            break;
-        }
-    if (lc >= nlev - 1) return;
-    std::vector<int32_t> root_seg[2], seg_item[2], item[2];
-    for (int d = 0; d < 2; ++d) {
-        root_seg[d].push_back(0);
-        seg_item[d].push_back(0);
-    }
-    int n_roots = 0;
-    for (int r = p->level_start[lc]; r < p->level_start[lc + 1]; ++r) {
-        if (p->box_child0[r] < 0) continue;
-        ++n_roots;
-        std::vector<std::vector<int32_t>> lev(1, std::vector<int32_t>{r});
-        while (true) {
-            std::vector<int32_t> next;
-            for (int b : lev.back())
-                if (p->box_child0[b] >= 0)
-                    for (int k = 0; k < 4; ++k) next.push_back(p->box_child0[b] + k);
-            if (next.empty()) break;
-            lev.push_back(next);
-        }
-        // upward: deepest level first, non-zero boxes into their parents (atomic)
-        for (int li = (int)lev.size() - 1; li >= 1; --li) {
-            bool any = false;
-            for (int c : lev[li]) {
-                if (!p->box_nz[c]) continue;
-                const int pa = p->box_parent[c];
-                item[0].insert(item[0].end(), {c, pa, c - p->box_child0[pa]});
-                any = true;
-            }
-            if (any) seg_item[0].push_back((int32_t)(item[0].size() / 3));
-        }
-        // downward: shallowest level first, every box from its parent
-        for (int li = 1; li < (int)lev.size(); ++li) {
-            for (int c : lev[li]) {
-                const int pa = p->box_parent[c];
-                item[1].insert(item[1].end(), {pa, c, c - p->box_child0[pa]});
-            }
-            seg_item[1].push_back((int32_t)(item[1].size() / 3));
-        }
-        for (int d = 0; d < 2; ++d) root_seg[d].push_back((int32_t)seg_item[d].size() - 1);
-    }
-    if (n_roots == 0) return;
-    for (int d = 0; d < 2; ++d) {
-        C.st_root_seg[d] = dev_upload(root_seg[d]);
-        C.st_seg_item[d] = dev_upload(seg_item[d]);
-        C.st_item[d] = dev_upload(item[d]);
-    }
-    const size_t smem = subtree_smem(P);
-    VPX_CUDA(cudaFuncSetAttribute(k_subtree<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    C.lc = lc;
-    C.n_roots = n_roots;
 }
 
 void free_chains(vpx_plan *p) {
     ChainPlan &C = p->fmm.chain;
-    for (int d = 0; d < 2; ++d) {
-        dev_free(C.st_root_seg[d]);
-        dev_free(C.st_seg_item[d]);
-        dev_free(C.st_item[d]);
-    }
     dev_free(C.tab_up);
     dev_free(C.tab_down);
     dev_free(C.kr_up);
@@ -540,27 +362,6 @@ void free_chains(vpx_plan *p) {
     dev_free(C.up_of);
     dev_free(C.ws);
     C = ChainPlan();
-}
-
-// One launch of the subtree chains below the cut level (mixed form): upward
-// into the cut level's boxes, or downward from them.
-void subtree_run(vpx_plan *p, bool up, double *x, int64_t ldm, int nrhs, cudaStream_t s) {
-    const ChainPlan &C = p->fmm.chain;
-    if (C.n_roots == 0) return;
-    SubtreeArgs a;
-    a.P = p->P;
-    a.nrhs = nrhs;
-    a.ldm = ldm;
-    const int d = up ? 0 : 1;
-    a.root_seg = C.st_root_seg[d];
-    a.seg_item = C.st_seg_item[d];
-    a.item = C.st_item[d];
-    a.tab = up ? C.tab_up : C.tab_down;
-    a.krange = up ? C.kr_up : C.kr_down;
-    a.x = x;
-    a.add = up ? 1 : 0;
-    launch_pdl(k_subtree<true>, dim3(C.n_roots), dim3(ST_THREADS), subtree_smem(p->P), s, a);
-    VPX_LAUNCH("k_subtree");
 }
 
 // Zeroes both queue blocks (one memset, ahead of the upward chain).

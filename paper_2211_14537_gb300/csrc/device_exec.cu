@@ -291,7 +291,7 @@ static void prepare_extension(vpx_plan *p) {
     // memory holds a cut leaf's interior stencil values, which along lines
     // would be the line points as well)
     if (p->opt.precision == VPX_PREC_MIXED)
-        extend_df_prepare(p->ext.mode == 1 ? 0 : p->ext.max_interior, p->K, p->st.Kbar, p->st.NG);
+        extend_df_prepare(p->ext.mode == 1 ? 0 : p->ext.max_interior, p->K, p->st.Kbar);
 }
 
 // Per-plan index arrays of the execute path: non-zero leaves and the
@@ -366,7 +366,6 @@ static void run_extension(vpx_plan *p, const double *f, int nrhs, int64_t ldf, d
         a.ldfe = ldfe;
         a.pinv_df = reinterpret_cast<const float2 *>(p->ext.pinv_df);
         a.cheb_df = reinterpret_cast<const float2 *>(p->ext.cheb_df);
-        a.agT_df = reinterpret_cast<const float2 *>(p->ext.agT_df);
         a.fe_sl = sl;
         a.fe_ex = ex;
         a.n_leaves = nl;
@@ -393,22 +392,14 @@ static void run_extension(vpx_plan *p, const double *f, int nrhs, int64_t ldf, d
         } else if (p->opt.precision == VPX_PREC_MIXED) {
             DevExt &x = p->ext;
             a.pinv_df_off = x.pinv_df_off;
-            if (getenv("VPX_EXT_THREE_STEPS")) {   // the earlier form: fit, table pass for the grid, coefficients
-                const int Kb2 = p->st.Kbar * p->st.Kbar;
-                const int64_t ldc = (int64_t)x.ncut * p->st.NG, ldF = (int64_t)x.ncut * Kb2;
-                launch_ext_coeff_df(a, x.ncut, x.max_interior, nrhs, x.cbuf, ldc, p->wk.status, s);
-                VecSet vc{x.cbuf, ldc, p->st.NG, nullptr, nullptr, x.ncut, 0};
-                gemm_run(x.grid_pass, vc, x.Fall, ldF, nrhs, true, s);
-                launch_ext_eval_df(a, x.ncut, x.n_tgt, x.tgt_cut, x.tgt_leaf,
-                                   reinterpret_cast<const ExtTgtGeo *>(x.tgt_geo), x.Fall, ldF,
-                                   reinterpret_cast<float2 *>(x.alpha), nrhs, p->wk.status, s);
-            } else {   // one kernel per cut leaf up to the coefficients, then the evaluation
-                launch_ext_fit_df(a, x.ncut, x.max_interior, nrhs, reinterpret_cast<float2 *>(x.alpha), p->wk.status,
-                                  s);
-                launch_ext_eval_df(a, x.ncut, x.n_tgt, x.tgt_cut, x.tgt_leaf,
-                                   reinterpret_cast<const ExtTgtGeo *>(x.tgt_geo), nullptr, 0,
-                                   reinterpret_cast<float2 *>(x.alpha), nrhs, p->wk.status, s);
-            }
+            const int Kb2 = p->st.Kbar * p->st.Kbar;
+            const int64_t ldc = (int64_t)x.ncut * p->st.NG, ldF = (int64_t)x.ncut * Kb2;
+            launch_ext_coeff_df(a, x.ncut, x.max_interior, nrhs, x.cbuf, ldc, p->wk.status, s);
+            VecSet vc{x.cbuf, ldc, p->st.NG, nullptr, nullptr, x.ncut, 0};
+            gemm_run(x.grid_pass, vc, x.Fall, ldF, nrhs, true, s);
+            launch_ext_eval_df(a, x.ncut, x.n_tgt, x.tgt_cut, x.tgt_leaf,
+                               reinterpret_cast<const ExtTgtGeo *>(x.tgt_geo), x.Fall, ldF,
+                               reinterpret_cast<float2 *>(x.alpha), nrhs, p->wk.status, s);
         } else {
             launch_pdl(k_extend, dim3(p->ext.ncut, nrhs), dim3(256), smem, s, a);
             VPX_LAUNCH("k_extend");
@@ -618,7 +609,7 @@ static void shape_key(const GemmCall &c, std::vector<int64_t> &key) {
     const GemmPass &g = *c.g;
     int64_t lg = 0;
     while ((int64_t(1) << lg) < (int64_t)g.n_pairs) ++lg;
-    const int64_t k[10] = {g.M, g.Kd, g.Kpad, g.ntab, g.slices, lg, c.nrhs, c.vs.slices != nullptr ? 1 : 0,
+    const int64_t k[10] = {g.M, g.Kd, g.Kpad, g.ntab, (int64_t)kSlicesS, lg, c.nrhs, c.vs.slices != nullptr ? 1 : 0,
                            gemm_ws_eligible(g, c.vs) ? 1 : 0, g.add};
     key.insert(key.end(), k, k + 10);
 }

@@ -475,13 +475,6 @@ void device_setup(vpx_plan *p) {
         x.pinv_df = dev_upload(pd);
         x.pinv_df_off = dev_upload(poff);
         x.cheb_df = dev_upload(cd);
-        if (!lines) {
-            const int Kb2t = st.Kbar * st.Kbar;
-            std::vector<DevExt::DfPair> at((size_t)st.NG * Kb2t);
-            for (int g = 0; g < Kb2t; ++g)
-                for (int k = 0; k < st.NG; ++k) at[(size_t)k * Kb2t + g] = split(Ag[(size_t)g * st.NG + k]);
-            x.agT_df = dev_upload(at);
-        }
         // A_{X_Sbar,G} c of every cut leaf as one table pass; targets of the Chebyshev stage
         const int Kb2 = st.Kbar * st.Kbar;
         if (x.ncut > 0 && !lines) {
@@ -489,7 +482,6 @@ void device_setup(vpx_plan *p) {
             for (int c = 0; c < x.ncut; ++c) tg.push_back({0, GPair{c, 0, (int64_t)c * Kb2, 1.0}});
             gemm_pass_upload_tables(x.grid_pass, Ag, 1, Kb2, st.NG, true);
             x.grid_pass.add = 0;
-            x.grid_pass.slices = kSlicesS;
             gemm_pass_set_pairs(x.grid_pass, tg);
         }
         std::vector<int32_t> tc, tl;
@@ -559,7 +551,7 @@ void device_free(vpx_plan *p) {
     dev_free(x.cut_leaf); dev_free(x.n_interior); dev_free(x.grid_src); dev_free(x.node_src);
     dev_free(x.stencil_off); dev_free(x.pinv_off); dev_free(x.reg_leaf_off); dev_free(x.owned_off);
     dev_free(x.owned); dev_free(x.pinv); dev_free(x.A_grid); dev_free(x.cheb_inv);
-    dev_free(x.pinv_df); dev_free(x.cheb_df); dev_free(x.pinv_df_off); dev_free(x.tgt_geo); dev_free(x.agT_df);
+    dev_free(x.pinv_df); dev_free(x.cheb_df); dev_free(x.pinv_df_off); dev_free(x.tgt_geo);
     gemm_pass_free(x.grid_pass);
     dev_free(x.tgt_cut); dev_free(x.tgt_leaf); dev_free(x.cbuf); dev_free(x.Fall); dev_free(x.alpha);
     dev_free(x.ray_c); dev_free(x.ray_g); dev_free(x.ray_src); dev_free(x.ray_coef);

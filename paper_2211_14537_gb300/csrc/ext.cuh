@@ -23,7 +23,6 @@ struct ExtArgs {
     const float2 *pinv_df;      // P_S as double-float (hi, lo), rows padded to an even length
     const int64_t *pinv_df_off; // start of each cut leaf's P_S in pinv_df (even)
     const float2 *cheb_df;      // [Kbar][Kbar] double-float
-    const float2 *agT_df;       // [NG][Kbar^2] the universal operator at X_Sbar, transposed, double-float
     const int32_t *leaf_level, *leaf_ix, *leaf_iy;
     const double *f;
     int64_t ldf;
@@ -41,12 +40,8 @@ struct ExtArgs {
 
 // mixed form (extend_df.cu): c = A_I^+ f_I into cbuf[rhs][cut][NG]; then, after
 // the grid values A_{X_Sbar,G} c are in Fall[rhs][cut][Kbar^2], the Chebyshev
-// stage for every target leaf (tgt_cut[t], tgt_leaf[t]); with Fall null the
-// coefficients are already in alpha
-void extend_df_prepare(int max_interior, int K, int Kbar, int NG);
-// mixed form, universal stencil: fit, grid and coefficients per cut leaf into alpha
-void launch_ext_fit_df(const ExtArgs &a, int ncut, int max_interior, int nrhs, float2 *alpha, int *status,
-                       cudaStream_t s);
+// stage for every target leaf (tgt_cut[t], tgt_leaf[t])
+void extend_df_prepare(int max_interior, int K, int Kbar);
 void launch_ext_coeff_df(const ExtArgs &a, int ncut, int max_interior, int nrhs, double *cbuf, int64_t ldc,
                          int *status, cudaStream_t s);
 void launch_ext_eval_df(const ExtArgs &a, int ncut, int n_tgt, const int32_t *tgt_cut, const int32_t *tgt_leaf,

@@ -15,9 +15,9 @@
 //                      target's nodes.
 //
 // Operators are stored as double-float pairs; data enter and leave as FP64.
-// Relative errors stay near 2^-47 times the extension's conditioning (step 2:
-// 2^-42 of its own terms), below the 35 and 42 bits of the leaf values that
-// the mixed form's slices keep.
+// Relative errors stay near 2^-47 times the extension's conditioning (step 2,
+// a five-slice pass: 2^-40 of its own terms), at or below the 39 bits of the
+// leaf values that the mixed form's slices keep.
 #include <cmath>
 
 #include "bulk.cuh"
@@ -138,61 +138,6 @@ __global__ void __launch_bounds__(256) k_ext_alpha_df(ExtArgs a, const double *F
     ext_alpha_from_grid(C, F, T1, Kb, alpha + rhs * lda + (int64_t)c * Kb2p);
 }
 
-// grid (cut leaves, rhs), 256 threads: the three steps before the evaluation
-// in one CTA per cut leaf (universal stencil): c = A_I^+ f_I (one warp per row,
-// the rows streamed once from HBM); the grid values, the data at interior grid
-// points and A_{X_Sbar,G} c elsewhere (the universal operator stored
-// transposed, [NG][Kbar^2], so that consecutive threads read consecutive grid
-// points); then the truncated Chebyshev coefficients.  Everything in
-// double-float (the grid step included: about 2^-47 of its terms).
-__global__ void __launch_bounds__(256) k_ext_fit_df(ExtArgs a, float2 *alpha, int64_t lda, int *status) {
-    pdl_entry();
-    extern __shared__ __align__(16) float2 fsm[];
-    __shared__ __align__(8) uint64_t s_bar;
-    const int c = blockIdx.x, rhs = blockIdx.y;
-    const int nI = a.n_interior[c], NG = a.NG, nIp = (nI + 1) & ~1;
-    const int Kb = a.Kbar, Kb2 = Kb * Kb, Kb2p = (Kb2 + 1) & ~1;
-    float2 *C = fsm;               // Kb2p: Chebyshev transform [m][ax] (first: the bulk copy's 16-byte start)
-    float2 *F = C + Kb2p;          // Kb2p: grid values [by][ax]
-    float2 *T1 = F + Kb2p;         // Kb2p
-    float2 *fI = T1 + Kb2p;        // nIp: interior stencil data
-    float2 *cs = fI + nIp;         // NG: fit coefficients
-    if (threadIdx.x == 0) {
-        bulk_bar_init(&s_bar);
-        bulk_expect(&s_bar, (uint32_t)(Kb2p * sizeof(float2)));
-        bulk_copy(C, a.cheb_df, (uint32_t)(Kb2p * sizeof(float2)), &s_bar);
-    }
-    const double *f = a.f + rhs * a.ldf + a.stencil_off[c];
-    for (int i = threadIdx.x; i < nI; i += blockDim.x) fI[i] = st_df(df_split_bits(f[i]));
-    __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    const float2 *Pc = a.pinv_df + a.pinv_df_off[c];
-    for (int k = warp; k < NG; k += nw) {
-        df32 sacc{0.f, 0.f};
-        for (int i = lane; i < nI; i += 32) df_mac(sacc, ld_df(Pc + (size_t)k * nIp + i), ld_df(fI + i));
-        sacc = df_warp_sum(sacc);
-        if (lane == 0) cs[k] = st_df(sacc);
-    }
-    __syncthreads();
-    const int32_t *gs = a.grid_src + (size_t)c * Kb2;
-    for (int g = threadIdx.x; g < Kb2; g += blockDim.x) {
-        const int src = gs[g];
-        if (src >= 0) {
-            F[g] = st_df(df_split_bits(f[src]));
-        } else {
-            df32 sacc{0.f, 0.f};
-            for (int k = 0; k < NG; ++k) df_mac(sacc, ld_df(a.agT_df + (size_t)k * Kb2 + g), ld_df(cs + k));
-            F[g] = st_df(df_norm(sacc));
-        }
-    }
-    __syncthreads();
-    if (!__syncthreads_and(bulk_wait(&s_bar, 0))) {
-        if (threadIdx.x == 0) set_status(status, VPX_ERR_TIMEOUT);
-        return;
-    }
-    ext_alpha_from_grid(C, F, T1, Kb, alpha + rhs * lda + (int64_t)c * Kb2p);
-}
-
 // grid (targets, rhs), 256 threads: the truncated expansion of the target's
 // cut leaf at the target's K x K nodes (interior nodes of the cut leaf itself
 // keep the data).  geo[t] = (x offset, y offset, node scale) of the target in
@@ -288,19 +233,14 @@ __global__ void __launch_bounds__(256) k_ext_eval_df(ExtArgs a, const int32_t *t
 static size_t kb2p(int Kb) { return ((size_t)Kb * Kb + 1) & ~(size_t)1; }
 static size_t alpha_smem(int Kb) { return sizeof(float2) * 3 * kb2p(Kb); }
 static size_t eval_smem(int K, int Kb) { return sizeof(float2) * (kb2p(Kb) + 3 * (size_t)K * Kb); }
-static size_t fit_smem(int max_interior, int NG, int Kb) {
-    return sizeof(float2) * (3 * kb2p(Kb) + (((size_t)max_interior + 1) & ~(size_t)1) + (size_t)NG);
-}
+
 
 static size_t coeff_smem(int max_interior) {
     const size_t nIp = (size_t)(max_interior + 1) & ~(size_t)1;
     return sizeof(float2) * (8 * nIp + nIp);
 }
 
-void extend_df_prepare(int max_interior, int K, int Kbar, int NG) {
-    if (fit_smem(max_interior, NG, Kbar) > 48 * 1024)
-        VPX_CUDA(cudaFuncSetAttribute(k_ext_fit_df, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)fit_smem(max_interior, NG, Kbar)));
+void extend_df_prepare(int max_interior, int K, int Kbar) {
     if (coeff_smem(max_interior) > 48 * 1024)
         VPX_CUDA(cudaFuncSetAttribute(k_ext_coeff_df, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)coeff_smem(max_interior)));
@@ -319,24 +259,13 @@ void launch_ext_coeff_df(const ExtArgs &a, int ncut, int max_interior, int nrhs,
     VPX_LAUNCH("k_ext_coeff_df");
 }
 
-void launch_ext_fit_df(const ExtArgs &a, int ncut, int max_interior, int nrhs, float2 *alpha, int *status,
-                       cudaStream_t s) {
-    const int64_t lda = (int64_t)ncut * kb2p(a.Kbar);
-    launch_pdl(k_ext_fit_df, dim3(ncut, nrhs), dim3(256), fit_smem(max_interior, a.NG, a.Kbar), s, a, alpha, lda,
-               status);
-    VPX_LAUNCH("k_ext_fit_df");
-}
-
 void launch_ext_eval_df(const ExtArgs &a, int ncut, int n_tgt, const int32_t *tgt_cut, const int32_t *tgt_leaf,
                         const ExtTgtGeo *geo, const double *Fall, int64_t ldF, float2 *alpha, int nrhs, int *status,
                         cudaStream_t s) {
     if (a.Kbar * a.Kbar > kExtPerThread * 256) fail(VPX_ERR_ARG, "extension grid larger than one block covers");
     const int64_t lda = (int64_t)ncut * kb2p(a.Kbar);
-    if (Fall) {   // the coefficients from given grid values (null: k_ext_fit_df made them)
-        launch_pdl(k_ext_alpha_df, dim3(ncut, nrhs), dim3(256), alpha_smem(a.Kbar), s, a, Fall, ldF, alpha, lda,
-                   status);
-        VPX_LAUNCH("k_ext_alpha_df");
-    }
+    launch_pdl(k_ext_alpha_df, dim3(ncut, nrhs), dim3(256), alpha_smem(a.Kbar), s, a, Fall, ldF, alpha, lda, status);
+    VPX_LAUNCH("k_ext_alpha_df");
     launch_pdl(k_ext_eval_df, dim3(n_tgt, nrhs), dim3(256), eval_smem(a.K, a.Kbar), s, a, tgt_cut, tgt_leaf, geo, alpha, lda,
                                                                           status);
     VPX_LAUNCH("k_ext_eval_df");

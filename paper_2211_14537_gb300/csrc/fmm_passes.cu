@@ -192,15 +192,7 @@ void setup_chains(vpx_plan *p, const std::vector<double> &m2m, const std::vector
 void free_chains(vpx_plan *p);
 void chain_reset(vpx_plan *p, cudaStream_t s);
 void chain_run(vpx_plan *p, bool up, double *x, int64_t ldm, int nrhs, cudaStream_t s);
-void subtree_run(vpx_plan *p, bool up, double *x, int64_t ldm, int nrhs, cudaStream_t s);
 
-// The mixed form's level chains below the cut level as one subtree launch per
-// direction (VPX_NO_SUBTREES keeps every level on its own pass): the cut
-// level, or -1.
-static int subtree_cut(const vpx_plan *p) {
-    if (p->opt.precision != VPX_PREC_MIXED || p->fmm.chain.n_roots == 0 || getenv("VPX_NO_SUBTREES")) return -1;
-    return p->fmm.chain.lc;
-}
 
 // The level chains as one persistent launch each in the FP64 form, one launch
 // per level in the mixed form: measured on the L-shape step, the persistent
@@ -373,13 +365,6 @@ void setup_passes(vpx_plan *p) {
         F.tc_coef = dev_upload(coef);
     }
     if (mixed) {
-        // slices per pass: near field and far field separately (environment overrides for experiments)
-        const char *sn = getenv("VPX_SLICES_NEAR"), *sf = getenv("VPX_SLICES_FAR");
-        const int s_near = sn ? std::max(5, std::min(6, atoi(sn))) : 5;
-        const int s_far = sf ? std::max(5, std::min(6, atoi(sf))) : 6;
-        F.near.slices = s_near;
-        for (GemmPass *g : {&F.l2m, &F.m2l, &F.s2l, &F.l2t, &F.m2t}) g->slices = s_far;
-        for (int l = 0; l <= kMaxLevel; ++l) F.m2m[l].slices = F.l2l[l].slices = s_far;
         gemm_ws_prepare_device();
         gemm_frag_prepare_device();
         for (GemmPass *g : {&F.near, &F.l2m, &F.m2l, &F.s2l, &F.l2t, &F.m2t}) gemm_ws_prepare(*g);
@@ -473,15 +458,9 @@ void run_potential_passes(vpx_plan *p, const double *fe, int64_t ldfe, int nrhs,
     // main stream: upward pass
     gemm_run(F.l2m, vf, mp, ldm, nrhs, mixed, s);
     ev_record_pass(p, 2, s);
-    const int lc = chains ? -1 : subtree_cut(p);
-    if (chains) {
-        chain_run(p, true, mp, ldm, nrhs, s);
-    } else if (lc >= 0) {   // the sparse levels into the cut level, then parents above it level by level
-        subtree_run(p, true, mp, ldm, nrhs, s);
-        for (int l = lc - 1; l >= 2; --l) gemm_run(F.m2m[l], vm, mp, ldm, nrhs, mixed, s);
-    } else {
+    if (chains) chain_run(p, true, mp, ldm, nrhs, s);
+    else
         for (int l = d.n_levels - 1; l >= 3; --l) gemm_run(F.m2m[l - 1], vm, mp, ldm, nrhs, mixed, s);
-    }
     if (mixed) slice_vectors(vmf, 0, nb, P2, kp_m, nrhs, s);
     // the final multipoles feed the constant terms and list i- on the third
     // stream, beside M2L on this one (all accumulate into distinct sums)
@@ -504,14 +483,9 @@ void run_potential_passes(vpx_plan *p, const double *fe, int64_t ldfe, int nrhs,
     gemm_run(F.m2l, vmf, lo, ldm, nrhs, mixed, s);
     VPX_CUDA(cudaStreamWaitEvent(s, (cudaEvent_t)p->ev_lc, 0));
     ev_record_pass(p, 4, s);
-    if (chains) {
-        chain_run(p, false, lo, ldm, nrhs, s);
-    } else if (lc >= 0) {   // parents above the cut level level by level, then the sparse levels below it
-        for (int l = 2; l < lc; ++l) gemm_run(F.l2l[l], vl, lo, ldm, nrhs, mixed, s);
-        subtree_run(p, false, lo, ldm, nrhs, s);
-    } else {
+    if (chains) chain_run(p, false, lo, ldm, nrhs, s);
+    else
         for (int l = 2; l + 1 < d.n_levels; ++l) gemm_run(F.l2l[l], vl, lo, ldm, nrhs, mixed, s);
-    }
     ev_record_pass(p, 5, s);
     gemm_run(F.l2t, vl, v, ldv, nrhs, mixed, s);
     ev_record_pass(p, 6, s);

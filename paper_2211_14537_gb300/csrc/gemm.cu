@@ -4,15 +4,16 @@
 // FP64 form: 64 x 64 output tile per CTA, 4 x 4 FP64 register tile per thread,
 // 16-deep k stages in shared memory.
 //
-// Mixed form (exact bf16 slices): each table row i is scaled by 2^-e_i and
-// split into S = 5 or 6 integer slices of 7 bits (|a_1| <= 128, |a_k| <= 64),
+// Mixed form (exact bf16 slices): each table row i is scaled by 2^-e_i with
+// max|row| < 2^(e_i - 1) and split into S = 4 (near field) or 5 (far field)
+// integer slices of 8 bits, balanced base-256 digits of magnitude <= 128;
 // each source vector likewise with its own exponent (slice_math.cuh).  A
-// product of two slices is an integer; per inner index the products of one
-// order d = k + l sum to at most 2 * 128 * 64 + (S - 2) * 64^2 <= 2^15, so for
-// an inner dimension <= 512 every order sum stays below 2^24 and the tensor
-// cores' fp32 accumulation of it is exact.  The orders are combined in
-// double-float fp32 and scaled by scale_p 2^{e_i + e_v - 14}; the truncation
-// error is about 2^-7S relative to max|row| max|vector|.  Two engines run it:
+// product of two slices is an integer of magnitude <= 2^14; per inner index
+// the products of order d sum to at most (d + 1) 2^14, so every order sum is
+// exact in the tensor cores' fp32 accumulation while K (d + 1) <= 1024
+// (slice_math.cuh).  The orders are combined in int64 and scaled by
+// scale_p 2^{e_i + e_v - 16 - 8(S-1)}; the truncation error is about
+// 2^-(8S-1) relative to max|row| max|vector|.  Two engines run it:
 // warp-specialised tcgen05 with TMA and TMEM accumulators (gemm_ws.cu) and
 // mma.sync with tables in fragment order (gemm_frag.cu); a double-float
 // engine on the fp32 pipes (gemm_rows.cu) takes the short level chains.
@@ -95,11 +96,12 @@ __global__ void __launch_bounds__(256) k_gemm_fp64(int M, int Kd, const double *
 
 // ------------------------------------------------------------ slicing
 
+// the slicing exponent of a table row (as slice_expo_of_bits): amax < 2^(e-1)
 __device__ __host__ inline int slice_expo(double amax) {
     if (!(amax > 0.0)) return 0;
     int e;
     frexp(amax, &e);
-    return e;
+    return e + 1;
 }
 
 // One warp per (vector, rhs): exponent and slices (slice_math.cuh), zero padded to Kpad.
@@ -159,8 +161,6 @@ void gemm_pass_set_pairs(GemmPass &g, std::vector<std::pair<int, GPair>> &tagged
             tfa.push_back({tagged[i].first, base + (int32_t)(k - i), (int32_t)std::min<size_t>(npa, j - k), 0});
         for (size_t k = i; k < j; k += kRowsTileN)
             tr.push_back({tagged[i].first, base + (int32_t)(k - i), (int32_t)std::min<size_t>(kRowsTileN, j - k), 0});
-        for (size_t k = i; k < j; k += kPairTileN)
-            tp.push_back({tagged[i].first, base + (int32_t)(k - i), (int32_t)std::min<size_t>(kPairTileN, j - k), 0});
         for (size_t k = i; k < j; ++k) pr.push_back(tagged[k].second);
         i = j;
     }
@@ -168,13 +168,12 @@ void gemm_pass_set_pairs(GemmPass &g, std::vector<std::pair<int, GPair>> &tagged
     // wave ends with its smallest tiles (stable: full tiles keep their table
     // order).  The row engine pairs tile i with pair i and keeps its order.
     auto by_count = [](const GTile &x, const GTile &y) { return x.count > y.count; };
-    for (std::vector<GTile> *v : {&tl, &tf, &tfa, &tp}) std::stable_sort(v->begin(), v->end(), by_count);
+    for (std::vector<GTile> *v : {&tl, &tf, &tfa}) std::stable_sort(v->begin(), v->end(), by_count);
     g.h_pairs = pr;
     g.n_pairs = (int)pr.size();
     g.n_tiles = (int)tl.size();
     g.n_tiles_f = (int)tf.size();
     g.n_tiles_r = (int)tr.size();
-    g.n_tiles_p = (int)tp.size();
     g.np_f = (int)npf;
     g.n_tiles_f_alt = (int)tfa.size();
     g.np_f_alt = (int)npa;
@@ -183,11 +182,10 @@ void gemm_pass_set_pairs(GemmPass &g, std::vector<std::pair<int, GPair>> &tagged
     g.tiles = dev_upload(tl);
     g.tiles_f = dev_upload(tf);
     g.tiles_r = dev_upload(tr);
-    g.tiles_p = dev_upload(tp);
 }
 
 static uint16_t bf16_bits_exact(double q) {
-    // q is an integer with |q| <= 256: exact in bf16
+    // q is an integer with |q| <= 128: exact in bf16
     __nv_bfloat16 b = __double2bfloat16(q);
     return *reinterpret_cast<uint16_t *>(&b);
 }
@@ -276,10 +274,9 @@ void gemm_pass_free(GemmPass &g) {
     dev_free(g.tiles_f);
     dev_free(g.tiles_f_alt);
     dev_free(g.tiles_r);
-    dev_free(g.tiles_p);
     dev_free(g.tdfT);
     dev_free(g.tint);
-    g.n_pairs = g.n_tiles = g.n_tiles_f = g.n_tiles_f_alt = g.n_tiles_r = g.n_tiles_p = 0;
+    g.n_pairs = g.n_tiles = g.n_tiles_f = g.n_tiles_f_alt = g.n_tiles_r = 0;
 }
 
 GemmChoice gemm_choice(const GemmPass &g) { return GemmChoice{g.engine, g.np_f}; }

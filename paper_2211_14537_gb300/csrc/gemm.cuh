@@ -18,9 +18,9 @@ namespace vpx {
 constexpr int kGemmTileN = 64;   // pairs per tile (FP64 and tcgen05 engines)
 constexpr int kFragBigPass = 4096;   // fragment engine: 32 pairs per tile from this many pairs on, else 8
 constexpr int kRowsTileN = 1;        // pairs per tile (double-float row engine)
-constexpr int kPairTileN = 128;      // pairs per tile (tcgen05 with pairs on M)
-constexpr int kSlicesS = 6;      // bf16 slices stored per operand in the mixed form (a pass uses 5 or 6)
-constexpr int kSliceBitsB = 7;   // bits per slice
+constexpr int kSlicesS = 5;      // bf16 slices per operand in the mixed form (39 bits); the int64
+                                 // recombination holds 2^24 * 256^4
+constexpr int kSliceBitsB = 8;   // bits per slice: balanced base-256 digits, |digit| <= 128
 
 struct GPair {
     int32_t src;      // source vector index
@@ -47,7 +47,6 @@ struct VecSet {                        // source vectors of a pass
 struct GemmPass {
     int M = 0, Kd = 0, Kpad = 0, Mpad = 0, ntab = 0;
     int add = 1;                       // 1: atomic add into out, 0: store
-    int slices = 5;                    // mixed form: slices used (5 or 6)
     int *status = nullptr;             // device status word (bounded waits report here)
     const double *tab = nullptr;       // [ntab][M][Kd] FP64 (row-major)
     const uint16_t *tslices = nullptr; // [ntab][S][Mpad][Kpad] bf16 bits (mixed form)
@@ -57,11 +56,10 @@ struct GemmPass {
     GTile *tiles = nullptr;            // kGemmTileN pairs each
     GTile *tiles_f = nullptr;          // np_f pairs each (fragment engine)
     GTile *tiles_r = nullptr;          // kRowsTileN pairs each (row engine)
-    GTile *tiles_p = nullptr;          // kPairTileN pairs each (tcgen05, pairs on M)
     const void *tdfT = nullptr;        // [ntab][Kd][M] double-float (float hi, lo): the row engine runs the pass
     const uint16_t *tint = nullptr;    // [ntab][S][Kpad/8][Mpad][8] slices, column chunks interleaved (tcgen05 engine)
-    int ws_kind = 0;                   // 0: not on that engine; 1: table rows on M; 2: pairs on M
-    int n_pairs = 0, n_tiles = 0, n_tiles_f = 0, np_f = 8, n_tiles_r = 0, n_tiles_p = 0;
+    int ws_kind = 0;                   // 0: not on that engine; 1: on it (table rows on M)
+    int n_pairs = 0, n_tiles = 0, n_tiles_f = 0, np_f = 8, n_tiles_r = 0;
     // the fragment engine's other tile width (8 <-> 32 pairs), for the autotuner
     GTile *tiles_f_alt = nullptr;
     int n_tiles_f_alt = 0, np_f_alt = 32;

@@ -14,8 +14,9 @@
 //    pre-sliced and are copied with cp.async.
 //
 // Slice products a_k b_l with k + l <= S + 1 accumulate per order d = k + l in
-// fp32, exactly (order sums stay below 2^24 for an inner dimension <= 512),
-// and the slice_math.cuh epilogue combines them.
+// fp32, exactly (order sums stay below 2^24 for the 64-deep chunks of
+// pre-sliced vectors and for the inner dimensions <= 128 of on-the-fly sliced
+// ones, slice_math.cuh), and the slice_math.cuh epilogue combines them.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -233,19 +234,15 @@ static size_t frag_smem(int S, int np, int kc, bool fly, int Kd) {
 
 template <int S, bool FLY, int NT>
 static void frag_attr() {
-    const int smax = (int)frag_smem(6, 32, F_MAX_KB_FLY, true, 16 * F_MAX_KB_FLY);
+    const int smax = (int)frag_smem(kSlicesS, 32, F_MAX_KB_FLY, true, 16 * F_MAX_KB_FLY);
     VPX_CUDA(cudaFuncSetAttribute(k_gemm_frag<S, FLY, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax));
 }
 
 void gemm_frag_prepare_device() {
-    frag_attr<5, true, 1>();
-    frag_attr<5, true, 4>();
-    frag_attr<5, false, 1>();
-    frag_attr<5, false, 4>();
-    frag_attr<6, true, 1>();
-    frag_attr<6, true, 4>();
-    frag_attr<6, false, 1>();
-    frag_attr<6, false, 4>();
+    frag_attr<kSlicesS, true, 1>();
+    frag_attr<kSlicesS, true, 4>();
+    frag_attr<kSlicesS, false, 1>();
+    frag_attr<kSlicesS, false, 4>();
 }
 
 bool gemm_frag_eligible(const GemmPass &g, const VecSet &vs) {
@@ -292,17 +289,11 @@ void gemm_frag_run(const GemmPass &g, const VecSet &vs, double *out, int64_t ldo
              (reinterpret_cast<uintptr_t>(vs.base) % 16 == 0);
     if (a.ks > 1 && !a.add) fail(VPX_ERR_ARG, "a pass split along its inner dimension must accumulate");
     if (!fly && vs.kpad < g.Kpad) fail(VPX_ERR_ARG, "pre-sliced vectors shorter than the table's inner dimension");
-    const int S = g.slices >= 6 ? 6 : 5;
-    const size_t smem = frag_smem(S, g.np_f, a.kc, fly, a.Kd);
+    const size_t smem = frag_smem(kSlicesS, g.np_f, a.kc, fly, a.Kd);
     dim3 grid((unsigned)(g.n_tiles_f * a.rb * a.ks), (unsigned)nrhs);
     cudaStream_t st = (cudaStream_t)s;
-    if (S == 6) {
-        if (fly) frag_launch<6, true>(g.np_f, grid, a.wm * 32, smem, st, a);
-        else frag_launch<6, false>(g.np_f, grid, a.wm * 32, smem, st, a);
-    } else {
-        if (fly) frag_launch<5, true>(g.np_f, grid, a.wm * 32, smem, st, a);
-        else frag_launch<5, false>(g.np_f, grid, a.wm * 32, smem, st, a);
-    }
+    if (fly) frag_launch<kSlicesS, true>(g.np_f, grid, a.wm * 32, smem, st, a);
+    else frag_launch<kSlicesS, false>(g.np_f, grid, a.wm * 32, smem, st, a);
     VPX_LAUNCH("k_gemm_frag");
 }
 

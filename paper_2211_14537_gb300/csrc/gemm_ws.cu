@@ -2,13 +2,15 @@
 // tensor cores as a warp-specialised pipeline.
 //
 // One CTA computes, for one table and one block of its rows and one block of
-// its pairs, the S(S+1)/2 slice products a_k b_l (k + l <= S + 1) into S
-// fp32 accumulators in tensor memory (one per order d = k + l; exact, see
-// gemm.cu), then recombines them.  Two orientations:
+// its pairs, the S(S+1)/2 slice products a_k b_l (0-based, k + l <= S - 1)
+// into S fp32 accumulators in tensor memory (one per order d = k + l; exact,
+// see slice_math.cuh), then recombines them.  Two orientations:
 //
-//   TM = true  (the default): M = 128 table rows, N = 64 pairs, S = 5 (near
-//              field) or 6 (far field: L2M, lists i, i+ and i-);
-//   TM = false (VPX_TC_PAIRS): M = 128 pairs, N = 48 or 64 table rows, S = 6.
+//   TM = true  (instantiated): M = 128 table rows, N = 64 pairs, S = 5 (five
+//              orders of 64 columns in a 512-column tensor-memory
+//              allocation): the near field, L2M and lists i, i+ and i-;
+//   TM = false: M = 128 pairs, N = table rows (the template allows it; no
+//              pass is routed to it).
 //
 // Roles (256 threads):
 //   warp 0, one lane   table tiles by TMA bulk copies (cp.async.bulk): the
@@ -59,11 +61,11 @@ __device__ inline bool tw_wait(uint64_t *bar, uint32_t parity) {
 
 struct WsArgs {
     int M, Mpad, Kpad, nvec;
-    const uint16_t *tint;      // [ntab][6][Kpad/8][Mpad][8] table slices, column chunks interleaved
+    const uint16_t *tint;      // [ntab][S][Kpad/8][Mpad][8] table slices, column chunks interleaved
     const int32_t *texpo;      // [ntab][Mpad]
     const GTile *tiles;
     const GPair *pairs;
-    const uint16_t *vslices;   // [rhs][nvec][6][Kpad]
+    const uint16_t *vslices;   // [rhs][nvec][S][Kpad]
     const int32_t *vexpo;
     double *out;
     int64_t ldo;
@@ -335,23 +337,14 @@ __global__ void __launch_bounds__(TW_THREADS, 1) k_gemm_ws(WsArgs a) {
 
 // ------------------------------------------------------------------ host
 
-static int ws_rows_n(const GemmPass &g) { return g.M <= 96 ? 48 : 64; }
-
-// Which orientation runs a mixed-form pass (0: none): 1 = table rows on M
-// (5 slices, rows a multiple of 128: the near field).  The pairs-on-M
-// orientation (2) is built but not chosen by default: its vector operand is a
-// gather of 16-byte pieces, and with one CTA per SM that gather runs at a
-// fraction of what the mma.sync engine reaches with many CTAs per pass (the
-// environment variable VPX_TC_PAIRS selects it).
+// Which mixed-form passes run here (0: none, 1: table rows on M): every pass
+// with an inner dimension in whole 32-deep stages.
+// The far-field tables (2(p+1) rows, 56 at p = 27) take one 128-row block,
+// whose copies read up to 127 rows past the last chunk into the interleaved
+// table's padding; rows >= M are computed and dropped.
 static int ws_kind(const GemmPass &g) {
     if (!g.tslices || g.Kpad % TW_K != 0) return 0;
-    if (g.slices == 6 && getenv("VPX_TC_PAIRS") != nullptr) return 2;
-    // table rows on M for 5 or 6 slices: the far-field tables (82 rows at
-    // p = 40) take one 128-row block, whose copies read up to 127 rows past
-    // the last chunk into the interleaved table's padding; rows >= M are
-    // computed and dropped
-    if (g.slices == 5 || g.slices == 6) return 1;
-    return 0;
+    return 1;
 }
 
 // the table slices re-laid as [tab][slice][Kpad/8][Mpad][8] (plus one row block
@@ -361,7 +354,7 @@ __global__ void k_interleave_table(const uint16_t *ts, int ntab, int Mpad, int K
     for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
         const size_t ts_row = e / Kpad;   // (tab, s, row)
         const int k = (int)(e % Kpad), row = (int)(ts_row % Mpad);
-        const size_t tsl = ts_row / Mpad;   // tab * 6 + s
+        const size_t tsl = ts_row / Mpad;   // tab * S + s
         ti[((tsl * (Kpad / 8) + k / 8) * Mpad + row) * 8 + (k % 8)] = ts[e];
     }
 }
@@ -377,11 +370,6 @@ void gemm_ws_prepare(GemmPass &g) {
     VPX_CUDA(cudaDeviceSynchronize());
     g.tint = ti;
     g.ws_kind = kind;
-    // the far-field (six-slice) passes start on the fragment engine: their
-    // tables (2(p+1) <= 64 rows at the operating p) fill less than half of the
-    // 128-row MMA block here (measured: M2L 156 us here, about 90 us there on
-    // the L-shape at p = 27); the autotuner keeps tcgen05 as a candidate
-    if (kind == 1 && g.slices == 6) g.engine = 1;
 }
 
 template <bool TM, int S, int NB>
@@ -391,10 +379,7 @@ static void ws_attr() {
 }
 
 void gemm_ws_prepare_device() {
-    ws_attr<true, 5, 64>();
-    ws_attr<true, 6, 64>();
-    ws_attr<false, 6, 48>();
-    ws_attr<false, 6, 64>();
+    ws_attr<true, kSlicesS, kGemmTileN>();
 }
 
 bool gemm_ws_eligible(const GemmPass &g, const VecSet &vs) {
@@ -417,20 +402,11 @@ void gemm_ws_run(const GemmPass &g, const VecSet &vs, double *out, int64_t ldo, 
     a.status = g.status;
     a.tint = g.tint;
     cudaStream_t st = (cudaStream_t)s;
-    if (g.ws_kind == 1) {
-        if (g.n_tiles == 0) return;
-        a.tiles = g.tiles;
-        dim3 grid(g.n_tiles, (g.M + TW_M - 1) / TW_M, nrhs);
-        if (g.slices == 5) launch_pdl(k_gemm_ws<true, 5, 64>, grid, dim3(TW_THREADS), WsShape<true, 5, 64>::SMEM, st, a);
-        else launch_pdl(k_gemm_ws<true, 6, 64>, grid, dim3(TW_THREADS), WsShape<true, 6, 64>::SMEM, st, a);
-    } else {
-        if (g.n_tiles_p == 0) return;
-        a.tiles = g.tiles_p;
-        const int nb = ws_rows_n(g);
-        dim3 grid(g.n_tiles_p, (g.M + nb - 1) / nb, nrhs);
-        if (nb == 48) launch_pdl(k_gemm_ws<false, 6, 48>, grid, dim3(TW_THREADS), WsShape<false, 6, 48>::SMEM, st, a);
-        else launch_pdl(k_gemm_ws<false, 6, 64>, grid, dim3(TW_THREADS), WsShape<false, 6, 64>::SMEM, st, a);
-    }
+    const dim3 rb(1, (g.M + TW_M - 1) / TW_M, nrhs);
+    if (g.n_tiles == 0) return;
+    a.tiles = g.tiles;
+    launch_pdl(k_gemm_ws<true, kSlicesS, kGemmTileN>, dim3(g.n_tiles, rb.y, rb.z), dim3(TW_THREADS),
+               WsShape<true, kSlicesS, kGemmTileN>::SMEM, st, a);
     VPX_LAUNCH("k_gemm_ws");
 }
 

@@ -47,7 +47,6 @@ struct DevExt {
     // double-float copies (hi, lo float pairs) for the mixed form
     struct DfPair { float hi, lo; };
     DfPair *pinv_df = nullptr, *cheb_df = nullptr;   // pinv_df: rows padded to an even length
-    DfPair *agT_df = nullptr;                          // [NG][Kbar^2] universal operator at X_Sbar, transposed
     int64_t *pinv_df_off = nullptr;
     double *tgt_geo = nullptr;                         // [n_tgt][4]: offset x, offset y, node scale, is-cut-leaf
     GemmPass grid_pass;                  // A_{X_Sbar,G} c for all cut leaves (one table)
@@ -94,9 +93,6 @@ struct ChainPlan {
     int32_t *up_of = nullptr;     // per box: parent, position among its siblings (pairs)
     int *ws = nullptr;            // both queue blocks, zeroed before every step
     size_t ws_ints = 0;
-    // the sparse levels below the cut level lc, one CTA per subtree root (mixed form)
-    int lc = -1, n_roots = 0;
-    int32_t *st_root_seg[2] = {nullptr, nullptr}, *st_seg_item[2] = {nullptr, nullptr}, *st_item[2] = {nullptr, nullptr};
 };
 
 struct FmmPasses {                // every contraction of the box FMM as a grouped table GEMM

@@ -2,18 +2,27 @@
 // its engines (gemm_frag.cu: mma.sync; gemm_ws.cu: tcgen05): splitting
 // an FP64 vector into bf16 integer slices, and the epilogue.
 //
-// Slicing.  e = exponent of max|v| (frexp convention); every element becomes the
-// integer N = round(v 2^{7S-e}) (|N| <= 2^42 for S = 6 stored slices), split
-// into balanced base-128 digits from the bottom: the lower S-1 digits in
-// [-64, 63], the top digit (the remainder) in [-128, 128].  Integer arithmetic
-// on the bit pattern only, apart from the exact digit -> bf16 conversion.
+// Slicing.  e = one more than the exponent of max|v| (frexp convention), so
+// that max|v| < 2^(e-1); every element becomes the integer
+// N = round(v 2^{8S-e}) (|N| < 2^39 for S = 5 slices), split into
+// balanced base-256 digits from the bottom: the lower S-1 digits in
+// [-128, 127], the top digit (the remainder) in [-128, 128].  Every digit is
+// an integer of magnitude <= 128, exact in bf16 (8 significant bits).
+// Integer arithmetic on the bit pattern only, apart from the exact digit ->
+// bf16 conversion.
 //
-// Epilogue.  Each order sum acc_d is an exact integer below 2^24 held in fp32:
-// it converts exactly to int32, and N = sum_d acc_d 128^{S-1-d} is an exact
-// int64 (|N| < 2^60).  The output N 2^{e_row + e_pair + e_vec - 14 - 7(S-1)}
-// m_pair is then one rounding of the exact slice-product sum: the int64 ->
-// FP64 conversion, the power of two applied to the exponent field, and one
-// FP64 multiply only for a pair scale that is not a power of two.
+// Epilogue.  The order-d sum (0-based, products a_k b_l with k + l = d) of
+// one inner index is at most (d + 1) 2^14 in magnitude, so over an inner
+// dimension K it is an exact integer in fp32 while K (d + 1) <= 1024: every
+// far-field pass with K <= 204 stays exact at five slices; the mma.sync
+// engine splits longer inner dimensions into exact 64-deep chunks, and on
+// tcgen05 only the last order (relative weight 2^-32; in the near field,
+// K = 256, orders 0..3 stay exact) can round.  Each order sum converts exactly to
+// int32, and N = sum_d acc_d 256^{S-1-d} is an exact int64 (|N| < 2^57 for
+// S <= 5).  The output N 2^{e_row + e_pair + e_vec - 16 - 8(S-1)} m_pair is
+// then one rounding of the slice-product sum: the int64 -> FP64 conversion,
+// the power of two applied to the exponent field, and one FP64 multiply only
+// for a pair scale that is not a power of two.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -26,43 +35,39 @@ namespace vpx {
 
 constexpr int kSliceMaxPerLane = 8;   // elements per lane when a warp slices one vector: Kpad <= 256
 
-// exponent e with max|x| in [2^{e-1}, 2^e), from the largest |bit pattern|
-// (|x| compares as its bit pattern); 0 for an all-zero vector
+// the slicing exponent e of a vector from its largest |bit pattern| (|x|
+// compares as its bit pattern): max|x| < 2^(e-1), one above the frexp
+// exponent, so that the top digit stays within [-128, 128]; 0 for an
+// all-zero vector
 __device__ inline int slice_expo_of_bits(uint64_t mb) {
     if (mb == 0) return 0;
     const int bex = (int)(mb >> 52);
-    if (bex != 0) return bex - 1022;
+    if (bex != 0) return bex - 1021;
     int e = 0;
     frexp(__longlong_as_double((long long)mb), &e);   // subnormal maximum
-    return e;
+    return e + 1;
 }
 
-// exponent e of the largest |x| over a warp's elements, given each lane's
-// max |bit pattern|: max|x| in [2^{e-1}, 2^e)
+// the slicing exponent of a warp's elements, given each lane's max |bit pattern|
 __device__ inline int slice_warp_expo(uint64_t mb) {
     for (int o = 16; o; o >>= 1) {
         const uint64_t t = (uint64_t)__shfl_xor_sync(0xffffffffu, (long long)mb, o);
         mb = t > mb ? t : mb;
     }
-    if (mb == 0) return 0;
-    const int bex = (int)(mb >> 52);
-    if (bex != 0) return bex - 1022;
-    int e = 0;
-    frexp(__longlong_as_double((long long)mb), &e);   // subnormal maximum
-    return e;
+    return slice_expo_of_bits(mb);
 }
 
 __device__ inline uint64_t slice_abs_bits(double x) {
     return (uint64_t)__double_as_longlong(x) & 0x7fffffffffffffffull;
 }
 
-// N = round(x 2^{7S-e}) for S = kSlicesS
+// N = round(x 2^{8S-e}) for S = kSlicesS
 __device__ inline int64_t slice_fixed_point(double x, int e) {
     const uint64_t b = (uint64_t)__double_as_longlong(x);
     const int ex = (int)((b >> 52) & 0x7ff);
     if (ex == 0) return 0;   // zero or subnormal: below the last slice for any normal max
     const uint64_t m = (b & 0xfffffffffffffull) | (1ull << 52);
-    const int sh = 1075 - ex - kSlicesS * kSliceBitsB + e;   // x 2^{7S-e} = m 2^{-sh}, sh >= 11
+    const int sh = 1075 - ex - kSlicesS * kSliceBitsB + e;   // x 2^{8S-e} = m 2^{-sh}, sh >= 6
     if (sh >= 64) return 0;
     const int64_t n = (int64_t)((m + (1ull << (sh - 1))) >> sh);
     return (b >> 63) ? -n : n;
@@ -72,8 +77,8 @@ __device__ inline int64_t slice_fixed_point(double x, int e) {
 __device__ inline void slice_digits(int64_t n, uint16_t (&d)[kSlicesS]) {
 #pragma unroll
     for (int k = kSlicesS - 1; k > 0; --k) {
-        const int64_t up = (n + 64) >> 7;
-        d[k] = __bfloat16_as_ushort(__float2bfloat16_rn((float)(n - up * 128)));
+        const int64_t up = (n + 128) >> 8;
+        d[k] = __bfloat16_as_ushort(__float2bfloat16_rn((float)(n - up * 256)));
         n = up;
     }
     d[0] = __bfloat16_as_ushort(__float2bfloat16_rn((float)n));
@@ -109,7 +114,8 @@ template <int S>
 __device__ inline double slice_output(const float (&acc)[S], const SliceScale &ps, int row_e) {
     int64_t n = __float2int_rn(acc[0]);
 #pragma unroll
-    for (int d = 1; d < S; ++d) n = n * 128 + __float2int_rn(acc[d]);
+    static_assert(S <= 5, "more slices than the int64 recombination holds");
+    for (int d = 1; d < S; ++d) n = n * 256 + __float2int_rn(acc[d]);
     const double v = slice_i64_scaled(n, row_e + ps.e - kSliceBitsB * (S - 1));
     return ps.mul == 1.0 ? v : v * ps.mul;
 }

@@ -9,9 +9,20 @@ from oracle import oracle as O
 EPS = np.finfo(float).eps
 
 # unit roundoff of the mixed form's extension: its grid stage (A c over the
-# coarse grid) is a six-slice bf16 pass, each operand rounded to 2^-42 of its
-# row or vector maximum and product orders above 7 dropped
-MIXED_EXT_EPS = 2.0 ** -40
+# coarse grid) is a five-slice bf16 pass (8-bit digits), each operand rounded
+# to 2^-40 of its row or vector maximum and product orders above 4 dropped
+MIXED_EXT_EPS = 2.0 ** -37
+
+# Two schedules of the mixed form (engine, pairs per tile, chain or per-level
+# launches, batch or single plan) sum the same slice products in other orders,
+# so a pass's FP64 output can differ in its last bit.  The next pass re-slices
+# that output: where a coefficient lies within one FP64 rounding of a half
+# unit of its fifth 8-bit digit, the two schedules round it to neighbouring
+# slice values, 2^-39 of its vector's maximum apart.  Such coefficients travel
+# through up to 15 levels of M2M/L2L and the M2L and L2T passes; 1e-10 of
+# max|V| (about 55 of those units) leaves room for a few per level and stays
+# ten times below the mixed form's own parity gate of 1e-9.
+MIXED_SCHEDULE_TOL = 1e-10
 
 
 def chebyshev_stage_norm(b, K, targets):

@@ -1,11 +1,13 @@
 """The autotuner (vpx_autotune) changes only the schedule of the mixed-form
 passes (engine, pairs per tile): results after tuning equal those before to
-1e-12 of the maximum, captured graphs pick the new choices up, and an FP64-form
+bounds.MIXED_SCHEDULE_TOL of the maximum (re-sliced expansions may round to
+the neighbouring last digit), captured graphs pick the new choices up, and an FP64-form
 plan has nothing to tune."""
 import numpy as np
 import pytest
 
 import workloads as W
+from bounds import MIXED_SCHEDULE_TOL
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -47,8 +49,10 @@ def test_autotune_keeps_results(V, name):
         V.vpx_execute(plan, f, v1, b1, stream=stream)
         assert V.vpx_sync_status(plan) == 0
     scale = float(v0.abs().max())
-    assert float((v1 - v0).abs().max()) <= 1e-12 * scale
-    assert float((b1 - b0).abs().max()) <= 1e-12 * scale
+    print("%s: after tuning max diff %.3e, boundary %.3e (scale %.3e)"
+          % (name, float((v1 - v0).abs().max()), float((b1 - b0).abs().max()), scale))
+    assert float((v1 - v0).abs().max()) <= MIXED_SCHEDULE_TOL * scale
+    assert float((b1 - b0).abs().max()) <= MIXED_SCHEDULE_TOL * scale
     # a second plan of the same shapes takes the cached choices without timing
     plan2 = _plan(V, wl, V.VPX_PREC_MIXED)
     assert V.vpx_autotune(plan2, f, stream=stream) == (npass, nchg)

@@ -13,7 +13,7 @@ import pytest
 
 import workloads as W
 from oracle import oracle as O
-from bounds import MIXED_EXT_EPS, extension_bounds
+from bounds import MIXED_EXT_EPS, MIXED_SCHEDULE_TOL, extension_bounds
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -75,15 +75,15 @@ def test_c5_batch_matches_single_executes(V, batch):
         d = max(float((vs[i] - v1).abs().max()) / float(v1.abs().max()),
                 float((vbs[i] - vb1).abs().max()) / float(vb1.abs().max()))
         worst = max(worst, d)
-    # targets accumulate contributions with FP64 atomics, whose order varies
+    # targets and expansions accumulate with FP64 atomics, whose order varies
     print("C5 batch vs single executes: max rel diff %.3e over %d trees" % (worst, len(plans)))
-    assert worst <= 1e-12
+    assert worst <= MIXED_SCHEDULE_TOL
 
 
 def test_c5_batch_sampled_against_oracle(V, batch):
     """The smallest, a middle and the largest tree of the batch, stage by stage
     against the oracle: the extension within 64 units of the mixed form's
-    extension arithmetic (2^-40, set by its six-slice grid stage) times each
+    extension arithmetic (2^-40 for its five-slice grid stage) times each
     cut leaf's forward-error factor kappa, and the potential of the
     oracle's own extended values on sampled leaf targets (direct quadrature)
     and boundary targets (interpolation of the leaf values on the containing
@@ -162,7 +162,7 @@ def test_c5_batch_graph_follows_its_arguments(V, batch):
         v1 = torch.empty(sizes[i][1], dtype=torch.float64, device="cuda")
         V.vpx_execute(plans[i], fs[i], v1, stream=stream)
         assert V.vpx_sync_status(plans[i]) == 0
-        assert float((vs[k] - v1).abs().max()) <= 1e-12 * float(v1.abs().max())
+        assert float((vs[k] - v1).abs().max()) <= MIXED_SCHEDULE_TOL * float(v1.abs().max())
         ref.append(v1)
     rev = sel[::-1]
     vs2, _ = _outputs([sizes[i] for i in rev])
@@ -170,14 +170,14 @@ def test_c5_batch_graph_follows_its_arguments(V, batch):
     for k, i in enumerate(rev):
         assert V.vpx_sync_status(plans[i]) == 0
         r = ref[len(sel) - 1 - k]
-        assert float((vs2[k] - r).abs().max()) <= 1e-12 * float(r.abs().max())
+        assert float((vs2[k] - r).abs().max()) <= MIXED_SCHEDULE_TOL * float(r.abs().max())
     # a plan created after the cached graph was captured
     extra = _plan(V, wls[1])
     f_extra = torch.tensor(wls[1].sources[0](extra.stencil_points()), dtype=torch.float64, device="cuda")
     vs3, _ = _outputs([sizes[1]])
     V.vpx_execute_batch([extra], [f_extra], vs3, None, stream=stream)
     assert V.vpx_sync_status(extra) == 0
-    assert float((vs3[0] - ref[1]).abs().max()) <= 1e-12 * float(ref[1].abs().max())
+    assert float((vs3[0] - ref[1]).abs().max()) <= MIXED_SCHEDULE_TOL * float(ref[1].abs().max())
 
 
 def test_c5_batch_rejects_bad_arguments(V, batch):
@@ -191,7 +191,7 @@ def test_c5_batch_rejects_bad_arguments(V, batch):
 
 def test_c5_batch_autotune_keeps_results(V, batch):
     """The batch autotuner (one engine / tile choice per pass role, timed on the
-    batch graph) leaves every tree's result unchanged to 1e-12."""
+    batch graph) leaves every tree's result unchanged to MIXED_SCHEDULE_TOL."""
     wls, plans, sizes, fs = batch
     stream = torch.cuda.Stream()
     vs, vbs = _outputs(sizes)
@@ -205,5 +205,5 @@ def test_c5_batch_autotune_keeps_results(V, batch):
     for i, p in enumerate(plans):
         assert V.vpx_sync_status(p) == 0
         scale = float(vs[i].abs().max())
-        assert float((vs2[i] - vs[i]).abs().max()) <= 1e-12 * scale
-        assert float((vbs2[i] - vbs[i]).abs().max()) <= 1e-12 * scale
+        assert float((vs2[i] - vs[i]).abs().max()) <= MIXED_SCHEDULE_TOL * scale
+        assert float((vbs2[i] - vbs[i]).abs().max()) <= MIXED_SCHEDULE_TOL * scale
