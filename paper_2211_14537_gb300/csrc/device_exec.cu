@@ -200,9 +200,11 @@ __global__ void k_finish(int64_t n_v, int nan_blocks, int nb, int K, const int32
                          const double *v, int64_t ldv, double *vb, int64_t ldb, int *status) {
     pdl_entry();
     const int rhs = blockIdx.y;
-    if ((int)blockIdx.x < nan_blocks) {
-        const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-        if (i < n_v && !isfinite(v[rhs * ldv + i])) set_status(status, VPX_ERR_NAN);
+    if ((int)blockIdx.x < nan_blocks) {   // grid-stride over the leaf values
+        bool bad = false;
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_v; i += (int64_t)nan_blocks * blockDim.x)
+            bad |= !isfinite(v[rhs * ldv + i]);
+        if (bad) set_status(status, VPX_ERR_NAN);
         return;
     }
     const int k = (blockIdx.x - nan_blocks) * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
@@ -419,7 +421,9 @@ void run_potential_scratch(vpx_plan *p, const double *fe, int64_t ldfe, int nrhs
     run_potential_passes(p, fe, ldfe, nrhs, v, ldv, vb, ldb, mp, lo, s, fe_sliced);
     const int nbd = (vb != nullptr) ? (int)p->bdry_leaf.size() : 0;
     const int64_t n_v = (int64_t)p->dt.n_leaves * p->KK;
-    const int nan_blocks = (int)((n_v + 255) / 256);
+    // a few thousand values per block: a block per 256 values spent most of
+    // the kernel's time starting blocks
+    const int nan_blocks = (int)std::min<int64_t>((n_v + 2047) / 2048, 1024);
     const int blocks = nan_blocks + (nbd + 7) / 8;
     if (blocks > 0) {
         launch_pdl(k_finish, dim3(blocks, nrhs), dim3(256), 0, s, n_v, nan_blocks, nbd, p->K, p->wk.bdry_leaf, p->wk.bdry_w, v, ldv,

@@ -368,6 +368,12 @@ void setup_passes(vpx_plan *p) {
         gemm_ws_prepare_device();
         gemm_frag_prepare_device();
         for (GemmPass *g : {&F.near, &F.l2m, &F.m2l, &F.s2l, &F.l2t, &F.m2t}) gemm_ws_prepare(*g);
+        // M2L starts on the mma.sync engine: its 2(p+1)-row tables fill under
+        // half of a 128-row tcgen05 block and its inner dimension is one or two
+        // stages deep, so a tcgen05 tile is mostly set-up (measured on the
+        // L-shape at p = 27: 0.147 ms on tcgen05 against 0.090 ms).  The
+        // autotuner keeps tcgen05 as a candidate.
+        F.m2l.engine = 1;
         const int kp_f = (KK + 31) / 32 * 32, kp_m = (P2 + 31) / 32 * 32;
         F.fe_sl = dev_alloc<uint16_t>((size_t)p->opt.max_rhs * nl * kSlicesS * kp_f);
         F.fe_ex = dev_alloc<int32_t>((size_t)p->opt.max_rhs * nl);

@@ -145,7 +145,7 @@ void gemm_pass_set_pairs(GemmPass &g, std::vector<std::pair<int, GPair>> &tagged
     std::stable_sort(tagged.begin(), tagged.end(),
                      [](const std::pair<int, GPair> &x, const std::pair<int, GPair> &y) { return x.first < y.first; });
     std::vector<GPair> pr;
-    std::vector<GTile> tl, tf, tfa, tr, tp;
+    std::vector<GTile> tl, tf, tfa, tr, tw;
     const size_t npf = frag_np == 8 || frag_np == 32 ? (size_t)frag_np : tagged.size() >= (size_t)kFragBigPass ? 32 : 8;
     const size_t npa = npf == 8 ? 32 : 8;
     size_t i = 0;
@@ -155,6 +155,8 @@ void gemm_pass_set_pairs(GemmPass &g, std::vector<std::pair<int, GPair>> &tagged
         const int32_t base = (int32_t)pr.size();
         for (size_t k = i; k < j; k += kGemmTileN)
             tl.push_back({tagged[i].first, base + (int32_t)(k - i), (int32_t)std::min<size_t>(kGemmTileN, j - k), 0});
+        for (size_t k = i; k < j; k += kWsTileN)
+            tw.push_back({tagged[i].first, base + (int32_t)(k - i), (int32_t)std::min<size_t>(kWsTileN, j - k), 0});
         for (size_t k = i; k < j; k += npf)
             tf.push_back({tagged[i].first, base + (int32_t)(k - i), (int32_t)std::min<size_t>(npf, j - k), 0});
         for (size_t k = i; k < j; k += npa)
@@ -168,12 +170,13 @@ void gemm_pass_set_pairs(GemmPass &g, std::vector<std::pair<int, GPair>> &tagged
     // wave ends with its smallest tiles (stable: full tiles keep their table
     // order).  The row engine pairs tile i with pair i and keeps its order.
     auto by_count = [](const GTile &x, const GTile &y) { return x.count > y.count; };
-    for (std::vector<GTile> *v : {&tl, &tf, &tfa}) std::stable_sort(v->begin(), v->end(), by_count);
+    for (std::vector<GTile> *v : {&tl, &tf, &tfa, &tw}) std::stable_sort(v->begin(), v->end(), by_count);
     g.h_pairs = pr;
     g.n_pairs = (int)pr.size();
     g.n_tiles = (int)tl.size();
     g.n_tiles_f = (int)tf.size();
     g.n_tiles_r = (int)tr.size();
+    g.n_tiles_w = (int)tw.size();
     g.np_f = (int)npf;
     g.n_tiles_f_alt = (int)tfa.size();
     g.np_f_alt = (int)npa;
@@ -182,6 +185,7 @@ void gemm_pass_set_pairs(GemmPass &g, std::vector<std::pair<int, GPair>> &tagged
     g.tiles = dev_upload(tl);
     g.tiles_f = dev_upload(tf);
     g.tiles_r = dev_upload(tr);
+    g.tiles_w = dev_upload(tw);
 }
 
 static uint16_t bf16_bits_exact(double q) {
@@ -274,9 +278,10 @@ void gemm_pass_free(GemmPass &g) {
     dev_free(g.tiles_f);
     dev_free(g.tiles_f_alt);
     dev_free(g.tiles_r);
+    dev_free(g.tiles_w);
     dev_free(g.tdfT);
     dev_free(g.tint);
-    g.n_pairs = g.n_tiles = g.n_tiles_f = g.n_tiles_f_alt = g.n_tiles_r = 0;
+    g.n_pairs = g.n_tiles = g.n_tiles_f = g.n_tiles_f_alt = g.n_tiles_r = g.n_tiles_w = 0;
 }
 
 GemmChoice gemm_choice(const GemmPass &g) { return GemmChoice{g.engine, g.np_f}; }

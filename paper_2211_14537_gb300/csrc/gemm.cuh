@@ -15,7 +15,8 @@
 
 namespace vpx {
 
-constexpr int kGemmTileN = 64;   // pairs per tile (FP64 and tcgen05 engines)
+constexpr int kGemmTileN = 64;   // pairs per tile (FP64 engine)
+constexpr int kWsTileN = 48;     // pairs per tile (tcgen05 engine)
 constexpr int kFragBigPass = 4096;   // fragment engine: 32 pairs per tile from this many pairs on, else 8
 constexpr int kRowsTileN = 1;        // pairs per tile (double-float row engine)
 constexpr int kSlicesS = 5;      // bf16 slices per operand in the mixed form (39 bits); the int64
@@ -56,10 +57,11 @@ struct GemmPass {
     GTile *tiles = nullptr;            // kGemmTileN pairs each
     GTile *tiles_f = nullptr;          // np_f pairs each (fragment engine)
     GTile *tiles_r = nullptr;          // kRowsTileN pairs each (row engine)
+    GTile *tiles_w = nullptr;          // kWsTileN pairs each (tcgen05 engine)
     const void *tdfT = nullptr;        // [ntab][Kd][M] double-float (float hi, lo): the row engine runs the pass
     const uint16_t *tint = nullptr;    // [ntab][S][Kpad/8][Mpad][8] slices, column chunks interleaved (tcgen05 engine)
     int ws_kind = 0;                   // 0: not on that engine; 1: on it (table rows on M)
-    int n_pairs = 0, n_tiles = 0, n_tiles_f = 0, np_f = 8, n_tiles_r = 0;
+    int n_pairs = 0, n_tiles = 0, n_tiles_f = 0, np_f = 8, n_tiles_r = 0, n_tiles_w = 0;
     // the fragment engine's other tile width (8 <-> 32 pairs), for the autotuner
     GTile *tiles_f_alt = nullptr;
     int n_tiles_f_alt = 0, np_f_alt = 32;

@@ -6,9 +6,12 @@
 // into S fp32 accumulators in tensor memory (one per order d = k + l; exact,
 // see slice_math.cuh), then recombines them.  Two orientations:
 //
-//   TM = true  (instantiated): M = 128 table rows, N = 64 pairs, S = 5 (five
-//              orders of 64 columns in a 512-column tensor-memory
-//              allocation): the near field, L2M and lists i, i+ and i-;
+//   TM = true  (instantiated): M = 128 table rows, N = 48 pairs, S = 5 (five
+//              orders of 48 columns in a 256-column tensor-memory
+//              allocation, and three stages in 82.5 KB of shared memory, so
+//              that two CTAs share an SM and each hides the other's set-up,
+//              pipeline fill and epilogue): the near field, L2M and lists i+
+//              and i-;
 //   TM = false: M = 128 pairs, N = table rows (the template allows it; no
 //              pass is routed to it).
 //
@@ -26,7 +29,7 @@
 //                      makes each thread's copies one arrival on the full
 //                      barrier;
 //   all warps          the epilogue once the done barrier flips.
-// Stages form a ring of TW_STAGES buffers of 32 inner indices each.  Every
+// Stages form a ring of TW_STAGES buffers of TW_K = 16 inner indices each.  Every
 // barrier wait is bounded; a timeout sets VPX_ERR_TIMEOUT, skips the epilogue,
 // and the CTA still releases its tensor memory.
 #include <cuda_bf16.h>
@@ -40,9 +43,12 @@
 
 namespace vpx {
 
-constexpr int TW_M = 128, TW_K = 32, TW_STAGES = 3, TW_THREADS = 256, TW_PROD0 = 64;   // producers: threads 64..255
+constexpr int TW_M = 128, TW_K = 16, TW_STAGES = 3, TW_THREADS = 256, TW_PROD0 = 64;   // producers: threads 64..255
 constexpr int TW_NPROD = TW_THREADS - TW_PROD0;
-constexpr uint32_t TW_TMEM_COLS = 512;
+constexpr int TW_KQ = TW_K / 8;   // 8-column chunks per stage
+
+// tensor-memory columns to allocate: a power of two >= 32
+constexpr uint32_t tw_tmem_cols(int n) { return n <= 32 ? 32u : 2u * tw_tmem_cols((n + 1) / 2); }
 
 __device__ inline uint32_t tw_smem(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -80,16 +86,17 @@ struct WsShape {
     static constexpr int A_SLICE = TW_M * TW_K;   // bf16 per A slice
     static constexpr int B_SLICE = NB * TW_K;     // bf16 per B slice
     static constexpr int STAGE = S * (A_SLICE + B_SLICE);
-    static constexpr uint32_t T_BYTES = (uint32_t)(S * 4 * TR * 16);   // table bytes per stage
+    static constexpr uint32_t T_BYTES = (uint32_t)(S * TW_KQ * TR * 16);   // table bytes per stage
     static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NB >> 3) << 17) |
                                       ((uint32_t)(TW_M >> 4) << 24);
     static constexpr size_t SMEM = (size_t)TW_STAGES * STAGE * sizeof(uint16_t);
-    static_assert(S * NB <= (int)TW_TMEM_COLS, "accumulators exceed tensor memory");
+    static constexpr uint32_t TMEM_COLS = tw_tmem_cols(S * NB);
+    static_assert(TMEM_COLS <= 512, "accumulators exceed tensor memory");
 };
 
 // grid: x = tile of pairs, y = block of table rows, z = rhs
 template <bool TM, int S, int NB>
-__global__ void __launch_bounds__(TW_THREADS, 1) k_gemm_ws(WsArgs a) {
+__global__ void __launch_bounds__(TW_THREADS, 2) k_gemm_ws(WsArgs a) {
     pdl_entry();
     typedef WsShape<TM, S, NB> Sh;
     extern __shared__ __align__(1024) uint16_t wsm[];
@@ -130,7 +137,7 @@ __global__ void __launch_bounds__(TW_THREADS, 1) k_gemm_ws(WsArgs a) {
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(tw_smem(&s_tmem)),
-                     "r"(TW_TMEM_COLS));
+                     "r"(Sh::TMEM_COLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -159,8 +166,8 @@ __global__ void __launch_bounds__(TW_THREADS, 1) k_gemm_ws(WsArgs a) {
                              : "memory");
                 const uint32_t sb = base + (uint32_t)(b * Sh::STAGE * 2) + t_off;
                 for (int s2 = 0; s2 < S; ++s2)
-                    for (int q = 0; q < 4; ++q) {
-                        const size_t chunk = ((size_t)(tile.tab * kSlicesS + s2) * kc_n + kt * 4 + q) * a.Mpad + row0;
+                    for (int q = 0; q < TW_KQ; ++q) {
+                        const size_t chunk = ((size_t)(tile.tab * kSlicesS + s2) * kc_n + kt * TW_KQ + q) * a.Mpad + row0;
                         asm volatile(
                             "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
                                 sb + s2 * t_slice + q * t_lbo),
@@ -217,7 +224,7 @@ __global__ void __launch_bounds__(TW_THREADS, 1) k_gemm_ws(WsArgs a) {
     } else {
         // ---- vector producers: 16-byte chunks of the pairs' slices; a thread's
         // chunks are the same (slice, pair, column chunk) at every stage
-        constexpr int NCH = (S * Sh::VR * 4 + TW_NPROD - 1) / TW_NPROD;
+        constexpr int NCH = (S * Sh::VR * TW_KQ + TW_NPROD - 1) / TW_NPROD;
         const int pt = tid - TW_PROD0;
         const uint16_t *VS = a.vslices + (size_t)rhs * a.nvec * kSlicesS * a.Kpad;
         const uint16_t *srcp[NCH];
@@ -226,8 +233,8 @@ __global__ void __launch_bounds__(TW_THREADS, 1) k_gemm_ws(WsArgs a) {
 #pragma unroll
         for (int i = 0; i < NCH; ++i) {
             const int c = pt + i * TW_NPROD;
-            const int s2 = c / (Sh::VR * 4), rem = c % (Sh::VR * 4), r = rem >> 2, q = rem & 3;
-            const bool live = c < S * Sh::VR * 4;
+            const int s2 = c / (Sh::VR * TW_KQ), rem = c % (Sh::VR * TW_KQ), r = rem / TW_KQ, q = rem % TW_KQ;
+            const bool live = c < S * Sh::VR * TW_KQ;
             nbytes[i] = (live && r < tile.count) ? 16 : 0;
             srcp[i] = VS + ((size_t)(live ? s_src[r] : 0) * kSlicesS + (live ? s2 : 0)) * a.Kpad + q * 8;
             dsto[i] = live ? (uint32_t)(s2 * v_slice + q * v_lbo + (r >> 3) * 128 + (r & 7) * 16) : 0u;
@@ -242,7 +249,7 @@ __global__ void __launch_bounds__(TW_THREADS, 1) k_gemm_ws(WsArgs a) {
             const int k0 = kt * TW_K;
 #pragma unroll
             for (int i = 0; i < NCH; ++i)
-                if (pt + i * TW_NPROD < S * Sh::VR * 4)
+                if (pt + i * TW_NPROD < S * Sh::VR * TW_KQ)
                     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sb + dsto[i]), "l"(srcp[i] + k0),
                                  "r"(nbytes[i]));
             asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];\n" ::"r"(tw_smem(&full[b])) : "memory");
@@ -331,7 +338,7 @@ __global__ void __launch_bounds__(TW_THREADS, 1) k_gemm_ws(WsArgs a) {
     __syncthreads();
     if (warp == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TW_TMEM_COLS));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(Sh::TMEM_COLS));
     }
 }
 
@@ -379,7 +386,7 @@ static void ws_attr() {
 }
 
 void gemm_ws_prepare_device() {
-    ws_attr<true, kSlicesS, kGemmTileN>();
+    ws_attr<true, kSlicesS, kWsTileN>();
 }
 
 bool gemm_ws_eligible(const GemmPass &g, const VecSet &vs) {
@@ -403,10 +410,10 @@ void gemm_ws_run(const GemmPass &g, const VecSet &vs, double *out, int64_t ldo, 
     a.tint = g.tint;
     cudaStream_t st = (cudaStream_t)s;
     const dim3 rb(1, (g.M + TW_M - 1) / TW_M, nrhs);
-    if (g.n_tiles == 0) return;
-    a.tiles = g.tiles;
-    launch_pdl(k_gemm_ws<true, kSlicesS, kGemmTileN>, dim3(g.n_tiles, rb.y, rb.z), dim3(TW_THREADS),
-               WsShape<true, kSlicesS, kGemmTileN>::SMEM, st, a);
+    if (g.n_tiles_w == 0) return;
+    a.tiles = g.tiles_w;
+    launch_pdl(k_gemm_ws<true, kSlicesS, kWsTileN>, dim3(g.n_tiles_w, rb.y, rb.z), dim3(TW_THREADS),
+               WsShape<true, kSlicesS, kWsTileN>::SMEM, st, a);
     VPX_LAUNCH("k_gemm_ws");
 }
 

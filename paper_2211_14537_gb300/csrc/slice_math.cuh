@@ -112,9 +112,9 @@ __device__ inline double slice_i64_scaled(int64_t n, int e) {
 // acc[0] is the most significant order
 template <int S>
 __device__ inline double slice_output(const float (&acc)[S], const SliceScale &ps, int row_e) {
+    static_assert(S <= 5, "more slices than the int64 recombination holds");
     int64_t n = __float2int_rn(acc[0]);
 #pragma unroll
-    static_assert(S <= 5, "more slices than the int64 recombination holds");
     for (int d = 1; d < S; ++d) n = n * 256 + __float2int_rn(acc[d]);
     const double v = slice_i64_scaled(n, row_e + ps.e - kSliceBitsB * (S - 1));
     return ps.mul == 1.0 ? v : v * ps.mul;
