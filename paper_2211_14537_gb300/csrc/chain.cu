@@ -35,6 +35,14 @@
 // besides: a timeout latches VPX_ERR_TIMEOUT and the CTA leaves.  The queue
 // state (claim and push counters, per-box counts, slots) is one zeroed block
 // per launch.
+//
+// The mixed form runs the warp-granular kernel k_wchain below (one warp per
+// box).  On the L-shape at p = 27 its chains take 73 us (up) and 81 us (down)
+// against 98 and 100 us for the CTA-per-box kernel and 71 and 79 us for one
+// launch per level: a level costs about 6 us either way, set by the memory
+// round trips of one box (its atomics and fence, the parent's counter, the
+// parent's load) rather than by launches.  So the mixed form's default stays
+// one launch per level; both kernels remain selectable.
 #include <algorithm>
 #include <cmath>
 #include <type_traits>
@@ -240,6 +248,142 @@ __global__ void __launch_bounds__(CH_THREADS) k_chain(ChainArgs a) {
     }
 }
 
+// ---------------------------------------------------------- warp-granular form
+
+// The mixed form's chains with ONE WARP per box instead of one CTA: the
+// schedule above at warp granularity (a warp that completes a parent goes on
+// with it; downward, a warp goes on with a first child and queues the rest),
+// so a CTA of CW_WARPS warps carries as many boxes at once.  The four tables
+// stay in shared memory, each row packed over its non-zero column range
+// (M2M is lower and L2L upper triangular, so half of P x P); lane l computes
+// rows l and l + 32.  Every box still costs the same double-float operations
+// as in k_chain, summed in column order per row.
+constexpr int CW_WARPS = 8, CW_THREADS = 32 * CW_WARPS;
+
+struct WChainArgs {
+    int P, nrhs, n_slots, n0, n_packed;
+    int64_t ldm;
+    const int32_t *items0;
+    const int2 *up_of;
+    const int32_t *child0, *need;
+    const float4 *tabp;           // packed rows: (re hi, re lo, im hi, im lo) over each row's column range
+    const int32_t *roff;          // [4][P] start of every row in tabp
+    const int16_t *krange;        // [4][P][2]
+    int *ws;
+    int n_boxes;
+    double *x;
+    int *status;
+};
+
+// lane 0: claim the next slot and wait for its box (as chain_claim)
+__device__ inline int wchain_claim(const WChainArgs &a) {
+    const int h = atomicAdd(a.ws, 1);
+    if (h >= a.n_slots) return -1;
+    if (h < a.n0) return a.items0[h];
+    const int *slot = a.ws + 2 + a.n_boxes + (h - a.n0);
+    const unsigned long long t0 = global_ns();
+    for (unsigned it = 0; it < (1u << 30); ++it) {
+        const int v = ld_acquire_int(slot);
+        if (v > 0) {
+            __threadfence();
+            return v - 1;
+        }
+        if ((it & 63u) == 63u && global_ns() - t0 > kWaitLimitNs) break;
+        __nanosleep(32);
+    }
+    set_status(a.status, VPX_ERR_TIMEOUT);
+    return -2;
+}
+
+template <bool UP>
+__global__ void __launch_bounds__(CW_THREADS) k_wchain(WChainArgs a) {
+    pdl_entry();
+    extern __shared__ __align__(16) float4 cw_sm[];
+    const int P = a.P, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float4 *s_tab = cw_sm;                                           // [n_packed]
+    float4 *s_x = cw_sm + a.n_packed + warp * P;                     // [CW_WARPS][P]: the source expansion
+    int *s_off = reinterpret_cast<int *>(cw_sm + a.n_packed + CW_WARPS * P);   // [4][P]
+    int16_t *s_kr = reinterpret_cast<int16_t *>(s_off + 4 * P);      // [4][P][2]
+    for (int i = threadIdx.x; i < a.n_packed; i += CW_THREADS) s_tab[i] = a.tabp[i];
+    for (int i = threadIdx.x; i < 4 * P; i += CW_THREADS) s_off[i] = a.roff[i];
+    for (int i = threadIdx.x; i < 8 * P; i += CW_THREADS) s_kr[i] = a.krange[i];
+    __syncthreads();
+    const int gw = blockIdx.x * CW_WARPS + warp, nw = gridDim.x * CW_WARPS;
+    int next_leaf = gw;
+    int c = -1;
+    for (;;) {
+        if (c < 0) {
+            if (UP) {
+                c = next_leaf < a.n0 ? a.items0[next_leaf] : -1;
+                next_leaf += nw;
+            } else {
+                int v = 0;
+                if (lane == 0) v = wchain_claim(a);
+                c = __shfl_sync(0xffffffffu, v, 0);
+            }
+            if (c < 0) break;
+        }
+        const int2 up = a.up_of[c];
+        const int par = up.x, pos = up.y;
+        const int src = UP ? c : par, dst = UP ? par : c;
+        for (int r = 0; r < a.nrhs; ++r) {
+            const double *xs = a.x + r * a.ldm + (int64_t)src * 2 * P;
+            for (int k = lane; k < P; k += 32) {
+                const df32 hr = df_split_bits(__ldcg(xs + 2 * k)), hi = df_split_bits(__ldcg(xs + 2 * k + 1));
+                s_x[k] = make_float4(hr.hi, hr.lo, hi.hi, hi.lo);
+            }
+            __syncwarp();
+            for (int l = lane; l < P; l += 32) {
+                const int klo = s_kr[(pos * P + l) * 2], khi = s_kr[(pos * P + l) * 2 + 1];
+                const float4 *T = s_tab + s_off[pos * P + l] - klo;
+                df32 sr{0.f, 0.f}, si{0.f, 0.f};
+                for (int k = klo; k <= khi; ++k) {
+                    const float4 t = T[k];
+                    const float4 v = s_x[k];
+                    df_mac(sr, df32{t.x, t.y}, df32{v.x, v.y});
+                    df_mac(sr, df32{-t.z, -t.w}, df32{v.z, v.w});
+                    df_mac(si, df32{t.x, t.y}, df32{v.z, v.w});
+                    df_mac(si, df32{t.z, t.w}, df32{v.x, v.y});
+                }
+                sr = df_norm(sr);
+                si = df_norm(si);
+                const double out_re = df_to_f64_scaled(sr, 0), out_im = df_to_f64_scaled(si, 0);
+                double *xd = a.x + r * a.ldm + (int64_t)dst * 2 * P + 2 * l;
+                if (UP) {
+                    atomicAdd(xd, out_re);
+                    atomicAdd(xd + 1, out_im);
+                } else {
+                    xd[0] = __ldcg(xd) + out_re;
+                    xd[1] = __ldcg(xd + 1) + out_im;
+                }
+            }
+            __syncwarp();   // s_x is rewritten for the next column
+        }
+        __threadfence();    // this box's results are visible before anything goes on from them
+        __syncwarp();
+        int next = -1;
+        if (lane == 0) {
+            if (UP) {       // the child that completes its parent's count goes on with the parent
+                const int nd = a.need[par];
+                if (nd > 0 && atomicAdd(a.ws + 2 + par, 1) == nd - 1) {
+                    __threadfence();
+                    next = par;
+                }
+            } else {        // on with the first child; the other three to the queue
+                const int ch = a.child0[c];
+                if (ch >= 0) {
+                    const int s = atomicAdd(a.ws + 1, 3);
+                    for (int k = 1; k < 4; ++k)
+                        if (s + k - 1 < a.n_slots - a.n0) atomicExch(a.ws + 2 + a.n_boxes + s + k - 1, ch + k + 1);
+                    next = ch;
+                }
+            }
+        }
+        c = __shfl_sync(0xffffffffu, next, 0);
+        __threadfence();    // what the box's other writers made visible is seen before it is read
+    }
+}
+
 // ------------------------------------------------------------------ host
 
 // The complex form of four real 2P x 2P translation tables (rows 2l, 2l+1 and
@@ -333,6 +477,40 @@ void setup_chains(vpx_plan *p, const std::vector<double> &m2m, const std::vector
     C.need = dev_upload(need);
     C.ws_ints = (size_t)(2 + nb + C.n_up) + (size_t)(2 + nb + C.n_down);
     C.ws = dev_alloc<int>(C.ws_ints);
+    if (mixed) {   // the warp-granular kernel's packed rows
+        auto pack = [&](const std::vector<double> &c, const std::vector<int16_t> &kr, int &n) {
+            std::vector<float> f;
+            std::vector<int32_t> off(4 * (size_t)P);
+            for (int t = 0; t < 4; ++t)
+                for (int l = 0; l < P; ++l) {
+                    off[(size_t)t * P + l] = (int32_t)(f.size() / 4);
+                    for (int k = kr[((size_t)t * P + l) * 2]; k <= kr[((size_t)t * P + l) * 2 + 1]; ++k)
+                        for (int ri = 0; ri < 2; ++ri) {
+                            const double v = c[(((size_t)t * P + l) * P + k) * 2 + ri];
+                            const float hi = (float)v;
+                            f.push_back(hi);
+                            f.push_back((float)(v - (double)hi));
+                        }
+                }
+            n = (int)(f.size() / 4);
+            return std::make_pair(dev_upload(f), dev_upload(off));
+        };
+        auto u = pack(cu, ku, C.np_up), d = pack(cd, kd, C.np_down);
+        C.tabw_up = u.first;
+        C.roff_up = u.second;
+        C.tabw_down = d.first;
+        C.roff_down = d.second;
+        C.smem_w = (size_t)(std::max(C.np_up, C.np_down) + CW_WARPS * P) * 16 + (size_t)4 * P * 4 + (size_t)8 * P * 2;
+        int occ_w = 0;
+        VPX_CUDA(cudaFuncSetAttribute(k_wchain<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C.smem_w));
+        VPX_CUDA(cudaFuncSetAttribute(k_wchain<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C.smem_w));
+        VPX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_w, k_wchain<true>, CW_THREADS, C.smem_w));
+        int dev = 0, nsm = 0;
+        VPX_CUDA(cudaGetDevice(&dev));
+        VPX_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        C.max_ctas_w = std::max(1, std::min(occ_w, 4)) * nsm;
+        if (occ_w <= 0) return;
+    }
     int occ = 0;
     const int nk = chain_nk(P);
     if (mixed && nk == 8)
@@ -361,6 +539,10 @@ void free_chains(vpx_plan *p) {
     dev_free(C.need);
     dev_free(C.up_of);
     dev_free(C.ws);
+    dev_free(C.tabw_up);
+    dev_free(C.tabw_down);
+    dev_free(C.roff_up);
+    dev_free(C.roff_down);
     C = ChainPlan();
 }
 
@@ -391,9 +573,34 @@ void chain_run(vpx_plan *p, bool up, double *x, int64_t ldm, int nrhs, cudaStrea
     a.ws = up ? C.ws : C.ws + (2 + p->dt.n_boxes + C.n_up);
     a.x = x;
     a.status = p->wk.status;
+    const bool mixed = p->opt.precision == VPX_PREC_MIXED;
+    if (mixed) {   // one warp per box
+        WChainArgs w;
+        w.P = a.P;
+        w.nrhs = nrhs;
+        w.n_slots = a.n_slots;
+        w.n0 = a.n0;
+        w.n_packed = up ? C.np_up : C.np_down;
+        w.ldm = ldm;
+        w.items0 = a.items0;
+        w.up_of = a.up_of;
+        w.child0 = a.child0;
+        w.need = a.need;
+        w.tabp = reinterpret_cast<const float4 *>(up ? C.tabw_up : C.tabw_down);
+        w.roff = up ? C.roff_up : C.roff_down;
+        w.krange = a.krange;
+        w.ws = a.ws;
+        w.n_boxes = a.n_boxes;
+        w.x = x;
+        w.status = a.status;
+        const dim3 grid((unsigned)std::min((a.n_slots + CW_WARPS - 1) / CW_WARPS, C.max_ctas_w));
+        if (up) launch_pdl(k_wchain<true>, grid, dim3(CW_THREADS), C.smem_w, s, w);
+        else launch_pdl(k_wchain<false>, grid, dim3(CW_THREADS), C.smem_w, s, w);
+        VPX_LAUNCH("k_wchain");
+        return;
+    }
     const dim3 grid((unsigned)std::min(a.n_slots, C.max_ctas));
     const size_t smem = 0;
-    const bool mixed = p->opt.precision == VPX_PREC_MIXED;
     const int nk = chain_nk(p->P);
     if (nk == 8) {
         if (mixed && up) launch_pdl(k_chain<true, true, 8>, grid, dim3(CH_THREADS), smem, s, a);

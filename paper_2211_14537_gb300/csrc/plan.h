@@ -93,6 +93,11 @@ struct ChainPlan {
     int32_t *up_of = nullptr;     // per box: parent, position among its siblings (pairs)
     int *ws = nullptr;            // both queue blocks, zeroed before every step
     size_t ws_ints = 0;
+    // mixed form: the warp-granular kernel's packed rows (double-float complex) and row starts
+    void *tabw_up = nullptr, *tabw_down = nullptr;
+    int32_t *roff_up = nullptr, *roff_down = nullptr;
+    int np_up = 0, np_down = 0, max_ctas_w = 0;
+    size_t smem_w = 0;
 };
 
 struct FmmPasses {                // every contraction of the box FMM as a grouped table GEMM
