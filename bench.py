@@ -510,15 +510,24 @@ def measured_peaks():
 
 # DRAM bytes (read + written) of one launch of the near-field kernel, from an
 # ncu capture, keyed by (workload, right-hand sides, SHA-256 prefix of the
-# kernel's source file).  A changed kernel source matches no key, so the line
-# then reports traffic as null until the kernel is captured again.
-NEAR_TRAFFIC = {}
+# kernel's source file and the headers it compiles with).  A changed kernel
+# source matches no key, so the line then reports traffic as null until the
+# kernel is captured again.
+NEAR_TRAFFIC = {
+    # profiles/k_gemm_ws_near_lshape_k16.md: 36,999,936 B read + 7,168 B written
+    ("lshape_expsin_k16", 1, "ab106811c4f6b827"): 37007104,
+}
+
+KERNEL_HEADERS = ("gemm.cuh", "slice_math.cuh", "bulk.cuh")
 
 
 def kernel_source_key(fname="gemm_ws.cu"):
     import hashlib
-    with open(os.path.join(ROOT, "paper_2211_14537_gb300", "csrc", fname), "rb") as fh:
-        return hashlib.sha256(fh.read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for name in (fname,) + KERNEL_HEADERS:
+        with open(os.path.join(ROOT, "paper_2211_14537_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def potential_error(V, plan, vals, idx, Vs):

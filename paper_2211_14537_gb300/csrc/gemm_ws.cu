@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(TW_THREADS, 2) k_gemm_ws(WsArgs a) {
     for (int i = tid; i < Sh::VR; i += TW_THREADS) {
         s_src[i] = 0;
         s_pdst[i] = -1;
-        s_ps[i] = SliceScale{1.0, 0};
+        s_ps[i] = SliceScale{1.0, 0, 1};
         if (i < tile.count) {
             const GPair pr = a.pairs[tile.first + i];
             s_src[i] = pr.src;

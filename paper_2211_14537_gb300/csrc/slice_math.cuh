@@ -87,26 +87,42 @@ __device__ inline void slice_digits(int64_t n, uint16_t (&d)[kSlicesS]) {
 struct SliceScale {
     double mul;     // pair scale / 2^e (1 when the scale is a power of two, else in [1, 2))
     int e;          // its exponent, including the vector's exponent and 2^-14
+    int pow2;       // 1: the scale is a power of two (mul = 1, no multiply)
 };
 
 __device__ inline SliceScale slice_pair_scale(double scale, int extra_e) {
     SliceScale s;
     int e = 0;
     const double m = frexp(scale, &e);   // scale = m 2^e, |m| in [0.5, 1)
-    s.mul = (m == 0.5) ? 1.0 : 2.0 * m;
+    s.pow2 = m == 0.5;
+    s.mul = s.pow2 ? 1.0 : 2.0 * m;
     s.e = e - 1 + extra_e;
     return s;
 }
 
-// n 2^e as a double: one rounding (the conversion), the scaling exact
+// The bit pattern of (double)a, a > 0, rounded to nearest with ties to even,
+// from integer operations only: the leading one at bit ex = 63 - clz(a); for
+// ex > 52 the ex - 52 bits below the 53 kept are rounded off, a carry out of
+// the 53 bits stepping the exponent field.  (The FP64 pipe, which the
+// conversion would use, issues about two operations per clock per SM here.)
+__device__ inline uint64_t slice_u64_to_f64_bits(uint64_t a) {
+    const int ex = 63 - __clzll((long long)a);
+    if (ex <= 52) return ((uint64_t)(ex + 1023) << 52) + ((a << (52 - ex)) - (1ull << 52));
+    const int sh = ex - 52;
+    const uint64_t q = a >> sh, r = a & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+    const uint64_t m = q + ((r > half || (r == half && (q & 1ull))) ? 1ull : 0ull);
+    return ((uint64_t)(ex + 1023) << 52) + (m - (1ull << 52));
+}
+
+// n 2^e as a double: one rounding (the conversion, as (double)n), the scaling
+// exact; integer operations unless the result leaves the normal range
 __device__ inline double slice_i64_scaled(int64_t n, int e) {
-    const double v = (double)n;
-    const uint64_t b = (uint64_t)__double_as_longlong(v);
-    const int ex = (int)((b >> 52) & 0x7ff);
-    if (ex == 0) return v;   // zero
-    const int ne = ex + e;
-    if (ne <= 0 || ne >= 2047) return ldexp(v, e);
-    return __longlong_as_double((long long)(b + ((uint64_t)(int64_t)e << 52)));
+    if (n == 0) return 0.0;
+    const uint64_t sgn = n < 0 ? (1ull << 63) : 0ull;
+    const uint64_t b = slice_u64_to_f64_bits(n < 0 ? (uint64_t)0 - (uint64_t)n : (uint64_t)n);
+    const int ne = (int)(b >> 52) + e;
+    if (ne <= 0 || ne >= 2047) return ldexp(__longlong_as_double((long long)(b | sgn)), e);
+    return __longlong_as_double((long long)((b + ((uint64_t)(int64_t)e << 52)) | sgn));
 }
 
 // acc[0] is the most significant order
@@ -117,7 +133,7 @@ __device__ inline double slice_output(const float (&acc)[S], const SliceScale &p
 #pragma unroll
     for (int d = 1; d < S; ++d) n = n * 256 + __float2int_rn(acc[d]);
     const double v = slice_i64_scaled(n, row_e + ps.e - kSliceBitsB * (S - 1));
-    return ps.mul == 1.0 ? v : v * ps.mul;
+    return ps.pow2 ? v : v * ps.mul;
 }
 
 }  // namespace vpx

@@ -94,7 +94,9 @@ def test_bench_line_carries_the_contract_keys(monkeypatch, capsys, wl_name):
     # the method's own work, 2K^4 + 2K^2 per near pair, over the near pass time; the peak is the measured one
     assert d["roofline"]["achieved"] == pytest.approx(4900 * (2 * 16 ** 4 + 2 * 256) / 0.05e-3 / 1e12)
     assert d["roofline"]["peak"] == pytest.approx(bench.measured_peaks()["bf16_tflops"])
-    assert d["roofline"]["traffic"] is None                                   # no capture of this kernel source
+    # traffic only from a capture of this kernel source (and none for a source no capture covers)
+    key = (d["config"]["workload"], 1, bench.kernel_source_key("gemm_ws.cu"))
+    assert d["roofline"]["traffic"] == bench.NEAR_TRAFFIC.get(key)
     assert d["rel_err_vs_oracle"] == pytest.approx(3e-11)
     assert d["forms"]["mixed"]["rel_err_end_to_end"] == 0.0
     assert set(d["e2e"]) >= {"value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step"}
@@ -154,3 +156,23 @@ def test_reference_arm_follows_the_workload(monkeypatch, capsys):
     assert d["impl"] == "reference" and d["config"]["workload"] == bench.workload("disk-multi-rhs").name
     assert d["steps"] == 2 and d["cpu_baseline"]["kind"] == "oracle"
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+
+
+def test_traffic_key_follows_the_kernel_and_its_headers(tmp_path, monkeypatch):
+    """The near kernel's traffic figure is keyed on its source and the headers
+    it compiles with: changing either leaves the bench line without one."""
+    import shutil
+    src = tmp_path / "paper_2211_14537_gb300" / "csrc"
+    src.mkdir(parents=True)
+    for name in ("gemm_ws.cu",) + bench.KERNEL_HEADERS:
+        shutil.copy(os.path.join(bench.ROOT, "paper_2211_14537_gb300", "csrc", name), src / name)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    k0 = bench.kernel_source_key("gemm_ws.cu")
+    with open(src / "slice_math.cuh", "a") as fh:
+        fh.write("\n")
+    k1 = bench.kernel_source_key("gemm_ws.cu")
+    with open(src / "gemm_ws.cu", "a") as fh:
+        fh.write("\n")
+    k2 = bench.kernel_source_key("gemm_ws.cu")
+    assert len({k0, k1, k2}) == 3
+    assert all(k[2] != k1 and k[2] != k2 for k in bench.NEAR_TRAFFIC)
