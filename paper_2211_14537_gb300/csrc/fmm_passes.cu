@@ -240,29 +240,105 @@ void setup_passes(vpx_plan *p) {
         F.l2m.add = 1;   // into the zeroed multipoles (the inner dimension may be split)
         gemm_pass_set_pairs(F.l2m, tg);
     }
-    // M2M per parent level, L2L per child level
+    // The level chains in bands of levels, one launch per band.  In the scaled
+    // variables a translation does not depend on the level, so the translation
+    // across d levels is a product of d of the four child tables: 4^d tables of
+    // depth d, from index (4^d - 4) / 3 on, numbered by the child positions
+    // along the path, pos_1 (the lower box in its parent) + 4 pos_2 + ...
+    //  Upward (M2M), bands of up to kBandUp levels: a launch reads every box
+    //  at level L (final after the band below) and the leaves of the levels
+    //  between L and the band's top level Lt = max(L - kBandUp, 2) (final from
+    //  L2M), and adds each one's translation into each of its ancestors down to
+    //  Lt.  It writes only boxes with children, at levels Lt .. L-1, and reads
+    //  only boxes at L and leaves, so no box is read and written in one launch;
+    //  every leaf's multipole reaches every ancestor once, through the boxes of
+    //  the levels read.
+    //  Downward (L2L), bands of two levels: lo(g) = lo'(g) + T lo'(c) + T T lo(a)
+    //  for g below c below a, lo' a box's own terms (M2L, lists i+, constants).
+    //  A first launch adds T lo'(c) for the boxes c of the levels between the
+    //  read levels; then a launch per band reads the final lo(a) at level L and
+    //  adds it into the children (depth 1) and grandchildren (depth 2).
     for (int l = 0; l <= kMaxLevel; ++l) {
         F.m2m[l] = GemmPass();
         F.l2l[l] = GemmPass();
     }
-    for (int l = 2; l + 1 < p->n_levels; ++l) {
-        Tagged tm, tl;
-        for (int b = p->level_start[l]; b < p->level_start[l + 1]; ++b) {
-            if (p->box_child0[b] < 0) continue;
-            for (int c = 0; c < 4; ++c) {
-                int ch = p->box_child0[b] + c;
-                if (p->box_nz[ch]) tm.push_back({c, GPair{ch, 0, (int64_t)b * P2, 1.0}});
-                tl.push_back({c, GPair{b, 0, (int64_t)ch * P2, 1.0}});
-            }
-        }
-        gemm_pass_upload_tables(F.m2m[l], m2m, 4, P2, P2, mixed);
-        gemm_pass_set_pairs(F.m2m[l], tm);
-        gemm_pass_upload_tables(F.l2l[l], l2l, 4, P2, P2, mixed);
-        gemm_pass_set_pairs(F.l2l[l], tl);
+    F.n_m2m = F.n_l2l = 0;
+    {
+        constexpr int kBandUp = 3;
+        const int D = p->n_levels - 1;
+        const size_t T2 = (size_t)P2 * P2;
+        auto off = [](int d) { return ((1 << (2 * d)) - 4) / 3; };
+        // tables of depths 1 .. depth, composed in FP64: upward T[pos_d] ... T[pos_1],
+        // downward T[pos_1] ... T[pos_d]
+        auto band_tables = [&](const std::vector<double> &t4, int depth, bool up, int &ntab) {
+            ntab = off(depth + 1);
+            std::vector<double> all((size_t)ntab * T2, 0.0);
+            std::copy(t4.begin(), t4.begin() + 4 * T2, all.begin());
+            for (int d = 2; d <= depth; ++d)
+                for (int code = 0; code < (1 << (2 * d)); ++code) {
+                    const int cp = code & ((1 << (2 * (d - 1))) - 1), pd = code >> (2 * (d - 1));
+                    const double *A = up ? &t4[pd * T2] : &all[(off(d - 1) + cp) * T2];
+                    const double *B = up ? &all[(off(d - 1) + cp) * T2] : &t4[pd * T2];
+                    double *C = &all[(off(d) + code) * T2];
+                    for (int i = 0; i < P2; ++i)
+                        for (int j = 0; j < P2; ++j) {
+                            const double a = A[(size_t)i * P2 + j];
+                            if (a == 0.0) continue;
+                            for (int k = 0; k < P2; ++k) C[(size_t)i * P2 + k] += a * B[(size_t)j * P2 + k];
+                        }
+                }
+            return all;
+        };
+        int ntu = 0, ntd = 0;
+        const std::vector<double> tu = band_tables(m2m, kBandUp, true, ntu), td = band_tables(l2l, 2, false, ntd);
+        gemm_pass_upload_tables(F.m2m_tab, tu, ntu, P2, P2, mixed);
+        gemm_pass_upload_tables(F.l2l_tab, td, ntd, P2, P2, mixed);
         if (mixed) {   // the level chains: double-float row engine
-            gemm_pass_use_rows(F.m2m[l], m2m);
-            gemm_pass_use_rows(F.l2l[l], l2l);
+            gemm_pass_use_rows(F.m2m_tab, tu);
+            gemm_pass_use_rows(F.l2l_tab, td);
         }
+        for (int L = D; L > 2;) {
+            const int Lt = std::max(L - kBandUp, 2);
+            Tagged tm;
+            for (int b = p->level_start[Lt + 1]; b < p->level_start[L + 1]; ++b) {
+                if (!p->box_nz[b] || (p->box_level[b] < L && p->box_child0[b] >= 0)) continue;
+                int c = b, code = 0, d = 0;
+                for (;;) {
+                    const int a = p->box_parent[c];
+                    if (a < 0 || p->box_level[a] < Lt) break;
+                    code += (c - p->box_child0[a]) << (2 * d);
+                    ++d;
+                    tm.push_back({off(d) + code, GPair{b, 0, (int64_t)a * P2, 1.0}});
+                    c = a;
+                }
+            }
+            gemm_pass_view(F.m2m[F.n_m2m], F.m2m_tab);
+            gemm_pass_set_pairs(F.m2m[F.n_m2m], tm);
+            ++F.n_m2m;
+            L = Lt;
+        }
+        Tagged pre;
+        for (int L = 2; L + 1 <= D; L += 2) {
+            Tagged tl;
+            for (int a = p->level_start[L]; a < p->level_start[L + 1]; ++a) {
+                const int c0 = p->box_child0[a];
+                if (c0 < 0) continue;
+                for (int i = 0; i < 4; ++i) {
+                    const int c = c0 + i, g0 = p->box_child0[c];
+                    tl.push_back({off(1) + i, GPair{a, 0, (int64_t)c * P2, 1.0}});
+                    if (g0 < 0) continue;
+                    for (int j = 0; j < 4; ++j) {
+                        tl.push_back({off(2) + j + 4 * i, GPair{a, 0, (int64_t)(g0 + j) * P2, 1.0}});
+                        pre.push_back({off(1) + j, GPair{c, 0, (int64_t)(g0 + j) * P2, 1.0}});
+                    }
+                }
+            }
+            gemm_pass_view(F.l2l[F.n_l2l], F.l2l_tab);
+            gemm_pass_set_pairs(F.l2l[F.n_l2l], tl);
+            ++F.n_l2l;
+        }
+        gemm_pass_view(F.l2l_pre, F.l2l_tab);
+        gemm_pass_set_pairs(F.l2l_pre, pre);
     }
     // M2L and S2L
     {
@@ -382,6 +458,7 @@ void setup_passes(vpx_plan *p) {
     }
     for (GemmPass *g : {&F.l2m, &F.m2l, &F.s2l, &F.l2t, &F.m2t, &F.near}) g->status = p->wk.status;
     for (int l = 0; l <= kMaxLevel; ++l) F.m2m[l].status = F.l2l[l].status = p->wk.status;
+    for (GemmPass *g : {&F.m2m_tab, &F.l2l_tab, &F.l2l_pre}) g->status = p->wk.status;
     setup_chains(p, m2m, l2l);
     VPX_CUDA(cudaDeviceSynchronize());
 }
@@ -399,6 +476,9 @@ void free_passes(vpx_plan *p) {
         gemm_pass_free(F.m2m[l]);
         gemm_pass_free(F.l2l[l]);
     }
+    gemm_pass_free(F.l2l_pre);
+    gemm_pass_free(F.m2m_tab);
+    gemm_pass_free(F.l2l_tab);
     dev_free(F.fe_sl);
     dev_free(F.fe_ex);
     dev_free(F.lc_off);
@@ -466,7 +546,7 @@ void run_potential_passes(vpx_plan *p, const double *fe, int64_t ldfe, int nrhs,
     ev_record_pass(p, 2, s);
     if (chains) chain_run(p, true, mp, ldm, nrhs, s);
     else
-        for (int l = d.n_levels - 1; l >= 3; --l) gemm_run(F.m2m[l - 1], vm, mp, ldm, nrhs, mixed, s);
+        for (int k = 0; k < F.n_m2m; ++k) gemm_run(F.m2m[k], vm, mp, ldm, nrhs, mixed, s);
     if (mixed) slice_vectors(vmf, 0, nb, P2, kp_m, nrhs, s);
     // the final multipoles feed the constant terms and list i- on the third
     // stream, beside M2L on this one (all accumulate into distinct sums)
@@ -489,9 +569,12 @@ void run_potential_passes(vpx_plan *p, const double *fe, int64_t ldfe, int nrhs,
     gemm_run(F.m2l, vmf, lo, ldm, nrhs, mixed, s);
     VPX_CUDA(cudaStreamWaitEvent(s, (cudaEvent_t)p->ev_lc, 0));
     ev_record_pass(p, 4, s);
-    if (chains) chain_run(p, false, lo, ldm, nrhs, s);
-    else
-        for (int l = 2; l + 1 < d.n_levels; ++l) gemm_run(F.l2l[l], vl, lo, ldm, nrhs, mixed, s);
+    if (chains) {
+        chain_run(p, false, lo, ldm, nrhs, s);
+    } else {
+        gemm_run(F.l2l_pre, vl, lo, ldm, nrhs, mixed, s);
+        for (int k = 0; k < F.n_l2l; ++k) gemm_run(F.l2l[k], vl, lo, ldm, nrhs, mixed, s);
+    }
     ev_record_pass(p, 5, s);
     gemm_run(F.l2t, vl, v, ldv, nrhs, mixed, s);
     ev_record_pass(p, 6, s);

@@ -269,19 +269,47 @@ bool gemm_pass_use_rows(GemmPass &g, const std::vector<double> &tab) {
 }
 
 void gemm_pass_free(GemmPass &g) {
-    dev_free(g.tab);
-    dev_free(g.tslices);
-    dev_free(g.texpo);
+    if (g.owns_tables) {
+        dev_free(g.tab);
+        dev_free(g.tslices);
+        dev_free(g.texpo);
+        dev_free(g.tfrag);
+        dev_free(g.tdfT);
+        dev_free(g.tint);
+    }
+    g.tab = nullptr;
+    g.tslices = nullptr;
+    g.texpo = nullptr;
+    g.tfrag = nullptr;
+    g.tdfT = nullptr;
+    g.tint = nullptr;
     dev_free(g.pairs);
     dev_free(g.tiles);
-    dev_free(g.tfrag);
     dev_free(g.tiles_f);
     dev_free(g.tiles_f_alt);
     dev_free(g.tiles_r);
     dev_free(g.tiles_w);
-    dev_free(g.tdfT);
-    dev_free(g.tint);
     g.n_pairs = g.n_tiles = g.n_tiles_f = g.n_tiles_f_alt = g.n_tiles_r = g.n_tiles_w = 0;
+}
+
+void gemm_pass_view(GemmPass &v, const GemmPass &base) {
+    v = GemmPass();
+    v.M = base.M;
+    v.Kd = base.Kd;
+    v.Kpad = base.Kpad;
+    v.Mpad = base.Mpad;
+    v.ntab = base.ntab;
+    v.add = base.add;
+    v.status = base.status;
+    v.tab = base.tab;
+    v.tslices = base.tslices;
+    v.texpo = base.texpo;
+    v.tfrag = base.tfrag;
+    v.tdfT = base.tdfT;
+    v.tint = base.tint;
+    v.ws_kind = base.ws_kind;
+    v.engine = base.engine;
+    v.owns_tables = false;
 }
 
 GemmChoice gemm_choice(const GemmPass &g) { return GemmChoice{g.engine, g.np_f}; }

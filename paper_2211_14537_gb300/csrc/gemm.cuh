@@ -66,6 +66,7 @@ struct GemmPass {
     GTile *tiles_f_alt = nullptr;
     int n_tiles_f_alt = 0, np_f_alt = 32;
     int engine = 0;                    // 0: default routing; 1: fragment engine even where tcgen05 is eligible
+    bool owns_tables = true;           // false: a view of another pass's tables (gemm_pass_view)
     std::vector<GPair> h_pairs;        // host copy (setup)
 };
 
@@ -93,6 +94,9 @@ void gemm_set_recorder(std::vector<GemmCall> *rec);
 void gemm_pass_set_pairs(GemmPass &g, std::vector<std::pair<int, GPair>> &tagged, int frag_np = 0);
 void gemm_pass_upload_tables(GemmPass &g, const std::vector<double> &tab, int ntab, int M, int Kd, bool mixed);
 void gemm_pass_free(GemmPass &g);
+// v takes base's tables (shared, not copied: base must outlive v) and routing;
+// its pairs are set afterwards with gemm_pass_set_pairs
+void gemm_pass_view(GemmPass &v, const GemmPass &base);
 // Hand a mixed-form pass to the double-float row engine (gemm_rows.cu) when
 // its rows fit one CTA and every pair scale is a power of two; returns whether.
 bool gemm_pass_use_rows(GemmPass &g, const std::vector<double> &tab);

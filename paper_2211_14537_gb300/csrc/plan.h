@@ -102,8 +102,11 @@ struct ChainPlan {
 
 struct FmmPasses {                // every contraction of the box FMM as a grouped table GEMM
     GemmPass l2m, m2l, s2l, l2t, m2t, near;
-    GemmPass m2m[kMaxLevel + 1];  // parents at level l
-    GemmPass l2l[kMaxLevel + 1];  // parents at level l
+    // the level chains in bands of levels (one launch each, views of the
+    // composed tables in m2m_tab / l2l_tab): upward bands from the deepest
+    // level, a first downward launch (l2l_pre), then downward bands
+    GemmPass m2m[kMaxLevel + 1], l2l[kMaxLevel + 1], l2l_pre, m2m_tab, l2l_tab;
+    int n_m2m = 0, n_l2l = 0;
     uint16_t *fe_sl = nullptr, *mp_sl = nullptr;   // exact bf16 slices of leaf values, multipoles (mixed form)
     // gather lists of the constant terms: boxes from lc_first on (locals), leaves (potentials)
     int lc_first = 0, lc_rows = 0;
