@@ -69,9 +69,10 @@ MULTI_RHS_COLUMNS = 64
 
 
 def workload(name="starfish"):
-    """The single-tree workloads: the adaptive starfish (the default line),
-    the L-shape refined to level 14 toward its corners (1.4 M targets) and the
-    exterior of three starfish inclusions (Section 6.2, 248 k targets)."""
+    """The single-tree workloads: the L-shape refined to level 14 toward its
+    corners (1.4 M targets, the default line), the adaptive starfish (185 k
+    targets) and the exterior of three starfish inclusions (Section 6.2, 248 k
+    targets)."""
     import workloads as W
     if name == "lshape":
         return W.lshape_expsin()
