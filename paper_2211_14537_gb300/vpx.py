@@ -461,12 +461,25 @@ def vpx_bie_corrections(plan: Plan, nq: int = 16):
     return off, pan, w
 
 
-def vpx_execute_host(plan: Plan, f_stencil: np.ndarray, nrhs: int = 1):
-    """End to end with host arrays: returns (v_leaf, v_bdry) as (nrhs, n) numpy arrays."""
+def vpx_execute_host(plan: Plan, f_stencil: np.ndarray, nrhs: int = 1, v_out: np.ndarray = None,
+                     b_out: np.ndarray = None):
+    """End to end with host arrays: returns (v_leaf, v_bdry) as (nrhs, n) numpy arrays.
+
+    v_out (nrhs, n_leaf_nodes) and b_out (nrhs, max(n_bdry, 1)), C-contiguous
+    float64, receive the results when given (for instance views of page-locked
+    buffers, whose copies run at the link's rate); otherwise new arrays."""
     _, nt, ns, nb = plan.sizes()
     f = np.ascontiguousarray(f_stencil, dtype=np.float64).reshape(nrhs, ns)
-    v = np.zeros((nrhs, nt))
-    b = np.zeros((nrhs, max(nb, 1)))
+
+    def out(a, shape):
+        if a is None:
+            return np.zeros(shape)
+        if a.dtype != np.float64 or a.shape != shape or not a.flags["C_CONTIGUOUS"]:
+            raise VpxError(VPX_ERR_ARG, "output array must be C-contiguous float64 of shape %s" % (shape,))
+        return a
+
+    v = out(v_out, (nrhs, nt))
+    b = out(b_out, (nrhs, max(nb, 1)))
     _check(load_library().vpx_execute_host(plan.handle, _dptr(f), nrhs, _dptr(v), _dptr(b)))
     return v, b[:, :nb]
 

@@ -343,6 +343,16 @@ def test_execute_host_matches_device(V):
     assert V.vpx_sync_status(plan) == 0
     assert np.max(np.abs(vh[0] - v.cpu().numpy())) <= 1e-14 * np.max(np.abs(vh))
     assert np.max(np.abs(bh[0] - vb.cpu().numpy())) <= 1e-14 * np.max(np.abs(vh))
+    # caller-provided page-locked outputs receive the same values (to the
+    # FP64 atomics' summation order, which varies between executes)
+    v_pin = torch.empty((1, nt), dtype=torch.float64).pin_memory()
+    b_pin = torch.empty((1, max(nb, 1)), dtype=torch.float64).pin_memory()
+    vp, bp = V.vpx_execute_host(plan, f, 1, v_pin.numpy(), b_pin.numpy())
+    assert np.shares_memory(vp, v_pin.numpy())
+    assert np.max(np.abs(vp - vh)) <= 1e-14 * np.max(np.abs(vh))
+    assert np.max(np.abs(bp - bh)) <= 1e-14 * np.max(np.abs(vh))
+    with pytest.raises(V.VpxError):
+        V.vpx_execute_host(plan, f, 1, np.zeros((1, nt), np.float32))
 
 
 def test_bounded_wait_reports_timeout_and_context_survives(V):
